@@ -1,0 +1,346 @@
+"""CPU oracle for the device data pass of CRAC-style checkpoint-restart.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+benchmark's CPU-baseline / reference leg import this module.  It shares no
+code with the CUDA library and never calls it: it works on plain host byte
+arrays that the caller copied out of device memory.
+
+What it computes, in the paper's terms:
+  * Checkpoint saves the memory of the *active* allocations only -- those
+    made by the cudaMalloc family and not yet freed (Sec. 3.2, "Saving the
+    library-allocated arena"), in the order they were allocated (Sec. 3.1,
+    log-and-replay restores regions "in the same order as when they were
+    allocated").  Device (cudaMalloc) and unified (cudaMallocManaged)
+    regions are both saved (Sec. 3.2, "restoring the CUDA
+    library-allocated regions").
+  * Restart copies the saved bytes back into the allocations (same
+    subsection), after which the device state equals the checkpointed one.
+  * Before the copy, pending device work is drained (Sec. 2.2, CheCUDA
+    step (a)); here the caller hands in bytes that already reflect it.
+
+The incremental part is this project's design, not the paper's (the paper
+copies every active allocation at every checkpoint): memory is cut into
+fixed-size chunks, each chunk gets a CRAC-FP64 fingerprint, and an image
+carries only the chunks whose fingerprint differs from the previous
+checkpoint's.  The steps below follow that definition in order, with numpy
+primitives for the bulk steps (nonzero, cumsum, concatenation).
+
+Image byte layout (all integers little-endian):
+  header, 80 bytes:
+    0  magic "CRACIMG1"      8  u32 version (1)     12 u32 flags (bit0 FULL)
+    16 u32 chunk_bytes       20 u32 hash_id (1)     24 u64 lineage
+    32 u64 epoch             40 u64 parent_epoch (all ones if none)
+    48 u64 n_allocs          56 u64 n_chunks        64 u64 k (chunks present)
+    72 u64 payload_bytes
+  alloc table: n_allocs x 40 bytes
+    u64 id, u64 orig_ptr, u64 bytes, u32 kind, u32 zero, u64 first_chunk
+  u64 fp[n_chunks]          fingerprints of every chunk at this epoch
+  u64 idx[k]                ascending global ids of the chunks present
+  payload                   those chunks' bytes, concatenated, tails unpadded
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+from dataclasses import dataclass
+
+import numpy as np
+
+MAGIC = b"CRACIMG1"
+VERSION = 1
+HASH_ID = 1
+FLAG_FULL = 1
+NO_PARENT = (1 << 64) - 1
+KIND_DEVICE = 0
+KIND_MANAGED = 1
+
+HEADER = struct.Struct("<8sIIIIQQQQQQQ")
+ALLOC = struct.Struct("<QQQIIQ")
+assert HEADER.size == 80 and ALLOC.size == 40
+
+
+class OracleError(Exception):
+    code = "ERROR"
+
+
+class InvalidArg(OracleError):
+    code = "INVALID_ARG"
+
+
+class Overlap(OracleError):
+    code = "OVERLAP"
+
+
+class UnknownPtr(OracleError):
+    code = "UNKNOWN_PTR"
+
+
+class ImageMismatch(OracleError):
+    code = "IMAGE_MISMATCH"
+
+
+class Corrupt(OracleError):
+    code = "CORRUPT"
+
+
+# ---------------------------------------------------------------------------
+# Fingerprints through the plain C transcription (crac_fp.c)
+# ---------------------------------------------------------------------------
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "liboracle_fp.so")
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            from oracle import build as _b
+            _b.build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.oracle_fp64.restype = ctypes.c_uint64
+        lib.oracle_fp64.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+        lib.oracle_fp_chunks.restype = None
+        lib.oracle_fp_chunks.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def fp64(chunk) -> int:
+    """CRAC-FP64 of one chunk (bytes-like or uint8 array, length >= 1)."""
+    a = np.ascontiguousarray(np.frombuffer(bytes(chunk), dtype=np.uint8)
+                             if not isinstance(chunk, np.ndarray) else chunk, dtype=np.uint8)
+    if a.size == 0:
+        raise InvalidArg("empty chunk")
+    return int(_load().oracle_fp64(a.ctypes.data, a.size))
+
+
+def fp_chunks(buf: np.ndarray, chunk_bytes: int) -> np.ndarray:
+    """Fingerprints of every chunk of one allocation's bytes."""
+    a = np.ascontiguousarray(buf, dtype=np.uint8)
+    n = -(-a.size // chunk_bytes)
+    out = np.empty(n, dtype=np.uint64)
+    if n:
+        _load().oracle_fp_chunks(a.ctypes.data, a.size, chunk_bytes, out.ctypes.data)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Image parsing
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Image:
+    flags: int
+    chunk_bytes: int
+    lineage: int
+    epoch: int
+    parent_epoch: int
+    allocs: list            # list of (id, orig_ptr, bytes, kind, first_chunk)
+    n_chunks: int
+    fp: np.ndarray
+    idx: np.ndarray
+    payload: memoryview
+
+    @property
+    def full(self) -> bool:
+        return bool(self.flags & FLAG_FULL)
+
+    @property
+    def k(self) -> int:
+        return int(self.idx.size)
+
+
+def parse_image(buf: bytes) -> Image:
+    mv = memoryview(bytes(buf))
+    if len(mv) < HEADER.size:
+        raise Corrupt("truncated header")
+    (magic, version, flags, chunk, hash_id, lineage, epoch, parent, n_allocs, n_chunks, k,
+     payload_bytes) = HEADER.unpack_from(mv, 0)
+    if magic != MAGIC or version != VERSION or hash_id != HASH_ID:
+        raise Corrupt("bad magic/version/hash id")
+    need = HEADER.size + ALLOC.size * n_allocs + 8 * n_chunks + 8 * k + payload_bytes
+    if len(mv) != need:
+        raise Corrupt(f"size {len(mv)} != {need}")
+    allocs = []
+    o = HEADER.size
+    for _ in range(n_allocs):
+        aid, ptr, nbytes, kind, _z, first = ALLOC.unpack_from(mv, o)
+        allocs.append((aid, ptr, nbytes, kind, first))
+        o += ALLOC.size
+    fp = np.frombuffer(mv[o:o + 8 * n_chunks], dtype="<u8").astype(np.uint64)
+    o += 8 * n_chunks
+    idx = np.frombuffer(mv[o:o + 8 * k], dtype="<u8").astype(np.uint64)
+    o += 8 * k
+    return Image(flags, chunk, lineage, epoch, parent, allocs, n_chunks, fp, idx,
+                 mv[o:o + payload_bytes])
+
+
+def chunk_len(alloc_bytes: int, local: int, chunk_bytes: int) -> int:
+    return min(chunk_bytes, alloc_bytes - local * chunk_bytes)
+
+
+# ---------------------------------------------------------------------------
+# The context: registry + fingerprint baseline + checkpoint/restart
+# ---------------------------------------------------------------------------
+
+@dataclass
+class _Alloc:
+    id: int
+    ptr: int
+    bytes: int
+    kind: int
+
+
+class OracleContext:
+    """One simulated process: its active-allocation table and last fingerprints."""
+
+    def __init__(self, chunk_bytes: int, lineage: int = 1):
+        if chunk_bytes < 16 or chunk_bytes & (chunk_bytes - 1):
+            raise InvalidArg("chunk_bytes must be a power of two >= 16")
+        self.S = int(chunk_bytes)
+        self.lineage = int(lineage)
+        self.allocs: list[_Alloc] = []
+        self.next_id = 0
+        self.fp_valid: dict[int, np.ndarray] = {}   # alloc id -> previous fingerprints
+        self.epoch = 0                               # highest epoch seen
+        self.last_epoch = NO_PARENT                  # parent for the next image
+
+    # -- registry (the cudaMalloc-family log of active mallocs, Sec. 3.2) ---
+    def register(self, ptr: int, nbytes: int, kind: int = KIND_DEVICE) -> int:
+        if nbytes <= 0 or ptr == 0 or ptr % 16 or kind not in (KIND_DEVICE, KIND_MANAGED):
+            raise InvalidArg("bad registration")
+        for a in self.allocs:
+            if ptr < a.ptr + a.bytes and a.ptr < ptr + nbytes:
+                raise Overlap("overlapping registration")
+        aid = self.next_id
+        self.next_id += 1
+        self.allocs.append(_Alloc(aid, int(ptr), int(nbytes), int(kind)))
+        return aid
+
+    def free(self, ptr: int) -> None:
+        for i, a in enumerate(self.allocs):
+            if a.ptr == ptr:
+                del self.allocs[i]
+                self.fp_valid.pop(a.id, None)
+                return
+        raise UnknownPtr("pointer not registered")
+
+    def layout(self) -> np.ndarray:
+        counts = [-(-a.bytes // self.S) for a in self.allocs]
+        return np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+
+    # -- checkpoint -------------------------------------------------------
+    def checkpoint(self, contents: list) -> bytes:
+        """Image of the active allocations; contents[i] = bytes of allocs[i]."""
+        if len(contents) != len(self.allocs):
+            raise InvalidArg("one content buffer per registered allocation")
+        S = self.S
+        first = self.layout()
+        n = int(first[-1])
+        fp_new = np.empty(n, dtype=np.uint64)
+        dirty = np.empty(n, dtype=bool)
+        bufs = []
+        # 1-3: fingerprint every chunk, compare with the previous table of the
+        # same allocation id; an allocation with no valid table is all dirty.
+        for i, a in enumerate(self.allocs):
+            buf = np.ascontiguousarray(np.asarray(contents[i]).view(np.uint8).reshape(-1))
+            if buf.size != a.bytes:
+                raise InvalidArg("content size differs from registered size")
+            bufs.append(buf)
+            lo, hi = int(first[i]), int(first[i + 1])
+            fa = fp_chunks(buf, S)
+            fp_new[lo:hi] = fa
+            prev = self.fp_valid.get(a.id)
+            dirty[lo:hi] = True if prev is None else (fa != prev)
+        # 4: ascending dirty ids; byte offsets are the exclusive prefix sum of
+        # the chunks' actual (unpadded) lengths.
+        idx = np.flatnonzero(dirty).astype(np.uint64)
+        alloc_of = np.searchsorted(first, idx.astype(np.int64), side="right") - 1
+        pieces = []
+        for c, a in zip(idx.tolist(), alloc_of.tolist()):
+            local = c - int(first[a])
+            lo = local * S
+            pieces.append(bufs[a][lo:lo + chunk_len(self.allocs[a].bytes, local, S)].tobytes())
+        # 5: payload = dirty chunk bytes in idx order.
+        payload = b"".join(pieces)
+        k = int(idx.size)
+        flags = FLAG_FULL if k == n else 0
+        epoch = self.epoch + 1
+        # 6: serialize.
+        out = [HEADER.pack(MAGIC, VERSION, flags, S, HASH_ID, self.lineage, epoch,
+                           self.last_epoch, len(self.allocs), n, k, len(payload))]
+        for i, a in enumerate(self.allocs):
+            out.append(ALLOC.pack(a.id, a.ptr, a.bytes, a.kind, 0, int(first[i])))
+        out.append(fp_new.astype("<u8").tobytes())
+        out.append(idx.astype("<u8").tobytes())
+        out.append(payload)
+        # 7: commit the new baseline.
+        self.fp_valid = {a.id: fp_new[int(first[i]):int(first[i + 1])].copy()
+                         for i, a in enumerate(self.allocs)}
+        self.epoch = epoch
+        self.last_epoch = epoch
+        return b"".join(out)
+
+    # -- restart ------------------------------------------------------------
+    def restart(self, chain: list) -> list:
+        """Bytes of every registered allocation after restoring chain[-1].
+
+        chain runs from an image with the FULL flag to the target, each entry
+        the parent of the next.  The registry must match the target's
+        allocation table (count, sizes, kinds, order).  Images are applied
+        oldest first; each chunk goes to the allocation with the same id in
+        the target's table.
+        """
+        imgs = [parse_image(b) for b in chain]
+        if not imgs or not imgs[0].full:
+            raise ImageMismatch("chain must start at a FULL image")
+        for p, c in zip(imgs, imgs[1:]):
+            if c.parent_epoch != p.epoch or c.lineage != p.lineage or c.chunk_bytes != p.chunk_bytes:
+                raise ImageMismatch("broken chain")
+        tgt = imgs[-1]
+        if tgt.chunk_bytes != self.S:
+            raise ImageMismatch("chunk size differs")
+        if len(tgt.allocs) != len(self.allocs):
+            raise ImageMismatch("allocation count differs")
+        for a, (_id, _p, nbytes, kind, _f) in zip(self.allocs, tgt.allocs):
+            if a.bytes != nbytes or a.kind != kind:
+                raise ImageMismatch("allocation size/kind differs")
+        S = self.S
+        pos_of_id = {t[0]: i for i, t in enumerate(tgt.allocs)}
+        mem = [np.zeros(a.bytes, dtype=np.uint8) for a in self.allocs]
+        covered = [np.zeros(-(-a.bytes // S), dtype=bool) for a in self.allocs]
+        for img in imgs:
+            firsts = np.array([t[4] for t in img.allocs] + [img.n_chunks], dtype=np.int64)
+            off = 0
+            for c in img.idx.tolist():
+                a = int(np.searchsorted(firsts, c, side="right") - 1)
+                aid, _p, nbytes, _k, first = img.allocs[a]
+                local = c - first
+                ln = chunk_len(nbytes, local, S)
+                pos = pos_of_id.get(aid)
+                if pos is not None:
+                    mem[pos][local * S:local * S + ln] = np.frombuffer(
+                        img.payload[off:off + ln], dtype=np.uint8)
+                    covered[pos][local] = True
+                off += ln
+            if off != len(img.payload):
+                raise Corrupt("payload length does not match the chunk list")
+        if not all(cv.all() for cv in covered):
+            raise ImageMismatch("chain does not cover every chunk of the target")
+        # Re-bind the registry to the image's allocation identities and adopt
+        # its fingerprints as the baseline for the next checkpoint.
+        for i, a in enumerate(self.allocs):
+            a.id = tgt.allocs[i][0]
+        self.next_id = max([self.next_id] + [t[0] + 1 for t in tgt.allocs])
+        self.fp_valid = {}
+        for i, a in enumerate(self.allocs):
+            lo = tgt.allocs[i][4]
+            self.fp_valid[a.id] = tgt.fp[lo:lo + -(-a.bytes // S)].copy()
+        self.lineage = tgt.lineage
+        self.epoch = max(self.epoch, tgt.epoch)
+        self.last_epoch = tgt.epoch
+        return mem

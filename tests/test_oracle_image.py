@@ -1,0 +1,211 @@
+"""Pins for the oracle's checkpoint/restart semantics (CPU only).
+
+Each test checks the oracle against something other than itself:
+  * the paper's problem statement: restart(checkpoint(M)) == M for every
+    active allocation, freed allocations are not saved, allocations keep
+    their registration order (Sec. 3.1-3.2);
+  * closed forms: a first (full) image's payload is the concatenation of the
+    allocations' bytes; the payload length equals the sum of the listed
+    chunks' lengths; the chunk count is the sum of ceil(bytes/S);
+  * brute force: the dirty set of an incremental image equals the set of
+    chunks whose bytes differ (byte comparison), which equals the set the
+    test mutated; an unmodified re-checkpoint yields an empty delta.
+"""
+import struct
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.usefixtures("oracle_lib")
+
+
+def _mk(sizes, seed=1, kind="u32_xorshift"):
+    return [W.host_contents(kind, s, seed + i) for i, s in enumerate(sizes)]
+
+
+def _ctx(sizes, S, base_ptr=1 << 40):
+    ctx = O.OracleContext(S, lineage=7)
+    p = base_ptr
+    for s in sizes:
+        ctx.register(p, s, O.KIND_DEVICE)
+        p += (s + 4095) // 4096 * 4096 + 4096
+    return ctx
+
+
+SIZES = [1, 7, 8, 4095, 4096, 4097, 3 * 4096 + 5, 20000]
+
+
+def test_full_image_payload_is_concatenation():
+    bufs = _mk(SIZES)
+    ctx = _ctx(SIZES, 4096)
+    img = O.parse_image(ctx.checkpoint(bufs))
+    assert img.full and img.parent_epoch == O.NO_PARENT and img.epoch == 1
+    assert bytes(img.payload) == b"".join(b.tobytes() for b in bufs)
+    assert img.n_chunks == sum(-(-s // 4096) for s in SIZES)
+    assert img.idx.tolist() == list(range(img.n_chunks))
+    assert [a[2] for a in img.allocs] == SIZES
+    assert [a[0] for a in img.allocs] == list(range(len(SIZES)))
+
+
+def test_header_layout_fields():
+    bufs = _mk([100])
+    ctx = _ctx([100], 64)
+    raw = ctx.checkpoint(bufs)
+    assert raw[:8] == b"CRACIMG1"
+    version, flags, chunk, hid = struct.unpack_from("<IIII", raw, 8)
+    assert (version, flags, chunk, hid) == (1, 1, 64, 1)
+    lineage, epoch, parent, na, nc, k, pb = struct.unpack_from("<7Q", raw, 24)
+    assert (lineage, epoch, parent, na, nc, k, pb) == (7, 1, 2**64 - 1, 1, 2, 2, 100)
+    assert len(raw) == 80 + 40 + 8 * 2 + 8 * 2 + 100
+
+
+def test_unmodified_recheckpoint_is_empty_delta():
+    bufs = _mk(SIZES)
+    ctx = _ctx(SIZES, 4096)
+    ctx.checkpoint(bufs)
+    img = O.parse_image(ctx.checkpoint(bufs))
+    assert img.k == 0 and len(img.payload) == 0 and not img.full
+    assert img.parent_epoch == 1 and img.epoch == 2
+
+
+@pytest.mark.parametrize("S", [64, 4096])
+def test_delta_equals_bytewise_dirty_set(S):
+    sizes = [5000, 70000, 4096 * 3, 1]
+    bufs = _mk(sizes, seed=3)
+    ctx = _ctx(sizes, S)
+    ctx.checkpoint(bufs)
+    first = W.chunk_layout(sizes, S)
+    n = int(first[-1])
+    muts = W.choose_mutations(99, n, 0.1)
+    before = [b.copy() for b in bufs]
+    W.apply_mutations_host(bufs, first, S, muts)
+    img = O.parse_image(ctx.checkpoint(bufs))
+    # brute force: byte comparison chunk by chunk
+    byte_dirty = []
+    for a, s in enumerate(sizes):
+        for local in range(-(-s // S)):
+            lo, hi = local * S, min(local * S + S, s)
+            if not np.array_equal(before[a][lo:hi], bufs[a][lo:hi]):
+                byte_dirty.append(int(first[a]) + local)
+    assert img.idx.tolist() == byte_dirty == sorted(m.chunk for m in muts)
+    # payload = concatenation of exactly those chunks' new bytes
+    exp = b""
+    for c in byte_dirty:
+        a = int(np.searchsorted(first, c, side="right") - 1)
+        local = c - int(first[a])
+        exp += bufs[a][local * S:min(local * S + S, sizes[a])].tobytes()
+    assert bytes(img.payload) == exp
+
+
+def test_roundtrip_full_and_chain():
+    sizes = [9000, 4096 * 4, 77]
+    bufs = _mk(sizes, seed=5)
+    ctx = _ctx(sizes, 1024)
+    chain = [ctx.checkpoint(bufs)]
+    states = [[b.copy() for b in bufs]]
+    first = W.chunk_layout(sizes, 1024)
+    for r in range(3):
+        W.apply_mutations_host(bufs, first, 1024, W.choose_mutations(10 + r, int(first[-1]), 0.2))
+        chain.append(ctx.checkpoint(bufs))
+        states.append([b.copy() for b in bufs])
+    for t in range(4):
+        r2 = _ctx(sizes, 1024)
+        got = r2.restart(chain[:t + 1])
+        for g, e in zip(got, states[t]):
+            assert np.array_equal(g, e)
+        # After restart the baseline is the image: an unmodified checkpoint is empty.
+        img = O.parse_image(r2.checkpoint(states[t]))
+        assert img.k == 0 and img.parent_epoch == t + 1
+
+
+def test_freed_allocation_vanishes_and_new_one_is_all_dirty():
+    sizes = [4096, 8192, 100]
+    bufs = _mk(sizes, seed=8)
+    ctx = _ctx(sizes, 4096)
+    ctx.checkpoint(bufs)
+    ptr1 = ctx.allocs[1].ptr
+    ctx.free(ptr1)
+    newbuf = W.host_contents("u32_xorshift", 5000, 77)
+    ctx.register(1 << 50, 5000, O.KIND_MANAGED)
+    img = O.parse_image(ctx.checkpoint([bufs[0], bufs[2], newbuf]))
+    assert [a[0] for a in img.allocs] == [0, 2, 3]
+    assert [a[3] for a in img.allocs] == [0, 0, 1]
+    # alloc 0 and 2 unchanged (no chunks); the new allocation is all dirty
+    assert img.idx.tolist() == [2, 3]
+    assert bytes(img.payload) == newbuf.tobytes()
+
+
+def test_chain_across_register_and_free():
+    sizes = [4096 * 2, 4096 * 3]
+    bufs = _mk(sizes, seed=12)
+    ctx = _ctx(sizes, 4096)
+    i0 = ctx.checkpoint(bufs)
+    ctx.free(ctx.allocs[0].ptr)
+    extra = W.host_contents("u32_xorshift", 4096 + 3, 13)
+    ctx.register(1 << 51, 4096 + 3, O.KIND_DEVICE)
+    bufs2 = [bufs[1], extra]
+    bufs2[0][:4] ^= 0xFF
+    i1 = ctx.checkpoint(bufs2)
+    r = O.OracleContext(4096, lineage=7)
+    r.register(1 << 30, 4096 * 3)
+    r.register(1 << 31, 4096 + 3)
+    got = r.restart([i0, i1])
+    assert np.array_equal(got[0], bufs2[0]) and np.array_equal(got[1], bufs2[1])
+    assert [a.id for a in r.allocs] == [1, 2] and r.next_id == 3
+
+
+def test_restart_mismatch_and_corruption():
+    bufs = _mk([4096, 100])
+    ctx = _ctx([4096, 100], 4096)
+    raw = ctx.checkpoint(bufs)
+    r = _ctx([4096, 101], 4096)
+    with pytest.raises(O.ImageMismatch):
+        r.restart([raw])
+    r = _ctx([4096], 4096)
+    with pytest.raises(O.ImageMismatch):
+        r.restart([raw])
+    with pytest.raises(O.Corrupt):
+        O.parse_image(raw[:-1])
+    bad = bytearray(raw)
+    bad[0] ^= 1
+    with pytest.raises(O.Corrupt):
+        O.parse_image(bytes(bad))
+    delta = ctx.checkpoint(bufs)
+    with pytest.raises(O.ImageMismatch):
+        _ctx([4096, 100], 4096).restart([delta])
+
+
+def test_registry_errors():
+    ctx = O.OracleContext(4096)
+    ctx.register(4096, 100)
+    with pytest.raises(O.Overlap):
+        ctx.register(4096 + 64, 10)
+    with pytest.raises(O.InvalidArg):
+        ctx.register(1 << 20, 0)
+    with pytest.raises(O.InvalidArg):
+        ctx.register((1 << 20) + 8, 16)
+    with pytest.raises(O.UnknownPtr):
+        ctx.free(12345 * 16)
+    ctx.register(4096 + 112, 16)   # adjacent, not overlapping
+    ctx.free(4096)
+    ctx.register(4096, 100)
+
+
+def test_offsets_and_counts_invariants():
+    sizes = [123457, 4096, 65536 + 17]
+    bufs = _mk(sizes, seed=21)
+    ctx = _ctx(sizes, 4096)
+    ctx.checkpoint(bufs)
+    first = W.chunk_layout(sizes, 4096)
+    W.apply_mutations_host(bufs, first, 4096, W.choose_mutations(4, int(first[-1]), 0.3))
+    img = O.parse_image(ctx.checkpoint(bufs))
+    lens = []
+    for c in img.idx.tolist():
+        a = int(np.searchsorted(first, c, side="right") - 1)
+        lens.append(O.chunk_len(sizes[a], c - int(first[a]), 4096))
+    assert sum(lens) == len(img.payload)
+    assert img.n_chunks == int(first[-1])
+    assert np.all(np.diff(img.idx.astype(np.int64)) > 0)
