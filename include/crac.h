@@ -1,0 +1,290 @@
+/*
+ * crac.h -- C ABI of libcrac: the device data pass of CRAC-style transparent
+ * CUDA checkpoint-restart on one GPU (sm_103a).
+ *
+ * The paper ("CRAC: Checkpoint-Restart Architecture for CUDA with Streams and
+ * UVM") interposes on the cudaMalloc family, logs the pointers of the
+ * buffers it creates, and at checkpoint time saves only the memory of the
+ * *active* allocations -- allocated and not yet freed -- copying it back at
+ * restart (Sec. 3.2, "Issue of library-allocated memory", "Saving the
+ * library-allocated arena", "restoring the CUDA library-allocated regions").
+ * Device (cudaMalloc) and unified-memory (cudaMallocManaged) regions are both
+ * saved (same subsection; UVM support, Sec. 1 and 2).  Before copying, the
+ * device's queue of pending work is drained (Sec. 2.2, step (a) of the
+ * CheCUDA scheme that CRAC keeps).
+ *
+ * This library is that data pass, re-designed for one GB300:
+ *   - crac_register_alloc / crac_free are the interposition points: the
+ *     caller reports each cudaMalloc-family allocation and each free.
+ *   - crac_checkpoint turns every registered allocation into an image.  Each
+ *     allocation is cut into fixed-size chunks; every chunk gets a 64-bit
+ *     content fingerprint; chunks whose fingerprint differs from the previous
+ *     checkpoint's are compacted into a contiguous device staging buffer and
+ *     drained to pinned host memory on a side stream.  The incremental
+ *     (fingerprint/delta) design is this library's, not the paper's: the
+ *     paper copies every active allocation at every checkpoint.
+ *   - crac_restart writes an image (and, for a delta, its chain of parents)
+ *     back into the registered allocations.
+ *
+ * All functions return crac_status_t: 0 on success, a negative CRAC_ERR_*
+ * code on failure.  No function aborts the process or traps on the device;
+ * on a CUDA failure the call returns CRAC_ERR_CUDA and crac_last_cuda_error()
+ * gives the cudaError_t value.  A failed checkpoint leaves the previous image
+ * and the fingerprint baseline untouched.
+ *
+ * Threads: each context has one mutex; calls on different contexts may run
+ * concurrently.  Streams are CUDA runtime streams (cudaStream_t); pass them
+ * as crac_stream_t.  A NULL stream means "drain the whole device first"
+ * (cudaDeviceSynchronize), as the paper does before it copies.
+ */
+#ifndef CRAC_H
+#define CRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CRAC_API __attribute__((visibility("default")))
+#else
+#define CRAC_API
+#endif
+
+/* Same object as cudaStream_t; declared here so callers need no CUDA header. */
+typedef struct CUstream_st *crac_stream_t;
+
+typedef int crac_status_t;
+#define CRAC_OK                   0
+#define CRAC_ERR_INVALID_ARG     -1  /* bad size, pointer, alignment or config */
+#define CRAC_ERR_UNKNOWN_PTR     -2  /* crac_free of a pointer never registered */
+#define CRAC_ERR_OVERLAP         -3  /* range overlaps a registered allocation */
+#define CRAC_ERR_CUDA            -4  /* a CUDA call failed; see crac_last_cuda_error */
+#define CRAC_ERR_OOM             -5  /* device or pinned host memory exhausted */
+#define CRAC_ERR_IMAGE_MISMATCH  -6  /* image does not fit the registry / chain */
+#define CRAC_ERR_TIMEOUT         -7  /* a bounded device or host wait ran out */
+#define CRAC_ERR_BUSY            -8  /* resource in use (e.g. image still draining) */
+#define CRAC_ERR_UNSUPPORTED     -9  /* not supported in this build/config */
+#define CRAC_ERR_CORRUPT        -10  /* serialized image malformed or truncated */
+
+typedef enum {
+    CRAC_KIND_DEVICE = 0,   /* cudaMalloc */
+    CRAC_KIND_MANAGED = 1   /* cudaMallocManaged; prefetched to the device before the pass */
+} crac_kind_t;
+
+/* Where a checkpoint image keeps its payload. */
+#define CRAC_RESIDENCY_HOST    0  /* drained to pinned host memory (default) */
+#define CRAC_RESIDENCY_DEVICE  1  /* kept in device memory (fast in-HBM rollback) */
+
+/* How the checkpoint device pass is launched. */
+#define CRAC_LAUNCH_BATCHED    0  /* one persistent graph-launched kernel over all allocations */
+#define CRAC_LAUNCH_PER_ALLOC  1  /* fingerprint + compact + gather launched per allocation */
+
+typedef struct crac_ctx crac_ctx_t;      /* one simulated process context */
+typedef struct crac_image crac_image_t;  /* library-owned, reference counted */
+
+/*
+ * Context configuration.  Call crac_config_default() first, then override.
+ * chunk_bytes:     power of two in [16, 2^24]; 0 means 65536.
+ * staging_bytes:   device staging capacity for one segment of the pass; the
+ *                  tracked bytes are processed in segments of at most this
+ *                  many bytes.  0 means min(tracked bytes, 8 GiB), at least
+ *                  one chunk.
+ * lineage:         identifier written into every image of this context (and
+ *                  used to find a deserialized delta's parent); 0 = assign a
+ *                  process-unique value.
+ * image_residency: CRAC_RESIDENCY_HOST or CRAC_RESIDENCY_DEVICE.
+ * launch_mode:     CRAC_LAUNCH_BATCHED or CRAC_LAUNCH_PER_ALLOC.
+ * threads, chunks_per_tile, ctas_per_sm, warps_per_chunk: work split of the
+ *                  batched kernel; 0 = automatic.  threads is 256;
+ *                  warps_per_chunk is 1 or 8.
+ * timeout_ns:      limit on every device-side spin-wait; 0 = 2 s.
+ */
+typedef struct crac_config {
+    uint32_t struct_size;
+    uint32_t chunk_bytes;
+    uint64_t staging_bytes;
+    uint64_t lineage;
+    uint32_t image_residency;
+    uint32_t launch_mode;
+    uint32_t threads;
+    uint32_t chunks_per_tile;
+    uint32_t ctas_per_sm;
+    uint32_t warps_per_chunk;
+    uint64_t timeout_ns;
+    int32_t device;          /* CUDA device ordinal; -1 = current device */
+    uint32_t reserved[7];
+} crac_config_t;
+
+/* Summary of an image (crac_image_info). */
+typedef struct crac_image_info {
+    uint64_t lineage;
+    uint64_t epoch;          /* 1 for a context's first checkpoint, then increasing */
+    uint64_t parent_epoch;   /* UINT64_MAX if none */
+    uint32_t flags;          /* bit 0 CRAC_IMAGE_FULL: every chunk is present */
+    uint32_t chunk_bytes;
+    uint64_t n_allocs;
+    uint64_t n_chunks;
+    uint64_t k;              /* chunks present in this image */
+    uint64_t payload_bytes;
+    uint64_t serialized_bytes;
+    uint32_t residency;
+    uint32_t complete;       /* 1 once the drain has finished */
+} crac_image_info_t;
+#define CRAC_IMAGE_FULL 1u
+
+/* Measurements of a context's most recent checkpoint (crac_ctx_last_pass). */
+typedef struct crac_pass_info {
+    uint64_t tracked_bytes;  /* sum of registered allocation sizes */
+    uint64_t n_chunks;
+    uint64_t k;              /* dirty chunks */
+    uint64_t payload_bytes;  /* dirty bytes */
+    uint32_t segments;
+    uint32_t kernel_launches;
+    float device_ms;         /* device time of the pass launches (CUDA events) */
+    float prefetch_ms;       /* device time of managed-memory prefetch */
+    uint32_t grid;           /* CTAs of the batched kernel */
+    uint32_t chunks_per_tile;
+    uint32_t warps_per_chunk;
+    uint32_t reserved[5];
+} crac_pass_info_t;
+
+/* ---- configuration and contexts --------------------------------------- */
+
+CRAC_API void crac_config_default(crac_config_t *cfg);
+
+/* Create a context.  cfg may be NULL (defaults).  *out receives the handle. */
+CRAC_API crac_status_t crac_ctx_create(const crac_config_t *cfg, crac_ctx_t **out);
+
+/* Destroy a context after waiting for its device work.  Images it produced
+ * stay valid until released. */
+CRAC_API crac_status_t crac_ctx_destroy(crac_ctx_t *ctx);
+
+/*
+ * Report an active allocation (the paper logs the pointers returned by the
+ * cudaMalloc family, Sec. 3.2).  ptr is a device or managed pointer, 16-byte
+ * aligned (every cudaMalloc-family pointer is 256-byte aligned); bytes >= 1.
+ * The library never frees or owns it.  Errors: CRAC_ERR_INVALID_ARG (NULL or
+ * misaligned ptr, bytes == 0, bad kind), CRAC_ERR_OVERLAP (intersects a
+ * registered range -- the overlap hazard of Sec. 3.2, "Issue of memory
+ * overlapping").  Allocations are kept in registration order, which is the
+ * order of their chunks in every image.
+ */
+CRAC_API crac_status_t crac_ctx_register_alloc(crac_ctx_t *ctx, void *ptr, size_t bytes,
+                                               crac_kind_t kind);
+
+/* Drop an allocation (the paper's cudaFree interposition).  The next image no
+ * longer contains it.  CRAC_ERR_UNKNOWN_PTR if ptr was not registered. */
+CRAC_API crac_status_t crac_ctx_free(crac_ctx_t *ctx, void *ptr);
+
+/*
+ * Checkpoint every registered allocation.
+ * Ordering: the image reflects all work enqueued on `stream` before the call
+ * (other streams must be joined by the caller); stream == NULL first
+ * synchronizes the whole device.  Managed allocations are prefetched to the
+ * device on `stream` before the pass.
+ * The call returns once the device pass has finished (it needs the dirty
+ * byte count to size the image); the drain of the payload to host memory
+ * may still be running -- crac_image_wait blocks until it is done.
+ * The first checkpoint of an allocation carries all of its chunks; later
+ * ones carry only chunks whose fingerprint changed.  *image_out receives a
+ * new reference that the caller releases with crac_image_release.
+ */
+CRAC_API crac_status_t crac_ctx_checkpoint(crac_ctx_t *ctx, crac_stream_t stream,
+                                           crac_image_t **image_out);
+
+/*
+ * Write `image` back into the registered allocations (Sec. 3.2: the saved
+ * memory is "copied back at restart time").  For a delta image the chain of
+ * parents back to the nearest image with CRAC_IMAGE_FULL is applied, each
+ * chunk taken from the newest image that holds it.  The registry must match
+ * the image's allocation table in count, sizes, kinds and order, and the
+ * context's chunk size must equal the image's; otherwise
+ * CRAC_ERR_IMAGE_MISMATCH and device memory is untouched.  Work is enqueued
+ * on `stream` (NULL: device-wide sync first); the call returns after
+ * enqueueing.  The images stay referenced by the context until that work has
+ * completed.  Afterwards the image's fingerprints are the baseline for the
+ * next checkpoint (so an unmodified checkpoint is empty), and the registered
+ * allocations take the image's allocation identities.
+ */
+CRAC_API crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image,
+                                        crac_stream_t stream);
+
+/* Forget the fingerprint baseline: the next checkpoint carries every chunk
+ * (a FULL image, which cuts the delta chain). */
+CRAC_API crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx);
+
+/* Measurements of the context's most recent checkpoint pass. */
+CRAC_API crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out);
+
+/* ---- default-context forms (one implicit context per process) -------- */
+
+CRAC_API crac_status_t crac_register_alloc(void *ptr, size_t bytes, crac_kind_t kind);
+CRAC_API crac_status_t crac_free(void *ptr);
+CRAC_API crac_status_t crac_checkpoint(crac_stream_t stream, crac_image_t **image_out);
+CRAC_API crac_status_t crac_restart(const crac_image_t *image, crac_stream_t stream);
+
+/* ---- images ----------------------------------------------------------- */
+
+/* Block until the image's drain has completed, at most timeout_ns
+ * (0 = no limit).  CRAC_ERR_TIMEOUT if the limit passes first. */
+CRAC_API crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns);
+
+CRAC_API crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out);
+
+/*
+ * Serialize into dst (cap bytes), little-endian:
+ *   header (80 B): "CRACIMG1", u32 version=1, u32 flags, u32 chunk_bytes,
+ *     u32 hash_id=1, u64 lineage, u64 epoch, u64 parent_epoch, u64 n_allocs,
+ *     u64 n_chunks, u64 k, u64 payload_bytes;
+ *   n_allocs x {u64 id, u64 orig_ptr, u64 bytes, u32 kind, u32 0, u64 first_chunk};
+ *   u64 fp[n_chunks]; u64 idx[k] (ascending); payload (chunks in idx order,
+ *   the last chunk of an allocation unpadded).
+ * *need receives the size.  dst == NULL: only *need is set.  cap < need:
+ * CRAC_ERR_INVALID_ARG.  Waits for the drain first.
+ */
+CRAC_API crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap,
+                                            size_t *need);
+
+/* Parse a serialized image into a new host-resident image (CRAC_ERR_CORRUPT if
+ * malformed).  A delta's parent is found among live images by (lineage,
+ * parent_epoch) when it is restored. */
+CRAC_API crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **out);
+
+/* Drop a reference.  The memory is freed when the last reference goes (a
+ * child delta holds a reference to its parent). */
+CRAC_API crac_status_t crac_image_release(crac_image_t *image);
+
+/* ---- diagnostics ------------------------------------------------------ */
+
+CRAC_API const char *crac_status_str(crac_status_t s);
+/* cudaError_t of the last CUDA failure seen by this thread (0 if none). */
+CRAC_API int crac_last_cuda_error(void);
+/* Number of kernels this library has launched in the process (graph kernel
+ * nodes included). */
+CRAC_API uint64_t crac_kernel_launches(void);
+
+/* Managed-memory helpers for callers without their own (e.g. PyTorch, which
+ * does not allocate managed memory): cudaMallocManaged / cudaFree. */
+CRAC_API crac_status_t crac_alloc_managed(size_t bytes, void **out);
+CRAC_API crac_status_t crac_free_managed(void *ptr);
+
+/* Host-side fault injection for tests: the next `count` times the named step
+ * is reached it fails as if the CUDA call there had failed (or, for
+ * CRAC_FAULT_DEVICE_WAIT, the batched kernel is launched so that one tile's
+ * predecessor never publishes, and its bounded wait runs out).  count 0
+ * clears.  No GPU fault is raised. */
+#define CRAC_FAULT_NONE         0
+#define CRAC_FAULT_PASS         1  /* launch of the checkpoint pass */
+#define CRAC_FAULT_DRAIN        2  /* D2H drain enqueue */
+#define CRAC_FAULT_H2D          3  /* restart H2D enqueue */
+#define CRAC_FAULT_ALLOC        4  /* staging / image memory allocation */
+#define CRAC_FAULT_DEVICE_WAIT  5  /* look-back wait times out on the device */
+CRAC_API void crac_debug_inject_fault(int step, int count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRAC_H */

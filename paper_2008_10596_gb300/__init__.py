@@ -1,0 +1,280 @@
+"""Python binding of libcrac (include/crac.h): argument marshalling only.
+
+Every function here forwards to the C function of the same name in the
+in-tree shared library paper_2008_10596_gb300/_lib/libcrac.so.  There is no
+fallback: importing this package without the built library raises
+ImportError.  Streams may be given as torch.cuda.Stream objects, raw
+cudaStream_t integers, or None (the NULL stream: device-wide sync first).
+Pointers are integers (e.g. tensor.data_ptr()).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcrac.so")
+TESTKIT_PATH = os.path.join(_HERE, "_lib", "libcrac_testkit.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcrac.so is not built ({LIB_PATH}); run "
+                      "python -c 'import __graft_entry__ as g; g.build()'")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CRAC_OK = 0
+CRAC_ERR_INVALID_ARG = -1
+CRAC_ERR_UNKNOWN_PTR = -2
+CRAC_ERR_OVERLAP = -3
+CRAC_ERR_CUDA = -4
+CRAC_ERR_OOM = -5
+CRAC_ERR_IMAGE_MISMATCH = -6
+CRAC_ERR_TIMEOUT = -7
+CRAC_ERR_BUSY = -8
+CRAC_ERR_UNSUPPORTED = -9
+CRAC_ERR_CORRUPT = -10
+
+CRAC_KIND_DEVICE = 0
+CRAC_KIND_MANAGED = 1
+CRAC_RESIDENCY_HOST = 0
+CRAC_RESIDENCY_DEVICE = 1
+CRAC_LAUNCH_BATCHED = 0
+CRAC_LAUNCH_PER_ALLOC = 1
+CRAC_IMAGE_FULL = 1
+
+CRAC_FAULT_NONE = 0
+CRAC_FAULT_PASS = 1
+CRAC_FAULT_DRAIN = 2
+CRAC_FAULT_H2D = 3
+CRAC_FAULT_ALLOC = 4
+CRAC_FAULT_DEVICE_WAIT = 5
+
+EXPORTED = [
+    "crac_config_default", "crac_ctx_create", "crac_ctx_destroy", "crac_ctx_register_alloc",
+    "crac_ctx_free", "crac_ctx_checkpoint", "crac_ctx_restart", "crac_ctx_invalidate",
+    "crac_ctx_last_pass", "crac_register_alloc", "crac_free", "crac_checkpoint", "crac_restart",
+    "crac_image_wait", "crac_image_info", "crac_image_serialize", "crac_image_deserialize",
+    "crac_image_release", "crac_status_str", "crac_last_cuda_error", "crac_kernel_launches",
+    "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault",
+]
+
+
+class CracConfig(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32),
+        ("staging_bytes", ctypes.c_uint64), ("lineage", ctypes.c_uint64),
+        ("image_residency", ctypes.c_uint32), ("launch_mode", ctypes.c_uint32),
+        ("threads", ctypes.c_uint32), ("chunks_per_tile", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
+        ("timeout_ns", ctypes.c_uint64), ("device", ctypes.c_int32),
+        ("reserved", ctypes.c_uint32 * 7),
+    ]
+
+
+class CracImageInfo(ctypes.Structure):
+    _fields_ = [
+        ("lineage", ctypes.c_uint64), ("epoch", ctypes.c_uint64), ("parent_epoch", ctypes.c_uint64),
+        ("flags", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32), ("n_allocs", ctypes.c_uint64),
+        ("n_chunks", ctypes.c_uint64), ("k", ctypes.c_uint64), ("payload_bytes", ctypes.c_uint64),
+        ("serialized_bytes", ctypes.c_uint64), ("residency", ctypes.c_uint32),
+        ("complete", ctypes.c_uint32),
+    ]
+
+
+class CracPassInfo(ctypes.Structure):
+    _fields_ = [
+        ("tracked_bytes", ctypes.c_uint64), ("n_chunks", ctypes.c_uint64), ("k", ctypes.c_uint64),
+        ("payload_bytes", ctypes.c_uint64), ("segments", ctypes.c_uint32),
+        ("kernel_launches", ctypes.c_uint32), ("device_ms", ctypes.c_float),
+        ("prefetch_ms", ctypes.c_float), ("grid", ctypes.c_uint32),
+        ("chunks_per_tile", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 5),
+    ]
+
+
+_vp = ctypes.c_void_p
+_st = ctypes.c_int
+_sigs = {
+    "crac_config_default": (None, [ctypes.POINTER(CracConfig)]),
+    "crac_ctx_create": (_st, [ctypes.POINTER(CracConfig), ctypes.POINTER(_vp)]),
+    "crac_ctx_destroy": (_st, [_vp]),
+    "crac_ctx_register_alloc": (_st, [_vp, _vp, ctypes.c_size_t, ctypes.c_int]),
+    "crac_ctx_free": (_st, [_vp, _vp]),
+    "crac_ctx_checkpoint": (_st, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "crac_ctx_restart": (_st, [_vp, _vp, _vp]),
+    "crac_ctx_invalidate": (_st, [_vp]),
+    "crac_ctx_last_pass": (_st, [_vp, ctypes.POINTER(CracPassInfo)]),
+    "crac_register_alloc": (_st, [_vp, ctypes.c_size_t, ctypes.c_int]),
+    "crac_free": (_st, [_vp]),
+    "crac_checkpoint": (_st, [_vp, ctypes.POINTER(_vp)]),
+    "crac_restart": (_st, [_vp, _vp]),
+    "crac_image_wait": (_st, [_vp, ctypes.c_uint64]),
+    "crac_image_info": (_st, [_vp, ctypes.POINTER(CracImageInfo)]),
+    "crac_image_serialize": (_st, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "crac_image_deserialize": (_st, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "crac_image_release": (_st, [_vp]),
+    "crac_status_str": (ctypes.c_char_p, [_st]),
+    "crac_last_cuda_error": (ctypes.c_int, []),
+    "crac_kernel_launches": (ctypes.c_uint64, []),
+    "crac_alloc_managed": (_st, [ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "crac_free_managed": (_st, [_vp]),
+    "crac_debug_inject_fault": (None, [ctypes.c_int, ctypes.c_int]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class CracError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.crac_status_str(code).decode()
+        if code == CRAC_ERR_CUDA:
+            msg += f" (cudaError {_lib.crac_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+def _check(st: int, where: str) -> None:
+    if st != CRAC_OK:
+        raise CracError(st, where)
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream or None
+    return int(s) or None
+
+
+def _ptr(p) -> int:
+    return p.data_ptr() if hasattr(p, "data_ptr") else int(p)
+
+
+# ---- configuration and contexts --------------------------------------------
+
+def crac_config_default(**overrides) -> CracConfig:
+    cfg = CracConfig()
+    _lib.crac_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def crac_ctx_create(cfg: CracConfig | None = None) -> int:
+    h = _vp()
+    _check(_lib.crac_ctx_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
+           "crac_ctx_create")
+    return h.value
+
+
+def crac_ctx_destroy(ctx: int) -> None:
+    _check(_lib.crac_ctx_destroy(ctx), "crac_ctx_destroy")
+
+
+def crac_ctx_register_alloc(ctx: int, ptr, nbytes: int, kind: int = CRAC_KIND_DEVICE) -> None:
+    _check(_lib.crac_ctx_register_alloc(ctx, _ptr(ptr), nbytes, kind), "crac_ctx_register_alloc")
+
+
+def crac_ctx_free(ctx: int, ptr) -> None:
+    _check(_lib.crac_ctx_free(ctx, _ptr(ptr)), "crac_ctx_free")
+
+
+def crac_ctx_checkpoint(ctx: int, stream=None) -> int:
+    h = _vp()
+    _check(_lib.crac_ctx_checkpoint(ctx, _stream(stream), ctypes.byref(h)), "crac_ctx_checkpoint")
+    return h.value
+
+
+def crac_ctx_restart(ctx: int, image: int, stream=None) -> None:
+    _check(_lib.crac_ctx_restart(ctx, image, _stream(stream)), "crac_ctx_restart")
+
+
+def crac_ctx_invalidate(ctx: int) -> None:
+    _check(_lib.crac_ctx_invalidate(ctx), "crac_ctx_invalidate")
+
+
+def crac_ctx_last_pass(ctx: int) -> dict:
+    info = CracPassInfo()
+    _check(_lib.crac_ctx_last_pass(ctx, ctypes.byref(info)), "crac_ctx_last_pass")
+    return {f: getattr(info, f) for f, _ in CracPassInfo._fields_ if f != "reserved"}
+
+
+# ---- default-context forms ---------------------------------------------------
+
+def crac_register_alloc(ptr, nbytes: int, kind: int = CRAC_KIND_DEVICE) -> None:
+    _check(_lib.crac_register_alloc(_ptr(ptr), nbytes, kind), "crac_register_alloc")
+
+
+def crac_free(ptr) -> None:
+    _check(_lib.crac_free(_ptr(ptr)), "crac_free")
+
+
+def crac_checkpoint(stream=None) -> int:
+    h = _vp()
+    _check(_lib.crac_checkpoint(_stream(stream), ctypes.byref(h)), "crac_checkpoint")
+    return h.value
+
+
+def crac_restart(image: int, stream=None) -> None:
+    _check(_lib.crac_restart(image, _stream(stream)), "crac_restart")
+
+
+# ---- images -----------------------------------------------------------------
+
+def crac_image_wait(image: int, timeout_ns: int = 0) -> None:
+    _check(_lib.crac_image_wait(image, timeout_ns), "crac_image_wait")
+
+
+def crac_image_info(image: int) -> dict:
+    info = CracImageInfo()
+    _check(_lib.crac_image_info(image, ctypes.byref(info)), "crac_image_info")
+    return {f: getattr(info, f) for f, _ in CracImageInfo._fields_}
+
+
+def crac_image_serialize(image: int) -> bytes:
+    need = ctypes.c_size_t()
+    _check(_lib.crac_image_serialize(image, None, 0, ctypes.byref(need)), "crac_image_serialize")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(_lib.crac_image_serialize(image, buf, need.value, ctypes.byref(need)), "crac_image_serialize")
+    return buf.raw
+
+
+def crac_image_deserialize(data: bytes) -> int:
+    h = _vp()
+    b = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(_lib.crac_image_deserialize(b, len(data), ctypes.byref(h)), "crac_image_deserialize")
+    return h.value
+
+
+def crac_image_release(image: int) -> None:
+    _check(_lib.crac_image_release(image), "crac_image_release")
+
+
+# ---- diagnostics ---------------------------------------------------------------
+
+def crac_status_str(code: int) -> str:
+    return _lib.crac_status_str(code).decode()
+
+
+def crac_last_cuda_error() -> int:
+    return _lib.crac_last_cuda_error()
+
+
+def crac_kernel_launches() -> int:
+    return _lib.crac_kernel_launches()
+
+
+def crac_alloc_managed(nbytes: int) -> int:
+    h = _vp()
+    _check(_lib.crac_alloc_managed(nbytes, ctypes.byref(h)), "crac_alloc_managed")
+    return h.value
+
+
+def crac_free_managed(ptr: int) -> None:
+    _check(_lib.crac_free_managed(ptr), "crac_free_managed")
+
+
+def crac_debug_inject_fault(step: int, count: int = 1) -> None:
+    _lib.crac_debug_inject_fault(step, count)

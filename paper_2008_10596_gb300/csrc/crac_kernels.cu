@@ -1,0 +1,641 @@
+// Device kernels of the checkpoint/restart data pass (sm_103a).
+//
+// The paper drains the device and copies the memory of every active
+// allocation to the host at checkpoint, and copies it back at restart
+// (Sec. 3.2, "Saving the library-allocated arena" and "restoring the CUDA
+// library-allocated regions").  This file implements that copy as an
+// incremental, HBM-bound pass:
+//
+//   K1 fingerprint  each chunk of each allocation -> 64-bit CRAC-FP64 value
+//   K2 dirty test   fp_new != fp_old (or no baseline) -> compacted dirty list
+//                   in ascending global chunk order, with byte offsets
+//   K3 gather       dirty chunks -> contiguous staging buffer
+//   K4 scatter      staging (or a device-resident image) -> allocations
+//
+// The batched path fuses K1-K3 into one persistent kernel: CTAs take tiles
+// of consecutive global chunks from an atomic ticket counter, hash them,
+// publish the tile's dirty count and bytes, and find their exclusive prefix
+// with a decoupled look-back over earlier tiles (Merrill & Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016).  The
+// gather then re-reads the tile's dirty chunks, which the hash has just
+// pulled into L2.  The per-allocation path runs K1, K2 and K3 as separate
+// launches per allocation and is kept as the comparison baseline.
+//
+// CRAC-FP64 (this project's hash; the paper has none), per chunk of len
+// bytes read as little-endian u64 words w_j (last word zero-padded):
+//   acc = sum_j f(w_j ^ (j+1)*K1)  mod 2^64,   f(x) = y ^ (y >> 32), y = x*M1
+//   fp  = fmix(acc ^ len*M3) with fmix: z^=z>>31; z*=M2; z^=z>>29; z*=M1; z^=z>>32
+// K1 = floor(2^64/phi); M1, M2, M3 = odd-forced 2^64*frac(sqrt 2, 3, 5).
+// The sum is associative and commutative, so any reduction order gives the
+// same bits.
+//
+// Every device-side wait is bounded by a %globaltimer limit; a wait that
+// runs out sets an error bit in the control block and the kernel finishes
+// with its output discarded by the host.  No kernel traps.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "crac_kernels.cuh"
+
+namespace crac {
+
+namespace {
+
+constexpr uint64_t kK1 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kM1 = 0x6A09E667F3BCC909ull;
+constexpr uint64_t kM2 = 0xBB67AE8584CAA73Bull;
+constexpr uint64_t kM3 = 0x3C6EF372FE94F82Bull;
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagInc = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr int kMaxCpt = 256;
+
+__device__ __forceinline__ uint64_t mixw(uint64_t w, uint64_t key) {
+    const uint64_t y = (w ^ key) * kM1;
+    return y ^ (y >> 32);
+}
+
+__device__ __forceinline__ uint64_t fp_finalize(uint64_t acc, uint64_t len) {
+    uint64_t z = acc ^ (len * kM3);
+    z ^= z >> 31;
+    z *= kM2;
+    z ^= z >> 29;
+    z *= kM1;
+    z ^= z >> 32;
+    return z;
+}
+
+__device__ __forceinline__ uint64_t warp_sum(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Partial CRAC-FP64 sum of one chunk over the vectors owned by thread gl of
+// a GT-thread group.  Vector v (16 bytes) holds words 2v and 2v+1.
+template <int GT>
+__device__ __forceinline__ uint64_t hash_partial(const uint8_t *__restrict__ src, uint32_t len,
+                                                 int gl) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(src);
+    const uint32_t nv = len >> 4;
+    uint64_t acc = 0;
+    uint64_t key = (2ull * (uint64_t)gl + 1ull) * kK1;   // key of word 2v at v = gl
+    constexpr uint64_t kStep = 2ull * GT * kK1;          // key advance for v += GT
+    uint32_t v = gl;
+    constexpr int U = 8;
+    for (; v + (U - 1) * GT < nv; v += U * GT) {
+        uint4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = __ldg(p + v + u * GT);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t w0 = ((uint64_t)q[u].y << 32) | q[u].x;
+            const uint64_t w1 = ((uint64_t)q[u].w << 32) | q[u].z;
+            acc += mixw(w0, key);
+            acc += mixw(w1, key + kK1);
+            key += kStep;
+        }
+    }
+    for (; v < nv; v += GT) {
+        const uint4 q = __ldg(p + v);
+        acc += mixw(((uint64_t)q.y << 32) | q.x, key);
+        acc += mixw(((uint64_t)q.w << 32) | q.z, key + kK1);
+        key += kStep;
+    }
+    const uint32_t rem = len & 15u;
+    if (rem && v == nv) {   // this thread owns the partial tail vector
+        const uint8_t *t = src + 16ull * nv;
+        uint64_t w0 = 0, w1 = 0;
+        for (uint32_t b = 0; b < rem; ++b) {
+            const uint64_t byte = t[b];
+            if (b < 8) w0 |= byte << (8 * b);
+            else w1 |= byte << (8 * (b - 8));
+        }
+        acc += mixw(w0, key);
+        if (rem > 8) acc += mixw(w1, key + kK1);
+    }
+    return acc;
+}
+
+// Copy len bytes with the GT threads of a group (thread gl).
+template <int GT>
+__device__ __forceinline__ void copy_group(uint8_t *__restrict__ dst,
+                                           const uint8_t *__restrict__ src, uint64_t len, int gl) {
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
+        const uint64_t nv = len >> 4;
+        const uint4 *s = reinterpret_cast<const uint4 *>(src);
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+        uint64_t v = gl;
+        constexpr int U = 4;
+        for (; v + (U - 1) * GT < nv; v += U * GT) {
+            uint4 q[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) q[u] = s[v + u * GT];
+#pragma unroll
+            for (int u = 0; u < U; ++u) __stcs(d + v + u * GT, q[u]);
+        }
+        for (; v < nv; v += GT) __stcs(d + v, s[v]);
+        for (uint64_t b = nv * 16 + gl; b < len; b += GT) dst[b] = src[b];
+    } else if ((((uintptr_t)dst | (uintptr_t)src) & 3u) == 0) {
+        const uint64_t nw = len >> 2;
+        const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+        uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+        for (uint64_t w = gl; w < nw; w += GT) d[w] = s[w];
+        for (uint64_t b = nw * 4 + gl; b < len; b += GT) dst[b] = src[b];
+    } else {
+        for (uint64_t b = gl; b < len; b += GT) dst[b] = src[b];
+    }
+}
+
+// Last allocation whose first chunk is <= c (allocations are non-empty, so
+// first_chunk is strictly increasing).
+__device__ __forceinline__ uint32_t find_alloc(const CkptDesc *__restrict__ d, uint32_t n,
+                                               uint64_t c) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d[mid].first_chunk <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t find_scatter(const ScatterDesc *__restrict__ d, uint32_t n,
+                                                 uint64_t c) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d[mid].img_first <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Decoupled look-back for tile `tile` (> 0), run by one full warp.  Returns
+// the exclusive prefix of dirty chunks (*k0) and dirty bytes (*d0).  Each of
+// the two quantities has its own status array and is resolved separately.
+__device__ void lookback(const CkptParams &P, uint32_t tile, int lane, uint64_t *k0,
+                         uint64_t *d0) {
+    uint64_t kacc = 0, dacc = 0;
+    bool kdone = false, ddone = false;
+    int64_t j = (int64_t)tile - 1;
+    const uint64_t t0 = globaltimer();
+    bool gave_up = false;
+    while (!(kdone && ddone)) {
+        const int64_t t = j - lane;
+        uint64_t wk = kFlagInc, wd = kFlagInc;   // tiles before 0: inclusive 0
+        if (t >= 0) {
+            uint32_t spins = 0;
+            for (;;) {
+                wk = ld_acquire(P.tile_cnt + t);
+                wd = ld_acquire(P.tile_bytes + t);
+                if ((wk >> 62) && (wd >> 62)) break;
+                if (gave_up || ((++spins & 31u) == 0 &&
+                                (globaltimer() - t0 > P.timeout_ns || spins > (1u << 28)))) {
+                    gave_up = true;
+                    atomicOr(&P.ctrl->err, kErrTimeout);
+                    wk = kFlagInc;
+                    wd = kFlagInc;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!kdone) {
+            const unsigned inc = __ballot_sync(kFull, (wk >> 62) == 2);
+            const int lim = inc ? __ffs(inc) - 1 : 31;
+            kacc += warp_sum(lane <= lim ? (wk & kValMask) : 0);
+            kdone = inc != 0;
+        }
+        if (!ddone) {
+            const unsigned inc = __ballot_sync(kFull, (wd >> 62) == 2);
+            const int lim = inc ? __ffs(inc) - 1 : 31;
+            dacc += warp_sum(lane <= lim ? (wd & kValMask) : 0);
+            ddone = inc != 0;
+        }
+        j -= 32;
+    }
+    *k0 = kacc;
+    *d0 = dacc;
+}
+
+// ---------------------------------------------------------------------------
+// Fused batched checkpoint pass: K1 + K2 + K3 in one persistent kernel.
+// ---------------------------------------------------------------------------
+template <int NT, int WPC>
+__global__ void __launch_bounds__(NT) ckpt_fused_kernel(const CkptParams P) {
+    constexpr int W = NT / 32;
+    constexpr int G = W / WPC;        // chunk groups per CTA
+    constexpr int GT = WPC * 32;      // threads per group
+    __shared__ uint32_t s_alloc[kMaxCpt];
+    __shared__ uint32_t s_len[kMaxCpt];    // dirty: chunk length; clean: 0
+    __shared__ uint32_t s_pos[kMaxCpt];    // position among the tile's dirty chunks
+    __shared__ uint64_t s_boff[kMaxCpt];   // byte offset among the tile's dirty bytes
+    __shared__ uint64_t s_part[2][W];
+    __shared__ uint64_t s_k0, s_d0;
+    __shared__ uint32_t s_tile;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = warp / WPC;
+    const int gl = threadIdx.x - g * GT;
+    const uint32_t log2S = P.log2_chunk;
+    const uint64_t S = 1ull << log2S;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t t = atomicAdd(&P.ctrl->ticket, 1u);
+            if (P.skip_first_ticket && t == 0) t = atomicAdd(&P.ctrl->ticket, 1u);
+            s_tile = t;
+        }
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= P.n_tiles) break;
+        const uint64_t c0 = P.c_begin + (uint64_t)tile * P.cpt;
+        const uint32_t nc = (uint32_t)min((uint64_t)P.cpt, P.c_end - c0);
+        for (uint32_t t = threadIdx.x; t < nc; t += NT) s_alloc[t] = find_alloc(P.desc, P.n_allocs, c0 + t);
+        __syncthreads();
+
+        // K1 + K2 per chunk: fingerprint, then compare with the baseline.
+        for (uint32_t r = 0; r * G < nc; ++r) {
+            const uint32_t ci = r * G + g;
+            uint64_t acc = 0;
+            uint32_t len = 0;
+            CkptDesc d{};
+            uint64_t local = 0;
+            if (ci < nc) {
+                d = P.desc[s_alloc[ci]];
+                local = c0 + ci - d.first_chunk;
+                len = (uint32_t)min(S, d.bytes - (local << log2S));
+                acc = hash_partial<GT>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S),
+                                       len, gl);
+            }
+            acc = warp_sum(acc);
+            if (WPC > 1) {
+                if (lane == 0) s_part[r & 1][warp] = acc;
+                __syncthreads();
+                if (ci < nc && gl == 0) {
+                    acc = 0;
+#pragma unroll
+                    for (int w = 0; w < WPC; ++w) acc += s_part[r & 1][g * WPC + w];
+                }
+            }
+            if (ci < nc && gl == 0) {
+                const uint64_t fp = fp_finalize(acc, len);
+                P.fp_new[c0 + ci] = fp;
+                const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
+                s_len[ci] = dirty ? len : 0u;
+            }
+        }
+        __syncthreads();
+
+        // K2 compaction: positions within the tile (ballot + warp scan), then
+        // the tile's global prefix by decoupled look-back.
+        if (warp == 0) {
+            uint32_t cnt = 0;
+            uint64_t bytes = 0;
+            for (uint32_t base = 0; base < nc; base += 32) {
+                const uint32_t i = base + lane;
+                const uint32_t l = i < nc ? s_len[i] : 0u;
+                const unsigned m = __ballot_sync(kFull, l != 0);
+                const uint64_t incl = warp_incl_scan(l, lane);
+                if (i < nc) {
+                    s_pos[i] = cnt + __popc(m & ((1u << lane) - 1u));
+                    s_boff[i] = bytes + incl - l;
+                }
+                cnt += __popc(m);
+                bytes += __shfl_sync(kFull, incl, 31);
+            }
+            uint64_t k0 = 0, d0 = 0;
+            if (tile == 0) {
+                if (lane == 0) {
+                    st_release(P.tile_cnt, kFlagInc | cnt);
+                    st_release(P.tile_bytes, kFlagInc | bytes);
+                }
+            } else {
+                if (lane == 0) {
+                    st_release(P.tile_cnt + tile, kFlagAgg | cnt);
+                    st_release(P.tile_bytes + tile, kFlagAgg | bytes);
+                }
+                lookback(P, tile, lane, &k0, &d0);
+                if (lane == 0) {
+                    st_release(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                    st_release(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                }
+            }
+            if (lane == 0) {
+                s_k0 = k0;
+                s_d0 = d0;
+                if (tile == P.n_tiles - 1) {
+                    P.ctrl->k = k0 + cnt;
+                    P.ctrl->D = d0 + bytes;
+                    if (k0 + cnt <= P.idx_cap) P.off_out[k0 + cnt] = d0 + bytes;
+                    else atomicOr(&P.ctrl->err, kErrBounds);
+                }
+            }
+        }
+        __syncthreads();
+        const uint64_t k0 = s_k0, d0 = s_d0;
+        for (uint32_t t = threadIdx.x; t < nc; t += NT) {
+            if (s_len[t]) {
+                const uint64_t j = k0 + s_pos[t];
+                if (j < P.idx_cap) {
+                    P.idx_out[j] = c0 + t;
+                    P.off_out[j] = d0 + s_boff[t];
+                } else {
+                    atomicOr(&P.ctrl->err, kErrBounds);
+                }
+            }
+        }
+        // K3 gather of this tile's dirty chunks into the staging buffer.
+        for (uint32_t ci = g; ci < nc; ci += G) {
+            const uint32_t len = s_len[ci];
+            if (!len) continue;
+            const CkptDesc d = P.desc[s_alloc[ci]];
+            const uint64_t local = c0 + ci - d.first_chunk;
+            const uint64_t dst = d0 + s_boff[ci];
+            if (dst + len > P.staging_cap) {
+                if (gl == 0) atomicOr(&P.ctrl->err, kErrBounds);
+                continue;
+            }
+            copy_group<GT>(P.staging + dst,
+                           reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S), len, gl);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-allocation path (comparison baseline): K1, K2, K3 as separate launches.
+// ---------------------------------------------------------------------------
+constexpr int kRangeNT = 256;
+constexpr int kRangeWPC = 8;
+
+// K1 over chunks [c0, c1) of one allocation: fingerprints and dirty lengths.
+__global__ void __launch_bounds__(kRangeNT)
+fp_range_kernel(const CkptDesc *__restrict__ dp, uint64_t c0, uint64_t c1, uint32_t log2S,
+                const uint64_t *__restrict__ fp_old, uint64_t *__restrict__ fp_new,
+                uint32_t *__restrict__ lens, uint64_t lens_base) {
+    constexpr int GT = kRangeWPC * 32;
+    __shared__ uint64_t s_part[kRangeNT / 32];
+    const CkptDesc d = *dp;
+    const uint64_t S = 1ull << log2S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint64_t c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
+        const uint64_t local = c - d.first_chunk;
+        const uint32_t len = (uint32_t)min(S, d.bytes - (local << log2S));
+        uint64_t acc = hash_partial<GT>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S),
+                                        len, threadIdx.x);
+        acc = warp_sum(acc);
+        if (lane == 0) s_part[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            acc = 0;
+            for (int w = 0; w < kRangeNT / 32; ++w) acc += s_part[w];
+            const uint64_t fp = fp_finalize(acc, len);
+            fp_new[c] = fp;
+            const bool dirty = d.base_first == kNoBase || fp_old[d.base_first + local] != fp;
+            lens[c - lens_base] = dirty ? len : 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// K2 over chunks [c0, c1): one CTA scans the dirty lengths and appends the
+// dirty chunks to the running list held in `carry`.
+__global__ void __launch_bounds__(1024)
+compact_range_kernel(const uint32_t *__restrict__ lens, uint64_t lens_base, uint64_t c0,
+                     uint64_t c1, uint64_t *__restrict__ idx_out, uint64_t *__restrict__ off_out,
+                     uint64_t idx_cap, PerAllocCarry *carry, CkptCtrl *ctrl) {
+    __shared__ uint32_t s_wcnt[32];
+    __shared__ uint64_t s_wbytes[32];
+    __shared__ uint64_t s_k, s_d;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_k = carry->k;
+        s_d = carry->D;
+        carry->unit_k0 = carry->k;
+    }
+    __syncthreads();
+    const uint64_t k_start = s_k;
+    for (uint64_t base = c0; base < c1; base += 1024) {
+        const uint64_t c = base + threadIdx.x;
+        const uint32_t l = c < c1 ? lens[c - lens_base] : 0u;
+        const unsigned m = __ballot_sync(kFull, l != 0);
+        const uint64_t incl = warp_incl_scan(l, lane);
+        if (lane == 31) {
+            s_wcnt[warp] = __popc(m);
+            s_wbytes[warp] = incl;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t wc = s_wcnt[lane];
+            const uint64_t wb = s_wbytes[lane];
+            uint32_t ic = wc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, ic, o);
+                if (lane >= o) ic += t;
+            }
+            const uint64_t ib = warp_incl_scan(wb, lane);
+            s_wcnt[lane] = ic - wc;      // exclusive
+            s_wbytes[lane] = ib - wb;
+        }
+        __syncthreads();
+        const uint64_t k = s_k + s_wcnt[warp] + __popc(m & ((1u << lane) - 1u));
+        const uint64_t o = s_d + s_wbytes[warp] + incl - l;
+        if (l) {
+            if (k < idx_cap) {
+                idx_out[k] = c;
+                off_out[k] = o;
+            } else {
+                atomicOr(&ctrl->err, kErrBounds);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            s_k = k + (l ? 1 : 0);
+            s_d = o + l;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        carry->unit_k = s_k - k_start;
+        carry->k = s_k;
+        carry->D = s_d;
+        ctrl->k = s_k;
+        ctrl->D = s_d;
+        if (s_k <= idx_cap) off_out[s_k] = s_d;
+        else atomicOr(&ctrl->err, kErrBounds);
+    }
+}
+
+// K3: copy the dirty chunks listed by the last K2 of this allocation.
+__global__ void __launch_bounds__(kRangeNT)
+gather_range_kernel(const CkptDesc *__restrict__ dp, uint32_t log2S,
+                    const uint64_t *__restrict__ idx, const uint64_t *__restrict__ off,
+                    const PerAllocCarry *__restrict__ carry, uint64_t idx_cap,
+                    uint8_t *__restrict__ staging, uint64_t staging_cap, CkptCtrl *ctrl) {
+    constexpr int GT = kRangeWPC * 32;
+    const CkptDesc d = *dp;
+    const uint64_t k0 = carry->unit_k0;
+    const uint64_t room = idx_cap > k0 ? idx_cap - k0 : 0ull;
+    const uint64_t kn = (uint64_t)carry->unit_k < room ? (uint64_t)carry->unit_k : room;
+    const uint64_t S = 1ull << log2S;
+    for (uint64_t j = k0 + blockIdx.x; j < k0 + kn; j += gridDim.x) {
+        const uint64_t local = idx[j] - d.first_chunk;
+        const uint64_t len = min(S, d.bytes - (local << log2S));
+        const uint64_t o = off[j];
+        if (o + len > staging_cap) {
+            if (threadIdx.x == 0) atomicOr(&ctrl->err, kErrBounds);
+            continue;
+        }
+        copy_group<GT>(staging + o, reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S),
+                       len, threadIdx.x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4 restore scatter: payload chunks -> allocations, filtered by the owner map
+// so that each target chunk is written once, by the newest image holding it.
+// ---------------------------------------------------------------------------
+constexpr int kScatterNT = 256;
+
+__global__ void __launch_bounds__(kScatterNT) scatter_kernel(const ScatterParams P) {
+    constexpr int GT = 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t S = 1ull << P.log2_chunk;
+    const uint64_t n = P.j1 - P.j0;
+    for (uint64_t e = (uint64_t)blockIdx.x * (kScatterNT / 32) + warp; e < n;
+         e += (uint64_t)gridDim.x * (kScatterNT / 32)) {
+        const uint64_t c = P.full ? P.j0 + e : P.idx[e];
+        const ScatterDesc d = P.desc[find_scatter(P.desc, P.n_desc, c)];
+        const uint64_t local = c - d.img_first;
+        if (d.dst == 0) continue;
+        const uint64_t tc = d.tgt_first + local;
+        if (tc >= P.n_owner) {
+            if (lane == 0) atomicOr(P.err, kErrBounds);
+            continue;
+        }
+        if (P.owner[tc] != P.image_index) continue;
+        const uint64_t len = min(S, d.bytes - (local << P.log2_chunk));
+        const uint64_t o = P.full ? d.payload_base + (local << P.log2_chunk) : P.off[e];
+        if (o < P.origin || o - P.origin + len > P.window) {
+            if (lane == 0) atomicOr(P.err, kErrBounds);
+            continue;
+        }
+        copy_group<GT>(reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk),
+                       P.payload + (o - P.origin), len, lane);
+    }
+}
+
+template <int NT, int WPC>
+cudaError_t launch_fused_t(const CkptParams &p, int grid, cudaStream_t s) {
+    ckpt_fused_kernel<NT, WPC><<<grid, NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+static uint64_t g_launches = 0;   // guarded by the callers' context lock is not enough
+                                  // across contexts; use an atomic builtin
+void count_launches(uint64_t n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+uint64_t launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+const void *ckpt_fused_fn(int threads, int wpc) {
+    if (threads != 256) return nullptr;
+    if (wpc == 1) return reinterpret_cast<const void *>(&ckpt_fused_kernel<256, 1>);
+    if (wpc == 8) return reinterpret_cast<const void *>(&ckpt_fused_kernel<256, 8>);
+    return nullptr;
+}
+
+int ckpt_fused_max_ctas_per_sm(int threads, int wpc) {
+    const void *fn = ckpt_fused_fn(threads, wpc);
+    if (!fn) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_ckpt_fused(const CkptParams &p, int threads, int wpc, int grid,
+                              cudaStream_t s) {
+    if (p.cpt == 0 || p.cpt > (uint32_t)kMaxCpt || grid <= 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (threads == 256 && wpc == 1) e = launch_fused_t<256, 1>(p, grid, s);
+    else if (threads == 256 && wpc == 8) e = launch_fused_t<256, 8>(p, grid, s);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_fp_range(const CkptDesc *d, uint64_t c0, uint64_t c1, uint32_t log2S,
+                            const uint64_t *fp_old, uint64_t *fp_new, uint32_t *lens,
+                            uint64_t lens_base, int grid, cudaStream_t s) {
+    if (c1 <= c0) return cudaSuccess;
+    fp_range_kernel<<<grid, kRangeNT, 0, s>>>(d, c0, c1, log2S, fp_old, fp_new, lens, lens_base);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_compact_range(const uint32_t *lens, uint64_t lens_base, uint64_t c0, uint64_t c1,
+                                 uint64_t *idx_out, uint64_t *off_out, uint64_t idx_cap,
+                                 PerAllocCarry *carry, CkptCtrl *ctrl, cudaStream_t s) {
+    compact_range_kernel<<<1, 1024, 0, s>>>(lens, lens_base, c0, c1, idx_out, off_out, idx_cap,
+                                            carry, ctrl);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_gather_range(const CkptDesc *d, uint32_t log2S, const uint64_t *idx,
+                                const uint64_t *off, PerAllocCarry *carry, uint64_t max_entries,
+                                uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap,
+                                CkptCtrl *ctrl, int grid, cudaStream_t s) {
+    if (max_entries == 0) return cudaSuccess;
+    gather_range_kernel<<<grid, kRangeNT, 0, s>>>(d, log2S, idx, off, carry, idx_cap, staging,
+                                                  staging_cap, ctrl);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s) {
+    if (p.j1 <= p.j0) return cudaSuccess;
+    scatter_kernel<<<grid, kScatterNT, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+}  // namespace crac

@@ -1,0 +1,111 @@
+// Internal interface between the host runtime (crac_runtime.cpp) and the
+// device kernels (crac_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace crac {
+
+// One registered allocation as the checkpoint pass sees it.
+struct CkptDesc {
+    uint64_t ptr;          // device / managed address (16-byte aligned)
+    uint64_t bytes;        // allocation size
+    uint64_t first_chunk;  // global id of its first chunk in this layout
+    uint64_t base_first;   // its first chunk in the baseline table, or kNoBase
+};
+constexpr uint64_t kNoBase = ~0ull;
+
+// Control block of one pass launch; zeroed before every launch.
+struct CkptCtrl {
+    unsigned int ticket;       // next tile to hand out
+    unsigned int err;          // kErr* bits
+    unsigned long long k;      // dirty chunks in this segment
+    unsigned long long D;      // dirty bytes in this segment
+    unsigned long long pad[5];
+};
+static_assert(sizeof(CkptCtrl) == 64, "CkptCtrl layout");
+constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
+constexpr unsigned kErrBounds = 2u;    // an output index/offset exceeded its buffer
+
+// Parameters of the fused batched pass over global chunks [c_begin, c_end).
+struct CkptParams {
+    const CkptDesc *desc;
+    uint32_t n_allocs;
+    uint32_t log2_chunk;
+    uint64_t c_begin, c_end;
+    uint32_t cpt;              // chunks per tile
+    uint32_t n_tiles;
+    const uint64_t *fp_old;    // baseline fingerprints (indexed by base_first + local)
+    uint64_t *fp_new;          // indexed by global chunk id
+    uint64_t *idx_out;         // segment-relative dirty list (global chunk ids)
+    uint64_t *off_out;         // segment-relative byte offsets, k+1 entries
+    uint64_t idx_cap;          // entries available in idx_out (off_out has idx_cap+1)
+    uint8_t *staging;
+    uint64_t staging_cap;
+    uint64_t *tile_cnt;        // look-back status words, n_tiles each
+    uint64_t *tile_bytes;
+    CkptCtrl *ctrl;
+    uint64_t timeout_ns;
+    uint32_t skip_first_ticket;  // fault injection: tile 0 is never processed
+};
+
+// Restore: one image allocation mapped onto the target layout.
+struct ScatterDesc {
+    uint64_t img_first;     // first chunk of this allocation in the image layout
+    uint64_t bytes;
+    uint64_t tgt_first;     // its first chunk in the target layout (owner map index)
+    uint64_t dst;           // current device address of the target allocation; 0 = dropped
+    uint64_t payload_base;  // FULL images: byte offset of its first chunk in the payload
+    uint64_t pad[3];
+};
+
+struct ScatterParams {
+    const ScatterDesc *desc;
+    uint32_t n_desc;
+    uint32_t log2_chunk;
+    uint32_t full;            // 1: entries are image chunk ids j0..j1 with implicit offsets
+    uint32_t image_index;     // position in the chain; only chunks owned by it are written
+    uint64_t j0, j1;          // entry range
+    const uint64_t *idx;      // list mode: image chunk id of entry j (indexed j - j0)
+    const uint64_t *off;      // list mode: payload offset of entry j (indexed j - j0)
+    const uint8_t *payload;   // device address of payload byte `origin`
+    uint64_t origin;
+    uint64_t window;          // bytes valid from `payload`
+    const uint16_t *owner;    // chain position owning each target chunk
+    uint64_t n_owner;
+    unsigned int *err;
+};
+
+// Per-allocation (baseline) path: running totals carried between launches.
+struct PerAllocCarry {
+    unsigned long long k, D;
+    unsigned long long unit_k0, unit_k;   // dirty-list range of the current unit
+    unsigned long long pad[4];
+};
+
+// ---- launchers (return cudaGetLastError() of the launch) ----------------
+cudaError_t launch_ckpt_fused(const CkptParams &p, int threads, int warps_per_chunk, int grid,
+                              cudaStream_t s);
+// Kernel entry of the fused pass for a (threads, warps_per_chunk) variant, for
+// building a graph kernel node; nullptr if the variant does not exist.
+const void *ckpt_fused_fn(int threads, int warps_per_chunk);
+int ckpt_fused_max_ctas_per_sm(int threads, int warps_per_chunk);
+
+cudaError_t launch_fp_range(const CkptDesc *d, uint64_t c0, uint64_t c1, uint32_t log2_chunk,
+                            const uint64_t *fp_old, uint64_t *fp_new, uint32_t *lens,
+                            uint64_t lens_base, int grid, cudaStream_t s);
+cudaError_t launch_compact_range(const uint32_t *lens, uint64_t lens_base, uint64_t c0,
+                                 uint64_t c1, uint64_t *idx_out, uint64_t *off_out,
+                                 uint64_t idx_cap, PerAllocCarry *carry, CkptCtrl *ctrl,
+                                 cudaStream_t s);
+cudaError_t launch_gather_range(const CkptDesc *d, uint32_t log2_chunk, const uint64_t *idx,
+                                const uint64_t *off, PerAllocCarry *carry, uint64_t max_entries,
+                                uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap,
+                                CkptCtrl *ctrl, int grid, cudaStream_t s);
+
+cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s);
+
+void count_launches(uint64_t n);
+uint64_t launches_so_far();
+
+}  // namespace crac

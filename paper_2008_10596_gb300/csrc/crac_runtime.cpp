@@ -1,0 +1,1520 @@
+// Host runtime of libcrac: allocation registry, fingerprint baseline,
+// checkpoint and restart orchestration, image store, and the C ABI.
+//
+// The paper keeps its own table of active cudaMalloc-family allocations
+// (only the pointers the app got back, not the library's arenas) and saves
+// exactly those buffers (Sec. 3.2, "Issue of library-allocated memory" and
+// "Saving the library-allocated arena").  Restart copies the saved bytes
+// back, in allocation order (Sec. 3.1-3.2).  This runtime is that table
+// plus the device-side machinery: per-context device scratch, a ping-pong
+// pair of fingerprint tables, arenas for image payloads in device and pinned
+// host memory, a side stream for the device-to-host drain, and a CUDA graph
+// that launches the fused checkpoint pass.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "crac.h"
+#include "crac_kernels.cuh"
+
+using namespace crac;
+
+namespace {
+
+constexpr uint64_t kNoParent = ~0ull;
+constexpr uint64_t kHeaderBytes = 80;
+constexpr uint64_t kAllocEntryBytes = 40;
+constexpr uint64_t kDefaultStagingMax = 8ull << 30;
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+
+thread_local int t_last_cuda = 0;
+std::atomic<int> g_fault_step{CRAC_FAULT_NONE};
+std::atomic<int> g_fault_count{0};
+std::atomic<uint64_t> g_lineage_counter{0};
+
+crac_status_t cuda_status(cudaError_t e) {
+    t_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? CRAC_ERR_OOM : CRAC_ERR_CUDA;
+}
+
+#define CK(expr)                                   \
+    do {                                           \
+        cudaError_t e_ = (expr);                   \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+#define TRY(expr)                                  \
+    do {                                           \
+        crac_status_t s_ = (expr);                 \
+        if (s_ != CRAC_OK) return s_;              \
+    } while (0)
+
+bool fault_hit(int step) {
+    if (g_fault_step.load() != step) return false;
+    int c = g_fault_count.load();
+    while (c > 0) {
+        if (g_fault_count.compare_exchange_weak(c, c - 1)) {
+            if (c - 1 == 0) g_fault_step.store(CRAC_FAULT_NONE);
+            return true;
+        }
+    }
+    return false;
+}
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// First-fit range allocator over [0, size) with coalescing frees.
+// ---------------------------------------------------------------------------
+class RangeAlloc {
+  public:
+    explicit RangeAlloc(uint64_t size) { free_[0] = size; }
+    bool alloc(uint64_t len, uint64_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                const uint64_t o = it->first, rest = it->second - len;
+                free_.erase(it);
+                if (rest) free_[o + len] = rest;
+                *off = o;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t len) {
+        if (!len) return;
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<uint64_t, uint64_t> free_;
+};
+
+struct Block {
+    uint8_t *p = nullptr;
+    uint64_t len = 0;
+    int region = -1;
+    uint64_t off = 0;
+};
+
+// Device or pinned-host memory arena: regions from cudaMalloc/cudaHostAlloc,
+// carved first-fit.  Image payloads and tables live here so that a steady
+// checkpoint loop allocates nothing from CUDA after warm-up.
+class Arena {
+  public:
+    Arena(bool device, int dev, uint64_t quantum) : device_(device), dev_(dev), quantum_(quantum) {}
+    crac_status_t alloc(uint64_t len, Block *b) {
+        if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
+        len = round_up(std::max<uint64_t>(len, 1), 256);
+        std::lock_guard<std::mutex> lk(mu_);
+        for (size_t r = 0; r < regions_.size(); ++r) {
+            uint64_t off;
+            if (regions_[r].ra.alloc(len, &off)) {
+                *b = Block{regions_[r].base + off, len, (int)r, off};
+                return CRAC_OK;
+            }
+        }
+        uint64_t sz = std::max(len, quantum_);
+        void *p = nullptr;
+        cudaError_t e;
+        {
+            DeviceGuard g(dev_);
+            e = device_ ? cudaMalloc(&p, sz) : cudaHostAlloc(&p, sz, cudaHostAllocPortable);
+            if (e != cudaSuccess && sz > len) {
+                cudaGetLastError();
+                sz = len;
+                e = device_ ? cudaMalloc(&p, sz) : cudaHostAlloc(&p, sz, cudaHostAllocPortable);
+            }
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            t_last_cuda = (int)e;
+            return CRAC_ERR_OOM;
+        }
+        regions_.push_back(Region{(uint8_t *)p, sz, RangeAlloc(sz)});
+        const int r = (int)regions_.size() - 1;
+        uint64_t off = 0;
+        regions_[r].ra.alloc(len, &off);
+        *b = Block{regions_[r].base + off, len, r, off};
+        return CRAC_OK;
+    }
+    void free(Block &b) {
+        if (b.region < 0) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        regions_[b.region].ra.release(b.off, b.len);
+        b = Block{};
+    }
+    void shrink(Block &b, uint64_t new_len) {
+        if (b.region < 0) return;
+        new_len = round_up(std::max<uint64_t>(new_len, 1), 256);
+        if (new_len >= b.len) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        regions_[b.region].ra.release(b.off + new_len, b.len - new_len);
+        b.len = new_len;
+    }
+
+  private:
+    struct Region {
+        uint8_t *base;
+        uint64_t size;
+        RangeAlloc ra;
+    };
+    bool device_;
+    int dev_;
+    uint64_t quantum_;
+    std::mutex mu_;
+    std::vector<Region> regions_;
+};
+
+std::mutex g_arena_mu;
+std::map<int, std::unique_ptr<Arena>> g_dev_arenas;
+std::unique_ptr<Arena> g_pinned_arena;
+
+Arena &device_arena(int dev) {
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    auto &a = g_dev_arenas[dev];
+    if (!a) a.reset(new Arena(true, dev, 1ull << 30));
+    return *a;
+}
+
+Arena &pinned_arena() {
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    if (!g_pinned_arena) g_pinned_arena.reset(new Arena(false, 0, 256ull << 20));
+    return *g_pinned_arena;
+}
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+crac_status_t ensure_dev(DevBuf &b, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.cap >= bytes) return CRAC_OK;
+    if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
+    if (b.p) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(b.p));
+        b = DevBuf{};
+    }
+    const size_t sz = round_up(bytes + bytes / 4, 1 << 20);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+        b.cap = bytes;
+    } else {
+        b.cap = sz;
+    }
+    b.p = p;
+    return CRAC_OK;
+}
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+crac_status_t ensure_host(HostBuf &b, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.cap >= bytes) return CRAC_OK;
+    if (b.p) {
+        CK(cudaFreeHost(b.p));
+        b = HostBuf{};
+    }
+    const size_t sz = round_up(bytes + bytes / 4, 1 << 16);
+    CK(cudaHostAlloc(&b.p, sz, cudaHostAllocPortable));
+    b.cap = sz;
+    return CRAC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Images
+// ---------------------------------------------------------------------------
+
+struct ImgAlloc {
+    uint64_t id, orig_ptr, bytes;
+    uint32_t kind;
+    uint64_t first_chunk;
+};
+
+// One segment of an image's payload.
+struct Piece {
+    uint64_t k0 = 0, k = 0;         // entries [k0, k0+k) of the image's dirty list
+    uint64_t off0 = 0, bytes = 0;   // payload bytes [off0, off0+bytes)
+    Block host;                     // host residency: pinned copy
+    Block dev;                      // device residency: payload
+    Block idx_dev, off_dev;         // device residency: idx[k], off[k+1] (piece-relative)
+};
+
+struct crac_image {
+    std::atomic<int> refs{1};
+    int device = 0;
+    uint32_t flags = 0, chunk_bytes = 0, residency = CRAC_RESIDENCY_HOST;
+    uint64_t lineage = 0, epoch = 0, parent_epoch = kNoParent;
+    std::vector<ImgAlloc> allocs;
+    uint64_t n_chunks = 0, k = 0, payload_bytes = 0;
+    Block fp_h, idx_h;              // pinned: fp[n_chunks], idx[k]
+    std::vector<Piece> pieces;
+    crac_image *parent = nullptr;   // strong reference, set for delta images
+    cudaEvent_t done = nullptr;     // drain complete
+    std::atomic<int> state{0};      // 0 pending, 1 complete, < 0 failed (status)
+    std::mutex mu;
+};
+
+namespace {
+
+std::mutex g_img_mu;
+std::multimap<std::pair<uint64_t, uint64_t>, crac_image *> g_images;   // (lineage, epoch)
+
+void table_add(crac_image *im) {
+    std::lock_guard<std::mutex> lk(g_img_mu);
+    g_images.emplace(std::make_pair(im->lineage, im->epoch), im);
+}
+
+void table_remove(crac_image *im) {
+    std::lock_guard<std::mutex> lk(g_img_mu);
+    auto r = g_images.equal_range(std::make_pair(im->lineage, im->epoch));
+    for (auto it = r.first; it != r.second; ++it) {
+        if (it->second == im) {
+            g_images.erase(it);
+            return;
+        }
+    }
+}
+
+void img_ref(crac_image *im) {
+    if (im) im->refs.fetch_add(1);
+}
+
+crac_status_t img_wait(const crac_image *cim, uint64_t timeout_ns) {
+    crac_image *im = const_cast<crac_image *>(cim);
+    if (im->state.load() == 1) return CRAC_OK;
+    if (im->state.load() < 0) return im->state.load();
+    DeviceGuard g(im->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(im->done);
+        if (e == cudaSuccess) {
+            im->state.store(1);
+            return CRAC_OK;
+        }
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            im->state.store(cuda_status(e));
+            return im->state.load();
+        }
+        if (timeout_ns) {
+            const uint64_t el = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                    std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ns) return CRAC_ERR_TIMEOUT;
+        }
+        std::this_thread::yield();
+    }
+}
+
+void img_unref(crac_image *im) {
+    while (im) {
+        if (im->refs.fetch_sub(1) != 1) return;
+        if (im->done) {
+            DeviceGuard g(im->device);
+            cudaEventSynchronize(im->done);
+            cudaEventDestroy(im->done);
+            cudaGetLastError();
+        }
+        table_remove(im);
+        Arena &pa = pinned_arena();
+        pa.free(im->fp_h);
+        pa.free(im->idx_h);
+        for (Piece &p : im->pieces) {
+            pa.free(p.host);
+            if (p.dev.region >= 0 || p.idx_dev.region >= 0 || p.off_dev.region >= 0) {
+                Arena &da = device_arena(im->device);
+                da.free(p.dev);
+                da.free(p.idx_dev);
+                da.free(p.off_dev);
+            }
+        }
+        crac_image *parent = im->parent;
+        delete im;
+        im = parent;
+    }
+}
+
+// Parent of a delta: the direct link if set, else a live image with the same
+// lineage and the parent's epoch (deserialized images).
+crac_image *img_parent(crac_image *im) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (im->parent) return im->parent;
+    if (im->parent_epoch == kNoParent) return nullptr;
+    std::lock_guard<std::mutex> lk2(g_img_mu);
+    auto r = g_images.equal_range(std::make_pair(im->lineage, im->parent_epoch));
+    for (auto it = r.first; it != r.second; ++it) {
+        if (it->second != im && it->second->state.load() >= 0) {
+            img_ref(it->second);
+            im->parent = it->second;
+            return im->parent;
+        }
+    }
+    return nullptr;
+}
+
+uint64_t chunk_len(uint64_t bytes, uint64_t local, uint32_t log2S) {
+    return std::min<uint64_t>(1ull << log2S, bytes - (local << log2S));
+}
+
+uint32_t log2u(uint64_t x) {
+    uint32_t l = 0;
+    while ((1ull << l) < x) ++l;
+    return l;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Contexts
+// ---------------------------------------------------------------------------
+
+struct AllocRec {
+    uint64_t id, ptr, bytes;
+    uint32_t kind;
+};
+
+struct crac_ctx {
+    std::mutex mu;
+    crac_config_t cfg{};
+    int device = 0;
+    int sm_count = 0;
+    uint32_t log2S = 16;
+    std::vector<AllocRec> allocs;
+    uint64_t next_id = 0;
+    uint64_t lineage = 0;
+    uint64_t epoch_max = 0;
+    crac_image *parent = nullptr;
+    uint64_t parent_epoch = kNoParent;
+    // fingerprint baseline
+    DevBuf fp[2];
+    int fp_cur = 0;
+    bool base_valid = false;
+    std::unordered_map<uint64_t, uint64_t> base_first;   // alloc id -> first chunk in fp[fp_cur]
+    // pass scratch
+    DevBuf desc, work, idx, off, staging, lens, carry;
+    HostBuf desc_h, ctrl_h;
+    // restart scratch
+    DevBuf owner, sdesc, sidx, soff, serr;
+    HostBuf owner_h, sdesc_h, soff_h, serr_h;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_last = nullptr, ev_pass = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaEvent_t ev_p0 = nullptr, ev_p1 = nullptr;
+    // graph for the fused pass: memset(ctrl+status) -> kernel -> D2H(ctrl)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t g_memset = nullptr, g_kernel = nullptr, g_copy = nullptr;
+    int g_threads = 0, g_wpc = 0;
+    crac_pass_info_t last{};
+    bool cuda_ready = false;
+};
+
+namespace {
+
+crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
+    crac_config_default(&c->cfg);
+    if (cfg_in) {
+        if (cfg_in->struct_size && cfg_in->struct_size != sizeof(crac_config_t)) return CRAC_ERR_INVALID_ARG;
+        c->cfg = *cfg_in;
+        c->cfg.struct_size = sizeof(crac_config_t);
+    }
+    crac_config_t &cfg = c->cfg;
+    if (cfg.chunk_bytes == 0) cfg.chunk_bytes = 65536;
+    if (cfg.chunk_bytes < 16 || cfg.chunk_bytes > (1u << 24) || (cfg.chunk_bytes & (cfg.chunk_bytes - 1)))
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.image_residency > CRAC_RESIDENCY_DEVICE || cfg.launch_mode > CRAC_LAUNCH_PER_ALLOC)
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.threads && cfg.threads != 256) return CRAC_ERR_INVALID_ARG;
+    if (cfg.warps_per_chunk && cfg.warps_per_chunk != 1 && cfg.warps_per_chunk != 8)
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
+    if (cfg.timeout_ns == 0) cfg.timeout_ns = kDefaultTimeoutNs;
+    c->log2S = log2u(cfg.chunk_bytes);
+    c->lineage = cfg.lineage ? cfg.lineage : (g_lineage_counter.fetch_add(1) + 1);
+    return CRAC_OK;
+}
+
+// CUDA resources are created on the first checkpoint or restart, so that the
+// registry works (and can be tested) without touching the device.
+crac_status_t ctx_cuda_ready(crac_ctx *c) {
+    if (c->cuda_ready) return CRAC_OK;
+    int dev = c->cfg.device;
+    if (dev < 0) CK(cudaGetDevice(&dev));
+    c->device = dev;
+    DeviceGuard g(dev);
+    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_last, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_pass, cudaEventDisableTiming));
+    CK(cudaEventCreate(&c->ev_t0));
+    CK(cudaEventCreate(&c->ev_t1));
+    CK(cudaEventCreate(&c->ev_p0));
+    CK(cudaEventCreate(&c->ev_p1));
+    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
+    TRY(ensure_host(c->serr_h, 256));
+    c->cuda_ready = true;
+    return CRAC_OK;
+}
+
+void ctx_free_all(crac_ctx *c) {
+    if (!c->cuda_ready) {
+        img_unref(c->parent);
+        c->parent = nullptr;
+        return;
+    }
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
+                      &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr})
+        if (b->p) cudaFree(b->p);
+    for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h})
+        if (b->p) cudaFreeHost(b->p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1})
+        if (e) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
+    cudaGetLastError();
+    img_unref(c->parent);
+    c->parent = nullptr;
+}
+
+// Work split of the fused kernel for the context's chunk size.
+void pick_split(const crac_ctx *c, int *wpc, uint32_t *cpt) {
+    const uint64_t S = 1ull << c->log2S;
+    int w = (int)c->cfg.warps_per_chunk;
+    if (!w) w = S >= 16384 ? 8 : 1;
+    uint32_t t = c->cfg.chunks_per_tile;
+    if (!t) {
+        const uint64_t tile_bytes = 128ull << 10;
+        t = (uint32_t)std::max<uint64_t>(1, tile_bytes / S);
+        const uint32_t groups = 8 / w;
+        t = std::max(t, groups);
+        t = std::min<uint32_t>(t, 256);
+    }
+    *wpc = w;
+    *cpt = t;
+}
+
+struct Segment {
+    uint64_t c0, c1, bytes;
+};
+
+// Split the global chunk range into segments of at most `cap` bytes.
+std::vector<Segment> make_segments(const std::vector<AllocRec> &allocs, const std::vector<uint64_t> &first,
+                                   uint32_t log2S, uint64_t cap) {
+    std::vector<Segment> out;
+    const uint64_t S = 1ull << log2S;
+    Segment cur{0, 0, 0};
+    for (size_t a = 0; a < allocs.size(); ++a) {
+        const uint64_t nch = first[a + 1] - first[a];
+        uint64_t local = 0;
+        while (local < nch) {
+            const uint64_t rest_bytes = allocs[a].bytes - (local << log2S);
+            const uint64_t room = cap - cur.bytes;
+            uint64_t take, tb;
+            if (rest_bytes <= room) {
+                take = nch - local;
+                tb = rest_bytes;
+            } else {
+                take = room / S;
+                tb = take * S;
+            }
+            if (take == 0) {
+                out.push_back(cur);
+                cur = Segment{cur.c1, cur.c1, 0};
+                continue;
+            }
+            cur.c1 += take;
+            cur.bytes += tb;
+            local += take;
+        }
+    }
+    if (cur.c1 > cur.c0) out.push_back(cur);
+    return out;
+}
+
+// Build (or update) the graph memset -> fused kernel -> ctrl D2H and launch it.
+crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, int wpc,
+                                 int grid, cudaStream_t s) {
+    const void *fn = ckpt_fused_fn(256, wpc);
+    if (!fn) return CRAC_ERR_INVALID_ARG;
+    CkptParams Pc = P;
+    void *args[] = {&Pc};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaMemsetParams mp{};
+    mp.dst = c->work.p;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = work_bytes / 4;
+    mp.height = 1;
+    mp.pitch = 0;
+    bool rebuilt = false;
+    if (c->gexec && c->g_wpc == wpc) {
+        // Width changes of a memset node may be rejected; rebuild then.
+        if (cudaGraphExecMemsetNodeSetParams(c->gexec, c->g_memset, &mp) != cudaSuccess ||
+            cudaGraphExecKernelNodeSetParams(c->gexec, c->g_kernel, &kp) != cudaSuccess ||
+            cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            c->g_wpc = 0;
+        }
+    }
+    if (!c->gexec || c->g_wpc != wpc) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+        CK(cudaGraphCreate(&c->graph, 0));
+        CK(cudaGraphAddMemsetNode(&c->g_memset, c->graph, nullptr, 0, &mp));
+        CK(cudaGraphAddKernelNode(&c->g_kernel, c->graph, &c->g_memset, 1, &kp));
+        CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, c->ctrl_h.p, P.ctrl,
+                                    sizeof(CkptCtrl), cudaMemcpyDeviceToHost));
+        CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+        c->g_wpc = wpc;
+        c->g_threads = 256;
+        rebuilt = true;
+    }
+    (void)rebuilt;
+    CK(cudaGraphLaunch(c->gexec, s));
+    count_launches(1);
+    return CRAC_OK;
+}
+
+// One segment of the checkpoint pass; on return the ctrl block is on the host.
+crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_dev,
+                          const std::vector<uint64_t> &first, uint64_t *idx_d, uint64_t *off_d,
+                          uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap,
+                          cudaStream_t s, CkptCtrl *ctrl_out, float *ms) {
+    const uint64_t nseg = sg.c1 - sg.c0;
+    const uint64_t *fp_old = (const uint64_t *)c->fp[c->fp_cur].p;
+    uint64_t *fp_new = (uint64_t *)c->fp[1 - c->fp_cur].p;
+    const bool inject_wait = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
+    if (fault_hit(CRAC_FAULT_PASS)) {
+        t_last_cuda = (int)cudaErrorLaunchFailure;
+        return CRAC_ERR_CUDA;
+    }
+    CK(cudaEventRecord(c->ev_t0, s));
+    if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
+        int wpc;
+        uint32_t cpt;
+        pick_split(c, &wpc, &cpt);
+        const uint64_t n_tiles = (nseg + cpt - 1) / cpt;
+        if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+        const size_t work_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
+        TRY(ensure_dev(c->work, work_bytes));
+        int per_sm = (int)c->cfg.ctas_per_sm;
+        if (!per_sm) per_sm = std::max(1, ckpt_fused_max_ctas_per_sm(256, wpc));
+        const int grid = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * per_sm);
+        CkptParams P{};
+        P.desc = desc_dev;
+        P.n_allocs = (uint32_t)c->allocs.size();
+        P.log2_chunk = c->log2S;
+        P.c_begin = sg.c0;
+        P.c_end = sg.c1;
+        P.cpt = cpt;
+        P.n_tiles = (uint32_t)n_tiles;
+        P.fp_old = fp_old;
+        P.fp_new = fp_new;
+        P.idx_out = idx_d;
+        P.off_out = off_d;
+        P.idx_cap = idx_cap;
+        P.staging = staging;
+        P.staging_cap = staging_cap;
+        P.ctrl = (CkptCtrl *)c->work.p;
+        P.tile_cnt = (uint64_t *)((uint8_t *)c->work.p + sizeof(CkptCtrl));
+        P.tile_bytes = P.tile_cnt + n_tiles;
+        P.timeout_ns = c->cfg.timeout_ns;
+        P.skip_first_ticket = (inject_wait && n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        TRY(launch_fused_graph(c, P, work_bytes, wpc, grid, s));
+        c->last.grid = (uint32_t)grid;
+        c->last.chunks_per_tile = cpt;
+        c->last.warps_per_chunk = (uint32_t)wpc;
+        c->last.kernel_launches += 1;
+    } else {
+        TRY(ensure_dev(c->work, sizeof(CkptCtrl)));
+        TRY(ensure_dev(c->lens, nseg * sizeof(uint32_t)));
+        TRY(ensure_dev(c->carry, sizeof(PerAllocCarry)));
+        CkptCtrl *ctrl = (CkptCtrl *)c->work.p;
+        CK(cudaMemsetAsync(ctrl, 0, sizeof(CkptCtrl), s));
+        CK(cudaMemsetAsync(c->carry.p, 0, sizeof(PerAllocCarry), s));
+        const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
+        for (size_t a = a0; a < c->allocs.size() && first[a] < sg.c1; ++a) {
+            const uint64_t u0 = std::max(first[a], sg.c0), u1 = std::min(first[a + 1], sg.c1);
+            if (u1 <= u0) continue;
+            const int g = (int)std::min<uint64_t>(u1 - u0, (uint64_t)c->sm_count * 8);
+            CK(launch_fp_range(desc_dev + a, u0, u1, c->log2S, fp_old, fp_new, (uint32_t *)c->lens.p,
+                               sg.c0, g, s));
+            CK(launch_compact_range((const uint32_t *)c->lens.p, sg.c0, u0, u1, idx_d, off_d, idx_cap,
+                                    (PerAllocCarry *)c->carry.p, ctrl, s));
+            CK(launch_gather_range(desc_dev + a, c->log2S, idx_d, off_d, (PerAllocCarry *)c->carry.p,
+                                   u1 - u0, idx_cap, staging, staging_cap, ctrl, g, s));
+            c->last.kernel_launches += 3;
+        }
+        CK(cudaMemcpyAsync(c->ctrl_h.p, ctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(c->ev_t1, s));
+    CK(cudaEventRecord(c->ev_pass, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1));
+    *ms += t;
+    *ctrl_out = *(const CkptCtrl *)c->ctrl_h.p;
+    if (ctrl_out->err & kErrTimeout) return CRAC_ERR_TIMEOUT;
+    if (ctrl_out->err) return CRAC_ERR_CORRUPT;
+    return CRAC_OK;
+}
+
+void free_image_blocks(crac_image *im) {
+    im->refs.store(1);
+    im->parent = nullptr;
+    img_unref(im);
+}
+
+crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
+    if (!out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    DeviceGuard g(c->device);
+    if (!s) CK(cudaDeviceSynchronize());   // the paper's queue drain before a checkpoint
+    const size_t na = c->allocs.size();
+    const uint32_t log2S = c->log2S;
+    const uint64_t S = 1ull << log2S;
+    std::vector<uint64_t> first(na + 1, 0);
+    uint64_t tracked = 0;
+    for (size_t a = 0; a < na; ++a) {
+        first[a + 1] = first[a] + ((c->allocs[a].bytes + S - 1) >> log2S);
+        tracked += c->allocs[a].bytes;
+    }
+    const uint64_t n = first[na];
+    c->last = crac_pass_info_t{};
+    c->last.tracked_bytes = tracked;
+    c->last.n_chunks = n;
+
+    std::unique_ptr<crac_image> im(new crac_image());
+    im->device = c->device;
+    im->chunk_bytes = (uint32_t)S;
+    im->residency = c->cfg.image_residency;
+    im->lineage = c->lineage;
+    im->epoch = c->epoch_max + 1;
+    im->parent_epoch = c->parent_epoch;
+    im->n_chunks = n;
+    im->allocs.resize(na);
+    for (size_t a = 0; a < na; ++a)
+        im->allocs[a] = ImgAlloc{c->allocs[a].id, c->allocs[a].ptr, c->allocs[a].bytes, c->allocs[a].kind, first[a]};
+    CK(cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming));
+
+    Arena &pa = pinned_arena();
+    Arena &da = device_arena(c->device);
+    crac_status_t st = CRAC_OK;
+    auto fail = [&](crac_status_t code) {
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(c->side);
+        cudaGetLastError();
+        free_image_blocks(im.release());
+        return code;
+    };
+
+    if (n > 0) {
+        st = pa.alloc(n * 8, &im->fp_h);
+        if (st == CRAC_OK) st = pa.alloc(n * 8, &im->idx_h);
+        if (st != CRAC_OK) return fail(st);
+        // fingerprint tables and descriptors
+        // Only the output table may grow: the baseline table keeps the previous
+        // layout, which it still fully holds.
+        st = ensure_dev(c->fp[1 - c->fp_cur], n * 8);
+        if (st == CRAC_OK) st = ensure_dev(c->desc, na * sizeof(CkptDesc));
+        if (st == CRAC_OK) st = ensure_host(c->desc_h, na * sizeof(CkptDesc));
+        if (st != CRAC_OK) return fail(st);
+        CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+        for (size_t a = 0; a < na; ++a) {
+            uint64_t bf = kNoBase;
+            if (c->base_valid) {
+                auto it = c->base_first.find(c->allocs[a].id);
+                if (it != c->base_first.end()) bf = it->second;
+            }
+            dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+        }
+        // Order after the previous operation of this context (drain / restore).
+        if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
+        if (cudaMemcpyAsync(c->desc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(cuda_status(cudaGetLastError()));
+        // Managed regions migrate to the device before they are read.
+        bool any_managed = false;
+        for (const AllocRec &r : c->allocs) any_managed |= r.kind == CRAC_KIND_MANAGED;
+        if (any_managed) {
+            cudaEventRecord(c->ev_p0, s);
+            cudaMemLocation loc{};
+            loc.type = cudaMemLocationTypeDevice;
+            loc.id = c->device;
+            for (const AllocRec &r : c->allocs) {
+                if (r.kind != CRAC_KIND_MANAGED) continue;
+                cudaError_t e = cudaMemPrefetchAsync((const void *)r.ptr, r.bytes, loc, 0, s);
+                if (e != cudaSuccess) return fail(cuda_status(e));
+            }
+            cudaEventRecord(c->ev_p1, s);
+        }
+        // Segments bounded by the staging capacity.
+        uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
+        cap = std::max(round_up(cap, 256), S);
+        const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
+        uint64_t max_seg_chunks = 0, max_seg_bytes = 0;
+        for (const Segment &sg : segs) {
+            max_seg_chunks = std::max(max_seg_chunks, sg.c1 - sg.c0);
+            max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
+        }
+        const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
+        if (host_res) {
+            st = ensure_dev(c->staging, max_seg_bytes);
+            if (st == CRAC_OK) st = ensure_dev(c->idx, max_seg_chunks * 8);
+            if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
+            if (st != CRAC_OK) return fail(st);
+        }
+        uint64_t k_base = 0, d_base = 0;
+        float ms = 0;
+        for (const Segment &sg : segs) {
+            const uint64_t nseg = sg.c1 - sg.c0;
+            Piece pc;
+            uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
+            uint8_t *stg = (uint8_t *)c->staging.p;
+            if (!host_res) {
+                st = da.alloc(sg.bytes, &pc.dev);
+                if (st == CRAC_OK) st = da.alloc(nseg * 8, &pc.idx_dev);
+                if (st == CRAC_OK) st = da.alloc((nseg + 1) * 8, &pc.off_dev);
+                if (st != CRAC_OK) {
+                    da.free(pc.dev);
+                    da.free(pc.idx_dev);
+                    da.free(pc.off_dev);
+                    return fail(st);
+                }
+                idx_d = (uint64_t *)pc.idx_dev.p;
+                off_d = (uint64_t *)pc.off_dev.p;
+                stg = pc.dev.p;
+            }
+            if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) {
+                im->pieces.push_back(pc);
+                return fail(cuda_status(cudaGetLastError()));
+            }
+            CkptCtrl ctrl{};
+            st = run_segment(c, sg, (const CkptDesc *)c->desc.p, first, idx_d, off_d, nseg, stg, sg.bytes, s,
+                             &ctrl, &ms);
+            if (st != CRAC_OK) {
+                im->pieces.push_back(pc);
+                return fail(st);
+            }
+            pc.k0 = k_base;
+            pc.k = ctrl.k;
+            pc.off0 = d_base;
+            pc.bytes = ctrl.D;
+            if (fault_hit(CRAC_FAULT_DRAIN)) {
+                im->pieces.push_back(pc);
+                t_last_cuda = (int)cudaErrorLaunchFailure;
+                return fail(CRAC_ERR_CUDA);
+            }
+            cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
+            if (host_res) {
+                if (ctrl.D) {
+                    st = pa.alloc(ctrl.D, &pc.host);
+                    if (st != CRAC_OK) {
+                        im->pieces.push_back(pc);
+                        return fail(st);
+                    }
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(pc.host.p, c->staging.p, ctrl.D, cudaMemcpyDeviceToHost, c->side);
+                }
+            } else {
+                da.shrink(pc.dev, ctrl.D);
+                da.shrink(pc.idx_dev, ctrl.k * 8);
+                da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
+            }
+            if (e == cudaSuccess && ctrl.k)
+                e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+            im->pieces.push_back(pc);
+            if (e != cudaSuccess) return fail(cuda_status(e));
+            k_base += ctrl.k;
+            d_base += ctrl.D;
+        }
+        cudaError_t e = cudaMemcpyAsync(im->fp_h.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToHost, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        im->k = k_base;
+        im->payload_bytes = d_base;
+        pa.shrink(im->idx_h, k_base * 8);
+        c->last.k = k_base;
+        c->last.payload_bytes = d_base;
+        c->last.segments = (uint32_t)segs.size();
+        c->last.device_ms = ms;
+        if (any_managed) {
+            float pm = 0;
+            cudaEventElapsedTime(&pm, c->ev_p0, c->ev_p1);
+            c->last.prefetch_ms = pm;
+        }
+    } else {
+        CK(cudaEventRecord(im->done, s));
+    }
+
+    // Commit: the new fingerprints become the baseline.
+    im->flags = im->k == n ? CRAC_IMAGE_FULL : 0u;
+    if (!(im->flags & CRAC_IMAGE_FULL) && c->parent) {
+        img_ref(c->parent);
+        im->parent = c->parent;
+    }
+    c->fp_cur = 1 - c->fp_cur;
+    c->base_first.clear();
+    for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
+    c->base_valid = true;
+    c->epoch_max = im->epoch;
+    c->parent_epoch = im->epoch;
+    crac_image *img = im.release();
+    img->refs.store(2);   // the caller's reference and the context's
+    img_unref(c->parent);
+    c->parent = img;
+    table_add(img);
+    *out = img;
+    return CRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Restart
+// ---------------------------------------------------------------------------
+
+crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
+    if (!img) return CRAC_ERR_INVALID_ARG;
+    if (img->state.load() < 0) return img->state.load();
+    if (img->chunk_bytes != (1u << c->log2S)) return CRAC_ERR_IMAGE_MISMATCH;
+    if (img->allocs.size() != c->allocs.size()) return CRAC_ERR_IMAGE_MISMATCH;
+    for (size_t a = 0; a < c->allocs.size(); ++a)
+        if (img->allocs[a].bytes != c->allocs[a].bytes || img->allocs[a].kind != c->allocs[a].kind)
+            return CRAC_ERR_IMAGE_MISMATCH;
+    // Chain back to the nearest FULL image.
+    std::vector<crac_image *> chain;
+    for (crac_image *cur = img;;) {
+        chain.push_back(cur);
+        if (cur->flags & CRAC_IMAGE_FULL) break;
+        if (chain.size() >= 65535) return CRAC_ERR_UNSUPPORTED;
+        crac_image *p = img_parent(cur);
+        if (!p || p->lineage != cur->lineage || p->chunk_bytes != cur->chunk_bytes) return CRAC_ERR_IMAGE_MISMATCH;
+        cur = p;
+    }
+    std::reverse(chain.begin(), chain.end());
+    for (crac_image *im : chain) TRY(img_wait(im, 0));
+
+    DeviceGuard g(c->device);
+    const uint32_t log2S = c->log2S;
+    const size_t na = img->allocs.size();
+    const uint64_t nt = img->n_chunks;
+    std::unordered_map<uint64_t, size_t> tpos;
+    for (size_t a = 0; a < na; ++a) tpos[img->allocs[a].id] = a;
+
+    // Owner map: for every target chunk, the newest chain image holding it.
+    TRY(ensure_host(c->owner_h, std::max<uint64_t>(nt, 1) * 2));
+    if (c->ev_last) CK(cudaEventSynchronize(c->ev_last));   // pinned scratch reuse
+    uint16_t *owner = (uint16_t *)c->owner_h.p;
+    std::fill(owner, owner + nt, (uint16_t)0xFFFF);
+    std::vector<uint64_t> survivors(chain.size(), 0);
+    std::vector<std::vector<int64_t>> img_map(chain.size());   // image alloc -> target alloc or -1
+    for (size_t i = 0; i < chain.size(); ++i) {
+        crac_image *im = chain[i];
+        std::vector<int64_t> &m = img_map[i];
+        m.resize(im->allocs.size());
+        for (size_t a = 0; a < im->allocs.size(); ++a) {
+            auto it = tpos.find(im->allocs[a].id);
+            m[a] = (it == tpos.end() || img->allocs[it->second].bytes != im->allocs[a].bytes) ? -1 : (int64_t)it->second;
+        }
+        if (im->flags & CRAC_IMAGE_FULL) {
+            for (size_t a = 0; a < im->allocs.size(); ++a) {
+                if (m[a] < 0) continue;
+                const uint64_t nch = ((im->allocs[a].bytes - 1) >> log2S) + 1;
+                std::fill(owner + img->allocs[m[a]].first_chunk, owner + img->allocs[m[a]].first_chunk + nch, (uint16_t)i);
+            }
+        } else {
+            const uint64_t *idx = (const uint64_t *)im->idx_h.p;
+            size_t a = 0;
+            for (uint64_t j = 0; j < im->k; ++j) {
+                const uint64_t cc = idx[j];
+                while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= cc) ++a;
+                if (m[a] < 0) continue;
+                owner[img->allocs[m[a]].first_chunk + (cc - im->allocs[a].first_chunk)] = (uint16_t)i;
+            }
+        }
+    }
+    for (uint64_t t = 0; t < nt; ++t) {
+        if (owner[t] == 0xFFFF) return CRAC_ERR_IMAGE_MISMATCH;
+        survivors[owner[t]]++;
+    }
+    if (fault_hit(CRAC_FAULT_H2D)) {
+        t_last_cuda = (int)cudaErrorLaunchFailure;
+        return CRAC_ERR_CUDA;
+    }
+
+    if (!s) CK(cudaDeviceSynchronize());
+    // Scratch: owner map, per-image scatter descriptors, list offsets.
+    size_t total_desc = 0;
+    uint64_t host_k_total = 0;
+    for (crac_image *im : chain) {
+        total_desc += im->allocs.size();
+        if (im->residency == CRAC_RESIDENCY_HOST && !(im->flags & CRAC_IMAGE_FULL)) host_k_total += im->k;
+    }
+    uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : kDefaultStagingMax;
+    uint64_t max_host_payload = 0;
+    for (crac_image *im : chain)
+        if (im->residency == CRAC_RESIDENCY_HOST) max_host_payload = std::max(max_host_payload, im->payload_bytes);
+    cap = std::max<uint64_t>(std::min(cap, round_up(std::max<uint64_t>(max_host_payload, 1), 256)), 1ull << log2S);
+    TRY(ensure_dev(c->owner, std::max<uint64_t>(nt, 1) * 2));
+    TRY(ensure_dev(c->sdesc, total_desc * sizeof(ScatterDesc)));
+    TRY(ensure_host(c->sdesc_h, total_desc * sizeof(ScatterDesc)));
+    TRY(ensure_dev(c->serr, 256));
+    if (max_host_payload) {
+        TRY(ensure_dev(c->staging, cap));
+        TRY(ensure_dev(c->sidx, host_k_total * 8));
+        TRY(ensure_dev(c->soff, host_k_total * 8));
+        TRY(ensure_host(c->soff_h, host_k_total * 8));
+    }
+    CK(cudaStreamWaitEvent(s, c->ev_last, 0));
+    CK(cudaMemsetAsync(c->serr.p, 0, 256, s));
+    CK(cudaMemcpyAsync(c->owner.p, owner, nt * 2, cudaMemcpyHostToDevice, s));
+    ScatterDesc *sdh = (ScatterDesc *)c->sdesc_h.p;
+    ScatterDesc *sdd = (ScatterDesc *)c->sdesc.p;
+    const int grid = c->sm_count * 8;
+    size_t dpos = 0;
+    uint64_t lpos = 0;   // start of this image's region in sidx / soff / soff_h
+    for (size_t i = 0; i < chain.size(); ++i) {
+        crac_image *im = chain[i];
+        const size_t nd = im->allocs.size();
+        ScatterDesc *dh = sdh + dpos;
+        ScatterDesc *dd = sdd + dpos;
+        dpos += nd;
+        if (!survivors[i]) continue;
+        uint64_t pbase = 0;
+        for (size_t a = 0; a < nd; ++a) {
+            const int64_t t = img_map[i][a];
+            dh[a] = ScatterDesc{im->allocs[a].first_chunk, im->allocs[a].bytes,
+                                t < 0 ? 0 : img->allocs[t].first_chunk, t < 0 ? 0 : c->allocs[t].ptr, pbase, {0, 0, 0}};
+            pbase += im->allocs[a].bytes;
+        }
+        CK(cudaMemcpyAsync(dd, dh, nd * sizeof(ScatterDesc), cudaMemcpyHostToDevice, s));
+        ScatterParams P{};
+        P.desc = dd;
+        P.n_desc = (uint32_t)nd;
+        P.log2_chunk = log2S;
+        P.image_index = (uint32_t)i;
+        P.owner = (const uint16_t *)c->owner.p;
+        P.n_owner = nt;
+        P.err = (unsigned int *)c->serr.p;
+        if (im->residency == CRAC_RESIDENCY_DEVICE) {
+            for (const Piece &pc : im->pieces) {
+                if (!pc.k) continue;
+                P.full = 0;
+                P.j0 = 0;
+                P.j1 = pc.k;
+                P.idx = (const uint64_t *)pc.idx_dev.p;
+                P.off = (const uint64_t *)pc.off_dev.p;
+                P.payload = pc.dev.p;
+                P.origin = 0;
+                P.window = pc.bytes;
+                CK(launch_scatter(P, (int)std::min<uint64_t>((pc.k + 7) / 8, (uint64_t)grid), s));
+            }
+            continue;
+        }
+        // Host image: H2D windows of at most `cap` payload bytes into staging.
+        const bool full = (im->flags & CRAC_IMAGE_FULL) != 0;
+        const uint64_t nent = full ? im->n_chunks : im->k;
+        const uint64_t *idx_h = (const uint64_t *)im->idx_h.p;
+        uint64_t *soff_h = (uint64_t *)c->soff_h.p + lpos;
+        uint64_t *sidx_d = (uint64_t *)c->sidx.p + lpos;
+        uint64_t *soff_d = (uint64_t *)c->soff.p + lpos;
+        if (!full) lpos += nent;
+        std::vector<uint64_t> fpre;   // FULL: payload offset of each allocation
+        if (full) {
+            fpre.resize(nd);
+            uint64_t acc = 0;
+            for (size_t a = 0; a < nd; ++a) {
+                fpre[a] = acc;
+                acc += im->allocs[a].bytes;
+            }
+        } else {
+            size_t a = 0;
+            uint64_t acc = 0;
+            for (uint64_t j = 0; j < nent; ++j) {
+                while (a + 1 < nd && im->allocs[a + 1].first_chunk <= idx_h[j]) ++a;
+                soff_h[j] = acc;
+                acc += chunk_len(im->allocs[a].bytes, idx_h[j] - im->allocs[a].first_chunk, log2S);
+            }
+            if (acc != im->payload_bytes) return CRAC_ERR_CORRUPT;
+        }
+        // offset and length of entry j
+        size_t fa = 0;
+        auto entry = [&](uint64_t j, uint64_t *o, uint64_t *len) {
+            if (full) {
+                while (fa + 1 < nd && im->allocs[fa + 1].first_chunk <= j) ++fa;
+                while (fa > 0 && im->allocs[fa].first_chunk > j) --fa;
+                const uint64_t local = j - im->allocs[fa].first_chunk;
+                *o = fpre[fa] + (local << log2S);
+                *len = chunk_len(im->allocs[fa].bytes, local, log2S);
+            } else {
+                *o = soff_h[j];
+                *len = (j + 1 < nent ? soff_h[j + 1] : im->payload_bytes) - soff_h[j];
+            }
+        };
+        if (!full && nent) {
+            CK(cudaMemcpyAsync(sidx_d, idx_h, nent * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(soff_d, soff_h, nent * 8, cudaMemcpyHostToDevice, s));
+        }
+        uint64_t j0 = 0;
+        while (j0 < nent) {
+            uint64_t o0, l0;
+            entry(j0, &o0, &l0);
+            uint64_t j1 = j0 + 1, end = o0 + l0;
+            while (j1 < nent) {
+                uint64_t o, l;
+                entry(j1, &o, &l);
+                if (o + l - o0 > cap) break;
+                end = o + l;
+                ++j1;
+            }
+            // H2D payload bytes [o0, end) from the pieces that hold them.
+            for (const Piece &pc : im->pieces) {
+                const uint64_t lo = std::max(o0, pc.off0), hi = std::min(end, pc.off0 + pc.bytes);
+                if (hi <= lo) continue;
+                CK(cudaMemcpyAsync((uint8_t *)c->staging.p + (lo - o0), pc.host.p + (lo - pc.off0), hi - lo,
+                                   cudaMemcpyHostToDevice, s));
+            }
+            P.full = full ? 1u : 0u;
+            P.j0 = j0;
+            P.j1 = j1;
+            P.idx = full ? nullptr : sidx_d + j0;
+            P.off = full ? nullptr : soff_d + j0;
+            P.payload = (const uint8_t *)c->staging.p;
+            P.origin = o0;
+            P.window = end - o0;
+            CK(launch_scatter(P, (int)std::min<uint64_t>((j1 - j0 + 7) / 8, (uint64_t)grid), s));
+            j0 = j1;
+        }
+    }
+    // Baseline = the image's fingerprints; registry takes the image's identities.
+    TRY(ensure_dev(c->fp[c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
+    if (nt) CK(cudaMemcpyAsync(c->fp[c->fp_cur].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_last, s));
+    CK(cudaEventSynchronize(c->ev_last));
+    if (*(const unsigned *)c->serr_h.p) return CRAC_ERR_CORRUPT;
+    c->base_first.clear();
+    for (size_t a = 0; a < na; ++a) {
+        c->allocs[a].id = img->allocs[a].id;
+        c->next_id = std::max(c->next_id, img->allocs[a].id + 1);
+        c->base_first[img->allocs[a].id] = img->allocs[a].first_chunk;
+    }
+    c->base_valid = true;
+    c->lineage = img->lineage;
+    c->epoch_max = std::max(c->epoch_max, img->epoch);
+    c->parent_epoch = img->epoch;
+    img_ref(img);
+    img_unref(c->parent);
+    c->parent = img;
+    return CRAC_OK;
+}
+
+crac_ctx *g_default = nullptr;
+std::mutex g_default_mu;
+
+crac_status_t default_ctx(crac_ctx **out) {
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (!g_default) {
+        crac_ctx *c = new crac_ctx();
+        const crac_status_t st = ctx_init(c, nullptr);
+        if (st != CRAC_OK) {
+            ctx_free_all(c);
+            delete c;
+            return st;
+        }
+        g_default = c;
+    }
+    *out = g_default;
+    return CRAC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void crac_config_default(crac_config_t *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->struct_size = sizeof(crac_config_t);
+    cfg->chunk_bytes = 65536;
+    cfg->image_residency = CRAC_RESIDENCY_HOST;
+    cfg->launch_mode = CRAC_LAUNCH_BATCHED;
+    cfg->timeout_ns = kDefaultTimeoutNs;
+    cfg->device = -1;
+}
+
+crac_status_t crac_ctx_create(const crac_config_t *cfg, crac_ctx_t **out) {
+    if (!out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    crac_ctx *c = new crac_ctx();
+    const crac_status_t st = ctx_init(c, cfg);
+    if (st != CRAC_OK) {
+        ctx_free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_destroy(crac_ctx_t *ctx) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(g_default_mu);
+        if (ctx == g_default) g_default = nullptr;
+    }
+    ctx_free_all(ctx);
+    delete ctx;
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_register_alloc(crac_ctx_t *ctx, void *ptr, size_t bytes, crac_kind_t kind) {
+    if (!ctx || !ptr || bytes == 0 || ((uintptr_t)ptr & 15u) ||
+        (kind != CRAC_KIND_DEVICE && kind != CRAC_KIND_MANAGED))
+        return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const uint64_t p = (uint64_t)(uintptr_t)ptr;
+    if (p + bytes < p) return CRAC_ERR_INVALID_ARG;
+    for (const AllocRec &r : ctx->allocs)
+        if (p < r.ptr + r.bytes && r.ptr < p + bytes) return CRAC_ERR_OVERLAP;
+    ctx->allocs.push_back(AllocRec{ctx->next_id++, p, (uint64_t)bytes, (uint32_t)kind});
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_free(crac_ctx_t *ctx, void *ptr) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const uint64_t p = (uint64_t)(uintptr_t)ptr;
+    for (size_t i = 0; i < ctx->allocs.size(); ++i) {
+        if (ctx->allocs[i].ptr == p) {
+            ctx->base_first.erase(ctx->allocs[i].id);
+            ctx->allocs.erase(ctx->allocs.begin() + i);
+            return CRAC_OK;
+        }
+    }
+    return CRAC_ERR_UNKNOWN_PTR;
+}
+
+crac_status_t crac_ctx_checkpoint(crac_ctx_t *ctx, crac_stream_t stream, crac_image_t **image_out) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TRY(ctx_cuda_ready(ctx));
+    return ctx_checkpoint(ctx, (cudaStream_t)stream, image_out);
+}
+
+crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image, crac_stream_t stream) {
+    if (!ctx || !image) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TRY(ctx_cuda_ready(ctx));
+    return ctx_restart(ctx, const_cast<crac_image *>(image), (cudaStream_t)stream);
+}
+
+crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->base_valid = false;
+    ctx->base_first.clear();
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out) {
+    if (!ctx || !out) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *out = ctx->last;
+    return CRAC_OK;
+}
+
+crac_status_t crac_register_alloc(void *ptr, size_t bytes, crac_kind_t kind) {
+    crac_ctx *c;
+    TRY(default_ctx(&c));
+    return crac_ctx_register_alloc(c, ptr, bytes, kind);
+}
+
+crac_status_t crac_free(void *ptr) {
+    crac_ctx *c;
+    TRY(default_ctx(&c));
+    return crac_ctx_free(c, ptr);
+}
+
+crac_status_t crac_checkpoint(crac_stream_t stream, crac_image_t **image_out) {
+    crac_ctx *c;
+    TRY(default_ctx(&c));
+    return crac_ctx_checkpoint(c, stream, image_out);
+}
+
+crac_status_t crac_restart(const crac_image_t *image, crac_stream_t stream) {
+    crac_ctx *c;
+    TRY(default_ctx(&c));
+    return crac_ctx_restart(c, image, stream);
+}
+
+crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns) {
+    if (!image) return CRAC_ERR_INVALID_ARG;
+    return img_wait(image, timeout_ns);
+}
+
+crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out) {
+    if (!image || !out) return CRAC_ERR_INVALID_ARG;
+    crac_image *im = const_cast<crac_image *>(image);
+    if (im->state.load() == 0 && im->done && cudaEventQuery(im->done) == cudaSuccess) im->state.store(1);
+    cudaGetLastError();
+    std::memset(out, 0, sizeof(*out));
+    out->lineage = im->lineage;
+    out->epoch = im->epoch;
+    out->parent_epoch = im->parent_epoch;
+    out->flags = im->flags;
+    out->chunk_bytes = im->chunk_bytes;
+    out->n_allocs = im->allocs.size();
+    out->n_chunks = im->n_chunks;
+    out->k = im->k;
+    out->payload_bytes = im->payload_bytes;
+    out->serialized_bytes = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
+                            im->payload_bytes;
+    out->residency = im->residency;
+    out->complete = im->state.load() == 1 ? 1u : 0u;
+    return CRAC_OK;
+}
+
+static void put32(uint8_t *&p, uint32_t v) {
+    for (int i = 0; i < 4; ++i) *p++ = (uint8_t)(v >> (8 * i));
+}
+static void put64(uint8_t *&p, uint64_t v) {
+    for (int i = 0; i < 8; ++i) *p++ = (uint8_t)(v >> (8 * i));
+}
+static uint32_t get32(const uint8_t *p) {
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+    return v;
+}
+static uint64_t get64(const uint8_t *p) {
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
+    if (!image || !need) return CRAC_ERR_INVALID_ARG;
+    crac_image *im = const_cast<crac_image *>(image);
+    const uint64_t total = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
+                           im->payload_bytes;
+    *need = (size_t)total;
+    if (!dst) return CRAC_OK;
+    if (cap < total) return CRAC_ERR_INVALID_ARG;
+    TRY(img_wait(im, 0));
+    uint8_t *p = (uint8_t *)dst;
+    std::memcpy(p, "CRACIMG1", 8);
+    p += 8;
+    put32(p, 1);
+    put32(p, im->flags);
+    put32(p, im->chunk_bytes);
+    put32(p, 1);
+    put64(p, im->lineage);
+    put64(p, im->epoch);
+    put64(p, im->parent_epoch);
+    put64(p, im->allocs.size());
+    put64(p, im->n_chunks);
+    put64(p, im->k);
+    put64(p, im->payload_bytes);
+    for (const ImgAlloc &a : im->allocs) {
+        put64(p, a.id);
+        put64(p, a.orig_ptr);
+        put64(p, a.bytes);
+        put32(p, a.kind);
+        put32(p, 0);
+        put64(p, a.first_chunk);
+    }
+    if (im->n_chunks) std::memcpy(p, im->fp_h.p, 8 * im->n_chunks);
+    p += 8 * im->n_chunks;
+    if (im->k) std::memcpy(p, im->idx_h.p, 8 * im->k);
+    p += 8 * im->k;
+    for (const Piece &pc : im->pieces) {
+        if (!pc.bytes) continue;
+        if (im->residency == CRAC_RESIDENCY_DEVICE) {
+            DeviceGuard g(im->device);
+            CK(cudaMemcpy(p + pc.off0, pc.dev.p, pc.bytes, cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(p + pc.off0, pc.host.p, pc.bytes);
+        }
+    }
+    return CRAC_OK;
+}
+
+crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **out) {
+    if (!src || !out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const uint8_t *b = (const uint8_t *)src;
+    if (n < kHeaderBytes || std::memcmp(b, "CRACIMG1", 8) != 0) return CRAC_ERR_CORRUPT;
+    if (get32(b + 8) != 1 || get32(b + 20) != 1) return CRAC_ERR_CORRUPT;
+    const uint32_t flags = get32(b + 12), chunk = get32(b + 16);
+    if (chunk < 16 || chunk > (1u << 24) || (chunk & (chunk - 1)) || (flags & ~CRAC_IMAGE_FULL)) return CRAC_ERR_CORRUPT;
+    const uint64_t na = get64(b + 48), nc = get64(b + 56), k = get64(b + 64), pb = get64(b + 72);
+    if (na > (n / kAllocEntryBytes) || nc > n / 8 || k > nc || pb > n) return CRAC_ERR_CORRUPT;
+    const uint64_t need = kHeaderBytes + kAllocEntryBytes * na + 8 * nc + 8 * k + pb;
+    if (need != n) return CRAC_ERR_CORRUPT;
+    std::unique_ptr<crac_image> im(new crac_image());
+    cudaGetDevice(&im->device);
+    im->flags = flags;
+    im->chunk_bytes = chunk;
+    im->residency = CRAC_RESIDENCY_HOST;
+    im->lineage = get64(b + 24);
+    im->epoch = get64(b + 32);
+    im->parent_epoch = get64(b + 40);
+    im->n_chunks = nc;
+    im->k = k;
+    im->payload_bytes = pb;
+    const uint32_t log2S = log2u(chunk);
+    const uint8_t *p = b + kHeaderBytes;
+    uint64_t expect_first = 0;
+    im->allocs.resize(na);
+    for (uint64_t a = 0; a < na; ++a, p += kAllocEntryBytes) {
+        ImgAlloc &r = im->allocs[a];
+        r = ImgAlloc{get64(p), get64(p + 8), get64(p + 16), get32(p + 24), get64(p + 32)};
+        if (r.bytes == 0 || r.kind > 1 || r.first_chunk != expect_first) return CRAC_ERR_CORRUPT;
+        expect_first += ((r.bytes - 1) >> log2S) + 1;
+    }
+    if (expect_first != nc || ((flags & CRAC_IMAGE_FULL) != 0) != (k == nc)) return CRAC_ERR_CORRUPT;
+    const uint8_t *fp = p, *idx = p + 8 * nc, *payload = idx + 8 * k;
+    // idx strictly ascending and payload length equal to the listed chunks' lengths
+    uint64_t acc = 0, prev = 0;
+    size_t a = 0;
+    for (uint64_t j = 0; j < k; ++j) {
+        const uint64_t c = get64(idx + 8 * j);
+        if (c >= nc || (j && c <= prev)) return CRAC_ERR_CORRUPT;
+        prev = c;
+        while (a + 1 < na && im->allocs[a + 1].first_chunk <= c) ++a;
+        acc += chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+    }
+    if (acc != pb) return CRAC_ERR_CORRUPT;
+    Arena &pa = pinned_arena();
+    crac_status_t st = CRAC_OK;
+    Piece pc;
+    pc.k = k;
+    pc.bytes = pb;
+    if (nc) st = pa.alloc(8 * nc, &im->fp_h);
+    if (st == CRAC_OK && k) st = pa.alloc(8 * k, &im->idx_h);
+    if (st == CRAC_OK && pb) st = pa.alloc(pb, &pc.host);
+    if (st != CRAC_OK) {
+        im->pieces.push_back(pc);
+        free_image_blocks(im.release());
+        return st;
+    }
+    if (nc) std::memcpy(im->fp_h.p, fp, 8 * nc);
+    if (k) std::memcpy(im->idx_h.p, idx, 8 * k);
+    if (pb) std::memcpy(pc.host.p, payload, pb);
+    im->pieces.push_back(pc);
+    im->state.store(1);
+    crac_image *img = im.release();
+    table_add(img);
+    *out = img;
+    return CRAC_OK;
+}
+
+crac_status_t crac_image_release(crac_image_t *image) {
+    if (!image) return CRAC_ERR_INVALID_ARG;
+    img_unref(image);
+    return CRAC_OK;
+}
+
+const char *crac_status_str(crac_status_t s) {
+    switch (s) {
+    case CRAC_OK: return "CRAC_OK";
+    case CRAC_ERR_INVALID_ARG: return "CRAC_ERR_INVALID_ARG";
+    case CRAC_ERR_UNKNOWN_PTR: return "CRAC_ERR_UNKNOWN_PTR";
+    case CRAC_ERR_OVERLAP: return "CRAC_ERR_OVERLAP";
+    case CRAC_ERR_CUDA: return "CRAC_ERR_CUDA";
+    case CRAC_ERR_OOM: return "CRAC_ERR_OOM";
+    case CRAC_ERR_IMAGE_MISMATCH: return "CRAC_ERR_IMAGE_MISMATCH";
+    case CRAC_ERR_TIMEOUT: return "CRAC_ERR_TIMEOUT";
+    case CRAC_ERR_BUSY: return "CRAC_ERR_BUSY";
+    case CRAC_ERR_UNSUPPORTED: return "CRAC_ERR_UNSUPPORTED";
+    case CRAC_ERR_CORRUPT: return "CRAC_ERR_CORRUPT";
+    default: return "CRAC_ERR_UNKNOWN";
+    }
+}
+
+int crac_last_cuda_error(void) { return t_last_cuda; }
+
+uint64_t crac_kernel_launches(void) { return launches_so_far(); }
+
+crac_status_t crac_alloc_managed(size_t bytes, void **out) {
+    if (!out || !bytes) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    CK(cudaMallocManaged(out, bytes, cudaMemAttachGlobal));
+    return CRAC_OK;
+}
+
+crac_status_t crac_free_managed(void *ptr) {
+    if (!ptr) return CRAC_ERR_INVALID_ARG;
+    CK(cudaFree(ptr));
+    return CRAC_OK;
+}
+
+void crac_debug_inject_fault(int step, int count) {
+    g_fault_count.store(count > 0 ? count : 0);
+    g_fault_step.store(count > 0 ? step : CRAC_FAULT_NONE);
+}
+
+}  // extern "C"

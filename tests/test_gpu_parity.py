@@ -1,0 +1,258 @@
+"""CUDA path vs the CPU oracle, byte for byte (GPU).
+
+Every image the library produces is serialized and compared with the
+oracle's image of the same device bytes; every restore is compared with the
+bytes the oracle's restart produces.  The work is integer/byte work, so the
+bar is bit-exactness.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2008_10596_gb300 as C
+import workloads as W
+from oracle import oracle as O
+from tests.gpu_harness import Harness, pattern_mutations
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
+
+KIB = 1024
+
+
+def test_config1_full_restore_incremental():
+    """One 16 MiB xorshift64 buffer, 4 KiB chunks; full, restore, 1% mutated, incremental."""
+    wl = W.config1()
+    h = Harness(wl.chunk_bytes, lineage=101)
+    try:
+        data = W.host_contents("u32_xorshift", wl.sizes[0], wl.seed)
+        b = h.add(wl.sizes[0], data=data)
+        img1, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        assert O.parse_image(lib1).full and bytes(O.parse_image(lib1).payload) == data.tobytes()
+        b.zero()
+        h.restart(img1)
+        assert np.array_equal(b.read(), data)
+        n = wl.sizes[0] // wl.chunk_bytes
+        muts = W.choose_mutations(wl.seed, n, wl.dirty_fraction)
+        assert len(muts) == 41
+        h.mutate(muts)
+        expect = data.copy()
+        W.apply_mutations_host([expect], np.array([0, n]), wl.chunk_bytes, muts)
+        assert np.array_equal(b.read(), expect)          # the mutator did what the spec says
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        im2 = O.parse_image(lib2)
+        assert im2.idx.tolist() == sorted(m.chunk for m in muts)
+        assert im2.parent_epoch == 1 and im2.epoch == 2
+        # an unmodified checkpoint is empty
+        img3, lib3, ora3 = h.checkpoint()
+        assert lib3 == ora3 and O.parse_image(lib3).k == 0
+        # restore the chain into zeroed memory
+        b.zero()
+        h.restart(img3, [ora1, ora2, ora3])
+        assert np.array_equal(b.read(), expect)
+    finally:
+        h.close()
+
+
+SIZES = [1, 7, 8, 4095, 4096, 4097]
+
+
+@pytest.mark.parametrize("S", [64, 4 * KIB, 64 * KIB, 256 * KIB])
+@pytest.mark.parametrize("pattern", ["none", "all", "first", "last", "tail", "alternating", "random10"])
+def test_sweep_sizes_patterns(S, pattern):
+    sizes = SIZES + [3 * S + 5, 2 * S]
+    h = Harness(S, lineage=200 + S % 97)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=10 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        first = h.first()
+        muts = pattern_mutations(first, sizes, S, pattern)
+        h.mutate(muts)
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        assert O.parse_image(lib2).idx.tolist() == sorted(m.chunk for m in muts)
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img2)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("cpt,wpc", [(1, 1), (3, 1), (8, 8), (17, 8), (256, 1)])
+def test_work_split_variants_identical(cpt, wpc):
+    """Tile size and warps-per-chunk change only the schedule, never the bytes."""
+    S = 4 * KIB
+    sizes = [123457, 4096 * 37 + 1, 64 * KIB, 5, 300000]
+    h = Harness(S, lineage=7, chunks_per_tile=cpt, warps_per_chunk=wpc)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=30 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=9))
+        _, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("mode", ["per_alloc", "segments", "device", "device_segments"])
+def test_launch_modes_and_residency(mode):
+    S = 4 * KIB
+    cfg = {}
+    if mode == "per_alloc":
+        cfg["launch_mode"] = C.CRAC_LAUNCH_PER_ALLOC
+    if mode in ("segments", "device_segments"):
+        cfg["staging_bytes"] = 40 * KIB      # forces many segments, allocations split
+    if mode.startswith("device"):
+        cfg["image_residency"] = C.CRAC_RESIDENCY_DEVICE
+    sizes = [100000, 4096, 77, 250000, 8192 * 3 + 1]
+    h = Harness(S, lineage=9, **cfg)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=50 + i)
+        img1, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=4))
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        h.mutate(pattern_mutations(h.first(), sizes, S, "alternating", seed=5))
+        img3, lib3, ora3 = h.checkpoint()
+        assert lib3 == ora3
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img3)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+        if mode == "per_alloc":
+            info = C.crac_ctx_last_pass(h.ctx)
+            assert info["kernel_launches"] == 3 * len(sizes)
+    finally:
+        h.close()
+
+
+def test_register_free_between_checkpoints_and_chain_restore():
+    S = 4 * KIB
+    h = Harness(S, lineage=77)
+    try:
+        for i, n in enumerate([5000, 20000, 4096]):
+            h.add(n, seed=70 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.free(1)
+        h.add(9000, seed=80)
+        h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, "first"))
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        assert [a[0] for a in O.parse_image(lib2).allocs] == [0, 2, 3]
+        want = h.host()
+        # restore the chain in a fresh context from deserialized images
+        h2 = Harness(S, lineage=999)
+        try:
+            for b in h.bufs:
+                h2.add(b.nbytes, data=np.zeros(b.nbytes, dtype=np.uint8))
+            d1 = C.crac_image_deserialize(lib1)
+            d2 = C.crac_image_deserialize(lib2)
+            h2.images += [d1, d2]
+            h2.restart(d2, [ora1, ora2])
+            for b, w in zip(h2.bufs, want):
+                assert np.array_equal(b.read(), w)
+            # the fresh context continues the lineage; an unmodified checkpoint is empty
+            _, lib3, ora3 = h2.checkpoint()
+            assert lib3 == ora3
+            im3 = O.parse_image(lib3)
+            assert im3.k == 0 and im3.lineage == 77 and im3.parent_epoch == 2
+        finally:
+            h2.close()
+    finally:
+        h.close()
+
+
+def test_managed_allocations():
+    S = 64 * KIB
+    h = Harness(S, lineage=31)
+    try:
+        h.add(300000, seed=1)
+        h.add(200000, kind=C.CRAC_KIND_MANAGED, seed=2)
+        h.add(64 * KIB, kind=C.CRAC_KIND_MANAGED, seed=3)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        assert [a[3] for a in O.parse_image(lib1).allocs] == [0, 1, 1]
+        h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, "alternating"))
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img2)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
+
+
+def test_restart_rejects_mismatch_and_leaves_memory():
+    S = 4 * KIB
+    h = Harness(S, lineage=3)
+    try:
+        h.add(10000, seed=1)
+        img, _, _ = h.checkpoint()
+        h2 = Harness(S, lineage=4)
+        try:
+            b = h2.add(10001, seed=2)
+            before = b.read()
+            with pytest.raises(C.CracError) as e:
+                C.crac_ctx_restart(h2.ctx, img, h2.stream)
+            assert e.value.code == C.CRAC_ERR_IMAGE_MISMATCH
+            assert np.array_equal(b.read(), before)
+        finally:
+            h2.close()
+        h3 = Harness(64, lineage=4)
+        try:
+            h3.add(10000, seed=2)
+            with pytest.raises(C.CracError) as e:
+                C.crac_ctx_restart(h3.ctx, img, h3.stream)
+            assert e.value.code == C.CRAC_ERR_IMAGE_MISMATCH
+        finally:
+            h3.close()
+    finally:
+        h.close()
+
+
+def test_default_context_forms():
+    S = 64 * KIB
+    t = torch.empty(100000, dtype=torch.uint8, device="cuda")
+    data = W.host_contents("u8", 100000, 5)
+    t.copy_(torch.from_numpy(data))
+    C.crac_register_alloc(t.data_ptr(), 100000, C.CRAC_KIND_DEVICE)
+    try:
+        img = C.crac_checkpoint(torch.cuda.current_stream())
+        C.crac_image_wait(img)
+        info = C.crac_image_info(img)
+        assert info["flags"] & C.CRAC_IMAGE_FULL and info["payload_bytes"] == 100000
+        assert info["chunk_bytes"] == S and info["complete"] == 1
+        t.zero_()
+        C.crac_restart(img, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), data)
+        C.crac_image_release(img)
+    finally:
+        C.crac_free(t.data_ptr())
+
+
+def test_empty_registry():
+    h = Harness(4 * KIB, lineage=12)
+    try:
+        img, lib, ora = h.checkpoint()
+        assert lib == ora
+        assert O.parse_image(lib).n_chunks == 0
+        h.restart(img)
+    finally:
+        h.close()
