@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def C():
-    from paper_2008_10596_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__._load_builder().build()
     import paper_2008_10596_gb300 as mod
     return mod
 
