@@ -271,6 +271,74 @@ CRAC_API uint64_t crac_kernel_launches(void);
 CRAC_API crac_status_t crac_alloc_managed(size_t bytes, void **out);
 CRAC_API crac_status_t crac_free_managed(void *ptr);
 
+/* ---- allocation-free pass ------------------------------------------- */
+
+/* One region for crac_pass_noalloc, stored in device memory (32 bytes). */
+typedef struct crac_region {
+    uint64_t ptr;          /* device or managed address, 16-byte aligned */
+    uint64_t bytes;        /* >= 1 */
+    uint64_t first_chunk;  /* global id of its first chunk: regions are laid out
+                              back to back, first_chunk[i+1] = first_chunk[i] +
+                              ceil(bytes[i] / chunk_bytes) */
+    uint64_t base_first;   /* where its previous fingerprints start in fp_old,
+                              or UINT64_MAX: no previous ones, every chunk dirty */
+} crac_region_t;
+
+/* Results of crac_pass_noalloc, written to device memory (24 bytes). */
+typedef struct crac_pass_totals {
+    uint32_t reserved;
+    uint32_t err;            /* 0; bit 0: a device wait ran out; bit 1: idx_cap
+                                or staging_cap was too small */
+    uint64_t k;              /* dirty chunks */
+    uint64_t payload_bytes;  /* dirty bytes written to staging */
+} crac_pass_totals_t;
+
+/* Tiles the scratch of crac_pass_noalloc holds.  A tile is 128 KiB of chunks
+ * (at least 1 chunk, 8..256 chunks below 16 KiB chunks), so the pass takes up
+ * to 4 GiB of regions for chunk sizes 512 B..128 KiB, and 32768 chunks for
+ * larger chunks. */
+#define CRAC_NOALLOC_MAX_TILES 32768u
+
+/*
+ * The checkpoint pass (fingerprint, dirty test, compaction, gather) over
+ * caller-owned device buffers, for callers that cannot allocate memory:
+ * code running where cudaMalloc is forbidden or unsafe -- inside an
+ * allocator hook or interposed cudaMalloc/cudaFree wrapper (the interposition
+ * point itself, where re-entering the allocator would recurse or deadlock),
+ * in a signal-driven or preemption-time checkpoint that must not change the
+ * device memory map, or in a process whose allocator is out of memory at the
+ * moment it must save its state.  The paper has no counterpart; it is an
+ * addition of this library.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree, pinned memory or library
+ * allocation.  Its only scratch (the pass control block and the look-back
+ * status words, 64 + 16 * CRAC_NOALLOC_MAX_TILES bytes) is a fixed array in
+ * the library's device memory, present on every device that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's address (once per device); make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads, without ordering) race and
+ * give wrong results.  Each call clears the part it uses before the pass.
+ *
+ * Works on the current device.  Inputs: regions_dev (n_regions entries,
+ * device memory), n_chunks (their total chunk count), chunk_bytes (power of
+ * two in [16, 2^24]), fp_old_dev (read where base_first != UINT64_MAX).
+ * Outputs (device memory): fp_new_dev[n_chunks]; idx_dev[idx_cap] ascending
+ * dirty chunk ids; off_dev[idx_cap + 1] their byte offsets in staging (off[k]
+ * = payload bytes); staging_dev[staging_cap]; *totals_dev.  Enqueued on
+ * `stream`; returns without waiting.  The result equals what
+ * crac_ctx_checkpoint computes for the same regions and baseline.
+ * Errors: CRAC_ERR_INVALID_ARG for NULL pointers, a bad chunk size, or a pass
+ * whose tiles exceed CRAC_NOALLOC_MAX_TILES (n_chunks beyond the limit for
+ * this chunk size); CRAC_ERR_CUDA if a launch fails.
+ */
+CRAC_API crac_status_t crac_pass_noalloc(const crac_region_t *regions_dev, uint32_t n_regions,
+                                         uint64_t n_chunks, uint32_t chunk_bytes,
+                                         const uint64_t *fp_old_dev, uint64_t *fp_new_dev,
+                                         uint64_t *idx_dev, uint64_t *off_dev, uint64_t idx_cap,
+                                         uint8_t *staging_dev, uint64_t staging_cap,
+                                         crac_pass_totals_t *totals_dev, crac_stream_t stream);
+
 /* Host-side fault injection for tests: the next `count` times the named step
  * is reached it fails as if the CUDA call there had failed (or, for
  * CRAC_FAULT_DEVICE_WAIT, the batched kernel is launched so that one tile's

@@ -55,8 +55,9 @@ EXPORTED = [
     "crac_ctx_last_pass", "crac_register_alloc", "crac_free", "crac_checkpoint", "crac_restart",
     "crac_image_wait", "crac_image_info", "crac_image_serialize", "crac_image_deserialize",
     "crac_image_release", "crac_status_str", "crac_last_cuda_error", "crac_kernel_launches",
-    "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault",
+    "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault", "crac_pass_noalloc",
 ]
+CRAC_NOALLOC_MAX_TILES = 32768
 
 
 class CracConfig(ctypes.Structure):
@@ -119,6 +120,8 @@ _sigs = {
     "crac_alloc_managed": (_st, [ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "crac_free_managed": (_st, [_vp]),
     "crac_debug_inject_fault": (None, [ctypes.c_int, ctypes.c_int]),
+    "crac_pass_noalloc": (_st, [_vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp, _vp,
+                                ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -278,3 +281,22 @@ def crac_free_managed(ptr: int) -> None:
 
 def crac_debug_inject_fault(step: int, count: int = 1) -> None:
     _lib.crac_debug_inject_fault(step, count)
+
+
+def crac_pass_noalloc(regions_dev, n_regions: int, n_chunks: int, chunk_bytes: int, fp_old_dev,
+                      fp_new_dev, idx_dev, off_dev, idx_cap: int, staging_dev, staging_cap: int,
+                      totals_dev, stream=None) -> None:
+    """The checkpoint pass over caller-owned device buffers, allocating nothing.
+
+    For callers that cannot allocate device memory at the moment they need a
+    checkpoint (inside an interposed cudaMalloc/cudaFree or allocator hook, at
+    preemption time, or when the allocator is exhausted).  regions_dev holds
+    n_regions x {u64 ptr, u64 bytes, u64 first_chunk, u64 base_first}; results
+    go to the output buffers and totals_dev = {u32 0, u32 err, u64 k, u64 bytes}.
+    Calls share one fixed scratch area, so calls that overlap on the GPU race.
+    """
+    _check(_lib.crac_pass_noalloc(_ptr(regions_dev), n_regions, n_chunks, chunk_bytes,
+                                  _ptr(fp_old_dev) if fp_old_dev is not None else None, _ptr(fp_new_dev),
+                                  _ptr(idx_dev), _ptr(off_dev), idx_cap,
+                                  _ptr(staging_dev) if staging_dev is not None else None, staging_cap,
+                                  _ptr(totals_dev), _stream(stream)), "crac_pass_noalloc")

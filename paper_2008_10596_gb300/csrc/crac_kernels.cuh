@@ -107,5 +107,7 @@ cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s);
 
 void count_launches(uint64_t n);
 uint64_t launches_so_far();
+// Record a CUDA error for crac_last_cuda_error() (calling thread).
+void note_cuda_error(int e);
 
 }  // namespace crac

@@ -270,6 +270,8 @@ crac_status_t ensure_host(HostBuf &b, size_t bytes) {
 
 }  // namespace
 
+void crac::note_cuda_error(int e) { t_last_cuda = e; }
+
 // ---------------------------------------------------------------------------
 // Images
 // ---------------------------------------------------------------------------
