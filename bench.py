@@ -87,7 +87,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -223,10 +223,11 @@ def run_crac(args):
         if world > 1:
             dist.barrier()
 
-    wl = W.config2()
+    wl = W.config2(total=args.total_mib << 20)
     S = wl.chunk_bytes
     sizes = wl.sizes
     B = wl.total_bytes
+    workload = WORKLOAD if args.total_mib == 4096 else WORKLOAD.replace("= 4 GiB", f"= {args.total_mib} MiB")
     first = W.chunk_layout(sizes, S)
     n = int(first[-1])
     g = torch.Generator(device=dev)
@@ -253,10 +254,12 @@ def run_crac(args):
             C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel(), C.CRAC_KIND_DEVICE)
         return ctx
 
-    ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
-    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST)
+    ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, reserve_device_bytes=8 * B)
+    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=3 * B)
     ctx_pa = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, launch_mode=C.CRAC_LAUNCH_PER_ALLOC)
     ctx_b = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
+    ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
+    ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
 
     def step(ctx, host=False, pass_ms=None, lat_ms=None):
         mutate()
@@ -268,30 +271,27 @@ def run_crac(args):
             lat_ms.append((time.perf_counter() - t0) * 1e3)
         if pass_ms is not None:
             info = C.crac_ctx_last_pass(ctx)
-            pass_ms.append((info["device_ms"], info["k"], info["payload_bytes"]))
+            pass_ms.append((info["device_ms"], info["k"], info["payload_bytes"], info["hash_ms"],
+                            info["finalize_ms"], info["gather_ms"]))
         C.crac_ctx_restart(ctx, img, stream)
         C.crac_image_release(img)
 
     # Base images (full) for each context.
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma):
         img = C.crac_ctx_checkpoint(ctx, stream)
         C.crac_image_wait(img)
         C.crac_image_release(img)
     torch.cuda.synchronize()
 
     # ---- value: device-resident images --------------------------------------
+    # Clocks are sampled from the start of the warm-up to the end of the timed
+    # steps (the timed region alone is shorter than the sampling period).
+    sampler = ClockSampler(None)
+    sampler.start()
     for _ in range(args.warmup):
         step(ctx_dev)
     torch.cuda.synchronize()
     barrier()
-    bus = None
-    try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id
-        bus = f"{bus:02x}:00" if isinstance(bus, int) else None
-    except Exception:
-        bus = None
-    sampler = ClockSampler(None)
-    sampler.start()
     launches0 = C.crac_kernel_launches()
     pass_ms, lat_ms = [], []
     torch.cuda.synchronize()
@@ -313,56 +313,86 @@ def run_crac(args):
     bytes_per_step = 2 * B
     value = bytes_per_step * args.steps * world / (t_ms / 1e3) / 1e9
 
-    # ---- dominant kernel roofline: the fused checkpoint pass -----------------
+    # ---- roofline: the dominant kernel is the split pass's streaming hash ------
     dev_ms = statistics.mean(p[0] for p in pass_ms)
     k_avg = statistics.mean(p[1] for p in pass_ms)
     d_avg = statistics.mean(p[2] for p in pass_ms)
-    alg = B + d_avg + 16 * n + 16 * k_avg
+    hash_ms = statistics.mean(p[3] for p in pass_ms)
+    fin_ms = statistics.mean(p[4] for p in pass_ms)
+    gat_ms = statistics.mean(p[5] for p in pass_ms)
     peak, peak_src = load_peaks()
-    achieved = alg / (dev_ms / 1e3) / 1e9
+    alg_hash = B + 8 * n                          # every tracked byte read once + one accumulator per chunk
+    achieved = alg_hash / (hash_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profile_traffic("ckpt_fused_c2_64KiB"), "kernel": "ckpt_fused_kernel<256,8>",
-                "alg_bytes_per_launch": int(alg), "avg_launch_ms": dev_ms,
+                "traffic": profile_traffic("split_hash_c2_64KiB"), "kernel": "split_hash_kernel",
+                "alg_bytes_per_launch": int(alg_hash), "avg_launch_ms": hash_ms,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
+    alg_pass = B + d_avg + 16 * n + 16 * k_avg    # read B, write D, fp old + new, idx + off
+    pass_info = {"kernels": "split: hash -> finalize+compact -> gather (one graph)", "device_ms": dev_ms,
+                 "hash_ms": hash_ms, "finalize_ms": fin_ms, "gather_ms": gat_ms,
+                 "alg_bytes": int(alg_pass), "achieved_gbs": alg_pass / (dev_ms / 1e3) / 1e9,
+                 "frac": alg_pass / (dev_ms / 1e3) / 1e9 / peak, "tracked_gbs": B / (dev_ms / 1e3) / 1e9}
 
-    # ---- batched vs per-allocation launches (checkpoint pass only) -----------
-    cmp_pa, cmp_b, wall_pa, wall_b = [], [], [], []
+    # ---- batched vs per-allocation launches, and the pass variants -------------
+    cmp = {"per_alloc": ([], []), "split": ([], []), "ldg": ([], []), "tma": ([], [])}
+    ctxs = {"per_alloc": ctx_pa, "split": ctx_b, "ldg": ctx_ldg, "tma": ctx_tma}
     for _ in range(max(3, min(args.steps, 5))):
         mutate()
-        for ctx, dl, wlst in ((ctx_pa, cmp_pa, wall_pa), (ctx_b, cmp_b, wall_b)):
+        for name, ctx in ctxs.items():
             t0 = time.perf_counter()
             img = C.crac_ctx_checkpoint(ctx, stream)
-            wlst.append((time.perf_counter() - t0) * 1e3)
-            dl.append(C.crac_ctx_last_pass(ctx)["device_ms"])
+            cmp[name][1].append((time.perf_counter() - t0) * 1e3)
+            cmp[name][0].append(C.crac_ctx_last_pass(ctx)["device_ms"])
             C.crac_image_release(img)
-    batched = {"per_alloc_device_ms": statistics.median(cmp_pa), "batched_device_ms": statistics.median(cmp_b),
-               "speedup_device": statistics.median(cmp_pa) / statistics.median(cmp_b),
-               "per_alloc_wall_ms": statistics.median(wall_pa), "batched_wall_ms": statistics.median(wall_b),
-               "speedup_wall": statistics.median(wall_pa) / statistics.median(wall_b),
-               "per_alloc_launches": 3 * len(sizes), "batched_launches": 1}
+    med = {k: (statistics.median(v[0]), statistics.median(v[1])) for k, v in cmp.items()}
+    batched = {"per_alloc_device_ms": med["per_alloc"][0], "batched_device_ms": med["split"][0],
+               "speedup_device": med["per_alloc"][0] / med["split"][0],
+               "per_alloc_wall_ms": med["per_alloc"][1], "batched_wall_ms": med["split"][1],
+               "speedup_wall": med["per_alloc"][1] / med["split"][1],
+               "per_alloc_launches": 3 * len(sizes), "batched_graph_launches": 1,
+               "variants_device_ms": {k: v[0] for k, v in med.items()}}
+
+    # ---- host link probe: pinned 1 GiB copies, best of 10 each way ------------
+    link = None
+    if not args.no_e2e:
+        hbuf = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+        dbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        best = {"h2d": 1e9, "d2h": 1e9}
+        for _ in range(10):
+            for d, (dst, src) in (("h2d", (dbuf, hbuf)), ("d2h", (hbuf, dbuf))):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dst.copy_(src, non_blocking=True)
+                b.record(stream)
+                b.synchronize()
+                best[d] = min(best[d], a.elapsed_time(b))
+        link = {"h2d_gbs": (1 << 30) / (best["h2d"] / 1e3) / 1e9, "d2h_gbs": (1 << 30) / (best["d2h"] / 1e3) / 1e9,
+                "probe": "pinned 1 GiB cudaMemcpyAsync, best of 10"}
+        del hbuf, dbuf
 
     # ---- e2e: host images through the C ABI ----------------------------------
-    e2e_steps = max(1, min(args.steps, 5))
-    for _ in range(1):
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    e2e = None
+    if e2e_steps:
         step(ctx_host, host=True)
-    torch.cuda.synchronize()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_pass = []
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        step(ctx_host, host=True, pass_ms=e_pass)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    te = e0.elapsed_time(e1)
-    k_e = statistics.mean(p[1] for p in e_pass)
-    d_e = statistics.mean(p[2] for p in e_pass)
-    d2h = int(d_e + 8 * k_e + 8 * n + 64)
-    h2d = int(B + d_e + 16 * k_e + 8 * n + 2 * n + 32 * len(sizes))
-    e2e = {"value": bytes_per_step * e2e_steps * world / (te / 1e3) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-           "ms_per_step": te / e2e_steps}
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_pass = []
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            step(ctx_host, host=True, pass_ms=e_pass)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = e0.elapsed_time(e1)
+        k_e = statistics.mean(p[1] for p in e_pass)
+        d_e = statistics.mean(p[2] for p in e_pass)
+        d2h = int(d_e + 8 * k_e + 8 * n + 64)
+        h2d = int(B + d_e + 16 * k_e + 8 * n + 2 * n + 32 * len(sizes))
+        e2e = {"value": bytes_per_step * e2e_steps * world / (te / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "ms_per_step": te / e2e_steps, "link": link}
 
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) -------------------
     cpu = None
@@ -378,19 +408,19 @@ def run_crac(args):
                                    "single thread")
         cpu["nproc"] = os.cpu_count()
 
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma):
         C.crac_ctx_destroy(ctx)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "allocs": len(sizes), "tracked_bytes": B, "chunk_bytes": S,
+                "config": {"workload": workload, "allocs": len(sizes), "tracked_bytes": B, "chunk_bytes": S,
                            "dirty_fraction": wl.dirty_fraction, "n_chunks": n,
                            "l2": "inputs (4 GiB) larger than L2 (126 MB); no flush",
                            "step": "mutate 10% + incremental ckpt + full restart (device-resident images)",
                            "parallelism": f"replicas{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "pass": pass_info, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "batched_vs_per_alloc": batched,
                 "ckpt_latency_ms": {"p50": statistics.median(lat_ms),
                                     "p99": float(np.percentile(lat_ms, 99))},
@@ -408,6 +438,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crac", choices=["crac", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host image) leg")
+    ap.add_argument("--total-mib", type=int, default=4096,
+                    help="tracked bytes of the config-2 workload (default 4096 = the full config)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "crac":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

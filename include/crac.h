@@ -101,6 +101,10 @@ typedef struct crac_image crac_image_t;  /* library-owned, reference counted */
  *                  batched kernel; 0 = automatic.  threads is 256;
  *                  warps_per_chunk is 1 or 8.
  * timeout_ns:      limit on every device-side spin-wait; 0 = 2 s.
+ * reserve_host_bytes, reserve_device_bytes: image memory (pinned host,
+ *                  device) reserved when the context first touches the GPU,
+ *                  so that steady-state checkpoints allocate nothing from
+ *                  CUDA.  The arenas are process-wide and only grow.
  */
 typedef struct crac_config {
     uint32_t struct_size;
@@ -115,8 +119,21 @@ typedef struct crac_config {
     uint32_t warps_per_chunk;
     uint64_t timeout_ns;
     int32_t device;          /* CUDA device ordinal; -1 = current device */
-    uint32_t reserved[7];
+    uint32_t pad0;
+    uint64_t reserve_host_bytes;    /* pinned image memory to reserve up front */
+    uint64_t reserve_device_bytes;  /* device image memory to reserve up front */
+    uint32_t pass_kernel;           /* CRAC_PASS_AUTO / _LDG / _TMA */
+    uint32_t reserved[1];
 } crac_config_t;
+
+/* Kernel of the batched pass (crac_config_t.pass_kernel). */
+#define CRAC_PASS_AUTO  0  /* the split pass */
+#define CRAC_PASS_LDG   1  /* one fused persistent kernel, 128-bit loads to registers;
+                              the gather re-reads dirty chunks from L2 */
+#define CRAC_PASS_TMA   2  /* one fused kernel, bulk copies into a shared-memory ring,
+                              warp-specialized; chunk sizes 1 KiB..64 KiB only */
+#define CRAC_PASS_SPLIT 3  /* three kernels in one graph: streaming hash, finalize +
+                              compaction, gather */
 
 /* Summary of an image (crac_image_info). */
 typedef struct crac_image_info {
@@ -148,7 +165,11 @@ typedef struct crac_pass_info {
     uint32_t grid;           /* CTAs of the batched kernel */
     uint32_t chunks_per_tile;
     uint32_t warps_per_chunk;
-    uint32_t reserved[5];
+    float hash_ms;           /* split pass: device time of each of its kernels */
+    float finalize_ms;
+    float gather_ms;
+    uint32_t pass_kernel;    /* CRAC_PASS_* that ran */
+    uint32_t reserved[1];
 } crac_pass_info_t;
 
 /* ---- configuration and contexts --------------------------------------- */

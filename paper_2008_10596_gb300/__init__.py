@@ -41,6 +41,10 @@ CRAC_RESIDENCY_DEVICE = 1
 CRAC_LAUNCH_BATCHED = 0
 CRAC_LAUNCH_PER_ALLOC = 1
 CRAC_IMAGE_FULL = 1
+CRAC_PASS_AUTO = 0
+CRAC_PASS_LDG = 1
+CRAC_PASS_TMA = 2
+CRAC_PASS_SPLIT = 3
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1
@@ -67,8 +71,9 @@ class CracConfig(ctypes.Structure):
         ("image_residency", ctypes.c_uint32), ("launch_mode", ctypes.c_uint32),
         ("threads", ctypes.c_uint32), ("chunks_per_tile", ctypes.c_uint32),
         ("ctas_per_sm", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
-        ("timeout_ns", ctypes.c_uint64), ("device", ctypes.c_int32),
-        ("reserved", ctypes.c_uint32 * 7),
+        ("timeout_ns", ctypes.c_uint64), ("device", ctypes.c_int32), ("pad0", ctypes.c_uint32),
+        ("reserve_host_bytes", ctypes.c_uint64), ("reserve_device_bytes", ctypes.c_uint64),
+        ("pass_kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
     ]
 
 
@@ -89,7 +94,8 @@ class CracPassInfo(ctypes.Structure):
         ("kernel_launches", ctypes.c_uint32), ("device_ms", ctypes.c_float),
         ("prefetch_ms", ctypes.c_float), ("grid", ctypes.c_uint32),
         ("chunks_per_tile", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 5),
+        ("hash_ms", ctypes.c_float), ("finalize_ms", ctypes.c_float), ("gather_ms", ctypes.c_float),
+        ("pass_kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
     ]
 
 

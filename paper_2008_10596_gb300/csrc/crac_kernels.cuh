@@ -91,6 +91,28 @@ cudaError_t launch_ckpt_fused(const CkptParams &p, int threads, int warps_per_ch
 const void *ckpt_fused_fn(int threads, int warps_per_chunk);
 int ckpt_fused_max_ctas_per_sm(int threads, int warps_per_chunk);
 
+// TMA-staged variant of the fused pass (chunk sizes 1-64 KiB): one CTA per
+// SM, ckpt_tma_threads() threads, ckpt_tma_smem() bytes of dynamic shared
+// memory, a tile of ckpt_tma_slot_bytes() / chunk_bytes chunks, and
+// warps_per_chunk = max(1, 8 * chunk_bytes / slot_bytes).
+const void *ckpt_tma_fn(int warps_per_chunk);
+int ckpt_tma_threads();
+size_t ckpt_tma_smem();
+uint32_t ckpt_tma_slot_bytes();
+cudaError_t ckpt_tma_prepare();   // raise the dynamic shared memory limit (once per device)
+
+// Split pass: three kernels with the signature (CkptParams, u64 *acc, u32 log2Seg),
+// run in order H -> F -> G.  acc holds one u64 per chunk of the segment and
+// must be zero before H; F uses cpt = split_finalize_threads() chunks per
+// tile and the look-back status words; G reads k from ctrl.
+const void *split_hash_fn();
+const void *split_finalize_fn();
+const void *split_gather_fn();
+int split_hash_threads();
+int split_finalize_threads();
+int split_gather_threads();
+int split_max_ctas_per_sm(const void *fn, int threads);
+
 cudaError_t launch_fp_range(const CkptDesc *d, uint64_t c0, uint64_t c1, uint32_t log2_chunk,
                             const uint64_t *fp_old, uint64_t *fp_new, uint32_t *lens,
                             uint64_t lens_base, int grid, cudaStream_t s);

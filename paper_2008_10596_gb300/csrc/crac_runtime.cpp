@@ -137,6 +137,14 @@ struct Block {
 class Arena {
   public:
     Arena(bool device, int dev, uint64_t quantum) : device_(device), dev_(dev), quantum_(quantum) {}
+    // Make sure at least `bytes` are free in one region (grows the arena once,
+    // so that later image allocations need no cudaMalloc / cudaHostAlloc).
+    crac_status_t reserve(uint64_t bytes) {
+        Block b;
+        crac_status_t st = alloc(bytes, &b);
+        if (st == CRAC_OK) free(b);
+        return st;
+    }
     crac_status_t alloc(uint64_t len, Block *b) {
         if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
         len = round_up(std::max<uint64_t>(len, 1), 256);
@@ -455,6 +463,13 @@ struct crac_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphNode_t g_memset = nullptr, g_kernel = nullptr, g_copy = nullptr;
     int g_threads = 0, g_wpc = 0;
+    const void *g_fn = nullptr;
+    bool tma_ready = false;
+    // graph for the split pass: memset -> hash -> finalize -> gather -> ctrl D2H
+    cudaGraph_t sgraph = nullptr;
+    cudaGraphExec_t sgexec = nullptr;
+    cudaGraphNode_t s_memset = nullptr, s_k[3] = {nullptr, nullptr, nullptr}, s_copy = nullptr;
+    cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};   // around each split-pass kernel
     crac_pass_info_t last{};
     bool cuda_ready = false;
 };
@@ -478,6 +493,9 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
     if (cfg.warps_per_chunk && cfg.warps_per_chunk != 1 && cfg.warps_per_chunk != 8)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel > CRAC_PASS_SPLIT) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
+        return CRAC_ERR_INVALID_ARG;
     if (cfg.timeout_ns == 0) cfg.timeout_ns = kDefaultTimeoutNs;
     c->log2S = log2u(cfg.chunk_bytes);
     c->lineage = cfg.lineage ? cfg.lineage : (g_lineage_counter.fetch_add(1) + 1);
@@ -500,8 +518,11 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     CK(cudaEventCreate(&c->ev_t1));
     CK(cudaEventCreate(&c->ev_p0));
     CK(cudaEventCreate(&c->ev_p1));
+    for (cudaEvent_t &e : c->sev) CK(cudaEventCreate(&e));
     TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
     TRY(ensure_host(c->serr_h, 256));
+    if (c->cfg.reserve_host_bytes) TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
+    if (c->cfg.reserve_device_bytes) TRY(device_arena(dev).reserve(c->cfg.reserve_device_bytes));
     c->cuda_ready = true;
     return CRAC_OK;
 }
@@ -521,7 +542,10 @@ void ctx_free_all(crac_ctx *c) {
         if (b->p) cudaFreeHost(b->p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
-    for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1})
+    if (c->sgexec) cudaGraphExecDestroy(c->sgexec);
+    if (c->sgraph) cudaGraphDestroy(c->sgraph);
+    for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1, c->sev[0], c->sev[1],
+                          c->sev[2], c->sev[3]})
         if (e) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
     cudaGetLastError();
@@ -585,17 +609,16 @@ std::vector<Segment> make_segments(const std::vector<AllocRec> &allocs, const st
 }
 
 // Build (or update) the graph memset -> fused kernel -> ctrl D2H and launch it.
-crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, int wpc,
-                                 int grid, cudaStream_t s) {
-    const void *fn = ckpt_fused_fn(256, wpc);
+crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, const void *fn,
+                                 int threads, size_t smem, int grid, cudaStream_t s) {
     if (!fn) return CRAC_ERR_INVALID_ARG;
     CkptParams Pc = P;
     void *args[] = {&Pc};
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void *>(fn);
     kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(256);
-    kp.sharedMemBytes = 0;
+    kp.blockDim = dim3(threads);
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     cudaMemsetParams mp{};
     mp.dst = c->work.p;
@@ -605,17 +628,17 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     mp.height = 1;
     mp.pitch = 0;
     bool rebuilt = false;
-    if (c->gexec && c->g_wpc == wpc) {
+    if (c->gexec && c->g_fn == fn) {
         // Width changes of a memset node may be rejected; rebuild then.
         if (cudaGraphExecMemsetNodeSetParams(c->gexec, c->g_memset, &mp) != cudaSuccess ||
             cudaGraphExecKernelNodeSetParams(c->gexec, c->g_kernel, &kp) != cudaSuccess ||
             cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
                                                cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
-            c->g_wpc = 0;
+            c->g_fn = nullptr;
         }
     }
-    if (!c->gexec || c->g_wpc != wpc) {
+    if (!c->gexec || c->g_fn != fn) {
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         if (c->graph) cudaGraphDestroy(c->graph);
         c->gexec = nullptr;
@@ -626,13 +649,74 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, c->ctrl_h.p, P.ctrl,
                                     sizeof(CkptCtrl), cudaMemcpyDeviceToHost));
         CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
-        c->g_wpc = wpc;
-        c->g_threads = 256;
+        c->g_fn = fn;
+        c->g_threads = threads;
         rebuilt = true;
     }
     (void)rebuilt;
+    CK(cudaEventRecord(c->ev_t0, s));   // after the host-side updates: times the device work only
     CK(cudaGraphLaunch(c->gexec, s));
     count_launches(1);
+    return CRAC_OK;
+}
+
+// Build (or update) the split-pass graph and launch it.
+crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
+                                 uint32_t log2Seg, const int grids[3], cudaStream_t s) {
+    const void *fns[3] = {split_hash_fn(), split_finalize_fn(), split_gather_fn()};
+    const int thr[3] = {split_hash_threads(), split_finalize_threads(), split_gather_threads()};
+    CkptParams Pc = P;
+    unsigned long long *accv = acc;
+    uint32_t segv = log2Seg;
+    void *args[] = {&Pc, &accv, &segv};
+    cudaKernelNodeParams kp[3];
+    for (int i = 0; i < 3; ++i) {
+        kp[i] = cudaKernelNodeParams{};
+        kp[i].func = const_cast<void *>(fns[i]);
+        kp[i].gridDim = dim3(grids[i]);
+        kp[i].blockDim = dim3(thr[i]);
+        kp[i].sharedMemBytes = 0;
+        kp[i].kernelParams = args;
+    }
+    cudaMemsetParams mp{};
+    mp.dst = c->work.p;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = work_bytes / 4;
+    mp.height = 1;
+    bool ok = c->sgexec != nullptr;
+    if (ok) {
+        ok = cudaGraphExecMemsetNodeSetParams(c->sgexec, c->s_memset, &mp) == cudaSuccess;
+        for (int i = 0; ok && i < 3; ++i)
+            ok = cudaGraphExecKernelNodeSetParams(c->sgexec, c->s_k[i], &kp[i]) == cudaSuccess;
+        if (ok)
+            ok = cudaGraphExecMemcpyNodeSetParams1D(c->sgexec, c->s_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    if (!ok) {
+        if (c->sgexec) cudaGraphExecDestroy(c->sgexec);
+        if (c->sgraph) cudaGraphDestroy(c->sgraph);
+        c->sgexec = nullptr;
+        c->sgraph = nullptr;
+        CK(cudaGraphCreate(&c->sgraph, 0));
+        CK(cudaGraphAddMemsetNode(&c->s_memset, c->sgraph, nullptr, 0, &mp));
+        cudaGraphNode_t prev = c->s_memset;
+        cudaGraphNode_t ev;
+        CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &prev, 1, c->sev[0]));
+        prev = ev;
+        for (int i = 0; i < 3; ++i) {
+            CK(cudaGraphAddKernelNode(&c->s_k[i], c->sgraph, &prev, 1, &kp[i]));
+            CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
+            prev = ev;
+        }
+        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                    cudaMemcpyDeviceToHost));
+        CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
+    }
+    CK(cudaEventRecord(c->ev_t0, s));
+    CK(cudaGraphLaunch(c->sgexec, s));
+    count_launches(3);
     return CRAC_OK;
 }
 
@@ -649,17 +733,80 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         t_last_cuda = (int)cudaErrorLaunchFailure;
         return CRAC_ERR_CUDA;
     }
-    CK(cudaEventRecord(c->ev_t0, s));
-    if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
+    const bool split = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
+                       (c->cfg.pass_kernel == CRAC_PASS_SPLIT || c->cfg.pass_kernel == CRAC_PASS_AUTO);
+    if (split) {
+        const uint32_t cptF = (uint32_t)split_finalize_threads();
+        const uint64_t n_tiles = (nseg + cptF - 1) / cptF;
+        if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+        const size_t status_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
+        const size_t work_bytes = status_bytes + 8 * nseg;
+        TRY(ensure_dev(c->work, work_bytes));
+        const uint32_t log2Seg = std::min<uint32_t>(c->log2S, 13);
+        CkptParams P{};
+        P.desc = desc_dev;
+        P.n_allocs = (uint32_t)c->allocs.size();
+        P.log2_chunk = c->log2S;
+        P.c_begin = sg.c0;
+        P.c_end = sg.c1;
+        P.cpt = cptF;
+        P.n_tiles = (uint32_t)n_tiles;
+        P.fp_old = fp_old;
+        P.fp_new = fp_new;
+        P.idx_out = idx_d;
+        P.off_out = off_d;
+        P.idx_cap = idx_cap;
+        P.staging = staging;
+        P.staging_cap = staging_cap;
+        P.ctrl = (CkptCtrl *)c->work.p;
+        P.tile_cnt = (uint64_t *)((uint8_t *)c->work.p + sizeof(CkptCtrl));
+        P.tile_bytes = P.tile_cnt + n_tiles;
+        P.timeout_ns = c->cfg.timeout_ns;
+        P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        unsigned long long *acc = (unsigned long long *)((uint8_t *)c->work.p + status_bytes);
+        const uint64_t n_slots = nseg << (c->log2S - log2Seg);
+        const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>(
+                           (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(split_hash_fn(), split_hash_threads())));
+        const int gf = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2);
+        const int gg = c->sm_count * 8;
+        const int grids[3] = {gh, gf, gg};
+        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, grids, s));
+        c->last.grid = (uint32_t)gh;
+        c->last.chunks_per_tile = cptF;
+        c->last.warps_per_chunk = 0;
+        c->last.kernel_launches += 3;
+        c->last.pass_kernel = CRAC_PASS_SPLIT;
+    } else if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
+        const uint64_t S = 1ull << c->log2S;
+        const bool tma = c->cfg.pass_kernel == CRAC_PASS_TMA;
         int wpc;
         uint32_t cpt;
-        pick_split(c, &wpc, &cpt);
+        const void *fn;
+        int threads;
+        size_t smem = 0;
+        int per_sm;
+        if (tma) {
+            if (!c->tma_ready) {
+                CK(ckpt_tma_prepare());
+                c->tma_ready = true;
+            }
+            cpt = (uint32_t)(ckpt_tma_slot_bytes() / S);
+            wpc = (int)std::max<uint64_t>(1, 8 * S / ckpt_tma_slot_bytes());
+            fn = ckpt_tma_fn(wpc);
+            threads = ckpt_tma_threads();
+            smem = ckpt_tma_smem();
+            per_sm = 1;
+        } else {
+            pick_split(c, &wpc, &cpt);
+            fn = ckpt_fused_fn(256, wpc);
+            threads = 256;
+            per_sm = (int)c->cfg.ctas_per_sm;
+            if (!per_sm) per_sm = std::max(1, ckpt_fused_max_ctas_per_sm(256, wpc));
+        }
         const uint64_t n_tiles = (nseg + cpt - 1) / cpt;
         if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
         const size_t work_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
         TRY(ensure_dev(c->work, work_bytes));
-        int per_sm = (int)c->cfg.ctas_per_sm;
-        if (!per_sm) per_sm = std::max(1, ckpt_fused_max_ctas_per_sm(256, wpc));
         const int grid = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * per_sm);
         CkptParams P{};
         P.desc = desc_dev;
@@ -681,7 +828,8 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.tile_bytes = P.tile_cnt + n_tiles;
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (inject_wait && n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
-        TRY(launch_fused_graph(c, P, work_bytes, wpc, grid, s));
+        TRY(launch_fused_graph(c, P, work_bytes, fn, threads, smem, grid, s));
+        c->last.pass_kernel = tma ? CRAC_PASS_TMA : CRAC_PASS_LDG;
         c->last.grid = (uint32_t)grid;
         c->last.chunks_per_tile = cpt;
         c->last.warps_per_chunk = (uint32_t)wpc;
@@ -691,6 +839,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         TRY(ensure_dev(c->lens, nseg * sizeof(uint32_t)));
         TRY(ensure_dev(c->carry, sizeof(PerAllocCarry)));
         CkptCtrl *ctrl = (CkptCtrl *)c->work.p;
+        CK(cudaEventRecord(c->ev_t0, s));
         CK(cudaMemsetAsync(ctrl, 0, sizeof(CkptCtrl), s));
         CK(cudaMemsetAsync(c->carry.p, 0, sizeof(PerAllocCarry), s));
         const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
@@ -714,6 +863,17 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
     float t = 0;
     CK(cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1));
     *ms += t;
+    if (split) {
+        float a = 0, b = 0, d = 0;
+        if (cudaEventElapsedTime(&a, c->sev[0], c->sev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, c->sev[1], c->sev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&d, c->sev[2], c->sev[3]) == cudaSuccess) {
+            c->last.hash_ms += a;
+            c->last.finalize_ms += b;
+            c->last.gather_ms += d;
+        }
+        cudaGetLastError();
+    }
     *ctrl_out = *(const CkptCtrl *)c->ctrl_h.p;
     if (ctrl_out->err & kErrTimeout) return CRAC_ERR_TIMEOUT;
     if (ctrl_out->err) return CRAC_ERR_CORRUPT;

@@ -17,13 +17,14 @@ from tests.gpu_harness import Harness, pattern_mutations
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 
 
+@pytest.mark.parametrize("kern", [C.CRAC_PASS_TMA, C.CRAC_PASS_LDG])
 @pytest.mark.parametrize("step,code", [(C.CRAC_FAULT_PASS, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_DRAIN, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_ALLOC, C.CRAC_ERR_OOM),
                                        (C.CRAC_FAULT_DEVICE_WAIT, C.CRAC_ERR_TIMEOUT)])
-def test_failed_checkpoint_leaves_state(step, code):
+def test_failed_checkpoint_leaves_state(step, code, kern):
     S = 4096
-    h = Harness(S, lineage=61, timeout_ns=20_000_000, chunks_per_tile=2)
+    h = Harness(S, lineage=61, timeout_ns=20_000_000, chunks_per_tile=2, pass_kernel=kern)
     try:
         for i, n in enumerate([200000, 70000]):
             h.add(n, seed=i + 1)

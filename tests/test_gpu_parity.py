@@ -58,11 +58,13 @@ def test_config1_full_restore_incremental():
 SIZES = [1, 7, 8, 4095, 4096, 4097]
 
 
-@pytest.mark.parametrize("S", [64, 4 * KIB, 64 * KIB, 256 * KIB])
+@pytest.mark.parametrize("S,kern", [(64, C.CRAC_PASS_AUTO), (4 * KIB, C.CRAC_PASS_TMA),
+                                    (4 * KIB, C.CRAC_PASS_LDG), (64 * KIB, C.CRAC_PASS_TMA),
+                                    (64 * KIB, C.CRAC_PASS_LDG), (256 * KIB, C.CRAC_PASS_AUTO)])
 @pytest.mark.parametrize("pattern", ["none", "all", "first", "last", "tail", "alternating", "random10"])
-def test_sweep_sizes_patterns(S, pattern):
+def test_sweep_sizes_patterns(S, kern, pattern):
     sizes = SIZES + [3 * S + 5, 2 * S]
-    h = Harness(S, lineage=200 + S % 97)
+    h = Harness(S, lineage=200 + S % 97, pass_kernel=kern)
     try:
         for i, n in enumerate(sizes):
             h.add(n, seed=10 + i)
@@ -89,7 +91,7 @@ def test_work_split_variants_identical(cpt, wpc):
     """Tile size and warps-per-chunk change only the schedule, never the bytes."""
     S = 4 * KIB
     sizes = [123457, 4096 * 37 + 1, 64 * KIB, 5, 300000]
-    h = Harness(S, lineage=7, chunks_per_tile=cpt, warps_per_chunk=wpc)
+    h = Harness(S, lineage=7, chunks_per_tile=cpt, warps_per_chunk=wpc, pass_kernel=C.CRAC_PASS_LDG)
     try:
         for i, n in enumerate(sizes):
             h.add(n, seed=30 + i)
@@ -98,6 +100,32 @@ def test_work_split_variants_identical(cpt, wpc):
         h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=9))
         _, lib2, ora2 = h.checkpoint()
         assert lib2 == ora2
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("S", [1 * KIB, 2 * KIB, 8 * KIB, 16 * KIB, 32 * KIB, 64 * KIB])
+def test_tma_chunk_sizes_ragged(S):
+    """The TMA pass at every chunk size it takes (1..64 chunks per 64 KiB tile,
+    1..8 warps per chunk), with ragged allocation ends that shift later
+    chunks off 16-byte alignment in the staging buffer."""
+    sizes = [S * 37 + 3, 5, S * 64, 4097, S * 3 + 16, 777777, S + 9]
+    h = Harness(S, lineage=300 + S // KIB, pass_kernel=C.CRAC_PASS_TMA)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=90 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        for seed in (1, 2):
+            h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=seed))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
     finally:
         h.close()
 
