@@ -261,7 +261,7 @@ def run_crac(args):
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
     ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
 
-    def step(ctx, host=False, pass_ms=None, lat_ms=None):
+    def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None):
         mutate()
         t0 = time.perf_counter()
         img = C.crac_ctx_checkpoint(ctx, stream)
@@ -274,6 +274,8 @@ def run_crac(args):
             pass_ms.append((info["device_ms"], info["k"], info["payload_bytes"], info["hash_ms"],
                             info["finalize_ms"], info["gather_ms"]))
         C.crac_ctx_restart(ctx, img, stream)
+        if rst is not None:
+            rst.append(C.crac_ctx_last_restart(ctx))
         C.crac_image_release(img)
 
     # Base images (full) for each context.
@@ -284,8 +286,9 @@ def run_crac(args):
     torch.cuda.synchronize()
 
     # ---- value: device-resident images --------------------------------------
-    # Clocks are sampled from the start of the warm-up to the end of the timed
-    # steps (the timed region alone is shorter than the sampling period).
+    # Clocks are sampled every 50 ms from the first warm-up step to the end of
+    # the last GPU leg (the device-resident timed loop alone is shorter than
+    # one sampling period).
     sampler = ClockSampler(None)
     sampler.start()
     for _ in range(args.warmup):
@@ -293,17 +296,16 @@ def run_crac(args):
     torch.cuda.synchronize()
     barrier()
     launches0 = C.crac_kernel_launches()
-    pass_ms, lat_ms = [], []
+    pass_ms, lat_ms, rst = [], [], []
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(ctx_dev, pass_ms=pass_ms, lat_ms=lat_ms)
+        step(ctx_dev, pass_ms=pass_ms, lat_ms=lat_ms, rst=rst)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
     t_ms = ev0.elapsed_time(ev1)
     if world > 1:
         tt = torch.tensor([t_ms], device=dev)
@@ -321,12 +323,25 @@ def run_crac(args):
     fin_ms = statistics.mean(p[4] for p in pass_ms)
     gat_ms = statistics.mean(p[5] for p in pass_ms)
     peak, peak_src = load_peaks()
+    psrc = f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"
+    # The step's dominant kernel is the restore scatter (every tracked byte read
+    # from the image payloads and written back, plus 8 B idx + 8 B off + 2 B
+    # owner per visited entry); its launches are timed by the library with
+    # CUDA events on the launching stream.
+    sc_ms = statistics.mean(r["device_ms"] for r in rst)
+    sc_entries = statistics.mean(r["entries_scanned"] for r in rst)
+    sc_bytes = statistics.mean(r["restored_bytes"] for r in rst)
+    alg_sc = 2 * sc_bytes + 18 * sc_entries
+    roofline = {"bound": "hbm", "achieved": alg_sc / (sc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg_sc / (sc_ms / 1e3) / 1e9 / peak, "traffic": profile_traffic("scatter_c2_64KiB"),
+                "kernel": "scatter_kernel (restore, all launches of a restart)",
+                "alg_bytes_per_launch": int(alg_sc), "avg_launch_ms": sc_ms,
+                "launches_per_restart": statistics.mean(r["scatter_launches"] for r in rst), "peak_source": psrc}
     alg_hash = B + 8 * n                          # every tracked byte read once + one accumulator per chunk
-    achieved = alg_hash / (hash_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profile_traffic("split_hash_c2_64KiB"), "kernel": "split_hash_kernel",
-                "alg_bytes_per_launch": int(alg_hash), "avg_launch_ms": hash_ms,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
+    roofline_hash = {"bound": "hbm", "achieved": alg_hash / (hash_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg_hash / (hash_ms / 1e3) / 1e9 / peak,
+                     "traffic": profile_traffic("split_hash_c2_64KiB"), "kernel": "split_hash_kernel",
+                     "alg_bytes_per_launch": int(alg_hash), "avg_launch_ms": hash_ms, "peak_source": psrc}
     alg_pass = B + d_avg + 16 * n + 16 * k_avg    # read B, write D, fp old + new, idx + off
     pass_info = {"kernels": "split: hash -> finalize+compact -> gather (one graph)", "device_ms": dev_ms,
                  "hash_ms": hash_ms, "finalize_ms": fin_ms, "gather_ms": gat_ms,
@@ -394,6 +409,9 @@ def run_crac(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "ms_per_step": te / e2e_steps, "link": link}
 
+    clocks = sampler.stop()
+    clocks["window"] = "warm-up through the end of the e2e leg"
+
     # ---- CPU oracle on a bounded sample (rank 0, N=1 only) -------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -420,7 +438,7 @@ def run_crac(args):
                            "l2": "inputs (4 GiB) larger than L2 (126 MB); no flush",
                            "step": "mutate 10% + incremental ckpt + full restart (device-resident images)",
                            "parallelism": f"replicas{world}"},
-                "roofline": roofline, "pass": pass_info, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "roofline_ckpt_hash": roofline_hash, "pass": pass_info, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "batched_vs_per_alloc": batched,
                 "ckpt_latency_ms": {"p50": statistics.median(lat_ms),
                                     "p99": float(np.percentile(lat_ms, 99))},
@@ -429,6 +447,356 @@ def run_crac(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# Config 3: device + managed memory, 4-stream mutator, 3 checkpoints + restart
+# ---------------------------------------------------------------------------
+
+def _rewrite_entries(torch, dev, rows):
+    arr = np.asarray(rows, dtype=np.uint64).reshape(-1, 3)
+    return torch.from_numpy(arr.view(np.int64)).to(dev)
+
+
+def run_config3(args):
+    import torch
+    import paper_2008_10596_gb300 as C
+    from paper_2008_10596_gb300 import testkit
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    scale = args.total_mib / 4096.0 if args.total_mib != 4096 else 1.0
+    wl = W.config3(device_total=int(12 * W.GIB * scale) // (64 * W.KIB) * (64 * W.KIB),
+                   managed_total=int(4 * W.GIB * scale) // (64 * W.KIB) * (64 * W.KIB))
+    S = wl.chunk_bytes
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.seed)
+    pool = torch.randn(64 << 20, generator=g, device=dev, dtype=torch.float32).to(torch.bfloat16)  # 128 MiB
+    pool_u8 = pool.view(torch.uint8)
+    bufs, kinds, managed = [], [], []
+    for n in wl.sizes:
+        bufs.append((torch.empty(n, dtype=torch.uint8, device=dev), n))
+        kinds.append(C.CRAC_KIND_DEVICE)
+    for n in wl.managed_sizes:
+        p = C.crac_alloc_managed(n)
+        managed.append(p)
+        bufs.append((p, n))
+        kinds.append(C.CRAC_KIND_MANAGED)
+    ptrs = [b.data_ptr() if hasattr(b, "data_ptr") else b for b, _ in bufs]
+    sizes = [n for _, n in bufs]
+    rng = np.random.default_rng(wl.seed)
+    # initial contents: bf16 N(0,1) copied from the pool at random offsets
+    rows = []
+    for ptr, n in zip(ptrs, sizes):
+        for o in range(0, n, 64 << 20):
+            ln = min(64 << 20, n - o)
+            src = pool_u8.data_ptr() + int(rng.integers(0, (pool_u8.numel() - ln) // 16 + 1)) * 16
+            rows.append((ptr + o, src, ln))
+    e = _rewrite_entries(torch, dev, rows)
+    testkit.rewrite(e.data_ptr(), len(rows), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pages = [(a, o) for a, n in enumerate(sizes) for o in range(0, n, S)]
+    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    main = torch.cuda.current_stream(dev)
+
+    def mutate(seed):
+        r = np.random.default_rng(seed)
+        pick = r.choice(len(pages), size=len(pages) // 4, replace=False)
+        rows = []
+        for i in pick:
+            a, o = pages[i]
+            ln = min(S, sizes[a] - o)
+            src = pool_u8.data_ptr() + int(r.integers(0, (pool_u8.numel() - ln) // 16 + 1)) * 16
+            rows.append((ptrs[a] + o, src, ln))
+        parts = np.array_split(np.asarray(rows, dtype=np.uint64), 4)
+        ents = [torch.from_numpy(pp.view(np.int64)).to(dev) for pp in parts]
+        torch.cuda.synchronize()
+        for st, en, pp in zip(streams, ents, parts):
+            testkit.rewrite(en.data_ptr(), len(pp), st)
+        for st in streams:           # the checkpoint is stream-synced: join the mutator streams
+            main.wait_stream(st)
+        return len(rows)
+
+    ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3, device=0,
+                                                  reserve_host_bytes=int(1.6 * sum(sizes))))
+    for ptr, n, k in zip(ptrs, sizes, kinds):
+        C.crac_ctx_register_alloc(ctx, ptr, n, k)
+    B = sum(sizes)
+    ckpts = []
+    imgs = []
+    for i in range(3):
+        if i:
+            mutate(wl.seed + i)
+        t0 = time.perf_counter()
+        img = C.crac_ctx_checkpoint(ctx, main)
+        t1 = time.perf_counter()
+        C.crac_image_wait(img)
+        t2 = time.perf_counter()
+        info = C.crac_ctx_last_pass(ctx)
+        ii = C.crac_image_info(img)
+        imgs.append(img)
+        ckpts.append({"epoch": ii["epoch"], "full": bool(ii["flags"] & 1), "dirty_bytes": ii["payload_bytes"],
+                      "pass_ms": info["device_ms"], "prefetch_ms": info["prefetch_ms"],
+                      "pass_tracked_gbs": B / (info["device_ms"] / 1e3) / 1e9,
+                      "call_ms": (t1 - t0) * 1e3, "drain_ms": (t2 - t1) * 1e3,
+                      "drain_gbs": ii["payload_bytes"] / max(t2 - t1, 1e-9) / 1e9})
+    # restart from the third image into zeroed memory, compare with a copy
+    keep = [torch.empty(n, dtype=torch.uint8, device=dev) for n in sizes]
+    rows = [(k.data_ptr(), p, n) for k, p, n in zip(keep, ptrs, sizes)]
+    e = _rewrite_entries(torch, dev, rows)
+    testkit.rewrite(e.data_ptr(), len(rows), main)
+    zero = torch.zeros(64 << 20, dtype=torch.uint8, device=dev)
+    rows = [(p + o, zero.data_ptr(), min(64 << 20, n - o)) for p, n in zip(ptrs, sizes) for o in range(0, n, 64 << 20)]
+    e = _rewrite_entries(torch, dev, rows)
+    testkit.rewrite(e.data_ptr(), len(rows), main)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C.crac_ctx_restart(ctx, imgs[-1], main)
+    torch.cuda.synchronize()
+    t_restart = time.perf_counter() - t0
+    back = [torch.empty(n, dtype=torch.uint8, device=dev) for n in sizes]
+    rows = [(b.data_ptr(), p, n) for b, p, n in zip(back, ptrs, sizes)]
+    e = _rewrite_entries(torch, dev, rows)
+    testkit.rewrite(e.data_ptr(), len(rows), main)
+    torch.cuda.synchronize()
+    exact = all(torch.equal(a, b) for a, b in zip(keep, back))
+    for img in imgs:
+        C.crac_image_release(img)
+    C.crac_ctx_destroy(ctx)
+    for p in managed:
+        C.crac_free_managed(p)
+    line = {"workload": f"c3: {len(wl.sizes)} device ({sum(wl.sizes) / 2**30:.1f} GiB) + {len(wl.managed_sizes)} "
+                        f"managed ({sum(wl.managed_sizes) / 2**30:.1f} GiB) allocations, 64 KiB chunks, 25% of pages "
+                        "rewritten (bf16) on 4 streams between checkpoints",
+            "tracked_bytes": B, "checkpoints": ckpts, "restart_ms": t_restart * 1e3,
+            "restart_gbs": B / t_restart / 1e9, "restart_chain": 3, "restored_exact": exact,
+            "note": "host-resident images; restart copies the chain's surviving chunks host->device"}
+    print(json.dumps(line), flush=True)
+    return 0 if exact else 1
+
+
+# ---------------------------------------------------------------------------
+# Config 4: 120 GiB / 2048 allocations, dirty sweep, autotuned chunk size
+# ---------------------------------------------------------------------------
+
+def run_config4(args):
+    import torch
+    import paper_2008_10596_gb300 as C
+    from paper_2008_10596_gb300 import testkit
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    total = (args.total_mib << 20) if args.total_mib != 4096 else 120 * W.GIB
+    wl = W.config4(total=total)
+    sizes = wl.sizes
+    B = sum(sizes)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.seed)
+    bufs = []
+    for i, n in enumerate(sizes):     # uint8 / fp32 N(0,1) / int64 uniform, cycling
+        if i % 3 == 0:
+            t = torch.randint(0, 256, (n,), generator=g, device=dev, dtype=torch.uint8)
+        elif i % 3 == 1:
+            t = torch.randn(n // 4, generator=g, device=dev, dtype=torch.float32).view(torch.uint8)
+        else:
+            t = torch.randint(-(1 << 62), 1 << 62, (n // 8,), generator=g, device=dev, dtype=torch.int64).view(torch.uint8)
+        bufs.append(t)
+    page_counts = torch.tensor([n // 4096 for n in sizes], device=dev, dtype=torch.int64)
+    page_first = torch.cumsum(page_counts, 0) - page_counts
+    bases = torch.tensor([b.data_ptr() for b in bufs], device=dev, dtype=torch.int64)
+    n_pages = int(page_counts.sum().item())
+    peak, _ = load_peaks()
+
+    def mutate(frac, seed):
+        k = int(round(frac * n_pages))
+        if k == 0:
+            return 0
+        gg = torch.Generator(device=dev)
+        gg.manual_seed(seed)
+        pid = torch.randperm(n_pages, generator=gg, device=dev)[:k]
+        a = torch.searchsorted(page_first, pid, right=True) - 1
+        ptr = bases[a] + (pid - page_first[a]) * 4096
+        mask = (torch.randint(0, 1 << 31, (k,), generator=gg, device=dev, dtype=torch.int64) * 2 + 1) & 0xFFFFFFFF
+        ent = torch.stack([ptr, torch.full_like(ptr, 4096), mask], dim=1).contiguous()
+        testkit.mutate_xor(ent.data_ptr(), k, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        return k
+
+    cands = [4 * W.KIB, 64 * W.KIB, 256 * W.KIB]
+    stream = torch.cuda.current_stream(dev)
+    points = []
+    for frac in (0.0, 0.01, 0.10, 0.50, 1.00):
+        ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=64 * W.KIB, lineage=4, device=0,
+                                                      staging_bytes=8 * W.GIB,
+                                                      image_residency=C.CRAC_RESIDENCY_DEVICE))
+        for b in bufs:
+            C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
+        C.crac_ctx_tune_observe(ctx, cands, stream)
+        for r in range(2):
+            mutate(frac, int(1000 * frac) + r)
+            obs = C.crac_ctx_tune_observe(ctx, cands, stream)
+        res = C.crac_ctx_tune_apply(ctx, 190.0, stream)
+        per = []
+        for S, ms, d in zip(obs["chunk_bytes"], obs["last_pass_ms"], obs["last_dirty_bytes"]):
+            nch = sum(-(-n // S) for n in sizes)
+            kk = d // S
+            alg = B + d + 16 * nch + 16 * kk
+            per.append({"chunk_bytes": S, "pass_ms": ms, "dirty_bytes": d, "tracked_gbs": B / (ms / 1e3) / 1e9,
+                        "hbm_frac": alg / (ms / 1e3) / 1e9 / peak})
+        points.append({"dirty_fraction_4k_pages": frac, "per_chunk_size": per,
+                       "chosen_chunk_bytes": res["chosen_chunk_bytes"],
+                       "chosen_pass_kernel": res["chosen_pass_kernel"], "cost_ms": res["cost_ms"],
+                       "variant_ms_at_chosen": res["variant_ms"]})
+        C.crac_ctx_destroy(ctx)
+    line = {"workload": f"c4: {len(sizes)} allocations, Zipf(1.1) sizes = {B / 2**30:.1f} GiB, uint8/fp32/int64",
+            "tracked_bytes": B, "link_gbs_assumed": 190.0, "peak_gbs": peak, "points": points,
+            "note": "pass = split graph (hash, finalize+compact, gather into 8 GiB staging segments), device time; "
+                    "dirty bytes measured by the pass against the previous observation"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Config 5: serving loop over 64 simulated process contexts
+# ---------------------------------------------------------------------------
+
+def run_config5(args):
+    import threading
+    import torch
+    import paper_2008_10596_gb300 as C
+    from paper_2008_10596_gb300 import testkit
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    seed = W.SEED_BASE + 5
+    rng = np.random.default_rng(seed)
+    n_ctx = 64
+    total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
+    raw = W.log_uniform(rng, n_ctx, 0.5 * W.GIB, 8 * W.GIB)
+    ctx_bytes = W.water_fill(raw, total, int(0.5 * W.GIB * total / (173 * W.GIB)),
+                             int(8 * W.GIB * total / (173 * W.GIB)) + 1, 64 * W.KIB)
+    S = 64 * W.KIB
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    procs = []
+    for i, cb in enumerate(ctx_bytes):
+        na = int(round(np.exp(rng.uniform(np.log(4), np.log(64)))))
+        w = rng.dirichlet(np.ones(na))
+        sizes = [max(64 * W.KIB, int(x * cb) // (64 * W.KIB) * (64 * W.KIB)) for x in w]
+        bufs = [torch.randn(n // 4, generator=g, device=dev).view(torch.uint8) for n in sizes]
+        stream = torch.cuda.Stream(dev)
+        ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=5000 + i, device=0,
+                                                      reserve_host_bytes=int(1.8 * total) if i == 0 else 0))
+        for b in bufs:
+            C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
+        first = W.chunk_layout(sizes, S)
+        muts = []
+        for r in range(4):
+            ms = W.choose_mutations(seed * 131 + i * 7 + r, int(first[-1]), 0.10)
+            rows = []
+            for m in ms:
+                a = int(np.searchsorted(first, m.chunk, side="right") - 1)
+                lo = (m.chunk - int(first[a])) * S
+                rows.append((bufs[a].data_ptr() + lo, min(S, sizes[a] - lo), m.mask))
+            muts.append(torch.from_numpy(np.array(rows, dtype=np.uint64).view(np.int64)).to(dev))
+        procs.append({"ctx": ctx, "bufs": bufs, "stream": stream, "muts": muts, "bytes": sum(sizes),
+                      "ckpts": 0, "images": [], "latest": None})
+    torch.cuda.synchronize()
+    # base (FULL) image of every context, before the measured loop
+    for p in procs:
+        img = C.crac_ctx_checkpoint(p["ctx"], p["stream"])
+        C.crac_image_wait(img)
+        p["latest"] = img
+        p["images"].append(img)
+    torch.cuda.synchronize()
+    server = C.crac_server_create(workers=8, staging_budget=24 * W.GIB, max_lease=4 * W.GIB)
+    n_req = args.requests
+    inter = rng.exponential(1.0 / args.rate, size=n_req)
+    arrivals = np.cumsum(inter)
+    targets = rng.integers(0, n_ctx, size=n_req)
+    kinds = np.where(rng.uniform(size=n_req) < 0.75, C.CRAC_REQ_CHECKPOINT, C.CRAC_REQ_RESTART)
+    lock = threading.Lock()
+    callbacks = []
+
+    def make_prep(p, k_mut, full):
+        def prep(stream, arg):
+            m = p["muts"][k_mut]
+            testkit.mutate_xor(m.data_ptr(), m.shape[0], stream)
+            if full:
+                C.crac_ctx_invalidate(p["ctx"])   # every 4th checkpoint of a context is FULL
+        return C.PREPARE_FN(prep)
+
+    tickets = []
+    results = {}
+
+    def collect():
+        for t, i, kind in iter(queue_get, None):
+            r = C.crac_server_wait(server, t)
+            p = procs[i]
+            with lock:
+                if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
+                    p["images"].append(r["image"])
+                    p["latest"] = r["image"]
+                    if len(p["images"]) > 6:       # history beyond the last few images is dropped
+                        C.crac_image_release(p["images"].pop(0))
+                results[t] = (kind, r, p["bytes"])
+
+    import queue as _q
+    qq = _q.Queue()
+    queue_get = qq.get
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = C.crac_time_now() + 0.05
+    for j in range(n_req):
+        i = int(targets[j])
+        p = procs[i]
+        t_arr = t0 + float(arrivals[j])
+        while C.crac_time_now() < t_arr:
+            time.sleep(min(0.002, max(0.0, t_arr - C.crac_time_now())))
+        if kinds[j] == C.CRAC_REQ_CHECKPOINT:
+            p["ckpts"] += 1
+            cb = make_prep(p, p["ckpts"] % 4, p["ckpts"] % 4 == 0)
+            callbacks.append(cb)
+            t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_CHECKPOINT, None, p["stream"], cb, None, t_arr)
+        else:
+            with lock:
+                img = p["latest"]
+            t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_RESTART, img, p["stream"], None, None, t_arr)
+        tickets.append(t)
+        qq.put((t, i, int(kinds[j])))
+    qq.put(None)
+    th.join()
+    t_end = max(r["t_done"] for _, r, _ in results.values())
+    stats = C.crac_server_stats(server)
+    C.crac_server_destroy(server)
+    lat = {"checkpoint": [], "restart": []}
+    scanned = payload = 0
+    fails = 0
+    for kind, r, nb in results.values():
+        if r["status"] != 0:
+            fails += 1
+            continue
+        lat["checkpoint" if kind == 0 else "restart"].append((r["t_done"] - r["t_arrival"]) * 1e3)
+        scanned += nb
+        payload += r["payload_bytes"]
+    wall = t_end - t0
+    allv = lat["checkpoint"] + lat["restart"]
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+
+    line = {"workload": f"c5: {n_ctx} contexts, {total / 2**30:.0f} GiB total (log-uniform 0.5-8 GiB scaled by "
+                        f"{total / (173 * W.GIB):.3f}), {n_req} requests Poisson {args.rate}/s, 75% ckpt / 25% restart, "
+                        "10% of chunks mutated before each checkpoint, 24 GiB staging budget, 8 slots",
+            "requests": n_req, "failed": fails, "wall_s": wall,
+            "latency_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)} for k, v in lat.items()},
+            "latency_all_ms": {"p50": pct(allv, 50), "p99": pct(allv, 99)},
+            "offered_gbs": sum(procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
+            "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
+            "server": stats}
+    for p in procs:
+        for img in p["images"]:
+            C.crac_image_release(img)
+        C.crac_ctx_destroy(p["ctx"])
+    print(json.dumps(line), flush=True)
+    return 0 if fails == 0 else 1
 
 
 def main():
@@ -441,10 +809,22 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host image) leg")
     ap.add_argument("--total-mib", type=int, default=4096,
                     help="tracked bytes of the config-2 workload (default 4096 = the full config)")
+    ap.add_argument("--requests", type=int, default=1200, help="c5: requests in the serving loop")
+    ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default): the headline line; c3/c4/c5: their own JSON lines")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "crac":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    return run_reference(args) if args.impl == "reference" else run_crac(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "c3":
+        return run_config3(args)
+    if args.workload == "c4":
+        return run_config4(args)
+    if args.workload == "c5":
+        return run_config5(args)
+    return run_crac(args)
 
 
 if __name__ == "__main__":

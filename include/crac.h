@@ -233,12 +233,137 @@ CRAC_API crac_status_t crac_ctx_checkpoint(crac_ctx_t *ctx, crac_stream_t stream
 CRAC_API crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image,
                                         crac_stream_t stream);
 
+/* ---- serving: many contexts, one GPU ---------------------------------- */
+
+/*
+ * A request server for many process contexts sharing one GPU.  Requests
+ * (checkpoint or restart of a context) are queued in arrival order; a
+ * request is admitted when a worker slot is free, no earlier request of the
+ * same context is still running, and its staging lease fits in the staging
+ * budget (first-fit in one device region; an earlier request that does not
+ * fit blocks later ones, so none starves).  Admitted requests run at once on
+ * their own streams, so the passes of different contexts overlap on the
+ * device, and requests arriving meanwhile join as slots and staging free up.
+ * Fingerprint baselines stay in each context's device memory between
+ * requests.  Each result is the same as if the request had run alone.
+ */
+typedef struct crac_server crac_server_t;
+
+typedef struct crac_server_config {
+    uint32_t struct_size;
+    uint32_t workers;          /* requests in flight at once; 0 = 4 */
+    uint64_t staging_budget;   /* device bytes shared by in-flight requests; 0 = 24 GiB */
+    uint64_t max_lease;        /* staging leased by one request (its segment size); 0 = 4 GiB */
+    int32_t device;            /* -1 = current device */
+    uint32_t reserved[5];
+} crac_server_config_t;
+
+#define CRAC_REQ_CHECKPOINT 0
+#define CRAC_REQ_RESTART    1
+
+/* Called on the worker thread right before a request's operation, with the
+ * request's stream: the application's own work to order before it. */
+typedef void (*crac_prepare_fn)(crac_stream_t stream, void *arg);
+
+typedef struct crac_request_result {
+    uint64_t ticket;
+    int32_t status;              /* CRAC_OK or the operation's error */
+    uint32_t type;
+    crac_image_t *image;         /* checkpoint: the new image (caller releases) */
+    double t_arrival, t_admit, t_done;   /* crac_time_now() clock, seconds */
+    uint64_t tracked_bytes;      /* the context's registered bytes */
+    uint64_t payload_bytes;      /* checkpoint: dirty bytes; restart: image payload */
+    uint64_t lease_bytes;        /* staging leased while it ran */
+} crac_request_result_t;
+
+typedef struct crac_server_stats {
+    uint64_t submitted, completed;
+    uint32_t queued, in_flight, max_in_flight, pad;
+    uint64_t staging_used, staging_high_water, staging_budget;
+} crac_server_stats_t;
+
+CRAC_API double crac_time_now(void);
+CRAC_API crac_status_t crac_server_create(const crac_server_config_t *cfg, crac_server_t **out);
+/* Waits for queued and running requests, then frees the server.  Results not
+ * yet collected are dropped (their images released). */
+CRAC_API crac_status_t crac_server_destroy(crac_server_t *server);
+/* Queue a request.  image: the image to restore (restart only; the server
+ * holds a reference until the request completes).  t_arrival: the request's scheduled
+ * arrival on the crac_time_now() clock (latency is measured from it); <= 0
+ * means now.  *ticket identifies the result. */
+CRAC_API crac_status_t crac_server_submit(crac_server_t *server, crac_ctx_t *ctx, uint32_t type,
+                                          const crac_image_t *image, crac_stream_t stream,
+                                          crac_prepare_fn prepare, void *prepare_arg, double t_arrival,
+                                          uint64_t *ticket);
+/* Wait (at most timeout_ns; 0 = no limit) for a request and take its result. */
+CRAC_API crac_status_t crac_server_wait(crac_server_t *server, uint64_t ticket, uint64_t timeout_ns,
+                                        crac_request_result_t *out);
+CRAC_API crac_status_t crac_server_stats(crac_server_t *server, crac_server_stats_t *out);
+
+/* ---- autotuning (chunk size and pass kernel) ------------------------- */
+
+#define CRAC_TUNE_MAX 8
+typedef struct crac_tune_result {
+    uint32_t n;                            /* candidate chunk sizes */
+    uint32_t rounds;                       /* delta observations per candidate */
+    uint32_t chosen_chunk_bytes;           /* set by crac_ctx_tune_apply */
+    uint32_t chosen_pass_kernel;
+    uint32_t chunk_bytes[CRAC_TUNE_MAX];
+    float last_pass_ms[CRAC_TUNE_MAX];     /* most recent observation (device time) */
+    uint64_t last_dirty_bytes[CRAC_TUNE_MAX];
+    float mean_pass_ms[CRAC_TUNE_MAX];     /* over the delta observations */
+    double mean_dirty_bytes[CRAC_TUNE_MAX];
+    float cost_ms[CRAC_TUNE_MAX];          /* pass + drain estimate (apply) */
+    float variant_ms[4];                   /* pass time per CRAC_PASS_* at the chosen
+                                              size (apply); 0 = not applicable */
+} crac_tune_result_t;
+
+/*
+ * One observation round of the autotuner, taken between two steps of the
+ * application (typically right before a checkpoint).  For every candidate
+ * chunk size (chunk_sizes[0..n), n <= CRAC_TUNE_MAX, each a valid chunk size)
+ * the library keeps a private fingerprint baseline of the registered memory;
+ * each round runs the real checkpoint pass for that size against its own
+ * baseline, on `stream`, without producing an image and without touching the
+ * context's own baseline, and records the device time and dirty bytes.  The
+ * first round only establishes the baselines.  A different list of sizes
+ * restarts the session.  *out (may be NULL) receives the statistics.
+ */
+CRAC_API crac_status_t crac_ctx_tune_observe(crac_ctx_t *ctx, crac_stream_t stream, const uint32_t *chunk_sizes,
+                                             uint32_t n, crac_tune_result_t *out);
+
+/*
+ * End the session: choose the chunk size with the lowest mean cost
+ * (pass time + dirty bytes / link_gbs; link_gbs <= 0 counts the device pass
+ * only), then time each pass kernel at that size on the current memory and
+ * keep the fastest.  If the chunk size changes, the context's baseline is
+ * dropped, so its next checkpoint is FULL (which also ends the delta chain,
+ * since a chain holds one chunk size).  Needs at least two observe rounds
+ * (CRAC_ERR_UNSUPPORTED otherwise).
+ */
+CRAC_API crac_status_t crac_ctx_tune_apply(crac_ctx_t *ctx, crac_stream_t stream, double link_gbs,
+                                           crac_tune_result_t *out);
+
 /* Forget the fingerprint baseline: the next checkpoint carries every chunk
  * (a FULL image, which cuts the delta chain). */
 CRAC_API crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx);
 
 /* Measurements of the context's most recent checkpoint pass. */
 CRAC_API crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out);
+
+/* Measurements of a context's most recent restart (crac_ctx_last_restart). */
+typedef struct crac_restart_info {
+    uint32_t chain_length;       /* images from the nearest FULL one to the target */
+    uint32_t images_used;        /* images that still owned at least one chunk */
+    uint64_t restored_bytes;     /* bytes written into allocations (= tracked bytes) */
+    uint64_t entries_scanned;    /* chunk entries the scatter kernels visited */
+    uint64_t h2d_bytes;          /* host image payload copied to the device */
+    uint32_t scatter_launches;
+    float device_ms;             /* device time from the first copy/launch to the last */
+    uint32_t reserved[4];
+} crac_restart_info_t;
+
+CRAC_API crac_status_t crac_ctx_last_restart(crac_ctx_t *ctx, crac_restart_info_t *out);
 
 /* ---- default-context forms (one implicit context per process) -------- */
 

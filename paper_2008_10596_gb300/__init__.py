@@ -60,6 +60,8 @@ EXPORTED = [
     "crac_image_wait", "crac_image_info", "crac_image_serialize", "crac_image_deserialize",
     "crac_image_release", "crac_status_str", "crac_last_cuda_error", "crac_kernel_launches",
     "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault", "crac_pass_noalloc",
+    "crac_ctx_tune_observe", "crac_ctx_tune_apply", "crac_ctx_last_restart", "crac_time_now", "crac_server_create",
+    "crac_server_destroy", "crac_server_submit", "crac_server_wait", "crac_server_stats",
 ]
 CRAC_NOALLOC_MAX_TILES = 32768
 
@@ -99,6 +101,58 @@ class CracPassInfo(ctypes.Structure):
     ]
 
 
+CRAC_TUNE_MAX = 8
+
+
+class CracRestartInfo(ctypes.Structure):
+    _fields_ = [("chain_length", ctypes.c_uint32), ("images_used", ctypes.c_uint32),
+                ("restored_bytes", ctypes.c_uint64), ("entries_scanned", ctypes.c_uint64),
+                ("h2d_bytes", ctypes.c_uint64), ("scatter_launches", ctypes.c_uint32),
+                ("device_ms", ctypes.c_float), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class CracTuneResult(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32), ("rounds", ctypes.c_uint32), ("chosen_chunk_bytes", ctypes.c_uint32),
+        ("chosen_pass_kernel", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32 * CRAC_TUNE_MAX),
+        ("last_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("last_dirty_bytes", ctypes.c_uint64 * CRAC_TUNE_MAX),
+        ("mean_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("mean_dirty_bytes", ctypes.c_double * CRAC_TUNE_MAX),
+        ("cost_ms", ctypes.c_float * CRAC_TUNE_MAX), ("variant_ms", ctypes.c_float * 4),
+    ]
+
+    def to_dict(self) -> dict:
+        n = self.n
+        return {"rounds": self.rounds, "chosen_chunk_bytes": self.chosen_chunk_bytes,
+                "chosen_pass_kernel": self.chosen_pass_kernel, "chunk_bytes": list(self.chunk_bytes[:n]),
+                "last_pass_ms": list(self.last_pass_ms[:n]), "last_dirty_bytes": list(self.last_dirty_bytes[:n]),
+                "mean_pass_ms": list(self.mean_pass_ms[:n]), "mean_dirty_bytes": list(self.mean_dirty_bytes[:n]),
+                "cost_ms": list(self.cost_ms[:n]), "variant_ms": list(self.variant_ms)}
+
+
+class CracServerConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("workers", ctypes.c_uint32),
+                ("staging_budget", ctypes.c_uint64), ("max_lease", ctypes.c_uint64),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+class CracRequestResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("type", ctypes.c_uint32),
+                ("image", ctypes.c_void_p), ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("tracked_bytes", ctypes.c_uint64),
+                ("payload_bytes", ctypes.c_uint64), ("lease_bytes", ctypes.c_uint64)]
+
+
+class CracServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("queued", ctypes.c_uint32),
+                ("in_flight", ctypes.c_uint32), ("max_in_flight", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("staging_used", ctypes.c_uint64), ("staging_high_water", ctypes.c_uint64),
+                ("staging_budget", ctypes.c_uint64)]
+
+
+CRAC_REQ_CHECKPOINT = 0
+CRAC_REQ_RESTART = 1
+PREPARE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
 _vp = ctypes.c_void_p
 _st = ctypes.c_int
 _sigs = {
@@ -126,6 +180,17 @@ _sigs = {
     "crac_alloc_managed": (_st, [ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "crac_free_managed": (_st, [_vp]),
     "crac_debug_inject_fault": (None, [ctypes.c_int, ctypes.c_int]),
+    "crac_ctx_tune_observe": (_st, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                    ctypes.POINTER(CracTuneResult)]),
+    "crac_ctx_tune_apply": (_st, [_vp, _vp, ctypes.c_double, ctypes.POINTER(CracTuneResult)]),
+    "crac_ctx_last_restart": (_st, [_vp, ctypes.POINTER(CracRestartInfo)]),
+    "crac_time_now": (ctypes.c_double, []),
+    "crac_server_create": (_st, [ctypes.POINTER(CracServerConfig), ctypes.POINTER(_vp)]),
+    "crac_server_destroy": (_st, [_vp]),
+    "crac_server_submit": (_st, [_vp, _vp, ctypes.c_uint32, _vp, _vp, PREPARE_FN, _vp, ctypes.c_double,
+                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "crac_server_wait": (_st, [_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(CracRequestResult)]),
+    "crac_server_stats": (_st, [_vp, ctypes.POINTER(CracServerStats)]),
     "crac_pass_noalloc": (_st, [_vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp, _vp,
                                 ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp]),
 }
@@ -198,6 +263,66 @@ def crac_ctx_checkpoint(ctx: int, stream=None) -> int:
 
 def crac_ctx_restart(ctx: int, image: int, stream=None) -> None:
     _check(_lib.crac_ctx_restart(ctx, image, _stream(stream)), "crac_ctx_restart")
+
+
+def crac_ctx_tune_observe(ctx: int, chunk_sizes, stream=None) -> dict:
+    arr = (ctypes.c_uint32 * len(chunk_sizes))(*chunk_sizes)
+    out = CracTuneResult()
+    _check(_lib.crac_ctx_tune_observe(ctx, _stream(stream), arr, len(chunk_sizes), ctypes.byref(out)),
+           "crac_ctx_tune_observe")
+    return out.to_dict()
+
+
+def crac_ctx_tune_apply(ctx: int, link_gbs: float = 0.0, stream=None) -> dict:
+    out = CracTuneResult()
+    _check(_lib.crac_ctx_tune_apply(ctx, _stream(stream), link_gbs, ctypes.byref(out)), "crac_ctx_tune_apply")
+    return out.to_dict()
+
+
+def crac_ctx_last_restart(ctx: int) -> dict:
+    info = CracRestartInfo()
+    _check(_lib.crac_ctx_last_restart(ctx, ctypes.byref(info)), "crac_ctx_last_restart")
+    return {f: getattr(info, f) for f, _ in CracRestartInfo._fields_ if f != "reserved"}
+
+
+def crac_time_now() -> float:
+    return _lib.crac_time_now()
+
+
+def crac_server_create(workers: int = 0, staging_budget: int = 0, max_lease: int = 0, device: int = -1) -> int:
+    cfg = CracServerConfig(ctypes.sizeof(CracServerConfig), workers, staging_budget, max_lease, device)
+    h = _vp()
+    _check(_lib.crac_server_create(ctypes.byref(cfg), ctypes.byref(h)), "crac_server_create")
+    return h.value
+
+
+def crac_server_destroy(server: int) -> None:
+    _check(_lib.crac_server_destroy(server), "crac_server_destroy")
+
+
+_NO_PREPARE = PREPARE_FN()
+
+
+def crac_server_submit(server: int, ctx: int, type_: int, image: int | None = None, stream=None,
+                       prepare=None, prepare_arg: int | None = None, t_arrival: float = 0.0) -> int:
+    """prepare: a PREPARE_FN instance (keep it alive until the request completes)."""
+    t = ctypes.c_uint64()
+    _check(_lib.crac_server_submit(server, ctx, type_, image, _stream(stream),
+                                   prepare if prepare is not None else _NO_PREPARE, prepare_arg,
+                                   t_arrival, ctypes.byref(t)), "crac_server_submit")
+    return t.value
+
+
+def crac_server_wait(server: int, ticket: int, timeout_ns: int = 0) -> dict:
+    r = CracRequestResult()
+    _check(_lib.crac_server_wait(server, ticket, timeout_ns, ctypes.byref(r)), "crac_server_wait")
+    return {f: getattr(r, f) for f, _ in CracRequestResult._fields_}
+
+
+def crac_server_stats(server: int) -> dict:
+    st = CracServerStats()
+    _check(_lib.crac_server_stats(server, ctypes.byref(st)), "crac_server_stats")
+    return {f: getattr(st, f) for f, _ in CracServerStats._fields_ if f != "pad"}
 
 
 def crac_ctx_invalidate(ctx: int) -> None:

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <climits>
 #include <cstring>
 #include <map>
@@ -471,7 +473,15 @@ struct crac_ctx {
     cudaGraphNode_t s_memset = nullptr, s_k[3] = {nullptr, nullptr, nullptr}, s_copy = nullptr;
     cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};   // around each split-pass kernel
     crac_pass_info_t last{};
+    crac_restart_info_t last_restart{};
+    cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
+    // autotuner session: one shadow context per candidate chunk size
+    std::vector<crac_ctx *> tune_ctx;
+    std::vector<double> tune_sum_ms, tune_sum_bytes;
+    std::vector<float> tune_last_ms;
+    std::vector<uint64_t> tune_last_bytes;
+    uint32_t tune_rounds = 0;
 };
 
 namespace {
@@ -519,6 +529,8 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     CK(cudaEventCreate(&c->ev_p0));
     CK(cudaEventCreate(&c->ev_p1));
     for (cudaEvent_t &e : c->sev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&c->ev_r0));
+    CK(cudaEventCreate(&c->ev_r1));
     TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
     TRY(ensure_host(c->serr_h, 256));
     if (c->cfg.reserve_host_bytes) TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
@@ -527,7 +539,23 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     return CRAC_OK;
 }
 
+void ctx_free_all(crac_ctx *c);
+
+void tune_clear(crac_ctx *c) {
+    for (crac_ctx *t : c->tune_ctx) {
+        ctx_free_all(t);
+        delete t;
+    }
+    c->tune_ctx.clear();
+    c->tune_sum_ms.clear();
+    c->tune_sum_bytes.clear();
+    c->tune_last_ms.clear();
+    c->tune_last_bytes.clear();
+    c->tune_rounds = 0;
+}
+
 void ctx_free_all(crac_ctx *c) {
+    tune_clear(c);
     if (!c->cuda_ready) {
         img_unref(c->parent);
         c->parent = nullptr;
@@ -545,7 +573,7 @@ void ctx_free_all(crac_ctx *c) {
     if (c->sgexec) cudaGraphExecDestroy(c->sgexec);
     if (c->sgraph) cudaGraphDestroy(c->sgraph);
     for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1, c->sev[0], c->sev[1],
-                          c->sev[2], c->sev[3]})
+                          c->sev[2], c->sev[3], c->ev_r0, c->ev_r1})
         if (e) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
     cudaGetLastError();
@@ -1189,6 +1217,11 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(cudaMemsetAsync(c->serr.p, 0, 256, s));
     CK(cudaMemcpyAsync(c->owner.p, owner, nt * 2, cudaMemcpyHostToDevice, s));
+    crac_restart_info_t ri{};
+    ri.chain_length = (uint32_t)chain.size();
+    for (size_t i = 0; i < chain.size(); ++i) ri.images_used += survivors[i] ? 1u : 0u;
+    for (const ImgAlloc &a : img->allocs) ri.restored_bytes += a.bytes;
+    CK(cudaEventRecord(c->ev_r0, s));
     ScatterDesc *sdh = (ScatterDesc *)c->sdesc_h.p;
     ScatterDesc *sdd = (ScatterDesc *)c->sdesc.p;
     const int grid = c->sm_count * 8;
@@ -1229,6 +1262,8 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
                 P.origin = 0;
                 P.window = pc.bytes;
                 CK(launch_scatter(P, (int)std::min<uint64_t>((pc.k + 7) / 8, (uint64_t)grid), s));
+                ri.entries_scanned += pc.k;
+                ri.scatter_launches++;
             }
             continue;
         }
@@ -1294,6 +1329,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
                 if (hi <= lo) continue;
                 CK(cudaMemcpyAsync((uint8_t *)c->staging.p + (lo - o0), pc.host.p + (lo - pc.off0), hi - lo,
                                    cudaMemcpyHostToDevice, s));
+                ri.h2d_bytes += hi - lo;
             }
             P.full = full ? 1u : 0u;
             P.j0 = j0;
@@ -1304,16 +1340,21 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
             P.origin = o0;
             P.window = end - o0;
             CK(launch_scatter(P, (int)std::min<uint64_t>((j1 - j0 + 7) / 8, (uint64_t)grid), s));
+            ri.entries_scanned += j1 - j0;
+            ri.scatter_launches++;
             j0 = j1;
         }
     }
     // Baseline = the image's fingerprints; registry takes the image's identities.
     TRY(ensure_dev(c->fp[c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
     if (nt) CK(cudaMemcpyAsync(c->fp[c->fp_cur].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->ev_r1, s));
     CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
     if (*(const unsigned *)c->serr_h.p) return CRAC_ERR_CORRUPT;
+    cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
+    c->last_restart = ri;
     c->base_first.clear();
     for (size_t a = 0; a < na; ++a) {
         c->allocs[a].id = img->allocs[a].id;
@@ -1328,6 +1369,331 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     img_unref(c->parent);
     c->parent = img;
     return CRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Trial passes and the autotuner
+// ---------------------------------------------------------------------------
+
+// The checkpoint pass without an image: fingerprints, dirty test, compaction
+// and gather into the context's staging, segment by segment.  With commit the
+// new fingerprints become the context's baseline.
+crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms, uint64_t *k_out,
+                             uint64_t *d_out) {
+    TRY(ctx_cuda_ready(c));
+    DeviceGuard g(c->device);
+    const size_t na = c->allocs.size();
+    const uint32_t log2S = c->log2S;
+    const uint64_t S = 1ull << log2S;
+    std::vector<uint64_t> first(na + 1, 0);
+    uint64_t tracked = 0;
+    for (size_t a = 0; a < na; ++a) {
+        first[a + 1] = first[a] + ((c->allocs[a].bytes + S - 1) >> log2S);
+        tracked += c->allocs[a].bytes;
+    }
+    const uint64_t n = first[na];
+    *ms = 0;
+    *k_out = 0;
+    *d_out = 0;
+    c->last = crac_pass_info_t{};
+    if (n == 0) return CRAC_OK;
+    TRY(ensure_dev(c->fp[1 - c->fp_cur], n * 8));
+    TRY(ensure_dev(c->desc, na * sizeof(CkptDesc)));
+    TRY(ensure_host(c->desc_h, na * sizeof(CkptDesc)));
+    CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+    for (size_t a = 0; a < na; ++a) {
+        uint64_t bf = kNoBase;
+        if (c->base_valid) {
+            auto it = c->base_first.find(c->allocs[a].id);
+            if (it != c->base_first.end()) bf = it->second;
+        }
+        dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+    }
+    CK(cudaStreamWaitEvent(s, c->ev_last, 0));
+    CK(cudaMemcpyAsync(c->desc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s));
+    uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
+    cap = std::max(round_up(cap, 256), S);
+    const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
+    uint64_t max_c = 0, max_b = 0;
+    for (const Segment &sg : segs) {
+        max_c = std::max(max_c, sg.c1 - sg.c0);
+        max_b = std::max(max_b, sg.bytes);
+    }
+    TRY(ensure_dev(c->staging, max_b));
+    TRY(ensure_dev(c->idx, max_c * 8));
+    TRY(ensure_dev(c->off, (max_c + 1) * 8));
+    for (const Segment &sg : segs) {
+        CkptCtrl ctrl{};
+        TRY(run_segment(c, sg, (const CkptDesc *)c->desc.p, first, (uint64_t *)c->idx.p, (uint64_t *)c->off.p,
+                        sg.c1 - sg.c0, (uint8_t *)c->staging.p, sg.bytes, s, &ctrl, ms));
+        *k_out += ctrl.k;
+        *d_out += ctrl.D;
+    }
+    CK(cudaEventRecord(c->ev_last, s));
+    if (commit) {
+        c->fp_cur = 1 - c->fp_cur;
+        c->base_first.clear();
+        for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
+        c->base_valid = true;
+    }
+    return CRAC_OK;
+}
+
+void tune_fill(const crac_ctx *c, crac_tune_result_t *out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->n = (uint32_t)c->tune_ctx.size();
+    out->rounds = c->tune_rounds;
+    for (size_t i = 0; i < c->tune_ctx.size(); ++i) {
+        out->chunk_bytes[i] = 1u << c->tune_ctx[i]->log2S;
+        out->last_pass_ms[i] = c->tune_last_ms[i];
+        out->last_dirty_bytes[i] = c->tune_last_bytes[i];
+        if (c->tune_rounds) {
+            out->mean_pass_ms[i] = (float)(c->tune_sum_ms[i] / c->tune_rounds);
+            out->mean_dirty_bytes[i] = c->tune_sum_bytes[i] / c->tune_rounds;
+        }
+    }
+}
+
+crac_status_t ctx_tune_observe(crac_ctx *c, cudaStream_t s, const uint32_t *sizes, uint32_t n,
+                               crac_tune_result_t *out) {
+    if (!sizes || n == 0 || n > CRAC_TUNE_MAX) return CRAC_ERR_INVALID_ARG;
+    bool same = c->tune_ctx.size() == n;
+    for (uint32_t i = 0; same && i < n; ++i) same = (1u << c->tune_ctx[i]->log2S) == sizes[i];
+    if (!same) {
+        tune_clear(c);
+        for (uint32_t i = 0; i < n; ++i) {
+            crac_config_t cfg = c->cfg;
+            cfg.chunk_bytes = sizes[i];
+            cfg.device = c->device;
+            cfg.reserve_host_bytes = cfg.reserve_device_bytes = 0;
+            if (cfg.pass_kernel == CRAC_PASS_TMA && (sizes[i] < 1024 || sizes[i] > 65536)) cfg.pass_kernel = CRAC_PASS_AUTO;
+            crac_ctx *t = new crac_ctx();
+            const crac_status_t st = ctx_init(t, &cfg);
+            if (st != CRAC_OK) {
+                ctx_free_all(t);
+                delete t;
+                tune_clear(c);
+                return st;
+            }
+            c->tune_ctx.push_back(t);
+        }
+        c->tune_sum_ms.assign(n, 0.0);
+        c->tune_sum_bytes.assign(n, 0.0);
+        c->tune_last_ms.assign(n, 0.f);
+        c->tune_last_bytes.assign(n, 0);
+        c->tune_rounds = 0;
+    }
+    bool counted = true;
+    for (uint32_t i = 0; i < n; ++i) {
+        crac_ctx *t = c->tune_ctx[i];
+        const bool had_base = t->base_valid;
+        counted = counted && had_base;
+        t->allocs = c->allocs;
+        float ms = 0;
+        uint64_t k = 0, d = 0;
+        TRY(ctx_trial_pass(t, s, true, &ms, &k, &d));
+        c->tune_last_ms[i] = ms;
+        c->tune_last_bytes[i] = d;
+        if (had_base) {
+            c->tune_sum_ms[i] += ms;
+            c->tune_sum_bytes[i] += (double)d;
+        }
+    }
+    if (counted) c->tune_rounds++;
+    tune_fill(c, out);
+    return CRAC_OK;
+}
+
+crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_tune_result_t *out) {
+    if (c->tune_ctx.empty() || c->tune_rounds == 0) return CRAC_ERR_UNSUPPORTED;
+    const uint32_t n = (uint32_t)c->tune_ctx.size();
+    std::vector<float> cost(n);
+    uint32_t best = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const double ms = c->tune_sum_ms[i] / c->tune_rounds;
+        const double bytes = c->tune_sum_bytes[i] / c->tune_rounds;
+        cost[i] = (float)(ms + (link_gbs > 0 ? bytes / (link_gbs * 1e9) * 1e3 : 0.0));
+        if (cost[i] < cost[best]) best = i;
+    }
+    crac_ctx *t = c->tune_ctx[best];
+    const uint32_t S = 1u << t->log2S;
+    // Pass kernels at the chosen size, each against the shadow's baseline.
+    float vms[4] = {0, 0, 0, 0};
+    uint32_t best_v = CRAC_PASS_SPLIT;
+    const uint32_t saved = t->cfg.pass_kernel;
+    for (uint32_t v : {(uint32_t)CRAC_PASS_SPLIT, (uint32_t)CRAC_PASS_LDG, (uint32_t)CRAC_PASS_TMA}) {
+        if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
+        t->cfg.pass_kernel = v;
+        float bestm = 0;
+        for (int r = 0; r < 2; ++r) {
+            float ms = 0;
+            uint64_t k = 0, d = 0;
+            const crac_status_t st = ctx_trial_pass(t, s, false, &ms, &k, &d);
+            if (st != CRAC_OK) {
+                t->cfg.pass_kernel = saved;
+                return st;
+            }
+            if (r == 0 || ms < bestm) bestm = ms;
+        }
+        vms[v] = bestm;
+        if (vms[best_v] == 0 || bestm < vms[best_v]) best_v = v;
+    }
+    tune_fill(c, out);
+    if (out) {
+        for (uint32_t i = 0; i < n; ++i) out->cost_ms[i] = cost[i];
+        for (int v = 0; v < 4; ++v) out->variant_ms[v] = vms[v];
+        out->chosen_chunk_bytes = S;
+        out->chosen_pass_kernel = best_v;
+    }
+    if (S != (1u << c->log2S)) {
+        c->cfg.chunk_bytes = S;
+        c->log2S = t->log2S;
+        c->base_valid = false;
+        c->base_first.clear();
+    }
+    c->cfg.pass_kernel = best_v;
+    tune_clear(c);
+    return CRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Request server
+// ---------------------------------------------------------------------------
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Run an operation of `c` with a leased staging buffer in place of its own.
+template <class F>
+crac_status_t with_staging(crac_ctx *c, void *p, uint64_t bytes, F &&op) {
+    const DevBuf saved = c->staging;
+    const uint64_t saved_cfg = c->cfg.staging_bytes;
+    if (p) {
+        c->staging = DevBuf{p, (size_t)bytes};
+        c->cfg.staging_bytes = bytes;
+    }
+    const crac_status_t st = op();
+    if (p) {
+        c->staging = saved;
+        c->cfg.staging_bytes = saved_cfg;
+    }
+    return st;
+}
+
+struct ServerReq {
+    crac_request_result_t r{};
+    crac_ctx *ctx = nullptr;
+    crac_image *img = nullptr;
+    cudaStream_t stream = nullptr;
+    crac_prepare_fn prep = nullptr;
+    void *prep_arg = nullptr;
+    uint64_t lease_off = 0;
+};
+
+}  // namespace
+
+struct crac_server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerReq *> queue;
+    std::map<uint64_t, ServerReq *> done;
+    std::map<crac_ctx *, int> busy;
+    std::vector<std::thread> workers;
+    bool stopping = false;
+    int device = 0;
+    uint64_t budget = 0, max_lease = 0, used = 0, high_water = 0;
+    uint64_t next_ticket = 1, submitted = 0, completed = 0;
+    uint32_t in_flight = 0, max_in_flight = 0;
+    void *staging = nullptr;
+    std::unique_ptr<RangeAlloc> ra;
+};
+
+namespace {
+
+uint64_t ctx_tracked(const crac_ctx *c) {
+    uint64_t t = 0;
+    for (const AllocRec &a : c->allocs) t += a.bytes;
+    return t;
+}
+
+void server_worker(crac_server *sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        ServerReq *q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            for (;;) {
+                if (sv->stopping && sv->queue.empty()) return;
+                // first request (arrival order) whose context is idle; it must
+                // fit the staging budget, otherwise everything waits behind it
+                auto it = sv->queue.begin();
+                while (it != sv->queue.end() && sv->busy.count((*it)->ctx)) ++it;
+                if (it != sv->queue.end()) {
+                    ServerReq *c = *it;
+                    uint64_t off = 0;
+                    const uint64_t want = c->r.lease_bytes;
+                    if (want == 0 || sv->ra->alloc(want, &off)) {
+                        c->lease_off = off;
+                        sv->used += want;
+                        sv->high_water = std::max(sv->high_water, sv->used);
+                        sv->busy[c->ctx] = 1;
+                        sv->queue.erase(it);
+                        sv->in_flight++;
+                        sv->max_in_flight = std::max(sv->max_in_flight, sv->in_flight);
+                        q = c;
+                        break;
+                    }
+                }
+                sv->cv_work.wait(lk);
+            }
+        }
+        q->r.t_admit = now_s();
+        void *lease = q->r.lease_bytes ? (uint8_t *)sv->staging + q->lease_off : nullptr;
+        if (q->prep) q->prep((crac_stream_t)q->stream, q->prep_arg);
+        crac_status_t st;
+        {
+            std::lock_guard<std::mutex> lk(q->ctx->mu);
+            st = ctx_cuda_ready(q->ctx);
+            if (st == CRAC_OK) {
+                if (q->r.type == CRAC_REQ_CHECKPOINT) {
+                    crac_image *img = nullptr;
+                    st = with_staging(q->ctx, lease, q->r.lease_bytes,
+                                      [&] { return ctx_checkpoint(q->ctx, q->stream, &img); });
+                    if (st == CRAC_OK) {
+                        q->r.image = img;
+                        q->r.payload_bytes = img->payload_bytes;
+                    }
+                } else {
+                    st = with_staging(q->ctx, lease, q->r.lease_bytes,
+                                      [&] { return ctx_restart(q->ctx, q->img, q->stream); });
+                    if (st == CRAC_OK) q->r.payload_bytes = q->img->payload_bytes;
+                }
+            }
+        }
+        // The lease is free once the drain has finished reading it.
+        if (st == CRAC_OK && q->r.image) st = img_wait(q->r.image, 0);
+        q->r.status = st;
+        q->r.t_done = now_s();
+        if (q->img) {
+            img_unref(q->img);
+            q->img = nullptr;
+        }
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (q->r.lease_bytes) {
+                sv->ra->release(q->lease_off, q->r.lease_bytes);
+                sv->used -= q->r.lease_bytes;
+            }
+            sv->busy.erase(q->ctx);
+            sv->in_flight--;
+            sv->completed++;
+            sv->done[q->r.ticket] = q;
+        }
+        sv->cv_work.notify_all();
+        sv->cv_done.notify_all();
+    }
 }
 
 crac_ctx *g_default = nullptr;
@@ -1434,6 +1800,153 @@ crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image, crac_
     return ctx_restart(ctx, const_cast<crac_image *>(image), (cudaStream_t)stream);
 }
 
+double crac_time_now(void) { return now_s(); }
+
+crac_status_t crac_server_create(const crac_server_config_t *cfg, crac_server_t **out) {
+    if (!out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    crac_server_config_t c{};
+    if (cfg) c = *cfg;
+    std::unique_ptr<crac_server> sv(new crac_server());
+    const uint32_t workers = c.workers ? c.workers : 4;
+    sv->budget = round_up(c.staging_budget ? c.staging_budget : (24ull << 30), 256);
+    sv->max_lease = round_up(c.max_lease ? c.max_lease : (4ull << 30), 256);
+    if (sv->max_lease > sv->budget) sv->max_lease = sv->budget;
+    int dev = c.device;
+    if (dev < 0) CK(cudaGetDevice(&dev));
+    sv->device = dev;
+    {
+        DeviceGuard g(dev);
+        if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
+        const cudaError_t e = cudaMalloc(&sv->staging, sv->budget);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+    }
+    sv->ra.reset(new RangeAlloc(sv->budget));
+    for (uint32_t i = 0; i < workers; ++i) sv->workers.emplace_back(server_worker, sv.get());
+    *out = sv.release();
+    return CRAC_OK;
+}
+
+crac_status_t crac_server_destroy(crac_server_t *sv) {
+    if (!sv) return CRAC_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stopping = true;
+    }
+    sv->cv_work.notify_all();
+    for (std::thread &t : sv->workers) t.join();
+    for (auto &kv : sv->done) {
+        if (kv.second->r.image) img_unref(kv.second->r.image);
+        delete kv.second;
+    }
+    {
+        DeviceGuard g(sv->device);
+        cudaFree(sv->staging);
+        cudaGetLastError();
+    }
+    delete sv;
+    return CRAC_OK;
+}
+
+crac_status_t crac_server_submit(crac_server_t *sv, crac_ctx_t *ctx, uint32_t type, const crac_image_t *image,
+                                 crac_stream_t stream, crac_prepare_fn prepare, void *prepare_arg, double t_arrival,
+                                 uint64_t *ticket) {
+    if (!sv || !ctx || !ticket || type > CRAC_REQ_RESTART || (type == CRAC_REQ_RESTART && !image))
+        return CRAC_ERR_INVALID_ARG;
+    ServerReq *q = new ServerReq();
+    q->ctx = ctx;
+    q->img = const_cast<crac_image *>(image);
+    q->stream = (cudaStream_t)stream;
+    q->prep = prepare;
+    q->prep_arg = prepare_arg;
+    q->r.type = type;
+    q->r.t_arrival = t_arrival > 0 ? t_arrival : now_s();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        q->r.tracked_bytes = ctx_tracked(ctx);
+        const uint64_t S = 1ull << ctx->log2S;
+        uint64_t lease = 0;
+        if (type == CRAC_REQ_CHECKPOINT && ctx->cfg.image_residency == CRAC_RESIDENCY_HOST)
+            lease = q->r.tracked_bytes;
+        if (type == CRAC_REQ_RESTART && image->residency == CRAC_RESIDENCY_HOST) lease = q->r.tracked_bytes;
+        if (lease) lease = std::max(round_up(std::min(lease, sv->max_lease), 256), round_up(S, 256));
+        if (lease > sv->budget) {
+            delete q;
+            return CRAC_ERR_INVALID_ARG;
+        }
+        q->r.lease_bytes = lease;
+    }
+    if (q->img) img_ref(q->img);   // kept alive until the request completes
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stopping) {
+            img_unref(q->img);
+            delete q;
+            return CRAC_ERR_BUSY;
+        }
+        q->r.ticket = sv->next_ticket++;
+        sv->submitted++;
+        sv->queue.push_back(q);
+        *ticket = q->r.ticket;
+    }
+    sv->cv_work.notify_all();
+    return CRAC_OK;
+}
+
+crac_status_t crac_server_wait(crac_server_t *sv, uint64_t ticket, uint64_t timeout_ns, crac_request_result_t *out) {
+    if (!sv || !out) return CRAC_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
+    for (;;) {
+        auto it = sv->done.find(ticket);
+        if (it != sv->done.end()) {
+            *out = it->second->r;
+            delete it->second;
+            sv->done.erase(it);
+            return CRAC_OK;
+        }
+        if (ticket == 0 || ticket >= sv->next_ticket) return CRAC_ERR_INVALID_ARG;
+        if (timeout_ns) {
+            if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) return CRAC_ERR_TIMEOUT;
+        } else {
+            sv->cv_done.wait(lk);
+        }
+    }
+}
+
+crac_status_t crac_server_stats(crac_server_t *sv, crac_server_stats_t *out) {
+    if (!sv || !out) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = sv->submitted;
+    out->completed = sv->completed;
+    out->queued = (uint32_t)sv->queue.size();
+    out->in_flight = sv->in_flight;
+    out->max_in_flight = sv->max_in_flight;
+    out->staging_used = sv->used;
+    out->staging_high_water = sv->high_water;
+    out->staging_budget = sv->budget;
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_tune_observe(crac_ctx_t *ctx, crac_stream_t stream, const uint32_t *chunk_sizes,
+                                    uint32_t n, crac_tune_result_t *out) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TRY(ctx_cuda_ready(ctx));
+    return ctx_tune_observe(ctx, (cudaStream_t)stream, chunk_sizes, n, out);
+}
+
+crac_status_t crac_ctx_tune_apply(crac_ctx_t *ctx, crac_stream_t stream, double link_gbs, crac_tune_result_t *out) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TRY(ctx_cuda_ready(ctx));
+    return ctx_tune_apply(ctx, (cudaStream_t)stream, link_gbs, out);
+}
+
 crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx) {
     if (!ctx) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1446,6 +1959,13 @@ crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out) {
     if (!ctx || !out) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
     *out = ctx->last;
+    return CRAC_OK;
+}
+
+crac_status_t crac_ctx_last_restart(crac_ctx_t *ctx, crac_restart_info_t *out) {
+    if (!ctx || !out) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *out = ctx->last_restart;
     return CRAC_OK;
 }
 
