@@ -535,10 +535,10 @@ def run_config3(args):
         ii = C.crac_image_info(img)
         imgs.append(img)
         ckpts.append({"epoch": ii["epoch"], "full": bool(ii["flags"] & 1), "dirty_bytes": ii["payload_bytes"],
-                      "pass_ms": info["device_ms"], "prefetch_ms": info["prefetch_ms"],
+                      "segments": info["segments"], "pass_ms": info["device_ms"], "prefetch_ms": info["prefetch_ms"],
                       "pass_tracked_gbs": B / (info["device_ms"] / 1e3) / 1e9,
-                      "call_ms": (t1 - t0) * 1e3, "drain_ms": (t2 - t1) * 1e3,
-                      "drain_gbs": ii["payload_bytes"] / max(t2 - t1, 1e-9) / 1e9})
+                      "call_ms": (t1 - t0) * 1e3, "until_drained_ms": (t2 - t0) * 1e3,
+                      "e2e_payload_gbs": ii["payload_bytes"] / max(t2 - t0, 1e-9) / 1e9})
     # restart from the third image into zeroed memory, compare with a copy
     keep = [torch.empty(n, dtype=torch.uint8, device=dev) for n in sizes]
     rows = [(k.data_ptr(), p, n) for k, p, n in zip(keep, ptrs, sizes)]

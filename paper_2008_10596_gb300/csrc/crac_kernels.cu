@@ -534,6 +534,9 @@ constexpr int kScatterNT = 256;
 
 __global__ void __launch_bounds__(kScatterNT) scatter_kernel(const ScatterParams P) {
     constexpr int GT = 32;
+    // A resolution or bounds error found earlier on this stream (chain not
+    // covering the target, index out of range) leaves memory untouched.
+    if (*(volatile unsigned int *)P.err) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t S = 1ull << P.log2_chunk;
     const uint64_t n = P.j1 - P.j0;
@@ -1081,15 +1084,121 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
         const uint64_t off = (q & ((1ull << spc) - 1)) << log2Seg;
         if (off >= clen) continue;   // beyond the end of a short last chunk (warp-uniform)
         const uint32_t len = (uint32_t)umin64(1ull << log2Seg, clen - off);
+        // Direct mode (S <= 8 KiB, the warp sees the whole chunk): the baseline
+        // fingerprint is loaded before the chunk so that both latencies overlap.
+        uint64_t fo = 0;
+        const bool has = d.base_first != kNoBase;
+        if (spc == 0 && lane == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
         uint64_t sum = hash_seg(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S) + off, len, off >> 3,
                                 lane);
         sum = warp_sum(sum);
-        if (lane == 0) atomicAdd(acc + (c - P.c_begin), (unsigned long long)sum);
+        if (lane == 0) {
+            if (spc == 0) {
+                // The warp has seen the whole chunk: finalize here and leave only
+                // the dirty length for the compaction kernel.
+                const uint64_t fp = fp_finalize(sum, len);
+                P.fp_new[c] = fp;
+                acc[c - P.c_begin] = (!has || fo != fp) ? len : 0ull;
+            } else {
+                atomicAdd(acc + (c - P.c_begin), (unsigned long long)sum);
+            }
+        }
+    }
+}
+
+// When log2Seg == log2_chunk the hash kernel has already finalized every
+// chunk and left its dirty length in acc; only the compaction remains.
+// Hash kernel for chunks of 512 B..4 KiB: one warp iteration covers 8 KiB,
+// i.e. 8192/S whole chunks, one group of LPC = 32*S/8192 lanes per chunk (16
+// vectors per lane), so a warp keeps 8 KiB in flight whatever the chunk size.
+// Every chunk is finalized in place (direct mode: acc receives the dirty
+// length).
+template <int LPC>
+__device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned long long *__restrict__ acc,
+                                                uint64_t c, const CkptDesc &d_warp, uint64_t a_next, int li) {
+    const uint32_t log2S = P.log2_chunk;
+    uint64_t sum = 0, fo = 0;
+    uint32_t len = 0;
+    bool has = false;
+    CkptDesc d = d_warp;
+    if (c < P.c_end) {
+        if (c >= a_next) d = P.desc[find_alloc(P.desc, P.n_allocs, c)];   // segment crosses an allocation end
+        const uint64_t local = c - d.first_chunk;
+        const uint64_t rest = d.bytes - (local << log2S);
+        len = (uint32_t)umin64(rest, 1ull << log2S);
+        has = d.base_first != kNoBase;
+        if (li == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
+        const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S));
+        const uint32_t nv = len >> 4;
+        uint4 q[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t v = li + LPC * u;
+            if (v < nv) q[u] = __ldg(p + v);
+        }
+        uint64_t key = (2ull * (uint64_t)li + 1ull) * kK1;
+        constexpr uint64_t kStep = 2ull * LPC * kK1;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t v = li + LPC * u;
+            if (v < nv) {
+                sum += mixw(((uint64_t)q[u].y << 32) | q[u].x, key);
+                sum += mixw(((uint64_t)q[u].w << 32) | q[u].z, key + kK1);
+            }
+            key += kStep;
+        }
+        const uint32_t rem = len & 15u;
+        if (rem && (uint32_t)li == (nv % LPC)) {
+            const uint8_t *t = reinterpret_cast<const uint8_t *>(p + nv);
+            uint64_t w0 = 0, w1 = 0;
+            for (uint32_t b = 0; b < rem; ++b) {
+                const uint64_t byte = t[b];
+                if (b < 8) w0 |= byte << (8 * b);
+                else w1 |= byte << (8 * (b - 8));
+            }
+            const uint64_t kt = (2ull * nv + 1ull) * kK1;
+            sum += mixw(w0, kt);
+            if (rem > 8) sum += mixw(w1, kt + kK1);
+        }
+    }
+#pragma unroll
+    for (int o = LPC / 2; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (li == 0 && c < P.c_end) {
+        const uint64_t fp = fp_finalize(sum, len);
+        P.fp_new[c] = fp;
+        acc[c - P.c_begin] = (!has || fo != fp) ? len : 0ull;
+    }
+}
+
+template <int LPC>
+__global__ void __launch_bounds__(kHashNT, 2)
+split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t) {
+    constexpr int CPS = 32 / LPC;   // chunks per 8 KiB segment
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp_g = ((uint64_t)blockIdx.x * kHashNT + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * kHashNT) >> 5;
+    const uint64_t n_slots = (P.c_end - P.c_begin + CPS - 1) / CPS;
+    const uint64_t per = (n_slots + n_warps - 1) / n_warps;
+    uint64_t q = warp_g * per;
+    const uint64_t q_end = umin64(q + per, n_slots);
+    CkptDesc d{};
+    uint64_t a_next = 0;
+    bool have = false;
+    for (; q < q_end; ++q) {
+        const uint64_t c0 = P.c_begin + q * CPS;
+        if (!have || c0 >= a_next) {
+            const uint32_t a = find_alloc(P.desc, P.n_allocs, c0);
+            d = P.desc[a];
+            a_next = a + 1 < P.n_allocs ? P.desc[a + 1].first_chunk : ~0ull;
+            have = true;
+        }
+        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a_next, lane % LPC);
     }
 }
 
 __global__ void __launch_bounds__(kFinNT)
-split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t) {
+split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t log2Seg) {
+    const bool direct = log2Seg == P.log2_chunk;
     __shared__ uint32_t s_wcnt[32];
     __shared__ uint64_t s_wbytes[32];
     __shared__ uint64_t s_k0, s_d0;
@@ -1108,7 +1217,9 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
         if (tile >= P.n_tiles) break;
         const uint64_t c = P.c_begin + (uint64_t)tile * kFinNT + threadIdx.x;
         uint32_t dl = 0;
-        if (c < P.c_end) {
+        if (c < P.c_end && direct) {
+            dl = (uint32_t)acc[c - P.c_begin];
+        } else if (c < P.c_end) {
             const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
             const uint64_t local = c - d.first_chunk;
             const uint32_t len = (uint32_t)min(S, d.bytes - (local << log2S));
@@ -1202,6 +1313,72 @@ split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Chain resolution and restore on the device (R3 + R2 for device-resident
+// chains), over every piece of every image of the chain in one launch each.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t find_piece(const RestorePiece *__restrict__ p, uint32_t n, uint64_t e) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (p[mid].entry_base <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Target chunk of entry e, or ~0 when its allocation is not restored.
+__device__ __forceinline__ uint64_t restore_target(const RestoreParams &P, const RestorePiece &pc, uint64_t e,
+                                                   uint64_t *c_out, ScatterDesc *d_out) {
+    const uint64_t c = reinterpret_cast<const uint64_t *>(pc.idx)[e - pc.entry_base];
+    const ScatterDesc *dd = P.desc + pc.desc_off;
+    const ScatterDesc d = dd[find_scatter(dd, pc.n_desc, c)];
+    *c_out = c;
+    *d_out = d;
+    if (d.dst == 0) return ~0ull;
+    return d.tgt_first + (c - d.img_first);
+}
+
+__global__ void __launch_bounds__(256) restore_mark_kernel(const RestoreParams P) {
+    for (uint64_t e = (uint64_t)blockIdx.x * 256 + threadIdx.x; e < P.n_entries; e += (uint64_t)gridDim.x * 256) {
+        const RestorePiece pc = P.pieces[find_piece(P.pieces, P.n_pieces, e)];
+        uint64_t c;
+        ScatterDesc d;
+        const uint64_t tc = restore_target(P, pc, e, &c, &d);
+        if (tc == ~0ull) continue;
+        if (tc < P.n_owner) atomicMax(P.owner + tc, pc.image_index + 1u);
+        else atomicOr(P.err, kErrBounds);
+    }
+}
+
+__global__ void __launch_bounds__(256) restore_check_kernel(const RestoreParams P) {
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < P.n_owner; i += (uint64_t)gridDim.x * 256)
+        if (P.owner[i] == 0) atomicOr(P.err, kErrUncovered);
+}
+
+__global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const RestoreParams P) {
+    if (*(volatile unsigned int *)P.err) return;   // uncovered or out of range: memory untouched
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t S = 1ull << P.log2_chunk;
+    for (uint64_t e = (uint64_t)blockIdx.x * (kScatterNT / 32) + warp; e < P.n_entries;
+         e += (uint64_t)gridDim.x * (kScatterNT / 32)) {
+        const RestorePiece pc = P.pieces[find_piece(P.pieces, P.n_pieces, e)];
+        uint64_t c;
+        ScatterDesc d;
+        const uint64_t tc = restore_target(P, pc, e, &c, &d);
+        if (tc >= P.n_owner || P.owner[tc] != pc.image_index + 1u) continue;
+        const uint64_t local = c - d.img_first;
+        const uint64_t len = min(S, d.bytes - (local << P.log2_chunk));
+        const uint64_t o = reinterpret_cast<const uint64_t *>(pc.off)[e - pc.entry_base];
+        if (o + len > pc.bytes) {
+            if (lane == 0) atomicOr(P.err, kErrBounds);
+            continue;
+        }
+        copy_group<32>(reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk),
+                       reinterpret_cast<const uint8_t *>(pc.payload) + o, len, lane);
+    }
+}
+
 template <int NT, int WPC>
 cudaError_t launch_fused_t(const CkptParams &p, int grid, cudaStream_t s) {
     ckpt_fused_kernel<NT, WPC><<<grid, NT, 0, s>>>(p);
@@ -1243,6 +1420,15 @@ cudaError_t ckpt_tma_prepare() {
 }
 
 const void *split_hash_fn() { return reinterpret_cast<const void *>(&split_hash_kernel); }
+const void *split_hash_small_fn(int lanes_per_chunk) {
+    switch (lanes_per_chunk) {
+    case 2: return reinterpret_cast<const void *>(&split_hash_small_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&split_hash_small_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&split_hash_small_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&split_hash_small_kernel<16>);
+    default: return nullptr;
+    }
+}
 const void *split_finalize_fn() { return reinterpret_cast<const void *>(&split_finalize_kernel); }
 const void *split_gather_fn() { return reinterpret_cast<const void *>(&split_gather_kernel); }
 int split_hash_threads() { return kHashNT; }
@@ -1306,6 +1492,30 @@ cudaError_t launch_gather_range(const CkptDesc *d, uint32_t log2S, const uint64_
     if (max_entries == 0) return cudaSuccess;
     gather_range_kernel<<<grid, kRangeNT, 0, s>>>(d, log2S, idx, off, carry, idx_cap, staging,
                                                   staging_cap, ctrl);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_restore_mark(const RestoreParams &p, int grid, cudaStream_t s) {
+    if (p.n_entries == 0) return cudaSuccess;
+    restore_mark_kernel<<<grid, 256, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_restore_check(const RestoreParams &p, int grid, cudaStream_t s) {
+    if (p.n_owner == 0) return cudaSuccess;
+    restore_check_kernel<<<grid, 256, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_restore_scatter(const RestoreParams &p, int grid, cudaStream_t s) {
+    if (p.n_entries == 0) return cudaSuccess;
+    restore_scatter_kernel<<<grid, kScatterNT, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(1);
     return e;

@@ -26,6 +26,7 @@ struct CkptCtrl {
 static_assert(sizeof(CkptCtrl) == 64, "CkptCtrl layout");
 constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
 constexpr unsigned kErrBounds = 2u;    // an output index/offset exceeded its buffer
+constexpr unsigned kErrUncovered = 4u; // restore: a target chunk no image of the chain holds
 
 // Parameters of the fused batched pass over global chunks [c_begin, c_end).
 struct CkptParams {
@@ -106,6 +107,9 @@ cudaError_t ckpt_tma_prepare();   // raise the dynamic shared memory limit (once
 // must be zero before H; F uses cpt = split_finalize_threads() chunks per
 // tile and the look-back status words; G reads k from ctrl.
 const void *split_hash_fn();
+// Hash kernel for 512 B <= chunk < 8 KiB: lanes_per_chunk = 32 * chunk / 8192;
+// it finalizes every chunk itself, so finalize runs with log2Seg = log2_chunk.
+const void *split_hash_small_fn(int lanes_per_chunk);
 const void *split_finalize_fn();
 const void *split_gather_fn();
 int split_hash_threads();
@@ -126,6 +130,32 @@ cudaError_t launch_gather_range(const CkptDesc *d, uint32_t log2_chunk, const ui
                                 CkptCtrl *ctrl, int grid, cudaStream_t s);
 
 cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s);
+// One piece of a device-resident image in a multi-image restore: its chunk
+// list, offsets and payload, where its entries start in the combined entry
+// space, its image's position in the chain and its descriptor range.
+struct RestorePiece {
+    uint64_t idx, off, payload;   // device addresses
+    uint64_t k;                   // entries
+    uint64_t entry_base;          // first entry in the combined space
+    uint64_t bytes;               // payload bytes (window)
+    uint32_t image_index;         // chain position (oldest = 0)
+    uint32_t desc_off, n_desc, pad;
+};
+struct RestoreParams {
+    const RestorePiece *pieces;
+    uint32_t n_pieces;
+    uint32_t log2_chunk;
+    uint64_t n_entries;
+    const ScatterDesc *desc;      // all images' descriptors, RestorePiece::desc_off into it
+    uint32_t *owner;              // per target chunk: newest chain position + 1 (0 = none)
+    uint64_t n_owner;
+    unsigned int *err;
+};
+// Multi-image restore: mark owners for every entry of every piece (atomicMax,
+// so the newest image wins in any order), check coverage, scatter owned chunks.
+cudaError_t launch_restore_mark(const RestoreParams &p, int grid, cudaStream_t s);
+cudaError_t launch_restore_check(const RestoreParams &p, int grid, cudaStream_t s);
+cudaError_t launch_restore_scatter(const RestoreParams &p, int grid, cudaStream_t s);
 
 void count_launches(uint64_t n);
 uint64_t launches_so_far();

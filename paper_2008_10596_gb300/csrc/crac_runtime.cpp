@@ -308,7 +308,9 @@ struct crac_image {
     uint64_t lineage = 0, epoch = 0, parent_epoch = kNoParent;
     std::vector<ImgAlloc> allocs;
     uint64_t n_chunks = 0, k = 0, payload_bytes = 0;
-    Block fp_h, idx_h;              // pinned: fp[n_chunks], idx[k]
+    Block fp_h, idx_h;              // pinned: fp[n_chunks], idx[k] (device images: on demand)
+    Block fp_dev;                   // device images: fp[n_chunks] in device memory
+    bool host_tables = true;        // fp_h / idx_h hold the tables
     std::vector<Piece> pieces;
     crac_image *parent = nullptr;   // strong reference, set for delta images
     cudaEvent_t done = nullptr;     // drain complete
@@ -380,6 +382,7 @@ void img_unref(crac_image *im) {
         Arena &pa = pinned_arena();
         pa.free(im->fp_h);
         pa.free(im->idx_h);
+        if (im->fp_dev.region >= 0) device_arena(im->device).free(im->fp_dev);
         for (Piece &p : im->pieces) {
             pa.free(p.host);
             if (p.dev.region >= 0 || p.idx_dev.region >= 0 || p.off_dev.region >= 0) {
@@ -393,6 +396,23 @@ void img_unref(crac_image *im) {
         delete im;
         im = parent;
     }
+}
+
+// Host copies of a device image's fingerprint table and chunk list (made on
+// the first request: serialization, or a restart chain resolved on the host).
+crac_status_t img_host_tables(crac_image *im) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (im->host_tables) return CRAC_OK;
+    TRY(img_wait(im, 0));
+    Arena &pa = pinned_arena();
+    if (im->n_chunks) TRY(pa.alloc(im->n_chunks * 8, &im->fp_h));
+    if (im->k) TRY(pa.alloc(im->k * 8, &im->idx_h));
+    DeviceGuard g(im->device);
+    if (im->n_chunks) CK(cudaMemcpy(im->fp_h.p, im->fp_dev.p, im->n_chunks * 8, cudaMemcpyDeviceToHost));
+    for (const Piece &pc : im->pieces)
+        if (pc.k) CK(cudaMemcpy(im->idx_h.p + pc.k0 * 8, pc.idx_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    im->host_tables = true;
+    return CRAC_OK;
 }
 
 // Parent of a delta: the direct link if set, else a live image with the same
@@ -451,6 +471,8 @@ struct crac_ctx {
     int fp_cur = 0;
     bool base_valid = false;
     std::unordered_map<uint64_t, uint64_t> base_first;   // alloc id -> first chunk in fp[fp_cur]
+    std::unordered_map<uint64_t, uint64_t> prev_base_first;   // autotuner shadows: the baseline before the last
+    bool prev_base_valid = false;                             // committed trial pass (still in fp[1 - fp_cur])
     // pass scratch
     DevBuf desc, work, idx, off, staging, lens, carry;
     HostBuf desc_h, ctrl_h;
@@ -472,6 +494,7 @@ struct crac_ctx {
     cudaGraphExec_t sgexec = nullptr;
     cudaGraphNode_t s_memset = nullptr, s_k[3] = {nullptr, nullptr, nullptr}, s_copy = nullptr;
     cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};   // around each split-pass kernel
+    const void *s_hash_fn = nullptr;
     crac_pass_info_t last{};
     crac_restart_info_t last_restart{};
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
@@ -690,8 +713,8 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
 
 // Build (or update) the split-pass graph and launch it.
 crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
-                                 uint32_t log2Seg, const int grids[3], cudaStream_t s) {
-    const void *fns[3] = {split_hash_fn(), split_finalize_fn(), split_gather_fn()};
+                                 uint32_t log2Seg, const void *hash_fn, const int grids[3], cudaStream_t s) {
+    const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn()};
     const int thr[3] = {split_hash_threads(), split_finalize_threads(), split_gather_threads()};
     CkptParams Pc = P;
     unsigned long long *accv = acc;
@@ -712,7 +735,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     mp.elementSize = 4;
     mp.width = work_bytes / 4;
     mp.height = 1;
-    bool ok = c->sgexec != nullptr;
+    bool ok = c->sgexec != nullptr && c->s_hash_fn == hash_fn;
     if (ok) {
         ok = cudaGraphExecMemsetNodeSetParams(c->sgexec, c->s_memset, &mp) == cudaSuccess;
         for (int i = 0; ok && i < 3; ++i)
@@ -741,6 +764,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
                                     cudaMemcpyDeviceToHost));
         CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
+        c->s_hash_fn = hash_fn;
     }
     CK(cudaEventRecord(c->ev_t0, s));
     CK(cudaGraphLaunch(c->sgexec, s));
@@ -770,7 +794,10 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         const size_t status_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
         const size_t work_bytes = status_bytes + 8 * nseg;
         TRY(ensure_dev(c->work, work_bytes));
+        // 512 B..4 KiB chunks: several whole chunks per warp iteration.
+        const bool small = c->log2S >= 9 && c->log2S < 13;
         const uint32_t log2Seg = std::min<uint32_t>(c->log2S, 13);
+        const void *hash_fn = small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn();
         CkptParams P{};
         P.desc = desc_dev;
         P.n_allocs = (uint32_t)c->allocs.size();
@@ -792,13 +819,14 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
         unsigned long long *acc = (unsigned long long *)((uint8_t *)c->work.p + status_bytes);
-        const uint64_t n_slots = nseg << (c->log2S - log2Seg);
+        const uint64_t n_slots = small ? (nseg + (8192u >> c->log2S) - 1) / (8192u >> c->log2S)
+                                       : nseg << (c->log2S - log2Seg);
         const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>(
-                           (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(split_hash_fn(), split_hash_threads())));
+                           (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(hash_fn, split_hash_threads())));
         const int gf = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2);
         const int gg = c->sm_count * 8;
         const int grids[3] = {gh, gf, gg};
-        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, grids, s));
+        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, s));
         c->last.grid = (uint32_t)gh;
         c->last.chunks_per_tile = cptF;
         c->last.warps_per_chunk = 0;
@@ -957,9 +985,15 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         return code;
     };
 
+    const bool dev_res = c->cfg.image_residency == CRAC_RESIDENCY_DEVICE;
+    im->host_tables = !dev_res;
     if (n > 0) {
-        st = pa.alloc(n * 8, &im->fp_h);
-        if (st == CRAC_OK) st = pa.alloc(n * 8, &im->idx_h);
+        if (dev_res) {
+            st = da.alloc(n * 8, &im->fp_dev);
+        } else {
+            st = pa.alloc(n * 8, &im->fp_h);
+            if (st == CRAC_OK) st = pa.alloc(n * 8, &im->idx_h);
+        }
         if (st != CRAC_OK) return fail(st);
         // fingerprint tables and descriptors
         // Only the output table may grow: the baseline table keeps the previous
@@ -1069,7 +1103,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                 da.shrink(pc.idx_dev, ctrl.k * 8);
                 da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
             }
-            if (e == cudaSuccess && ctrl.k)
+            if (e == cudaSuccess && ctrl.k && host_res)
                 e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
             if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
             im->pieces.push_back(pc);
@@ -1077,13 +1111,22 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             k_base += ctrl.k;
             d_base += ctrl.D;
         }
-        cudaError_t e = cudaMemcpyAsync(im->fp_h.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToHost, c->side);
-        if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        cudaError_t e;
+        if (host_res) {
+            e = cudaMemcpyAsync(im->fp_h.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        } else {
+            // Device image: its tables stay in device memory; done once the
+            // fingerprint table has its own copy.
+            e = cudaMemcpyAsync(im->fp_dev.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaEventRecord(im->done, s);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, s);
+        }
         if (e != cudaSuccess) return fail(cuda_status(e));
         im->k = k_base;
         im->payload_bytes = d_base;
-        pa.shrink(im->idx_h, k_base * 8);
+        if (host_res) pa.shrink(im->idx_h, k_base * 8);
         c->last.k = k_base;
         c->last.payload_bytes = d_base;
         c->last.segments = (uint32_t)segs.size();
@@ -1122,6 +1165,121 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
 // Restart
 // ---------------------------------------------------------------------------
 
+// After a successful restore: the registry takes the image's identities and
+// its fingerprints (already in fp[fp_cur]) become the baseline.
+void restart_commit(crac_ctx *c, crac_image *img) {
+    c->base_first.clear();
+    for (size_t a = 0; a < img->allocs.size(); ++a) {
+        c->allocs[a].id = img->allocs[a].id;
+        c->next_id = std::max(c->next_id, img->allocs[a].id + 1);
+        c->base_first[img->allocs[a].id] = img->allocs[a].first_chunk;
+    }
+    c->base_valid = true;
+    c->lineage = img->lineage;
+    c->epoch_max = std::max(c->epoch_max, img->epoch);
+    c->parent_epoch = img->epoch;
+    img_ref(img);
+    img_unref(c->parent);
+    c->parent = img;
+}
+
+// Image allocation -> target allocation (-1: not restored), by allocation id.
+std::vector<int64_t> map_allocs(const crac_image *im, const crac_image *tgt,
+                                const std::unordered_map<uint64_t, size_t> &tpos) {
+    std::vector<int64_t> m(im->allocs.size());
+    for (size_t a = 0; a < im->allocs.size(); ++a) {
+        auto it = tpos.find(im->allocs[a].id);
+        m[a] = (it == tpos.end() || tgt->allocs[it->second].bytes != im->allocs[a].bytes) ? -1 : (int64_t)it->second;
+    }
+    return m;
+}
+
+// Restore from a chain held entirely in device memory, resolved on the device
+// in three launches over every piece of every image of the chain: owner
+// marks (the newest image wins), a coverage check, owner-filtered scatter --
+// no host round trip before them.  An uncovered chunk stops the scatter
+// (memory untouched) and reports IMAGE_MISMATCH.
+crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<crac_image *> &chain, cudaStream_t s) {
+    DeviceGuard g(c->device);
+    const uint64_t nt = img->n_chunks;
+    std::unordered_map<uint64_t, size_t> tpos;
+    for (size_t a = 0; a < img->allocs.size(); ++a) tpos[img->allocs[a].id] = a;
+    if (fault_hit(CRAC_FAULT_H2D)) {
+        t_last_cuda = (int)cudaErrorLaunchFailure;
+        return CRAC_ERR_CUDA;
+    }
+    if (!s) CK(cudaDeviceSynchronize());
+    size_t total_desc = 0, n_pieces = 0;
+    for (crac_image *im : chain) {
+        total_desc += im->allocs.size();
+        for (const Piece &pc : im->pieces) n_pieces += pc.k ? 1 : 0;
+    }
+    const size_t desc_bytes = round_up(total_desc * sizeof(ScatterDesc), 256);
+    const size_t piece_bytes = round_up(std::max<size_t>(n_pieces, 1) * sizeof(RestorePiece), 256);
+    TRY(ensure_dev(c->owner, std::max<uint64_t>(nt, 1) * 4));
+    TRY(ensure_dev(c->sdesc, desc_bytes + piece_bytes));
+    TRY(ensure_host(c->sdesc_h, desc_bytes + piece_bytes));
+    TRY(ensure_dev(c->serr, 256));
+    TRY(ensure_dev(c->fp[1 - c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
+    if (c->ev_last) CK(cudaEventSynchronize(c->ev_last));   // pinned descriptor scratch reuse
+    ScatterDesc *sdh = (ScatterDesc *)c->sdesc_h.p;
+    RestorePiece *rph = (RestorePiece *)((uint8_t *)c->sdesc_h.p + desc_bytes);
+    size_t dpos = 0, ppos = 0;
+    uint64_t entries = 0;
+    for (size_t i = 0; i < chain.size(); ++i) {
+        const crac_image *im = chain[i];
+        const std::vector<int64_t> m = map_allocs(im, img, tpos);
+        const size_t d0 = dpos;
+        for (size_t a = 0; a < im->allocs.size(); ++a, ++dpos)
+            sdh[dpos] = ScatterDesc{im->allocs[a].first_chunk, im->allocs[a].bytes,
+                                    m[a] < 0 ? 0 : img->allocs[m[a]].first_chunk, m[a] < 0 ? 0 : c->allocs[m[a]].ptr,
+                                    0, {0, 0, 0}};
+        for (const Piece &pc : im->pieces) {
+            if (!pc.k) continue;
+            rph[ppos++] = RestorePiece{(uint64_t)pc.idx_dev.p, (uint64_t)pc.off_dev.p, (uint64_t)pc.dev.p, pc.k,
+                                       entries, pc.bytes, (uint32_t)i, (uint32_t)d0, (uint32_t)im->allocs.size(), 0};
+            entries += pc.k;
+        }
+    }
+    for (crac_image *im : chain) CK(cudaStreamWaitEvent(s, im->done, 0));
+    CK(cudaStreamWaitEvent(s, c->ev_last, 0));
+    CK(cudaMemsetAsync(c->serr.p, 0, 256, s));
+    if (nt) CK(cudaMemsetAsync(c->owner.p, 0, nt * 4, s));
+    CK(cudaMemcpyAsync(c->sdesc.p, c->sdesc_h.p, desc_bytes + ppos * sizeof(RestorePiece), cudaMemcpyHostToDevice, s));
+    crac_restart_info_t ri{};
+    ri.chain_length = ri.images_used = (uint32_t)chain.size();
+    for (const ImgAlloc &a : img->allocs) ri.restored_bytes += a.bytes;
+    ri.entries_scanned = entries;
+    ri.scatter_launches = entries ? 1 : 0;
+    RestoreParams P{};
+    P.pieces = (const RestorePiece *)((uint8_t *)c->sdesc.p + desc_bytes);
+    P.n_pieces = (uint32_t)ppos;
+    P.log2_chunk = c->log2S;
+    P.n_entries = entries;
+    P.desc = (const ScatterDesc *)c->sdesc.p;
+    P.owner = (uint32_t *)c->owner.p;
+    P.n_owner = nt;
+    P.err = (unsigned int *)c->serr.p;
+    const uint64_t grid = (uint64_t)c->sm_count * 8;
+    CK(cudaEventRecord(c->ev_r0, s));
+    CK(launch_restore_mark(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 255) / 256, grid)), s));
+    CK(launch_restore_check(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
+    CK(launch_restore_scatter(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 7) / 8, grid)), s));
+    CK(cudaEventRecord(c->ev_r1, s));
+    if (nt) CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, img->fp_dev.p, nt * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_last, s));
+    CK(cudaEventSynchronize(c->ev_last));
+    const unsigned err = *(const unsigned *)c->serr_h.p;
+    if (err & kErrUncovered) return CRAC_ERR_IMAGE_MISMATCH;
+    if (err) return CRAC_ERR_CORRUPT;
+    cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
+    c->last_restart = ri;
+    c->fp_cur = 1 - c->fp_cur;
+    restart_commit(c, img);
+    return CRAC_OK;
+}
+
 crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     if (!img) return CRAC_ERR_INVALID_ARG;
     if (img->state.load() < 0) return img->state.load();
@@ -1141,7 +1299,15 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
         cur = p;
     }
     std::reverse(chain.begin(), chain.end());
-    for (crac_image *im : chain) TRY(img_wait(im, 0));
+    bool all_dev = true;
+    for (crac_image *im : chain)
+        all_dev = all_dev && im->residency == CRAC_RESIDENCY_DEVICE && im->device == c->device &&
+                  (im->n_chunks == 0 || im->fp_dev.region >= 0);
+    if (all_dev) return restart_device(c, img, chain, s);
+    for (crac_image *im : chain) {
+        TRY(img_wait(im, 0));
+        TRY(img_host_tables(im));
+    }
 
     DeviceGuard g(c->device);
     const uint32_t log2S = c->log2S;
@@ -1345,29 +1511,20 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
             j0 = j1;
         }
     }
-    // Baseline = the image's fingerprints; registry takes the image's identities.
-    TRY(ensure_dev(c->fp[c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
-    if (nt) CK(cudaMemcpyAsync(c->fp[c->fp_cur].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
+    // The image's fingerprints go to the spare table, which becomes the
+    // baseline only once the restore has succeeded.
+    TRY(ensure_dev(c->fp[1 - c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
     CK(cudaEventRecord(c->ev_r1, s));
+    if (nt) CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
     if (*(const unsigned *)c->serr_h.p) return CRAC_ERR_CORRUPT;
     cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
     c->last_restart = ri;
-    c->base_first.clear();
-    for (size_t a = 0; a < na; ++a) {
-        c->allocs[a].id = img->allocs[a].id;
-        c->next_id = std::max(c->next_id, img->allocs[a].id + 1);
-        c->base_first[img->allocs[a].id] = img->allocs[a].first_chunk;
-    }
-    c->base_valid = true;
-    c->lineage = img->lineage;
-    c->epoch_max = std::max(c->epoch_max, img->epoch);
-    c->parent_epoch = img->epoch;
-    img_ref(img);
-    img_unref(c->parent);
-    c->parent = img;
+    c->fp_cur = 1 - c->fp_cur;
+    restart_commit(c, img);
+    (void)na;
     return CRAC_OK;
 }
 
@@ -1431,6 +1588,8 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     }
     CK(cudaEventRecord(c->ev_last, s));
     if (commit) {
+        c->prev_base_first = c->base_first;
+        c->prev_base_valid = c->base_valid;
         c->fp_cur = 1 - c->fp_cur;
         c->base_first.clear();
         for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
@@ -1518,7 +1677,14 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
     }
     crac_ctx *t = c->tune_ctx[best];
     const uint32_t S = 1u << t->log2S;
-    // Pass kernels at the chosen size, each against the shadow's baseline.
+    // Pass kernels at the chosen size, each against the baseline before the
+    // last observation (still in the other fingerprint buffer), so that they
+    // see the last round's dirty set rather than an unchanged memory.
+    if (t->prev_base_valid) {
+        t->fp_cur = 1 - t->fp_cur;
+        t->base_first = t->prev_base_first;
+        t->base_valid = true;
+    }
     float vms[4] = {0, 0, 0, 0};
     uint32_t best_v = CRAC_PASS_SPLIT;
     const uint32_t saved = t->cfg.pass_kernel;
@@ -2046,6 +2212,7 @@ crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t 
     if (!dst) return CRAC_OK;
     if (cap < total) return CRAC_ERR_INVALID_ARG;
     TRY(img_wait(im, 0));
+    TRY(img_host_tables(im));
     uint8_t *p = (uint8_t *)dst;
     std::memcpy(p, "CRACIMG1", 8);
     p += 8;

@@ -44,9 +44,10 @@ def test_failed_checkpoint_leaves_state(step, code, kern):
         h.close()
 
 
-def test_failed_restart_leaves_memory():
+@pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
+def test_failed_restart_leaves_memory(residency):
     S = 4096
-    h = Harness(S, lineage=62)
+    h = Harness(S, lineage=62, image_residency=residency)
     try:
         b = h.add(50000, seed=3)
         img, _, _ = h.checkpoint()

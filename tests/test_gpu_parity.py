@@ -104,13 +104,17 @@ def test_work_split_variants_identical(cpt, wpc):
         h.close()
 
 
-@pytest.mark.parametrize("S", [1 * KIB, 2 * KIB, 8 * KIB, 16 * KIB, 32 * KIB, 64 * KIB])
-def test_tma_chunk_sizes_ragged(S):
-    """The TMA pass at every chunk size it takes (1..64 chunks per 64 KiB tile,
-    1..8 warps per chunk), with ragged allocation ends that shift later
-    chunks off 16-byte alignment in the staging buffer."""
+@pytest.mark.parametrize("S,kern", [(s, C.CRAC_PASS_TMA) for s in (1 * KIB, 2 * KIB, 8 * KIB, 16 * KIB,
+                                                                   32 * KIB, 64 * KIB)] +
+                         [(s, C.CRAC_PASS_SPLIT) for s in (256, 512, 1 * KIB, 2 * KIB, 8 * KIB, 16 * KIB)])
+def test_chunk_sizes_ragged(S, kern):
+    """Every chunk-size regime of the TMA pass (1..64 chunks per 64 KiB tile,
+    1..8 warps per chunk) and of the split pass (several chunks per warp
+    iteration below 8 KiB, one whole chunk at 8 KiB, segments above), with
+    ragged allocation ends that shift later chunks off 16-byte alignment in
+    the staging buffer and segments that straddle allocation ends."""
     sizes = [S * 37 + 3, 5, S * 64, 4097, S * 3 + 16, 777777, S + 9]
-    h = Harness(S, lineage=300 + S // KIB, pass_kernel=C.CRAC_PASS_TMA)
+    h = Harness(S, lineage=300 + S // 256, pass_kernel=kern)
     try:
         for i, n in enumerate(sizes):
             h.add(n, seed=90 + i)
@@ -159,6 +163,11 @@ def test_launch_modes_and_residency(mode):
         h.restart(img3)
         for b, w in zip(h.bufs, want):
             assert np.array_equal(b.read(), w)
+        # the restored image is the baseline: an unmodified checkpoint is empty
+        _, lib4, ora4 = h.checkpoint()
+        assert lib4 == ora4 and O.parse_image(lib4).k == 0
+        info = C.crac_ctx_last_restart(h.ctx)
+        assert info["chain_length"] == 3 and info["restored_bytes"] == sum(sizes)
         if mode == "per_alloc":
             info = C.crac_ctx_last_pass(h.ctx)
             assert info["kernel_launches"] == 3 * len(sizes)
