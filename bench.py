@@ -683,7 +683,7 @@ def run_config5(args):
         bufs = [torch.randn(n // 4, generator=g, device=dev).view(torch.uint8) for n in sizes]
         stream = torch.cuda.Stream(dev)
         ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=5000 + i, device=0,
-                                                      reserve_host_bytes=int(1.8 * total) if i == 0 else 0))
+                                                      reserve_host_bytes=int(2.0 * total) if i == 0 else 0))
         for b in bufs:
             C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
         first = W.chunk_layout(sizes, S)
@@ -732,10 +732,12 @@ def run_config5(args):
             p = procs[i]
             with lock:
                 if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
-                    p["images"].append(r["image"])
+                    # keep only the latest image: its chain holds what a restart
+                    # needs, and each FULL checkpoint frees the older history
+                    for old in p["images"]:
+                        C.crac_image_release(old)
+                    p["images"] = [r["image"]]
                     p["latest"] = r["image"]
-                    if len(p["images"]) > 6:       # history beyond the last few images is dropped
-                        C.crac_image_release(p["images"].pop(0))
                 results[t] = (kind, r, p["bytes"])
 
     import queue as _q
@@ -767,13 +769,21 @@ def run_config5(args):
     stats = C.crac_server_stats(server)
     C.crac_server_destroy(server)
     lat = {"checkpoint": [], "restart": []}
+    wait = {"checkpoint": [], "restart": []}
+    serv = {"checkpoint": [], "restart": []}
+    full_serv = []
     scanned = payload = 0
     fails = 0
     for kind, r, nb in results.values():
         if r["status"] != 0:
             fails += 1
             continue
-        lat["checkpoint" if kind == 0 else "restart"].append((r["t_done"] - r["t_arrival"]) * 1e3)
+        key = "checkpoint" if kind == 0 else "restart"
+        lat[key].append((r["t_done"] - r["t_arrival"]) * 1e3)
+        wait[key].append((r["t_admit"] - r["t_arrival"]) * 1e3)
+        serv[key].append((r["t_done"] - r["t_admit"]) * 1e3)
+        if kind == 0 and r["payload_bytes"] >= nb:
+            full_serv.append((r["t_done"] - r["t_admit"]) * 1e3)
         scanned += nb
         payload += r["payload_bytes"]
     wall = t_end - t0
@@ -788,6 +798,11 @@ def run_config5(args):
             "requests": n_req, "failed": fails, "wall_s": wall,
             "latency_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)} for k, v in lat.items()},
             "latency_all_ms": {"p50": pct(allv, 50), "p99": pct(allv, 99)},
+            "queue_wait_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99)} for k, v in wait.items()},
+            "service_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "max": max(v) if v else None}
+                           for k, v in serv.items()},
+            "full_checkpoint_service_ms": {"p50": pct(full_serv, 50), "p99": pct(full_serv, 99), "n": len(full_serv)},
+            "memory": C.crac_memory_stats(),
             "offered_gbs": sum(procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
             "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
             "server": stats}

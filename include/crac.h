@@ -412,6 +412,22 @@ CRAC_API int crac_last_cuda_error(void);
  * nodes included). */
 CRAC_API uint64_t crac_kernel_launches(void);
 
+/* Image memory held by the library's arenas (process-wide). */
+typedef struct crac_memory_stats {
+    uint64_t host_region_bytes;     /* pinned host memory obtained from CUDA */
+    uint64_t host_used_bytes;       /* of which carved out for live images */
+    uint64_t device_region_bytes;   /* device memory obtained for device images */
+    uint64_t device_used_bytes;
+    uint32_t host_regions, device_regions;
+    uint32_t host_grow_events;      /* cudaHostAlloc calls made on the request path after
+                                       start-up reservations (background growth, which
+                                       starts once the pinned arena is 80% used, is not
+                                       counted) */
+    uint32_t device_grow_events;
+} crac_memory_stats_t;
+
+CRAC_API crac_status_t crac_memory_stats(crac_memory_stats_t *out);
+
 /* Managed-memory helpers for callers without their own (e.g. PyTorch, which
  * does not allocate managed memory): cudaMallocManaged / cudaFree. */
 CRAC_API crac_status_t crac_alloc_managed(size_t bytes, void **out);

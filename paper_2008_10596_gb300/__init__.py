@@ -61,7 +61,7 @@ EXPORTED = [
     "crac_image_release", "crac_status_str", "crac_last_cuda_error", "crac_kernel_launches",
     "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault", "crac_pass_noalloc",
     "crac_ctx_tune_observe", "crac_ctx_tune_apply", "crac_ctx_last_restart", "crac_time_now", "crac_server_create",
-    "crac_server_destroy", "crac_server_submit", "crac_server_wait", "crac_server_stats",
+    "crac_server_destroy", "crac_server_submit", "crac_server_wait", "crac_server_stats", "crac_memory_stats",
 ]
 CRAC_NOALLOC_MAX_TILES = 32768
 
@@ -149,6 +149,13 @@ class CracServerStats(ctypes.Structure):
                 ("staging_budget", ctypes.c_uint64)]
 
 
+class CracMemoryStats(ctypes.Structure):
+    _fields_ = [("host_region_bytes", ctypes.c_uint64), ("host_used_bytes", ctypes.c_uint64),
+                ("device_region_bytes", ctypes.c_uint64), ("device_used_bytes", ctypes.c_uint64),
+                ("host_regions", ctypes.c_uint32), ("device_regions", ctypes.c_uint32),
+                ("host_grow_events", ctypes.c_uint32), ("device_grow_events", ctypes.c_uint32)]
+
+
 CRAC_REQ_CHECKPOINT = 0
 CRAC_REQ_RESTART = 1
 PREPARE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -185,6 +192,7 @@ _sigs = {
     "crac_ctx_tune_apply": (_st, [_vp, _vp, ctypes.c_double, ctypes.POINTER(CracTuneResult)]),
     "crac_ctx_last_restart": (_st, [_vp, ctypes.POINTER(CracRestartInfo)]),
     "crac_time_now": (ctypes.c_double, []),
+    "crac_memory_stats": (_st, [ctypes.POINTER(CracMemoryStats)]),
     "crac_server_create": (_st, [ctypes.POINTER(CracServerConfig), ctypes.POINTER(_vp)]),
     "crac_server_destroy": (_st, [_vp]),
     "crac_server_submit": (_st, [_vp, _vp, ctypes.c_uint32, _vp, _vp, PREPARE_FN, _vp, ctypes.c_double,
@@ -283,6 +291,12 @@ def crac_ctx_last_restart(ctx: int) -> dict:
     info = CracRestartInfo()
     _check(_lib.crac_ctx_last_restart(ctx, ctypes.byref(info)), "crac_ctx_last_restart")
     return {f: getattr(info, f) for f, _ in CracRestartInfo._fields_ if f != "reserved"}
+
+
+def crac_memory_stats() -> dict:
+    st = CracMemoryStats()
+    _check(_lib.crac_memory_stats(ctypes.byref(st)), "crac_memory_stats")
+    return {f: getattr(st, f) for f, _ in CracMemoryStats._fields_}
 
 
 def crac_time_now() -> float:

@@ -139,6 +139,9 @@ struct Block {
 class Arena {
   public:
     Arena(bool device, int dev, uint64_t quantum) : device_(device), dev_(dev), quantum_(quantum) {}
+    ~Arena() {
+        if (grower_.joinable()) grower_.join();
+    }
     // Make sure at least `bytes` are free in one region (grows the arena once,
     // so that later image allocations need no cudaMalloc / cudaHostAlloc).
     crac_status_t reserve(uint64_t bytes) {
@@ -155,9 +158,12 @@ class Arena {
             uint64_t off;
             if (regions_[r].ra.alloc(len, &off)) {
                 *b = Block{regions_[r].base + off, len, (int)r, off};
+                used_ += len;
+                maybe_pregrow_locked();
                 return CRAC_OK;
             }
         }
+        grows_++;
         uint64_t sz = std::max(len, quantum_);
         void *p = nullptr;
         cudaError_t e;
@@ -176,16 +182,19 @@ class Arena {
             return CRAC_ERR_OOM;
         }
         regions_.push_back(Region{(uint8_t *)p, sz, RangeAlloc(sz)});
+        total_ += sz;
         const int r = (int)regions_.size() - 1;
         uint64_t off = 0;
         regions_[r].ra.alloc(len, &off);
         *b = Block{regions_[r].base + off, len, r, off};
+        used_ += len;
         return CRAC_OK;
     }
     void free(Block &b) {
         if (b.region < 0) return;
         std::lock_guard<std::mutex> lk(mu_);
         regions_[b.region].ra.release(b.off, b.len);
+        used_ -= b.len;
         b = Block{};
     }
     void shrink(Block &b, uint64_t new_len) {
@@ -194,7 +203,43 @@ class Arena {
         if (new_len >= b.len) return;
         std::lock_guard<std::mutex> lk(mu_);
         regions_[b.region].ra.release(b.off + new_len, b.len - new_len);
+        used_ -= b.len - new_len;
         b.len = new_len;
+    }
+    // Pinned memory takes a long time to obtain (page pinning), so once the
+    // pinned arena is 80% used a background thread adds a region of a quarter
+    // of its size (at least 1 GiB): a steady workload then rarely pins memory
+    // on the request path.
+    void maybe_pregrow_locked() {
+        if (device_ || growing_ || total_ == 0 || used_ * 5 < total_ * 4) return;
+        if (grower_.joinable()) grower_.join();
+        growing_ = true;
+        const uint64_t sz = std::max<uint64_t>(total_ / 4, 1ull << 30);
+        grower_ = std::thread([this, sz] {
+            void *p = nullptr;
+            const cudaError_t e = cudaHostAlloc(&p, sz, cudaHostAllocPortable);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (e == cudaSuccess) {
+                regions_.push_back(Region{(uint8_t *)p, sz, RangeAlloc(sz)});
+                total_ += sz;
+                pregrows_++;
+            } else {
+                cudaGetLastError();
+            }
+            growing_ = false;
+        });
+    }
+    // Growth after a reservation counts from here on.
+    void mark_reserved() {
+        std::lock_guard<std::mutex> lk(mu_);
+        grows_ = 0;
+    }
+    void stats(uint64_t *total, uint64_t *used, uint32_t *regions, uint32_t *grows) {
+        std::lock_guard<std::mutex> lk(mu_);
+        *total = total_;
+        *used = used_;
+        *regions = (uint32_t)regions_.size();
+        *grows = grows_;
     }
 
   private:
@@ -208,6 +253,10 @@ class Arena {
     uint64_t quantum_;
     std::mutex mu_;
     std::vector<Region> regions_;
+    uint64_t total_ = 0, used_ = 0;
+    uint32_t grows_ = 0, pregrows_ = 0;
+    bool growing_ = false;
+    std::thread grower_;
 };
 
 std::mutex g_arena_mu;
@@ -556,8 +605,14 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     CK(cudaEventCreate(&c->ev_r1));
     TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
     TRY(ensure_host(c->serr_h, 256));
-    if (c->cfg.reserve_host_bytes) TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
-    if (c->cfg.reserve_device_bytes) TRY(device_arena(dev).reserve(c->cfg.reserve_device_bytes));
+    if (c->cfg.reserve_host_bytes) {
+        TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
+        pinned_arena().mark_reserved();
+    }
+    if (c->cfg.reserve_device_bytes) {
+        TRY(device_arena(dev).reserve(c->cfg.reserve_device_bytes));
+        device_arena(dev).mark_reserved();
+    }
     c->cuda_ready = true;
     return CRAC_OK;
 }
@@ -2345,6 +2400,23 @@ const char *crac_status_str(crac_status_t s) {
 }
 
 int crac_last_cuda_error(void) { return t_last_cuda; }
+
+crac_status_t crac_memory_stats(crac_memory_stats_t *out) {
+    if (!out) return CRAC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    pinned_arena().stats(&out->host_region_bytes, &out->host_used_bytes, &out->host_regions, &out->host_grow_events);
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    for (auto &kv : g_dev_arenas) {
+        uint64_t t, u;
+        uint32_t r, gcount;
+        kv.second->stats(&t, &u, &r, &gcount);
+        out->device_region_bytes += t;
+        out->device_used_bytes += u;
+        out->device_regions += r;
+        out->device_grow_events += gcount;
+    }
+    return CRAC_OK;
+}
 
 uint64_t crac_kernel_launches(void) { return launches_so_far(); }
 
