@@ -517,7 +517,7 @@ def run_config3(args):
         return len(rows)
 
     ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3, device=0,
-                                                  reserve_host_bytes=int(1.6 * sum(sizes))))
+                                                  reserve_host_bytes=int(2.2 * sum(sizes))))
     for ptr, n, k in zip(ptrs, sizes, kinds):
         C.crac_ctx_register_alloc(ctx, ptr, n, k)
     B = sum(sizes)

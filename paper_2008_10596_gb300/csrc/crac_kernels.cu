@@ -1017,7 +1017,7 @@ constexpr int kGatherNT = 256;
 // Partial CRAC-FP64 sum of a segment (<= 8 KiB) whose first word is word j0
 // of its chunk, over the lanes of one warp.
 __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, uint32_t len, uint64_t j0,
-                                             int lane) {
+                                             int lane, uint4 *__restrict__ copy_to = nullptr) {
     const uint4 *p = reinterpret_cast<const uint4 *>(src);
     const uint32_t nv = len >> 4;
     constexpr int U = 16;
@@ -1026,6 +1026,13 @@ __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, ui
     for (int u = 0; u < U; ++u) {
         const uint32_t v = lane + 32u * u;
         if (v < nv) q[u] = __ldg(p + v);
+    }
+    if (copy_to) {   // FULL checkpoint: the vectors also go straight to staging
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t v = lane + 32u * u;
+            if (v < nv) __stcs(copy_to + v, q[u]);
+        }
     }
     uint64_t acc = 0;
     uint64_t key = (j0 + 2ull * (uint64_t)lane + 1ull) * kK1;
@@ -1089,8 +1096,14 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
         uint64_t fo = 0;
         const bool has = d.base_first != kNoBase;
         if (spc == 0 && lane == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
-        uint64_t sum = hash_seg(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S) + off, len, off >> 3,
-                                lane);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S) + off;
+        uint4 *copy_to = nullptr;
+        if (P.full_copy) {   // FULL checkpoint: the segment's final staging offset is known
+            const uint64_t o = P.alloc_prefix[a] + (local << log2S) + off - P.seg_base;
+            if (o + len <= P.staging_cap) copy_to = reinterpret_cast<uint4 *>(P.staging + o);
+            else if (lane == 0) atomicOr(&P.ctrl->err, kErrBounds);
+        }
+        uint64_t sum = hash_seg(src, len, off >> 3, lane, copy_to);
         sum = warp_sum(sum);
         if (lane == 0) {
             if (spc == 0) {
@@ -1115,14 +1128,19 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
 // length).
 template <int LPC>
 __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned long long *__restrict__ acc,
-                                                uint64_t c, const CkptDesc &d_warp, uint64_t a_next, int li) {
+                                                uint64_t c, const CkptDesc &d_warp, uint32_t a_warp,
+                                                uint64_t a_next, int li) {
     const uint32_t log2S = P.log2_chunk;
     uint64_t sum = 0, fo = 0;
     uint32_t len = 0;
     bool has = false;
     CkptDesc d = d_warp;
+    uint32_t a = a_warp;
     if (c < P.c_end) {
-        if (c >= a_next) d = P.desc[find_alloc(P.desc, P.n_allocs, c)];   // segment crosses an allocation end
+        if (c >= a_next) {   // the segment crosses an allocation end
+            a = find_alloc(P.desc, P.n_allocs, c);
+            d = P.desc[a];
+        }
         const uint64_t local = c - d.first_chunk;
         const uint64_t rest = d.bytes - (local << log2S);
         len = (uint32_t)umin64(rest, 1ull << log2S);
@@ -1146,6 +1164,19 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
                 sum += mixw(((uint64_t)q[u].w << 32) | q[u].z, key + kK1);
             }
             key += kStep;
+        }
+        if (P.full_copy) {   // FULL checkpoint: the chunk goes straight to its staging offset
+            const uint64_t o = P.alloc_prefix[a] + (local << log2S) - P.seg_base;
+            if (o + len <= P.staging_cap) {
+                uint4 *dst = reinterpret_cast<uint4 *>(P.staging + o);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t v = li + LPC * u;
+                    if (v < nv) __stcs(dst + v, q[u]);
+                }
+            } else if (li == 0) {
+                atomicOr(&P.ctrl->err, kErrBounds);
+            }
         }
         const uint32_t rem = len & 15u;
         if (rem && (uint32_t)li == (nv % LPC)) {
@@ -1183,16 +1214,17 @@ split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc
     const uint64_t q_end = umin64(q + per, n_slots);
     CkptDesc d{};
     uint64_t a_next = 0;
+    uint32_t a = 0;
     bool have = false;
     for (; q < q_end; ++q) {
         const uint64_t c0 = P.c_begin + q * CPS;
         if (!have || c0 >= a_next) {
-            const uint32_t a = find_alloc(P.desc, P.n_allocs, c0);
+            a = find_alloc(P.desc, P.n_allocs, c0);
             d = P.desc[a];
             a_next = a + 1 < P.n_allocs ? P.desc[a + 1].first_chunk : ~0ull;
             have = true;
         }
-        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a_next, lane % LPC);
+        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a, a_next, lane % LPC);
     }
 }
 
@@ -1293,6 +1325,7 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
 
 __global__ void __launch_bounds__(kGatherNT)
 split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
+    if (P.full_copy) return;   // the hash kernel has already written every chunk
     const int lane = threadIdx.x & 31;
     const uint64_t kd = (uint64_t)P.ctrl->k;
     const uint64_t k = kd < P.idx_cap ? kd : P.idx_cap;

@@ -48,6 +48,13 @@ struct CkptParams {
     CkptCtrl *ctrl;
     uint64_t timeout_ns;
     uint32_t skip_first_ticket;  // fault injection: tile 0 is never processed
+    // Split pass, FULL checkpoints only (no chunk has a baseline, every size a
+    // multiple of 16): the hash kernels write each chunk straight to its final
+    // staging offset alloc_prefix[a] + local*S - seg_base, and the gather is
+    // skipped.
+    uint32_t full_copy;
+    const uint64_t *alloc_prefix;   // payload bytes of all allocations before each one
+    uint64_t seg_base;              // payload offset of the segment's first chunk
 };
 
 // Restore: one image allocation mapped onto the target layout.

@@ -546,6 +546,7 @@ struct crac_ctx {
     const void *s_hash_fn = nullptr;
     crac_pass_info_t last{};
     crac_restart_info_t last_restart{};
+    bool full_copy_ok = false;   // current pass: no baseline anywhere and 16-byte sizes
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
     // autotuner session: one shadow context per candidate chunk size
@@ -873,6 +874,15 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.tile_bytes = P.tile_cnt + n_tiles;
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        // FULL pass: chunks are written to staging by the hash kernel.
+        P.full_copy = c->full_copy_ok && staging ? 1u : 0u;
+        P.alloc_prefix = (const uint64_t *)(desc_dev + c->allocs.size());
+        {
+            const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
+            uint64_t pre = 0;
+            for (size_t a = 0; a < a0; ++a) pre += c->allocs[a].bytes;
+            P.seg_base = pre + ((sg.c0 - first[a0]) << c->log2S);
+        }
         unsigned long long *acc = (unsigned long long *)((uint8_t *)c->work.p + status_bytes);
         const uint64_t n_slots = small ? (nseg + (8192u >> c->log2S) - 1) / (8192u >> c->log2S)
                                        : nseg << (c->log2S - log2Seg);
@@ -1054,21 +1064,29 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         // Only the output table may grow: the baseline table keeps the previous
         // layout, which it still fully holds.
         st = ensure_dev(c->fp[1 - c->fp_cur], n * 8);
-        if (st == CRAC_OK) st = ensure_dev(c->desc, na * sizeof(CkptDesc));
-        if (st == CRAC_OK) st = ensure_host(c->desc_h, na * sizeof(CkptDesc));
+        if (st == CRAC_OK) st = ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8));
+        if (st == CRAC_OK) st = ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8));
         if (st != CRAC_OK) return fail(st);
         CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+        uint64_t *prefix_h = (uint64_t *)(dh + na);   // payload bytes before each allocation
+        bool any_base = false, all16 = true;
+        uint64_t pre = 0;
         for (size_t a = 0; a < na; ++a) {
             uint64_t bf = kNoBase;
             if (c->base_valid) {
                 auto it = c->base_first.find(c->allocs[a].id);
                 if (it != c->base_first.end()) bf = it->second;
             }
+            any_base |= bf != kNoBase;
+            all16 &= (c->allocs[a].bytes & 15) == 0;
             dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+            prefix_h[a] = pre;
+            pre += c->allocs[a].bytes;
         }
+        c->full_copy_ok = !any_base && all16;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
-        if (cudaMemcpyAsync(c->desc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(cuda_status(cudaGetLastError()));
         // Managed regions migrate to the device before they are read.
         bool any_managed = false;
@@ -1610,19 +1628,27 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     c->last = crac_pass_info_t{};
     if (n == 0) return CRAC_OK;
     TRY(ensure_dev(c->fp[1 - c->fp_cur], n * 8));
-    TRY(ensure_dev(c->desc, na * sizeof(CkptDesc)));
-    TRY(ensure_host(c->desc_h, na * sizeof(CkptDesc)));
+    TRY(ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8)));
+    TRY(ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8)));
     CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+    uint64_t *prefix_h = (uint64_t *)(dh + na);
+    bool any_base = false, all16 = true;
+    uint64_t pre = 0;
     for (size_t a = 0; a < na; ++a) {
         uint64_t bf = kNoBase;
         if (c->base_valid) {
             auto it = c->base_first.find(c->allocs[a].id);
             if (it != c->base_first.end()) bf = it->second;
         }
+        any_base |= bf != kNoBase;
+        all16 &= (c->allocs[a].bytes & 15) == 0;
         dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+        prefix_h[a] = pre;
+        pre += c->allocs[a].bytes;
     }
+    c->full_copy_ok = !any_base && all16;
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
-    CK(cudaMemcpyAsync(c->desc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
     uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
     cap = std::max(round_up(cap, 256), S);
     const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);

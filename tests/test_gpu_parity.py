@@ -293,3 +293,29 @@ def test_empty_registry():
         h.restart(img)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("S", [1 * KIB, 4 * KIB, 8 * KIB, 64 * KIB])
+@pytest.mark.parametrize("staging", [0, 300 * KIB])
+def test_full_checkpoint_write_through(S, staging):
+    """FULL checkpoints with every size a multiple of 16: the hash kernel writes
+    chunks straight to their staging offsets (segments starting mid-allocation
+    included) and the gather is skipped; the image must still be the oracle's."""
+    sizes = [16 * 4097, S * 5, 48, 1024 * KIB + 16 * 3, S * 2 + 32]
+    h = Harness(S, lineage=400 + S // KIB, staging_bytes=staging, pass_kernel=C.CRAC_PASS_SPLIT)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=120 + i)
+        img1, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=6))
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img2)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
