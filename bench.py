@@ -122,6 +122,20 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
+def aggregate_over_ranks(t_ms: float, units: float, world: int, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    and the units of all ranks.  Works with NCCL (device tensors) and gloo."""
+    if world <= 1:
+        return t_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
@@ -307,13 +321,10 @@ def run_crac(args):
     torch.cuda.synchronize()
     barrier()
     t_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    launches = C.crac_kernel_launches() - launches0 + args.steps   # + one mutator launch per step
     bytes_per_step = 2 * B
-    value = bytes_per_step * args.steps * world / (t_ms / 1e3) / 1e9
+    t_ms, job_bytes = aggregate_over_ranks(t_ms, bytes_per_step * args.steps, world, dev)
+    launches = C.crac_kernel_launches() - launches0 + args.steps   # + one mutator launch per step
+    value = job_bytes / (t_ms / 1e3) / 1e9
 
     # ---- roofline: the dominant kernel is the split pass's streaming hash ------
     dev_ms = statistics.mean(p[0] for p in pass_ms)
