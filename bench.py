@@ -284,13 +284,15 @@ def run_crac(args):
         if lat_ms is not None:
             lat_ms.append((time.perf_counter() - t0) * 1e3)
         if pass_ms is not None:
-            info = C.crac_ctx_last_pass(ctx)
-            pass_ms.append((info["device_ms"], info["k"], info["payload_bytes"], info["hash_ms"],
-                            info["finalize_ms"], info["gather_ms"]))
+            # filled in place (no per-field Python work inside the timed loop)
+            pass_ms.append(C.crac_ctx_last_pass(ctx, C.CracPassInfo()))
         C.crac_ctx_restart(ctx, img, stream)
         if rst is not None:
-            rst.append(C.crac_ctx_last_restart(ctx))
+            rst.append(C.crac_ctx_last_restart(ctx, C.CracRestartInfo()))
         C.crac_image_release(img)
+
+    def pass_rows(infos):
+        return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms) for i in infos]
 
     # Base images (full) for each context.
     for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma):
@@ -327,6 +329,8 @@ def run_crac(args):
     value = job_bytes / (t_ms / 1e3) / 1e9
 
     # ---- roofline: the dominant kernel is the split pass's streaming hash ------
+    pass_ms = pass_rows(pass_ms)
+    rst = [C.restart_info_dict(r) for r in rst]
     dev_ms = statistics.mean(p[0] for p in pass_ms)
     k_avg = statistics.mean(p[1] for p in pass_ms)
     d_avg = statistics.mean(p[2] for p in pass_ms)
@@ -412,6 +416,7 @@ def run_crac(args):
         torch.cuda.synchronize()
         barrier()
         te = e0.elapsed_time(e1)
+        e_pass = pass_rows(e_pass)
         k_e = statistics.mean(p[1] for p in e_pass)
         d_e = statistics.mean(p[2] for p in e_pass)
         d2h = int(d_e + 8 * k_e + 8 * n + 64)

@@ -122,7 +122,7 @@ typedef struct crac_config {
     uint32_t pad0;
     uint64_t reserve_host_bytes;    /* pinned image memory to reserve up front */
     uint64_t reserve_device_bytes;  /* device image memory to reserve up front */
-    uint32_t pass_kernel;           /* CRAC_PASS_AUTO / _LDG / _TMA */
+    uint32_t pass_kernel;           /* CRAC_PASS_* */
     uint32_t reserved[1];
 } crac_config_t;
 
@@ -316,6 +316,11 @@ typedef struct crac_tune_result {
     float cost_ms[CRAC_TUNE_MAX];          /* pass + drain estimate (apply) */
     float variant_ms[4];                   /* pass time per CRAC_PASS_* at the chosen
                                               size (apply); 0 = not applicable */
+    uint32_t chosen_chunks_per_tile;       /* LDG tile kept by apply (0 = not tuned:
+                                              fixed in the config, or LDG not chosen) */
+    uint32_t ldg_tiles[3];                 /* LDG tiles (chunks) timed by apply; 0 = unused */
+    float ldg_tile_ms[3];                  /* pass time of each of those tiles */
+    uint32_t pad0;
 } crac_tune_result_t;
 
 /*
@@ -336,7 +341,10 @@ CRAC_API crac_status_t crac_ctx_tune_observe(crac_ctx_t *ctx, crac_stream_t stre
  * End the session: choose the chunk size with the lowest mean cost
  * (pass time + dirty bytes / link_gbs; link_gbs <= 0 counts the device pass
  * only), then time each pass kernel at that size on the current memory and
- * keep the fastest.  If the chunk size changes, the context's baseline is
+ * keep the fastest.  When the configuration leaves chunks_per_tile at 0, the
+ * LDG kernel is timed at three tile sizes (half, equal to and twice its
+ * default) and, if LDG wins, the fastest tile is written to the context's
+ * chunks_per_tile.  If the chunk size changes, the context's baseline is
  * dropped, so its next checkpoint is FULL (which also ends the delta chain,
  * since a chain holds one chunk size).  Needs at least two observe rounds
  * (CRAC_ERR_UNSUPPORTED otherwise).

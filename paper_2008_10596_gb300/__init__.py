@@ -118,6 +118,8 @@ class CracTuneResult(ctypes.Structure):
         ("last_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("last_dirty_bytes", ctypes.c_uint64 * CRAC_TUNE_MAX),
         ("mean_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("mean_dirty_bytes", ctypes.c_double * CRAC_TUNE_MAX),
         ("cost_ms", ctypes.c_float * CRAC_TUNE_MAX), ("variant_ms", ctypes.c_float * 4),
+        ("chosen_chunks_per_tile", ctypes.c_uint32), ("ldg_tiles", ctypes.c_uint32 * 3),
+        ("ldg_tile_ms", ctypes.c_float * 3), ("pad0", ctypes.c_uint32),
     ]
 
     def to_dict(self) -> dict:
@@ -126,7 +128,10 @@ class CracTuneResult(ctypes.Structure):
                 "chosen_pass_kernel": self.chosen_pass_kernel, "chunk_bytes": list(self.chunk_bytes[:n]),
                 "last_pass_ms": list(self.last_pass_ms[:n]), "last_dirty_bytes": list(self.last_dirty_bytes[:n]),
                 "mean_pass_ms": list(self.mean_pass_ms[:n]), "mean_dirty_bytes": list(self.mean_dirty_bytes[:n]),
-                "cost_ms": list(self.cost_ms[:n]), "variant_ms": list(self.variant_ms)}
+                "cost_ms": list(self.cost_ms[:n]), "variant_ms": list(self.variant_ms),
+                "chosen_chunks_per_tile": self.chosen_chunks_per_tile,
+                "ldg_tiles": [t for t in self.ldg_tiles if t],
+                "ldg_tile_ms": [m for t, m in zip(self.ldg_tiles, self.ldg_tile_ms) if t]}
 
 
 class CracServerConfig(ctypes.Structure):
@@ -287,9 +292,15 @@ def crac_ctx_tune_apply(ctx: int, link_gbs: float = 0.0, stream=None) -> dict:
     return out.to_dict()
 
 
-def crac_ctx_last_restart(ctx: int) -> dict:
-    info = CracRestartInfo()
+def crac_ctx_last_restart(ctx: int, out: "CracRestartInfo | None" = None):
+    """The last restart's statistics as a dict; given `out`, fills it and
+    returns it unconverted."""
+    info = CracRestartInfo() if out is None else out
     _check(_lib.crac_ctx_last_restart(ctx, ctypes.byref(info)), "crac_ctx_last_restart")
+    return info if out is not None else restart_info_dict(info)
+
+
+def restart_info_dict(info: "CracRestartInfo") -> dict:
     return {f: getattr(info, f) for f, _ in CracRestartInfo._fields_ if f != "reserved"}
 
 
@@ -343,9 +354,15 @@ def crac_ctx_invalidate(ctx: int) -> None:
     _check(_lib.crac_ctx_invalidate(ctx), "crac_ctx_invalidate")
 
 
-def crac_ctx_last_pass(ctx: int) -> dict:
-    info = CracPassInfo()
+def crac_ctx_last_pass(ctx: int, out: "CracPassInfo | None" = None):
+    """The last pass's statistics as a dict; given `out` (a CracPassInfo), fills
+    it and returns it unconverted (no per-field Python work, for timed loops)."""
+    info = CracPassInfo() if out is None else out
     _check(_lib.crac_ctx_last_pass(ctx, ctypes.byref(info)), "crac_ctx_last_pass")
+    return info if out is not None else pass_info_dict(info)
+
+
+def pass_info_dict(info: "CracPassInfo") -> dict:
     return {f: getattr(info, f) for f, _ in CracPassInfo._fields_ if f != "reserved"}
 
 

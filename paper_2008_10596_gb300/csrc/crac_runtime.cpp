@@ -555,6 +555,7 @@ struct crac_ctx {
     std::vector<float> tune_last_ms;
     std::vector<uint64_t> tune_last_bytes;
     uint32_t tune_rounds = 0;
+    bool cpt_tuned = false;      // cfg.chunks_per_tile was written by the tuner
 };
 
 namespace {
@@ -667,7 +668,9 @@ void pick_split(const crac_ctx *c, int *wpc, uint32_t *cpt) {
     if (!w) w = S >= 16384 ? 8 : 1;
     uint32_t t = c->cfg.chunks_per_tile;
     if (!t) {
-        const uint64_t tile_bytes = 128ull << 10;
+        // One chunk per warp: 128 KiB tiles; a CTA per chunk: 256 KiB tiles,
+        // which hide the look-back better (measured at 64 KiB chunks).
+        const uint64_t tile_bytes = w == 8 ? 256ull << 10 : 128ull << 10;
         t = (uint32_t)std::max<uint64_t>(1, tile_bytes / S);
         const uint32_t groups = 8 / w;
         t = std::max(t, groups);
@@ -1707,6 +1710,7 @@ crac_status_t ctx_tune_observe(crac_ctx *c, cudaStream_t s, const uint32_t *size
             cfg.chunk_bytes = sizes[i];
             cfg.device = c->device;
             cfg.reserve_host_bytes = cfg.reserve_device_bytes = 0;
+            if (c->cpt_tuned) cfg.chunks_per_tile = 0;
             if (cfg.pass_kernel == CRAC_PASS_TMA && (sizes[i] < 1024 || sizes[i] > 65536)) cfg.pass_kernel = CRAC_PASS_AUTO;
             crac_ctx *t = new crac_ctx();
             const crac_status_t st = ctx_init(t, &cfg);
@@ -1768,30 +1772,71 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
     }
     float vms[4] = {0, 0, 0, 0};
     uint32_t best_v = CRAC_PASS_SPLIT;
-    const uint32_t saved = t->cfg.pass_kernel;
+    const uint32_t saved = t->cfg.pass_kernel, saved_cpt = t->cfg.chunks_per_tile;
+    // LDG tiles to try: the configured one, or around the default when unset.
+    uint32_t tiles[3] = {saved_cpt, 0, 0};
+    float tile_ms[3] = {0, 0, 0};
+    if (saved_cpt == 0) {
+        int w;
+        uint32_t t0;
+        pick_split(t, &w, &t0);
+        const uint32_t lo = std::max<uint32_t>(1, t0 / 2), hi = std::min<uint32_t>(256, 2 * t0);
+        tiles[0] = t0;
+        tiles[1] = lo != t0 ? lo : 0;
+        tiles[2] = hi != t0 ? hi : 0;
+    }
+    uint32_t best_tile = 0;
+    auto time_pass = [&](float *best_ms) {
+        for (int r = 0; r < 2; ++r) {
+            float ms = 0;
+            uint64_t k = 0, d = 0;
+            TRY(ctx_trial_pass(t, s, false, &ms, &k, &d));
+            if (r == 0 || ms < *best_ms) *best_ms = ms;
+        }
+        return CRAC_OK;
+    };
     for (uint32_t v : {(uint32_t)CRAC_PASS_SPLIT, (uint32_t)CRAC_PASS_LDG, (uint32_t)CRAC_PASS_TMA}) {
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
         t->cfg.pass_kernel = v;
         float bestm = 0;
-        for (int r = 0; r < 2; ++r) {
+        const int n_tiles = v == CRAC_PASS_LDG && saved_cpt == 0 ? 3 : 1;
+        for (int j = 0; j < n_tiles; ++j) {
+            if (v == CRAC_PASS_LDG && saved_cpt == 0) {
+                if (!tiles[j]) continue;
+                t->cfg.chunks_per_tile = tiles[j];
+            }
             float ms = 0;
-            uint64_t k = 0, d = 0;
-            const crac_status_t st = ctx_trial_pass(t, s, false, &ms, &k, &d);
+            const crac_status_t st = time_pass(&ms);
+            t->cfg.chunks_per_tile = saved_cpt;
             if (st != CRAC_OK) {
                 t->cfg.pass_kernel = saved;
                 return st;
             }
-            if (r == 0 || ms < bestm) bestm = ms;
+            if (v == CRAC_PASS_LDG) tile_ms[j] = ms;
+            if (bestm == 0 || ms < bestm) {
+                bestm = ms;
+                if (v == CRAC_PASS_LDG && saved_cpt == 0) best_tile = tiles[j];
+            }
         }
         vms[v] = bestm;
         if (vms[best_v] == 0 || bestm < vms[best_v]) best_v = v;
     }
+    if (best_v != CRAC_PASS_LDG) best_tile = 0;
     tune_fill(c, out);
     if (out) {
         for (uint32_t i = 0; i < n; ++i) out->cost_ms[i] = cost[i];
         for (int v = 0; v < 4; ++v) out->variant_ms[v] = vms[v];
         out->chosen_chunk_bytes = S;
         out->chosen_pass_kernel = best_v;
+        out->chosen_chunks_per_tile = best_tile;
+        for (int j = 0; j < 3; ++j) {
+            out->ldg_tiles[j] = vms[CRAC_PASS_LDG] > 0 ? tiles[j] : 0;
+            out->ldg_tile_ms[j] = out->ldg_tiles[j] ? tile_ms[j] : 0.f;
+        }
+    }
+    if (saved_cpt == 0) {
+        c->cfg.chunks_per_tile = best_tile;
+        c->cpt_tuned = best_tile != 0;
     }
     if (S != (1u << c->log2S)) {
         c->cfg.chunk_bytes = S;

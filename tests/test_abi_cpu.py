@@ -47,10 +47,15 @@ def test_status_strings(C):
 def test_config_validation(C):
     for bad in (dict(chunk_bytes=3000), dict(chunk_bytes=8), dict(chunk_bytes=1 << 25),
                 dict(image_residency=7), dict(launch_mode=9), dict(threads=128),
-                dict(warps_per_chunk=3), dict(chunks_per_tile=1000)):
+                dict(warps_per_chunk=3), dict(chunks_per_tile=1000), dict(pass_kernel=5),
+                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
+                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10)):
         with pytest.raises(C.CracError) as e:
             C.crac_ctx_create(C.crac_config_default(**bad))
         assert e.value.code == C.CRAC_ERR_INVALID_ARG
+    for ok in (dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=1024),
+               dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=64 << 10)):
+        C.crac_ctx_destroy(C.crac_ctx_create(C.crac_config_default(**ok)))
 
 
 def test_registry_host_logic(C):

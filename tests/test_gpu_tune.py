@@ -62,6 +62,14 @@ def test_tune_observe_exact_dirty_bytes_and_choice():
         assert res["chosen_chunk_bytes"] == 4 * KIB
         assert res["chosen_pass_kernel"] in (C.CRAC_PASS_SPLIT, C.CRAC_PASS_LDG, C.CRAC_PASS_TMA)
         assert all(v > 0 for v in res["variant_ms"][1:4])
+        # LDG was timed at its default 4 KiB tile (32 chunks) and at half and twice it
+        assert res["ldg_tiles"] == [32, 16, 64]
+        assert all(m > 0 for m in res["ldg_tile_ms"])
+        assert res["variant_ms"][C.CRAC_PASS_LDG] == min(res["ldg_tile_ms"])
+        if res["chosen_pass_kernel"] == C.CRAC_PASS_LDG:
+            assert res["chosen_chunks_per_tile"] in res["ldg_tiles"]
+        else:
+            assert res["chosen_chunks_per_tile"] == 0
         # the retuned context: a FULL image at 4 KiB, then an exact delta
         img = C.crac_ctx_checkpoint(ctx, stream)
         imgs.append(img)
