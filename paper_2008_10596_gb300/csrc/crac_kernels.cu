@@ -86,13 +86,18 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Look-back status words.  A word holds the flag and the value together and
+// its reader needs nothing else the writing CTA produced (it only adds the
+// values up), so plain gpu-scope (relaxed) accesses suffice: a release would
+// make every publish wait for the writer's earlier stores, such as its
+// fingerprints, to be acknowledged.
+__device__ __forceinline__ void st_status(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+__device__ __forceinline__ uint64_t ld_status(const uint64_t *p) {
     uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -218,8 +223,8 @@ __device__ void lookback(const CkptParams &P, uint32_t tile, int lane, uint64_t 
         if (t >= 0) {
             uint32_t spins = 0;
             for (;;) {
-                wk = ld_acquire(P.tile_cnt + t);
-                wd = ld_acquire(P.tile_bytes + t);
+                wk = ld_status(P.tile_cnt + t);
+                wd = ld_status(P.tile_bytes + t);
                 if ((wk >> 62) && (wd >> 62)) break;
                 if (gave_up || ((++spins & 31u) == 0 &&
                                 (globaltimer() - t0 > P.timeout_ns || spins > (1u << 28)))) {
@@ -340,18 +345,18 @@ __global__ void __launch_bounds__(NT) ckpt_fused_kernel(const CkptParams P) {
             uint64_t k0 = 0, d0 = 0;
             if (tile == 0) {
                 if (lane == 0) {
-                    st_release(P.tile_cnt, kFlagInc | cnt);
-                    st_release(P.tile_bytes, kFlagInc | bytes);
+                    st_status(P.tile_cnt, kFlagInc | cnt);
+                    st_status(P.tile_bytes, kFlagInc | bytes);
                 }
             } else {
                 if (lane == 0) {
-                    st_release(P.tile_cnt + tile, kFlagAgg | cnt);
-                    st_release(P.tile_bytes + tile, kFlagAgg | bytes);
+                    st_status(P.tile_cnt + tile, kFlagAgg | cnt);
+                    st_status(P.tile_bytes + tile, kFlagAgg | bytes);
                 }
                 lookback(P, tile, lane, &k0, &d0);
                 if (lane == 0) {
-                    st_release(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
-                    st_release(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                    st_status(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                    st_status(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
                 }
             }
             if (lane == 0) {
@@ -394,6 +399,18 @@ __global__ void __launch_bounds__(NT) ckpt_fused_kernel(const CkptParams P) {
         }
         __syncthreads();
     }
+}
+
+// Last allocation whose first chunk is <= c, over a first_chunk column
+// cached in shared memory.
+__device__ __forceinline__ uint32_t find_first_cached(const uint64_t *first, uint32_t n, uint64_t c) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (first[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -607,6 +624,13 @@ struct __align__(16) Meta {
 };
 constexpr size_t kBarOff = (size_t)kNSlot * kSlot + (size_t)kNSlot * sizeof(Meta);
 constexpr size_t kSmemBytes = kBarOff + 4 * kNSlot * sizeof(uint64_t) + kNSlot * sizeof(uint32_t);
+// The allocations' first_chunk column, when it fits in what the slots leave
+// of the 227 KiB a CTA may have, so that the producer's chunk -> allocation
+// search stays on chip.
+constexpr size_t kFirstOff = (kSmemBytes + 15) & ~(size_t)15;
+constexpr uint32_t kCachedAllocs = 3072;
+constexpr size_t kSmemMax = kFirstOff + (size_t)kCachedAllocs * sizeof(uint64_t);
+static_assert(kSmemMax <= 227 * 1024, "TMA pass shared memory");
 }  // namespace tma
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -701,16 +725,19 @@ __device__ __forceinline__ uint64_t hash_smem(const uint8_t *chunk, uint32_t len
 }
 
 __device__ __forceinline__ void tma_producer(const CkptParams &P, uint8_t *slots, tma::Meta *meta, uint64_t *full,
-                                             uint64_t *empty, uint32_t *armed, int lane) {
+                                             uint64_t *scanned, uint64_t *empty, uint32_t *armed,
+                                             const uint64_t *s_first, int lane) {
     using namespace tma;
     const uint32_t log2S = P.log2_chunk;
     const uint64_t S = 1ull << log2S;
-    // A ticket is taken only once a slot is free for it, so every tile a CTA
-    // holds is already loading: a predecessor's aggregate never waits behind
-    // another CTA's queue.
+    // The next tile's ticket is taken once the slot's previous tile has its
+    // staging offset (its store is being issued), so a tile is held without
+    // loading only for the length of one store, and the ticket round trip
+    // and the chunk lookups overlap that store.  The slot and its Meta are
+    // written only after the store has read them (`empty`).
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % kNSlot, par = (it / kNSlot) & 1u;
-        if (!mbar_wait(&empty[s], par ^ 1u, P)) return;
+        if (!mbar_wait(&scanned[s], par ^ 1u, P)) return;
         uint32_t t = 0;
         if (lane == 0) {
             t = atomicAdd(&P.ctrl->ticket, 1u);
@@ -719,6 +746,7 @@ __device__ __forceinline__ void tma_producer(const CkptParams &P, uint8_t *slots
         const uint32_t tile = __shfl_sync(kFull, t, 0);
         Meta &m = meta[s];
         if (tile >= P.n_tiles) {
+            if (!mbar_wait(&empty[s], par ^ 1u, P)) return;
             if (lane == 0) {
                 m.tile = kDone;
                 armed[s] = 2u | par;   // the last phase of this slot is the done marker
@@ -731,6 +759,7 @@ __device__ __forceinline__ void tma_producer(const CkptParams &P, uint8_t *slots
         const uint32_t nc = (uint32_t)min((uint64_t)P.cpt, P.c_end - c0);
         const uint8_t *src[2] = {nullptr, nullptr};
         uint32_t len[2] = {0, 0};
+        uint64_t fpo[2] = {0, 0};
         uint32_t tx = 0;
         uint64_t hb = 0;
 #pragma unroll
@@ -738,19 +767,30 @@ __device__ __forceinline__ void tma_producer(const CkptParams &P, uint8_t *slots
             const uint32_t i = lane + 32 * k;
             bool has = false;
             if (i < nc) {
-                const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c0 + i)];
-                const uint64_t local = c0 + i - d.first_chunk;
+                const uint64_t c = c0 + i;
+                const uint32_t a = P.first_cached ? find_first_cached(s_first, P.n_allocs, c)
+                                                  : find_alloc(P.desc, P.n_allocs, c);
+                const CkptDesc d = P.desc[a];
+                const uint64_t local = c - d.first_chunk;
                 len[k] = (uint32_t)min(S, d.bytes - (local << log2S));
                 src[k] = reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S);
                 has = d.base_first != kNoBase;
-                m.fpo[i] = has ? d.base_first + local : 0ull;
-                m.len[i] = len[k];
+                fpo[k] = has ? d.base_first + local : 0ull;
                 tx += len[k] & ~15u;
             }
             hb |= (uint64_t)__ballot_sync(kFull, has) << (32 * k);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) tx += __shfl_xor_sync(kFull, tx, o);
+        if (!mbar_wait(&empty[s], par ^ 1u, P)) return;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t i = lane + 32 * k;
+            if (i < nc) {
+                m.fpo[i] = fpo[k];
+                m.len[i] = len[k];
+            }
+        }
         if (lane == 0) {
             m.tile = tile;
             m.nc = nc;
@@ -862,8 +902,8 @@ __device__ __forceinline__ void tma_hasher(const CkptParams &P, const uint8_t *s
                 m.cnt = cnt;
                 m.bytes = bytes;
                 const uint64_t f = m.tile == 0 ? kFlagInc : kFlagAgg;
-                st_release(P.tile_cnt + m.tile, f | cnt);
-                st_release(P.tile_bytes + m.tile, f | bytes);
+                st_status(P.tile_cnt + m.tile, f | cnt);
+                st_status(P.tile_bytes + m.tile, f | bytes);
             }
         }
         __syncwarp();
@@ -890,8 +930,8 @@ __device__ __forceinline__ void tma_scan(const CkptParams &P, tma::Meta *meta, u
         if (tile != 0) {   // tile 0 was published inclusive by the hashers
             lookback(P, tile, lane, &k0, &d0);
             if (lane == 0) {
-                st_release(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
-                st_release(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                st_status(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                st_status(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
             }
         }
         if (lane == 0) {
@@ -969,8 +1009,11 @@ __global__ void __launch_bounds__(tma::kThreads, 1) ckpt_tma_kernel(const CkptPa
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kBarOff);
     uint64_t *full = bars, *hashed = bars + kNSlot, *scanned = bars + 2 * kNSlot, *empty = bars + 3 * kNSlot;
     uint32_t *armed = reinterpret_cast<uint32_t *>(bars + 4 * kNSlot);
+    uint64_t *s_first = reinterpret_cast<uint64_t *>(smem + kFirstOff);
     __shared__ uint32_t go[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (P.first_cached)
+        for (uint32_t a = threadIdx.x; a < P.n_allocs; a += kThreads) s_first[a] = P.desc[a].first_chunk;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kNSlot; ++s) {
             mbar_init(&full[s], 1);
@@ -983,7 +1026,7 @@ __global__ void __launch_bounds__(tma::kThreads, 1) ckpt_tma_kernel(const CkptPa
     }
     __syncthreads();
     if (warp < kHW) tma_hasher<WPC>(P, slots, meta, full, hashed, go, warp, lane);
-    else if (warp == kHW) tma_producer(P, slots, meta, full, empty, armed, lane);
+    else if (warp == kHW) tma_producer(P, slots, meta, full, scanned, empty, armed, s_first, lane);
     else if (warp == kHW + 1) tma_scan(P, meta, hashed, scanned, lane);
     else tma_store(P, slots, meta, scanned, empty, lane);
     __syncthreads();
@@ -1284,18 +1327,18 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
             uint64_t k0 = 0, d0 = 0;
             if (tile == 0) {
                 if (lane == 0) {
-                    st_release(P.tile_cnt, kFlagInc | cnt);
-                    st_release(P.tile_bytes, kFlagInc | bytes);
+                    st_status(P.tile_cnt, kFlagInc | cnt);
+                    st_status(P.tile_bytes, kFlagInc | bytes);
                 }
             } else {
                 if (lane == 0) {
-                    st_release(P.tile_cnt + tile, kFlagAgg | cnt);
-                    st_release(P.tile_bytes + tile, kFlagAgg | bytes);
+                    st_status(P.tile_cnt + tile, kFlagAgg | cnt);
+                    st_status(P.tile_bytes + tile, kFlagAgg | bytes);
                 }
                 lookback(P, tile, lane, &k0, &d0);
                 if (lane == 0) {
-                    st_release(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
-                    st_release(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                    st_status(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                    st_status(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
                 }
             }
             if (lane == 0) {
@@ -1440,13 +1483,16 @@ const void *ckpt_tma_fn(int wpc) {
 }
 
 int ckpt_tma_threads() { return tma::kThreads; }
-size_t ckpt_tma_smem() { return tma::kSmemBytes; }
+size_t ckpt_tma_smem(uint32_t n_allocs) {
+    return n_allocs <= tma::kCachedAllocs ? tma::kFirstOff + (size_t)n_allocs * sizeof(uint64_t) : tma::kSmemBytes;
+}
+uint32_t ckpt_tma_cached_allocs() { return tma::kCachedAllocs; }
 uint32_t ckpt_tma_slot_bytes() { return tma::kSlot; }
 
 cudaError_t ckpt_tma_prepare() {
     for (int w : {1, 2, 4, 8}) {
         const cudaError_t e = cudaFuncSetAttribute(ckpt_tma_fn(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)tma::kSmemBytes);
+                                                   (int)tma::kSmemMax);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

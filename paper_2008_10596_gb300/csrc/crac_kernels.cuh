@@ -55,6 +55,9 @@ struct CkptParams {
     uint32_t full_copy;
     const uint64_t *alloc_prefix;   // payload bytes of all allocations before each one
     uint64_t seg_base;              // payload offset of the segment's first chunk
+    // TMA pass: the allocations' first_chunk column fits in the CTA's shared
+    // memory (n_allocs <= ckpt_tma_cached_allocs()) and is searched there.
+    uint32_t first_cached;
 };
 
 // Restore: one image allocation mapped onto the target layout.
@@ -99,13 +102,15 @@ cudaError_t launch_ckpt_fused(const CkptParams &p, int threads, int warps_per_ch
 const void *ckpt_fused_fn(int threads, int warps_per_chunk);
 int ckpt_fused_max_ctas_per_sm(int threads, int warps_per_chunk);
 
+
 // TMA-staged variant of the fused pass (chunk sizes 1-64 KiB): one CTA per
 // SM, ckpt_tma_threads() threads, ckpt_tma_smem() bytes of dynamic shared
 // memory, a tile of ckpt_tma_slot_bytes() / chunk_bytes chunks, and
 // warps_per_chunk = max(1, 8 * chunk_bytes / slot_bytes).
 const void *ckpt_tma_fn(int warps_per_chunk);
 int ckpt_tma_threads();
-size_t ckpt_tma_smem();
+size_t ckpt_tma_smem(uint32_t n_allocs);   // dynamic shared memory of a launch over n_allocs
+uint32_t ckpt_tma_cached_allocs();
 uint32_t ckpt_tma_slot_bytes();
 cudaError_t ckpt_tma_prepare();   // raise the dynamic shared memory limit (once per device)
 

@@ -918,7 +918,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
             wpc = (int)std::max<uint64_t>(1, 8 * S / ckpt_tma_slot_bytes());
             fn = ckpt_tma_fn(wpc);
             threads = ckpt_tma_threads();
-            smem = ckpt_tma_smem();
+            smem = ckpt_tma_smem((uint32_t)std::min<size_t>(c->allocs.size(), UINT32_MAX));
             per_sm = 1;
         } else {
             pick_split(c, &wpc, &cpt);
@@ -952,6 +952,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.tile_bytes = P.tile_cnt + n_tiles;
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (inject_wait && n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        P.first_cached = tma && c->allocs.size() <= ckpt_tma_cached_allocs() ? 1u : 0u;
         TRY(launch_fused_graph(c, P, work_bytes, fn, threads, smem, grid, s));
         c->last.pass_kernel = tma ? CRAC_PASS_TMA : CRAC_PASS_LDG;
         c->last.grid = (uint32_t)grid;

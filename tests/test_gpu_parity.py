@@ -12,6 +12,7 @@ import torch
 import paper_2008_10596_gb300 as C
 import workloads as W
 from oracle import oracle as O
+from paper_2008_10596_gb300 import testkit
 from tests.gpu_harness import Harness, pattern_mutations
 
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
@@ -132,6 +133,69 @@ def test_chunk_sizes_ragged(S, kern):
             assert np.array_equal(b.read(), w)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("n_allocs", [3072, 3073])
+@pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
+def test_tma_many_allocations(n_allocs, residency):
+    """The TMA pass keeps the allocations' first_chunk column in shared memory
+    up to 3072 allocations and searches the table in global memory beyond;
+    both give the oracle's images.  The allocations are 256-byte-aligned
+    pieces of one device buffer, with ragged sizes."""
+    S = 4 * KIB
+    rng = np.random.default_rng(n_allocs + residency)
+    sizes = [int(x) for x in rng.integers(1, 3 * S, size=n_allocs)]
+    offs = np.zeros(n_allocs + 1, dtype=np.int64)
+    offs[1:] = np.cumsum([(n + 255) // 256 * 256 for n in sizes])
+    buf = torch.from_numpy(W.host_contents("u32_xorshift", int(offs[-1]), 77)).to("cuda")
+    base = buf.data_ptr()
+    ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=600 + n_allocs % 7,
+                                                  pass_kernel=C.CRAC_PASS_TMA, image_residency=residency))
+    ora = O.OracleContext(S, lineage=600 + n_allocs % 7)
+    stream = torch.cuda.current_stream()
+    imgs = []
+
+    def host():
+        h = buf.cpu().numpy()
+        return [h[offs[i]:offs[i] + n] for i, n in enumerate(sizes)]
+
+    def checkpoint():
+        img = C.crac_ctx_checkpoint(ctx, stream)
+        imgs.append(img)
+        C.crac_image_wait(img)
+        assert C.crac_ctx_last_pass(ctx)["pass_kernel"] == C.CRAC_PASS_TMA
+        return img, C.crac_image_serialize(img), ora.checkpoint(host())
+
+    try:
+        for i, n in enumerate(sizes):
+            C.crac_ctx_register_alloc(ctx, base + int(offs[i]), n)
+            ora.register(base + int(offs[i]), n)
+        _, lib1, ora1 = checkpoint()
+        assert lib1 == ora1
+        first = W.chunk_layout(sizes, S)
+        muts = pattern_mutations(first, sizes, S, "random10", seed=n_allocs)
+        rows = []
+        for m in muts:
+            a = int(np.searchsorted(first, m.chunk, side="right") - 1)
+            lo = (m.chunk - int(first[a])) * S
+            rows.append((base + int(offs[a]) + lo, min(S, sizes[a] - lo), m.mask))
+        ent = torch.from_numpy(np.array(rows, dtype=np.uint64).view(np.int64)).to("cuda")
+        testkit.mutate_xor(ent.data_ptr(), len(rows), stream)
+        torch.cuda.synchronize()
+        img2, lib2, ora2 = checkpoint()
+        assert lib2 == ora2
+        assert O.parse_image(lib2).idx.tolist() == sorted(m.chunk for m in muts)
+        want = buf.clone()
+        buf.zero_()
+        C.crac_ctx_restart(ctx, img2, stream)
+        torch.cuda.synchronize()
+        for i, n in enumerate(sizes):   # the 256-byte padding between allocations stays zero
+            assert torch.equal(buf[offs[i]:offs[i] + n], want[offs[i]:offs[i] + n])
+    finally:
+        torch.cuda.synchronize()
+        for img in imgs:
+            C.crac_image_release(img)
+        C.crac_ctx_destroy(ctx)
 
 
 @pytest.mark.parametrize("mode", ["per_alloc", "segments", "device", "device_segments"])
