@@ -275,18 +275,22 @@ def run_crac(args):
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
     ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
 
-    def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None):
+    def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None, phases=None):
         mutate()
         t0 = time.perf_counter()
         img = C.crac_ctx_checkpoint(ctx, stream)
+        t1 = time.perf_counter()
         if host:
             C.crac_image_wait(img)
+        t2 = time.perf_counter()
         if lat_ms is not None:
-            lat_ms.append((time.perf_counter() - t0) * 1e3)
+            lat_ms.append((t2 - t0) * 1e3)
         if pass_ms is not None:
             # filled in place (no per-field Python work inside the timed loop)
             pass_ms.append(C.crac_ctx_last_pass(ctx, C.CracPassInfo()))
         C.crac_ctx_restart(ctx, img, stream)
+        if phases is not None:
+            phases.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, (time.perf_counter() - t2) * 1e3))
         if rst is not None:
             rst.append(C.crac_ctx_last_restart(ctx, C.CracRestartInfo()))
         C.crac_image_release(img)
@@ -408,10 +412,10 @@ def run_crac(args):
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e_pass = []
+        e_pass, e_phase = [], []
         e0.record(stream)
         for _ in range(e2e_steps):
-            step(ctx_host, host=True, pass_ms=e_pass)
+            step(ctx_host, host=True, pass_ms=e_pass, phases=e_phase)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -423,7 +427,10 @@ def run_crac(args):
         h2d = int(B + d_e + 16 * k_e + 8 * n + 2 * n + 32 * len(sizes))
         e2e = {"value": bytes_per_step * e2e_steps * world / (te / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-               "ms_per_step": te / e2e_steps, "link": link}
+               "ms_per_step": te / e2e_steps, "link": link,
+               "phases_ms": {"checkpoint_call": statistics.median(p[0] for p in e_phase),
+                             "drain_wait": statistics.median(p[1] for p in e_phase),
+                             "restart_call": statistics.median(p[2] for p in e_phase)}}
 
     clocks = sampler.stop()
     clocks["window"] = "warm-up through the end of the e2e leg"
@@ -594,32 +601,28 @@ def run_config3(args):
 # Config 4: 120 GiB / 2048 allocations, dirty sweep, autotuned chunk size
 # ---------------------------------------------------------------------------
 
-def run_config4(args):
+def c4_memory(total: int, n: int, dev):
+    """Config-4-shaped device memory (Zipf sizes, uint8 / fp32 / int64 contents)
+    and a mutator that rewrites a fraction of its 4 KiB pages."""
     import torch
-    import paper_2008_10596_gb300 as C
     from paper_2008_10596_gb300 import testkit
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    total = (args.total_mib << 20) if args.total_mib != 4096 else 120 * W.GIB
-    wl = W.config4(total=total)
+    wl = W.config4(total=total, n=n)
     sizes = wl.sizes
-    B = sum(sizes)
     g = torch.Generator(device=dev)
     g.manual_seed(wl.seed)
     bufs = []
-    for i, n in enumerate(sizes):     # uint8 / fp32 N(0,1) / int64 uniform, cycling
+    for i, nb in enumerate(sizes):     # uint8 / fp32 N(0,1) / int64 uniform, cycling
         if i % 3 == 0:
-            t = torch.randint(0, 256, (n,), generator=g, device=dev, dtype=torch.uint8)
+            t = torch.randint(0, 256, (nb,), generator=g, device=dev, dtype=torch.uint8)
         elif i % 3 == 1:
-            t = torch.randn(n // 4, generator=g, device=dev, dtype=torch.float32).view(torch.uint8)
+            t = torch.randn(nb // 4, generator=g, device=dev, dtype=torch.float32).view(torch.uint8)
         else:
-            t = torch.randint(-(1 << 62), 1 << 62, (n // 8,), generator=g, device=dev, dtype=torch.int64).view(torch.uint8)
+            t = torch.randint(-(1 << 62), 1 << 62, (nb // 8,), generator=g, device=dev, dtype=torch.int64).view(torch.uint8)
         bufs.append(t)
     page_counts = torch.tensor([n // 4096 for n in sizes], device=dev, dtype=torch.int64)
     page_first = torch.cumsum(page_counts, 0) - page_counts
     bases = torch.tensor([b.data_ptr() for b in bufs], device=dev, dtype=torch.int64)
     n_pages = int(page_counts.sum().item())
-    peak, _ = load_peaks()
 
     def mutate(frac, seed):
         k = int(round(frac * n_pages))
@@ -636,6 +639,18 @@ def run_config4(args):
         torch.cuda.synchronize()
         return k
 
+    return sizes, bufs, mutate
+
+
+def run_config4(args):
+    import torch
+    import paper_2008_10596_gb300 as C
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    total = (args.total_mib << 20) if args.total_mib != 4096 else 120 * W.GIB
+    sizes, bufs, mutate = c4_memory(total, 2048, dev)
+    B = sum(sizes)
+    peak, _ = load_peaks()
     cands = [4 * W.KIB, 64 * W.KIB, 256 * W.KIB]
     stream = torch.cuda.current_stream(dev)
     points = []
@@ -660,12 +675,70 @@ def run_config4(args):
         points.append({"dirty_fraction_4k_pages": frac, "per_chunk_size": per,
                        "chosen_chunk_bytes": res["chosen_chunk_bytes"],
                        "chosen_pass_kernel": res["chosen_pass_kernel"], "cost_ms": res["cost_ms"],
-                       "variant_ms_at_chosen": res["variant_ms"]})
+                       "variant_ms_at_chosen": res["variant_ms"],
+                       "chosen_ldg_chunks_per_tile": res["chosen_chunks_per_tile"],
+                       "ldg_tile_ms": dict(zip(res["ldg_tiles"], res["ldg_tile_ms"]))})
         C.crac_ctx_destroy(ctx)
     line = {"workload": f"c4: {len(sizes)} allocations, Zipf(1.1) sizes = {B / 2**30:.1f} GiB, uint8/fp32/int64",
             "tracked_bytes": B, "link_gbs_assumed": 190.0, "peak_gbs": peak, "points": points,
             "note": "pass = split graph (hash, finalize+compact, gather into 8 GiB staging segments), device time; "
                     "dirty bytes measured by the pass against the previous observation"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Pass kernels side by side: chunk size x dirty fraction x kernel
+# ---------------------------------------------------------------------------
+
+PASS_NAMES = {"split": 3, "ldg": 1, "tma": 2}
+
+
+def run_passes(args):
+    """Each pass kernel on the same config-4-shaped memory (default 32 GiB,
+    512 allocations), at each chunk size and fraction of rewritten 4 KiB
+    pages: device time of a delta pass (best of 3) against a baseline taken
+    right before it, device-resident images."""
+    import torch
+    import paper_2008_10596_gb300 as C
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
+    n_allocs = max(16, int(512 * total / (32 * W.GIB)))
+    sizes, bufs, mutate = c4_memory(total, n_allocs, dev)
+    B = sum(sizes)
+    peak, _ = load_peaks()
+    stream = torch.cuda.current_stream(dev)
+    points = []
+    for S in [int(x) * W.KIB for x in args.chunk_kib.split(",")]:
+        n = sum(-(-b // S) for b in sizes)
+        for frac in [float(x) for x in args.dirty.split(",")]:
+            for name in args.kernels.split(","):
+                ctx = C.crac_ctx_create(C.crac_config_default(
+                    chunk_bytes=S, lineage=5, device=0, staging_bytes=8 * W.GIB,
+                    image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=PASS_NAMES[name],
+                    ctas_per_sm=args.ctas_per_sm if name == "ldg" else 0,
+                    chunks_per_tile=args.chunks_per_tile if name == "ldg" else 0))
+                for b in bufs:
+                    C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
+                C.crac_image_release(C.crac_ctx_checkpoint(ctx, stream))
+                best = None
+                for r in range(3):
+                    mutate(frac, 7 + r)
+                    C.crac_image_release(C.crac_ctx_checkpoint(ctx, stream))
+                    info = C.crac_ctx_last_pass(ctx)
+                    if best is None or info["device_ms"] < best["device_ms"]:
+                        best = info
+                C.crac_ctx_destroy(ctx)
+                ms, D, k = best["device_ms"], best["payload_bytes"], best["k"]
+                alg = B + D + 16 * n + 16 * k
+                points.append({"chunk_bytes": S, "dirty_fraction_4k_pages": frac, "kernel": name,
+                               "grid": best["grid"], "chunks_per_tile": best["chunks_per_tile"],
+                               "pass_ms": ms, "dirty_bytes": D, "k": k, "tracked_gbs": B / (ms / 1e3) / 1e9,
+                               "hbm_frac": alg / (ms / 1e3) / 1e9 / peak})
+    line = {"workload": f"passes: {len(sizes)} allocations, Zipf(1.1) sizes = {B / 2**30:.1f} GiB, "
+                        "uint8/fp32/int64", "tracked_bytes": B, "peak_gbs": peak, "points": points,
+            "note": "hbm_frac = (B + D + 16 n + 16 k) / device time / peak; the split pass moves B + 2D"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -842,8 +915,13 @@ def main():
                     help="tracked bytes of the config-2 workload (default 4096 = the full config)")
     ap.add_argument("--requests", type=int, default=1200, help="c5: requests in the serving loop")
     ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2 (default): the headline line; c3/c4/c5: their own JSON lines")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes"],
+                    help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
+    ap.add_argument("--chunk-kib", default="4,64", help="passes: chunk sizes in KiB")
+    ap.add_argument("--dirty", default="0,0.1,0.5,1", help="passes: fractions of 4 KiB pages rewritten")
+    ap.add_argument("--kernels", default="split,ldg,tma", help="passes: pass kernels")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="passes: LDG CTAs per SM (0 = occupancy)")
+    ap.add_argument("--chunks-per-tile", type=int, default=0, help="passes: LDG tile in chunks (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "crac":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -855,6 +933,8 @@ def main():
         return run_config4(args)
     if args.workload == "c5":
         return run_config5(args)
+    if args.workload == "passes":
+        return run_passes(args)
     return run_crac(args)
 
 

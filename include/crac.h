@@ -315,7 +315,8 @@ typedef struct crac_tune_result {
     double mean_dirty_bytes[CRAC_TUNE_MAX];
     float cost_ms[CRAC_TUNE_MAX];          /* pass + drain estimate (apply) */
     float variant_ms[4];                   /* pass time per CRAC_PASS_* at the chosen
-                                              size (apply); 0 = not applicable */
+                                              size (apply); 0 = not applicable or
+                                              not timed */
     uint32_t chosen_chunks_per_tile;       /* LDG tile kept by apply (0 = not tuned:
                                               fixed in the config, or LDG not chosen) */
     uint32_t ldg_tiles[3];                 /* LDG tiles (chunks) timed by apply; 0 = unused */
@@ -338,13 +339,14 @@ CRAC_API crac_status_t crac_ctx_tune_observe(crac_ctx_t *ctx, crac_stream_t stre
                                              uint32_t n, crac_tune_result_t *out);
 
 /*
- * End the session: choose the chunk size with the lowest mean cost
- * (pass time + dirty bytes / link_gbs; link_gbs <= 0 counts the device pass
- * only), then time each pass kernel at that size on the current memory and
- * keep the fastest.  When the configuration leaves chunks_per_tile at 0, the
- * LDG kernel is timed at three tile sizes (half, equal to and twice its
- * default) and, if LDG wins, the fastest tile is written to the context's
- * chunks_per_tile.  If the chunk size changes, the context's baseline is
+ * End the session.  Each candidate chunk size has a mean cost from the
+ * observations (pass time + dirty bytes / link_gbs; link_gbs <= 0 counts the
+ * device pass only).  At every size whose cost is within 5% of the lowest,
+ * each pass kernel is timed on the last observation's dirty set, and the
+ * size and kernel with the lowest pass + drain time are kept.  When the
+ * configuration leaves chunks_per_tile at 0, the LDG kernel is timed at three
+ * tile sizes (half, equal to and twice its default) and, if LDG wins, the
+ * fastest tile is written to the context's chunks_per_tile.  If the chunk size changes, the context's baseline is
  * dropped, so its next checkpoint is FULL (which also ends the delta chain,
  * since a chain holds one chunk size).  Needs at least two observe rounds
  * (CRAC_ERR_UNSUPPORTED otherwise).

@@ -1750,43 +1750,39 @@ crac_status_t ctx_tune_observe(crac_ctx *c, cudaStream_t s, const uint32_t *size
     return CRAC_OK;
 }
 
-crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_tune_result_t *out) {
-    if (c->tune_ctx.empty() || c->tune_rounds == 0) return CRAC_ERR_UNSUPPORTED;
-    const uint32_t n = (uint32_t)c->tune_ctx.size();
-    std::vector<float> cost(n);
-    uint32_t best = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        const double ms = c->tune_sum_ms[i] / c->tune_rounds;
-        const double bytes = c->tune_sum_bytes[i] / c->tune_rounds;
-        cost[i] = (float)(ms + (link_gbs > 0 ? bytes / (link_gbs * 1e9) * 1e3 : 0.0));
-        if (cost[i] < cost[best]) best = i;
-    }
-    crac_ctx *t = c->tune_ctx[best];
+// Pass kernels (and LDG tiles) timed on one candidate chunk size.
+struct VariantTiming {
+    float vms[4] = {0, 0, 0, 0};   // best time per CRAC_PASS_*; 0 = not applicable
+    uint32_t best_v = CRAC_PASS_SPLIT;
+    uint32_t tiles[3] = {0, 0, 0};
+    float tile_ms[3] = {0, 0, 0};
+    uint32_t best_tile = 0;        // LDG tile of the best LDG time (0 = configured)
+};
+
+// Time every pass kernel on the shadow context `t`, each against the
+// baseline before its last observation (still in the other fingerprint
+// buffer), so that they see the last round's dirty set rather than an
+// unchanged memory.  With chunks_per_tile unset, LDG is timed at half, equal
+// to and twice its default tile.
+crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
     const uint32_t S = 1u << t->log2S;
-    // Pass kernels at the chosen size, each against the baseline before the
-    // last observation (still in the other fingerprint buffer), so that they
-    // see the last round's dirty set rather than an unchanged memory.
     if (t->prev_base_valid) {
         t->fp_cur = 1 - t->fp_cur;
         t->base_first = t->prev_base_first;
         t->base_valid = true;
+        t->prev_base_valid = false;
     }
-    float vms[4] = {0, 0, 0, 0};
-    uint32_t best_v = CRAC_PASS_SPLIT;
     const uint32_t saved = t->cfg.pass_kernel, saved_cpt = t->cfg.chunks_per_tile;
-    // LDG tiles to try: the configured one, or around the default when unset.
-    uint32_t tiles[3] = {saved_cpt, 0, 0};
-    float tile_ms[3] = {0, 0, 0};
+    vt->tiles[0] = saved_cpt;
     if (saved_cpt == 0) {
         int w;
         uint32_t t0;
         pick_split(t, &w, &t0);
         const uint32_t lo = std::max<uint32_t>(1, t0 / 2), hi = std::min<uint32_t>(256, 2 * t0);
-        tiles[0] = t0;
-        tiles[1] = lo != t0 ? lo : 0;
-        tiles[2] = hi != t0 ? hi : 0;
+        vt->tiles[0] = t0;
+        vt->tiles[1] = lo != t0 ? lo : 0;
+        vt->tiles[2] = hi != t0 ? hi : 0;
     }
-    uint32_t best_tile = 0;
     auto time_pass = [&](float *best_ms) {
         for (int r = 0; r < 2; ++r) {
             float ms = 0;
@@ -1800,11 +1796,11 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
         t->cfg.pass_kernel = v;
         float bestm = 0;
-        const int n_tiles = v == CRAC_PASS_LDG && saved_cpt == 0 ? 3 : 1;
-        for (int j = 0; j < n_tiles; ++j) {
-            if (v == CRAC_PASS_LDG && saved_cpt == 0) {
-                if (!tiles[j]) continue;
-                t->cfg.chunks_per_tile = tiles[j];
+        const bool ldg_tiles = v == CRAC_PASS_LDG && saved_cpt == 0;
+        for (int j = 0; j < (ldg_tiles ? 3 : 1); ++j) {
+            if (ldg_tiles) {
+                if (!vt->tiles[j]) continue;
+                t->cfg.chunks_per_tile = vt->tiles[j];
             }
             float ms = 0;
             const crac_status_t st = time_pass(&ms);
@@ -1813,31 +1809,71 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
                 t->cfg.pass_kernel = saved;
                 return st;
             }
-            if (v == CRAC_PASS_LDG) tile_ms[j] = ms;
+            if (v == CRAC_PASS_LDG) vt->tile_ms[j] = ms;
             if (bestm == 0 || ms < bestm) {
                 bestm = ms;
-                if (v == CRAC_PASS_LDG && saved_cpt == 0) best_tile = tiles[j];
+                if (ldg_tiles) vt->best_tile = vt->tiles[j];
             }
         }
-        vms[v] = bestm;
-        if (vms[best_v] == 0 || bestm < vms[best_v]) best_v = v;
+        vt->vms[v] = bestm;
+        if (vt->vms[vt->best_v] == 0 || bestm < vt->vms[vt->best_v]) vt->best_v = v;
     }
-    if (best_v != CRAC_PASS_LDG) best_tile = 0;
+    t->cfg.pass_kernel = saved;
+    if (vt->best_v != CRAC_PASS_LDG) vt->best_tile = 0;
+    return CRAC_OK;
+}
+
+crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_tune_result_t *out) {
+    if (c->tune_ctx.empty() || c->tune_rounds == 0) return CRAC_ERR_UNSUPPORTED;
+    const uint32_t n = (uint32_t)c->tune_ctx.size();
+    std::vector<float> cost(n), drain(n);
+    uint32_t best = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const double ms = c->tune_sum_ms[i] / c->tune_rounds;
+        const double bytes = c->tune_sum_bytes[i] / c->tune_rounds;
+        drain[i] = (float)(link_gbs > 0 ? bytes / (link_gbs * 1e9) * 1e3 : 0.0);
+        cost[i] = (float)ms + drain[i];
+        if (cost[i] < cost[best]) best = i;
+    }
+    // The observations ran one pass kernel; sizes that come close under it
+    // may differ once every kernel is tried (a fused kernel is fastest where
+    // most chunks are dirty, at the sizes it supports), so every size within
+    // 5% of the lowest cost has its kernels timed, and the lowest pass +
+    // drain time wins.
+    uint32_t win = best;
+    VariantTiming win_vt;
+    float win_total = 0;
+    bool have = false;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (cost[i] > cost[best] * 1.05f) continue;
+        VariantTiming vt;
+        TRY(time_variants(c->tune_ctx[i], s, &vt));
+        const float total = vt.vms[vt.best_v] + drain[i];
+        if (!have || total < win_total) {
+            win = i;
+            win_vt = vt;
+            win_total = total;
+            have = true;
+        }
+    }
+    crac_ctx *t = c->tune_ctx[win];
+    const uint32_t S = 1u << t->log2S;
+    const uint32_t saved_cpt = t->cfg.chunks_per_tile;
     tune_fill(c, out);
     if (out) {
         for (uint32_t i = 0; i < n; ++i) out->cost_ms[i] = cost[i];
-        for (int v = 0; v < 4; ++v) out->variant_ms[v] = vms[v];
+        for (int v = 0; v < 4; ++v) out->variant_ms[v] = win_vt.vms[v];
         out->chosen_chunk_bytes = S;
-        out->chosen_pass_kernel = best_v;
-        out->chosen_chunks_per_tile = best_tile;
+        out->chosen_pass_kernel = win_vt.best_v;
+        out->chosen_chunks_per_tile = win_vt.best_tile;
         for (int j = 0; j < 3; ++j) {
-            out->ldg_tiles[j] = vms[CRAC_PASS_LDG] > 0 ? tiles[j] : 0;
-            out->ldg_tile_ms[j] = out->ldg_tiles[j] ? tile_ms[j] : 0.f;
+            out->ldg_tiles[j] = win_vt.vms[CRAC_PASS_LDG] > 0 ? win_vt.tiles[j] : 0;
+            out->ldg_tile_ms[j] = out->ldg_tiles[j] ? win_vt.tile_ms[j] : 0.f;
         }
     }
     if (saved_cpt == 0) {
-        c->cfg.chunks_per_tile = best_tile;
-        c->cpt_tuned = best_tile != 0;
+        c->cfg.chunks_per_tile = win_vt.best_tile;
+        c->cpt_tuned = win_vt.best_tile != 0;
     }
     if (S != (1u << c->log2S)) {
         c->cfg.chunk_bytes = S;
@@ -1845,7 +1881,7 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
         c->base_valid = false;
         c->base_first.clear();
     }
-    c->cfg.pass_kernel = best_v;
+    c->cfg.pass_kernel = win_vt.best_v;
     tune_clear(c);
     return CRAC_OK;
 }
