@@ -274,6 +274,7 @@ def run_crac(args):
     ctx_b = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
     ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
+    ctx_sparse = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_SPARSE)
 
     def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None, phases=None):
         mutate()
@@ -299,7 +300,7 @@ def run_crac(args):
         return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms) for i in infos]
 
     # Base images (full) for each context.
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse):
         img = C.crac_ctx_checkpoint(ctx, stream)
         C.crac_image_wait(img)
         C.crac_image_release(img)
@@ -368,8 +369,8 @@ def run_crac(args):
                  "frac": alg_pass / (dev_ms / 1e3) / 1e9 / peak, "tracked_gbs": B / (dev_ms / 1e3) / 1e9}
 
     # ---- batched vs per-allocation launches, and the pass variants -------------
-    cmp = {"per_alloc": ([], []), "split": ([], []), "ldg": ([], []), "tma": ([], [])}
-    ctxs = {"per_alloc": ctx_pa, "split": ctx_b, "ldg": ctx_ldg, "tma": ctx_tma}
+    cmp = {"per_alloc": ([], []), "split": ([], []), "ldg": ([], []), "tma": ([], []), "sparse": ([], [])}
+    ctxs = {"per_alloc": ctx_pa, "split": ctx_b, "ldg": ctx_ldg, "tma": ctx_tma, "sparse": ctx_sparse}
     for _ in range(max(3, min(args.steps, 5))):
         mutate()
         for name, ctx in ctxs.items():
@@ -449,7 +450,7 @@ def run_crac(args):
                                    "single thread")
         cpu["nproc"] = os.cpu_count()
 
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse):
         C.crac_ctx_destroy(ctx)
 
     if rank == 0:
@@ -691,7 +692,7 @@ def run_config4(args):
 # Pass kernels side by side: chunk size x dirty fraction x kernel
 # ---------------------------------------------------------------------------
 
-PASS_NAMES = {"split": 3, "ldg": 1, "tma": 2}
+PASS_NAMES = {"split": 3, "ldg": 1, "tma": 2, "sparse": 4}
 
 
 def run_passes(args):
@@ -919,7 +920,7 @@ def main():
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--chunk-kib", default="4,64", help="passes: chunk sizes in KiB")
     ap.add_argument("--dirty", default="0,0.1,0.5,1", help="passes: fractions of 4 KiB pages rewritten")
-    ap.add_argument("--kernels", default="split,ldg,tma", help="passes: pass kernels")
+    ap.add_argument("--kernels", default="split,ldg,tma,sparse", help="passes: pass kernels")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="passes: LDG CTAs per SM (0 = occupancy)")
     ap.add_argument("--chunks-per-tile", type=int, default=0, help="passes: LDG tile in chunks (0 = default)")
     args = ap.parse_args()

@@ -134,6 +134,16 @@ typedef struct crac_config {
                               warp-specialized; chunk sizes 1 KiB..64 KiB only */
 #define CRAC_PASS_SPLIT 3  /* three kernels in one graph: streaming hash, finalize +
                               compaction, gather */
+#define CRAC_PASS_SPARSE 4 /* the split pass without compaction: the hash kernel writes
+                              every chunk to its uncompacted offset in the image's
+                              payload buffer and the dirty list points into it, so no
+                              byte is read twice (B read + B written, against B + 2D).
+                              Pays off when most chunks are dirty.  Device-resident
+                              images only; an image then holds the tracked bytes of
+                              its segments instead of the dirty ones (serialization
+                              still writes the compact payload).  Falls back to the
+                              split pass when an allocation size is not a multiple of
+                              16 bytes. */
 
 /* Summary of an image (crac_image_info). */
 typedef struct crac_image_info {
@@ -314,7 +324,7 @@ typedef struct crac_tune_result {
     float mean_pass_ms[CRAC_TUNE_MAX];     /* over the delta observations */
     double mean_dirty_bytes[CRAC_TUNE_MAX];
     float cost_ms[CRAC_TUNE_MAX];          /* pass + drain estimate (apply) */
-    float variant_ms[4];                   /* pass time per CRAC_PASS_* at the chosen
+    float variant_ms[8];                   /* pass time per CRAC_PASS_* at the chosen
                                               size (apply); 0 = not applicable or
                                               not timed */
     uint32_t chosen_chunks_per_tile;       /* LDG tile kept by apply (0 = not tuned:

@@ -45,6 +45,7 @@ CRAC_PASS_AUTO = 0
 CRAC_PASS_LDG = 1
 CRAC_PASS_TMA = 2
 CRAC_PASS_SPLIT = 3
+CRAC_PASS_SPARSE = 4
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1
@@ -117,7 +118,7 @@ class CracTuneResult(ctypes.Structure):
         ("chosen_pass_kernel", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32 * CRAC_TUNE_MAX),
         ("last_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("last_dirty_bytes", ctypes.c_uint64 * CRAC_TUNE_MAX),
         ("mean_pass_ms", ctypes.c_float * CRAC_TUNE_MAX), ("mean_dirty_bytes", ctypes.c_double * CRAC_TUNE_MAX),
-        ("cost_ms", ctypes.c_float * CRAC_TUNE_MAX), ("variant_ms", ctypes.c_float * 4),
+        ("cost_ms", ctypes.c_float * CRAC_TUNE_MAX), ("variant_ms", ctypes.c_float * 8),
         ("chosen_chunks_per_tile", ctypes.c_uint32), ("ldg_tiles", ctypes.c_uint32 * 3),
         ("ldg_tile_ms", ctypes.c_float * 3), ("pad0", ctypes.c_uint32),
     ]
@@ -128,7 +129,7 @@ class CracTuneResult(ctypes.Structure):
                 "chosen_pass_kernel": self.chosen_pass_kernel, "chunk_bytes": list(self.chunk_bytes[:n]),
                 "last_pass_ms": list(self.last_pass_ms[:n]), "last_dirty_bytes": list(self.last_dirty_bytes[:n]),
                 "mean_pass_ms": list(self.mean_pass_ms[:n]), "mean_dirty_bytes": list(self.mean_dirty_bytes[:n]),
-                "cost_ms": list(self.cost_ms[:n]), "variant_ms": list(self.variant_ms),
+                "cost_ms": list(self.cost_ms[:n]), "variant_ms": list(self.variant_ms[:5]),
                 "chosen_chunks_per_tile": self.chosen_chunks_per_tile,
                 "ldg_tiles": [t for t in self.ldg_tiles if t],
                 "ldg_tile_ms": [m for t, m in zip(self.ldg_tiles, self.ldg_tile_ms) if t]}

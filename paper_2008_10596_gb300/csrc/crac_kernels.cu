@@ -53,6 +53,8 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr int kMaxCpt = 256;
+// Direct-mode hash output per chunk: its length, and this bit when dirty.
+constexpr uint64_t kAccDirty = 1ull << 63;
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
@@ -1151,10 +1153,10 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
         if (lane == 0) {
             if (spc == 0) {
                 // The warp has seen the whole chunk: finalize here and leave only
-                // the dirty length for the compaction kernel.
+                // the length and the dirty bit for the compaction kernel.
                 const uint64_t fp = fp_finalize(sum, len);
                 P.fp_new[c] = fp;
-                acc[c - P.c_begin] = (!has || fo != fp) ? len : 0ull;
+                acc[c - P.c_begin] = len | ((!has || fo != fp) ? kAccDirty : 0ull);
             } else {
                 atomicAdd(acc + (c - P.c_begin), (unsigned long long)sum);
             }
@@ -1163,7 +1165,7 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
 }
 
 // When log2Seg == log2_chunk the hash kernel has already finalized every
-// chunk and left its dirty length in acc; only the compaction remains.
+// chunk and left its length and dirty bit in acc; only the compaction remains.
 // Hash kernel for chunks of 512 B..4 KiB: one warp iteration covers 8 KiB,
 // i.e. 8192/S whole chunks, one group of LPC = 32*S/8192 lanes per chunk (16
 // vectors per lane), so a warp keeps 8 KiB in flight whatever the chunk size.
@@ -1240,7 +1242,7 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
     if (li == 0 && c < P.c_end) {
         const uint64_t fp = fp_finalize(sum, len);
         P.fp_new[c] = fp;
-        acc[c - P.c_begin] = (!has || fo != fp) ? len : 0ull;
+        acc[c - P.c_begin] = len | ((!has || fo != fp) ? kAccDirty : 0ull);
     }
 }
 
@@ -1276,6 +1278,7 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
     const bool direct = log2Seg == P.log2_chunk;
     __shared__ uint32_t s_wcnt[32];
     __shared__ uint64_t s_wbytes[32];
+    __shared__ uint64_t s_wdirty[32];
     __shared__ uint64_t s_k0, s_d0;
     __shared__ uint32_t s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1291,25 +1294,38 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
         const uint32_t tile = s_tile;
         if (tile >= P.n_tiles) break;
         const uint64_t c = P.c_begin + (uint64_t)tile * kFinNT + threadIdx.x;
-        uint32_t dl = 0;
+        uint32_t dl = 0, len = 0;
         if (c < P.c_end && direct) {
-            dl = (uint32_t)acc[c - P.c_begin];
+            const uint64_t v = acc[c - P.c_begin];
+            len = (uint32_t)v;
+            dl = (v & kAccDirty) ? len : 0u;
         } else if (c < P.c_end) {
             const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
             const uint64_t local = c - d.first_chunk;
-            const uint32_t len = (uint32_t)min(S, d.bytes - (local << log2S));
+            len = (uint32_t)min(S, d.bytes - (local << log2S));
             const uint64_t fp = fp_finalize(acc[c - P.c_begin], len);
             P.fp_new[c] = fp;
             const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
             dl = dirty ? len : 0u;
         }
+        // Bytes that advance the staging offset: the dirty ones, or in the
+        // sparse pass every chunk's (each sits at its uncompacted offset).
+        const uint32_t sv = P.sparse ? len : dl;
         const unsigned m = __ballot_sync(kFull, dl != 0);
-        const uint64_t incl = warp_incl_scan(dl, lane);
+        const uint64_t incl = warp_incl_scan(sv, lane);
+        if (P.sparse) {
+            const uint64_t wd = warp_sum((uint64_t)dl);
+            if (lane == 0) s_wdirty[warp] = wd;
+        }
         if (lane == 31) {
             s_wcnt[warp] = __popc(m);
             s_wbytes[warp] = incl;
         }
         __syncthreads();
+        if (P.sparse && warp == 1) {   // the tile's dirty bytes, one atomic per tile
+            const uint64_t td = warp_sum(s_wdirty[lane]);
+            if (lane == 0 && td) atomicAdd(&P.ctrl->payload, (unsigned long long)td);
+        }
         if (warp == 0) {
             const uint32_t wc = s_wcnt[lane];
             const uint64_t wb = s_wbytes[lane];
@@ -1357,7 +1373,7 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
             const uint64_t j = s_k0 + s_wcnt[warp] + __popc(m & ((1u << lane) - 1u));
             if (j < P.idx_cap) {
                 P.idx_out[j] = c;
-                P.off_out[j] = s_d0 + s_wbytes[warp] + incl - dl;
+                P.off_out[j] = s_d0 + s_wbytes[warp] + incl - sv;
             } else {
                 atomicOr(&P.ctrl->err, kErrBounds);
             }

@@ -20,8 +20,9 @@ struct CkptCtrl {
     unsigned int ticket;       // next tile to hand out
     unsigned int err;          // kErr* bits
     unsigned long long k;      // dirty chunks in this segment
-    unsigned long long D;      // dirty bytes in this segment
-    unsigned long long pad[5];
+    unsigned long long D;      // dirty bytes in this segment (sparse pass: all its bytes)
+    unsigned long long payload;  // sparse pass: dirty bytes in this segment
+    unsigned long long pad[4];
 };
 static_assert(sizeof(CkptCtrl) == 64, "CkptCtrl layout");
 constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
@@ -55,6 +56,11 @@ struct CkptParams {
     uint32_t full_copy;
     const uint64_t *alloc_prefix;   // payload bytes of all allocations before each one
     uint64_t seg_base;              // payload offset of the segment's first chunk
+    // Sparse split pass (with full_copy, on delta checkpoints too): every
+    // chunk is written at its uncompacted offset, each dirty entry's offset
+    // points there, ctrl->D counts the segment's bytes and ctrl->payload the
+    // dirty ones; nothing is gathered.
+    uint32_t sparse;
     // TMA pass: the allocations' first_chunk column fits in the CTA's shared
     // memory (n_allocs <= ckpt_tma_cached_allocs()) and is searched there.
     uint32_t first_cached;

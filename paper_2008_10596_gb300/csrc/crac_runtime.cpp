@@ -345,6 +345,8 @@ struct ImgAlloc {
 struct Piece {
     uint64_t k0 = 0, k = 0;         // entries [k0, k0+k) of the image's dirty list
     uint64_t off0 = 0, bytes = 0;   // payload bytes [off0, off0+bytes)
+    uint64_t span = 0;              // sparse piece: bytes of `dev` that the entries'
+                                    // offsets index (0: compact, offsets are prefixes)
     Block host;                     // host residency: pinned copy
     Block dev;                      // device residency: payload
     Block idx_dev, off_dev;         // device residency: idx[k], off[k+1] (piece-relative)
@@ -547,6 +549,7 @@ struct crac_ctx {
     crac_pass_info_t last{};
     crac_restart_info_t last_restart{};
     bool full_copy_ok = false;   // current pass: no baseline anywhere and 16-byte sizes
+    bool sparse_ok = false;      // current pass: CRAC_PASS_SPARSE, device images, 16-byte sizes
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
     // autotuner session: one shadow context per candidate chunk size
@@ -577,7 +580,9 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
     if (cfg.warps_per_chunk && cfg.warps_per_chunk != 1 && cfg.warps_per_chunk != 8)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
-    if (cfg.pass_kernel > CRAC_PASS_SPLIT) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
+        return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
         return CRAC_ERR_INVALID_ARG;
     if (cfg.timeout_ns == 0) cfg.timeout_ns = kDefaultTimeoutNs;
@@ -845,7 +850,8 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         return CRAC_ERR_CUDA;
     }
     const bool split = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
-                       (c->cfg.pass_kernel == CRAC_PASS_SPLIT || c->cfg.pass_kernel == CRAC_PASS_AUTO);
+                       (c->cfg.pass_kernel == CRAC_PASS_SPLIT || c->cfg.pass_kernel == CRAC_PASS_AUTO ||
+                        c->cfg.pass_kernel == CRAC_PASS_SPARSE);
     if (split) {
         const uint32_t cptF = (uint32_t)split_finalize_threads();
         const uint64_t n_tiles = (nseg + cptF - 1) / cptF;
@@ -877,8 +883,10 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.tile_bytes = P.tile_cnt + n_tiles;
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
-        // FULL pass: chunks are written to staging by the hash kernel.
-        P.full_copy = c->full_copy_ok && staging ? 1u : 0u;
+        // FULL pass, or the sparse pass: chunks are written to staging by the
+        // hash kernel, at their uncompacted offsets.
+        P.sparse = c->sparse_ok && staging ? 1u : 0u;
+        P.full_copy = (c->full_copy_ok || P.sparse) && staging ? 1u : 0u;
         P.alloc_prefix = (const uint64_t *)(desc_dev + c->allocs.size());
         {
             const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
@@ -899,7 +907,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         c->last.chunks_per_tile = cptF;
         c->last.warps_per_chunk = 0;
         c->last.kernel_launches += 3;
-        c->last.pass_kernel = CRAC_PASS_SPLIT;
+        c->last.pass_kernel = P.sparse ? CRAC_PASS_SPARSE : CRAC_PASS_SPLIT;
     } else if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
         const uint64_t S = 1ull << c->log2S;
         const bool tma = c->cfg.pass_kernel == CRAC_PASS_TMA;
@@ -1088,6 +1096,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             pre += c->allocs[a].bytes;
         }
         c->full_copy_ok = !any_base && all16;
+        c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE && dev_res && all16;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
         if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1158,7 +1167,9 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             pc.k0 = k_base;
             pc.k = ctrl.k;
             pc.off0 = d_base;
-            pc.bytes = ctrl.D;
+            const bool sparse = c->sparse_ok && !host_res;
+            pc.bytes = sparse ? ctrl.payload : ctrl.D;
+            pc.span = sparse ? ctrl.D : 0;
             if (fault_hit(CRAC_FAULT_DRAIN)) {
                 im->pieces.push_back(pc);
                 t_last_cuda = (int)cudaErrorLaunchFailure;
@@ -1186,7 +1197,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             im->pieces.push_back(pc);
             if (e != cudaSuccess) return fail(cuda_status(e));
             k_base += ctrl.k;
-            d_base += ctrl.D;
+            d_base += pc.bytes;
         }
         cudaError_t e;
         if (host_res) {
@@ -1314,7 +1325,8 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
         for (const Piece &pc : im->pieces) {
             if (!pc.k) continue;
             rph[ppos++] = RestorePiece{(uint64_t)pc.idx_dev.p, (uint64_t)pc.off_dev.p, (uint64_t)pc.dev.p, pc.k,
-                                       entries, pc.bytes, (uint32_t)i, (uint32_t)d0, (uint32_t)im->allocs.size(), 0};
+                                       entries, pc.span ? pc.span : pc.bytes, (uint32_t)i, (uint32_t)d0,
+                                       (uint32_t)im->allocs.size(), 0};
             entries += pc.k;
         }
     }
@@ -1503,7 +1515,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
                 P.off = (const uint64_t *)pc.off_dev.p;
                 P.payload = pc.dev.p;
                 P.origin = 0;
-                P.window = pc.bytes;
+                P.window = pc.span ? pc.span : pc.bytes;
                 CK(launch_scatter(P, (int)std::min<uint64_t>((pc.k + 7) / 8, (uint64_t)grid), s));
                 ri.entries_scanned += pc.k;
                 ri.scatter_launches++;
@@ -1651,6 +1663,8 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
         pre += c->allocs[a].bytes;
     }
     c->full_copy_ok = !any_base && all16;
+    c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE &&
+                   c->cfg.image_residency == CRAC_RESIDENCY_DEVICE && all16;
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
     uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
@@ -1669,7 +1683,7 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
         TRY(run_segment(c, sg, (const CkptDesc *)c->desc.p, first, (uint64_t *)c->idx.p, (uint64_t *)c->off.p,
                         sg.c1 - sg.c0, (uint8_t *)c->staging.p, sg.bytes, s, &ctrl, ms));
         *k_out += ctrl.k;
-        *d_out += ctrl.D;
+        *d_out += c->sparse_ok ? ctrl.payload : ctrl.D;
     }
     CK(cudaEventRecord(c->ev_last, s));
     if (commit) {
@@ -1752,7 +1766,7 @@ crac_status_t ctx_tune_observe(crac_ctx *c, cudaStream_t s, const uint32_t *size
 
 // Pass kernels (and LDG tiles) timed on one candidate chunk size.
 struct VariantTiming {
-    float vms[4] = {0, 0, 0, 0};   // best time per CRAC_PASS_*; 0 = not applicable
+    float vms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // best time per CRAC_PASS_*; 0 = not applicable
     uint32_t best_v = CRAC_PASS_SPLIT;
     uint32_t tiles[3] = {0, 0, 0};
     float tile_ms[3] = {0, 0, 0};
@@ -1792,8 +1806,10 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
         }
         return CRAC_OK;
     };
-    for (uint32_t v : {(uint32_t)CRAC_PASS_SPLIT, (uint32_t)CRAC_PASS_LDG, (uint32_t)CRAC_PASS_TMA}) {
+    for (uint32_t v : {(uint32_t)CRAC_PASS_SPLIT, (uint32_t)CRAC_PASS_LDG, (uint32_t)CRAC_PASS_TMA,
+                       (uint32_t)CRAC_PASS_SPARSE}) {
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
+        if (v == CRAC_PASS_SPARSE && t->cfg.image_residency != CRAC_RESIDENCY_DEVICE) continue;
         t->cfg.pass_kernel = v;
         float bestm = 0;
         const bool ldg_tiles = v == CRAC_PASS_LDG && saved_cpt == 0;
@@ -1862,7 +1878,7 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
     tune_fill(c, out);
     if (out) {
         for (uint32_t i = 0; i < n; ++i) out->cost_ms[i] = cost[i];
-        for (int v = 0; v < 4; ++v) out->variant_ms[v] = win_vt.vms[v];
+        for (int v = 0; v < 8; ++v) out->variant_ms[v] = win_vt.vms[v];
         out->chosen_chunk_bytes = S;
         out->chosen_pass_kernel = win_vt.best_v;
         out->chosen_chunks_per_tile = win_vt.best_tile;
@@ -2366,6 +2382,30 @@ static uint64_t get64(const uint8_t *p) {
     return v;
 }
 
+namespace {
+// Compact payload of a sparse device piece: its dirty chunks, in list order,
+// taken from their uncompacted offsets.
+crac_status_t sparse_compact(const crac_image *im, const Piece &pc, uint8_t *out) {
+    std::vector<uint8_t> span(pc.span);
+    std::vector<uint64_t> off(pc.k);
+    CK(cudaMemcpy(span.data(), pc.dev.p, pc.span, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(off.data(), pc.off_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    const uint64_t *idx = (const uint64_t *)im->idx_h.p + pc.k0;
+    const uint32_t log2S = log2u(im->chunk_bytes);
+    uint64_t o = 0;
+    size_t a = 0;
+    for (uint64_t j = 0; j < pc.k; ++j) {
+        const uint64_t c = idx[j];   // ascending
+        while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= c) ++a;
+        const uint64_t len = chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+        if (off[j] + len > pc.span || o + len > pc.bytes) return CRAC_ERR_CORRUPT;
+        std::memcpy(out + o, span.data() + off[j], len);
+        o += len;
+    }
+    return o == pc.bytes ? CRAC_OK : CRAC_ERR_CORRUPT;
+}
+}  // namespace
+
 crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
     if (!image || !need) return CRAC_ERR_INVALID_ARG;
     crac_image *im = const_cast<crac_image *>(image);
@@ -2406,7 +2446,8 @@ crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t 
         if (!pc.bytes) continue;
         if (im->residency == CRAC_RESIDENCY_DEVICE) {
             DeviceGuard g(im->device);
-            CK(cudaMemcpy(p + pc.off0, pc.dev.p, pc.bytes, cudaMemcpyDeviceToHost));
+            if (pc.span) TRY(sparse_compact(im, pc, p + pc.off0));
+            else CK(cudaMemcpy(p + pc.off0, pc.dev.p, pc.bytes, cudaMemcpyDeviceToHost));
         } else {
             std::memcpy(p + pc.off0, pc.host.p, pc.bytes);
         }

@@ -49,12 +49,14 @@ def test_config_validation(C):
                 dict(image_residency=7), dict(launch_mode=9), dict(threads=128),
                 dict(warps_per_chunk=3), dict(chunks_per_tile=1000), dict(pass_kernel=5),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
-                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10)):
+                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10),
+                dict(pass_kernel=C.CRAC_PASS_SPARSE)):        # needs device-resident images
         with pytest.raises(C.CracError) as e:
             C.crac_ctx_create(C.crac_config_default(**bad))
         assert e.value.code == C.CRAC_ERR_INVALID_ARG
     for ok in (dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=1024),
-               dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=64 << 10)):
+               dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=64 << 10),
+               dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE)):
         C.crac_ctx_destroy(C.crac_ctx_create(C.crac_config_default(**ok)))
 
 

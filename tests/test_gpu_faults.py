@@ -17,16 +17,19 @@ from tests.gpu_harness import Harness, pattern_mutations
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 
 
-@pytest.mark.parametrize("kern", [C.CRAC_PASS_TMA, C.CRAC_PASS_LDG])
+@pytest.mark.parametrize("kern", [C.CRAC_PASS_TMA, C.CRAC_PASS_LDG, C.CRAC_PASS_SPARSE])
 @pytest.mark.parametrize("step,code", [(C.CRAC_FAULT_PASS, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_DRAIN, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_ALLOC, C.CRAC_ERR_OOM),
                                        (C.CRAC_FAULT_DEVICE_WAIT, C.CRAC_ERR_TIMEOUT)])
 def test_failed_checkpoint_leaves_state(step, code, kern):
     S = 4096
-    h = Harness(S, lineage=61, timeout_ns=20_000_000, chunks_per_tile=2, pass_kernel=kern)
+    extra = {"image_residency": C.CRAC_RESIDENCY_DEVICE} if kern == C.CRAC_PASS_SPARSE else {}
+    h = Harness(S, lineage=61, timeout_ns=20_000_000, chunks_per_tile=2, pass_kernel=kern, **extra)
     try:
-        for i, n in enumerate([200000, 70000]):
+        # > 1024 chunks, so that the split finalize (the sparse pass's
+        # look-back) has a second tile whose wait can run out
+        for i, n in enumerate([200000, 70000, 4 * 1024 * 1024 + 65536]):
             h.add(n, seed=i + 1)
         _, lib1, ora1 = h.checkpoint()
         assert lib1 == ora1

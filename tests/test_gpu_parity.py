@@ -135,6 +135,95 @@ def test_chunk_sizes_ragged(S, kern):
         h.close()
 
 
+@pytest.mark.parametrize("S,staging", [(512, 0), (4 * KIB, 0), (8 * KIB, 0), (64 * KIB, 0), (256 * KIB, 0),
+                                       (4 * KIB, 96 * KIB), (64 * KIB, 320 * KIB)])
+@pytest.mark.parametrize("pattern", ["none", "all", "alternating", "random10"])
+def test_sparse_pass(S, staging, pattern):
+    """The sparse split pass (every chunk written at its uncompacted offset,
+    the dirty list pointing into it): same serialized images as the oracle,
+    device-side restore of the chain, in the hash kernel's direct (512 B -
+    8 KiB) and segmented (64, 256 KiB) modes, in one or several staging
+    segments.  All sizes are multiples of 16 bytes, so the pass is sparse."""
+    sizes = [16, 4096, S * 5 + 48, 3 * S, 100000 // 16 * 16, S + 16]
+    h = Harness(S, lineage=700 + S % 97, pass_kernel=C.CRAC_PASS_SPARSE, staging_bytes=staging,
+                image_residency=C.CRAC_RESIDENCY_DEVICE)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=120 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        assert C.crac_ctx_last_pass(h.ctx)["pass_kernel"] == C.CRAC_PASS_SPARSE
+        imgs = []
+        for seed in (1, 2):
+            muts = pattern_mutations(h.first(), sizes, S, pattern, seed=seed)
+            h.mutate(muts)
+            img, lib, ora = h.checkpoint()
+            assert lib == ora
+            assert O.parse_image(lib).idx.tolist() == sorted(m.chunk for m in muts)
+            info = C.crac_ctx_last_pass(h.ctx)
+            assert info["pass_kernel"] == C.CRAC_PASS_SPARSE
+            assert info["payload_bytes"] == C.crac_image_info(img)["payload_bytes"]
+            imgs.append(img)
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(imgs[-1])
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+        _, lib4, ora4 = h.checkpoint()   # the restored image is the baseline
+        assert lib4 == ora4 and O.parse_image(lib4).k == 0
+    finally:
+        h.close()
+
+
+def test_sparse_pass_fallback_and_mixed_chain():
+    """A size that is not a multiple of 16 makes the sparse kernel choice run
+    the compacting split pass.  And a chain whose FULL image comes back from
+    serialization (host-resident) and whose delta is a sparse device image is
+    restored through the host path, which reads the sparse offsets."""
+    S = 4 * KIB
+    dev = {"pass_kernel": C.CRAC_PASS_SPARSE, "image_residency": C.CRAC_RESIDENCY_DEVICE}
+    h = Harness(S, lineage=711, **dev)
+    try:
+        h.add(40000, seed=1)
+        h.add(12345, seed=2)
+        for pattern in (None, "alternating"):
+            if pattern:
+                h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, pattern, seed=4))
+            _, lib, ora = h.checkpoint()
+            assert lib == ora
+            assert C.crac_ctx_last_pass(h.ctx)["pass_kernel"] == C.CRAC_PASS_SPLIT
+    finally:
+        h.close()
+    sizes = [40000, 12352, 4096 * 3]
+    h1 = Harness(S, lineage=712, **dev)
+    h2 = Harness(S, lineage=713, **dev)
+    try:
+        for i, n in enumerate(sizes):
+            h1.add(n, seed=10 + i)
+            h2.add(n, data=np.zeros(n, dtype=np.uint8))
+        _, lib1, ora1 = h1.checkpoint()
+        assert lib1 == ora1
+        full = C.crac_image_deserialize(lib1)
+        h2.images.append(full)
+        h2.restart(full, [ora1])
+        assert C.crac_image_info(full)["residency"] == C.CRAC_RESIDENCY_HOST
+        h2.mutate(pattern_mutations(h2.first(), sizes, S, "alternating", seed=6))
+        img2, lib2, ora2 = h2.checkpoint()
+        assert lib2 == ora2 and O.parse_image(lib2).k > 0
+        assert C.crac_ctx_last_pass(h2.ctx)["pass_kernel"] == C.CRAC_PASS_SPARSE
+        want = h2.host()
+        for b in h2.bufs:
+            b.zero()
+        h2.restart(img2)
+        assert C.crac_ctx_last_restart(h2.ctx)["chain_length"] == 2
+        for b, w in zip(h2.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h2.close()
+        h1.close()
+
+
 @pytest.mark.parametrize("n_allocs", [3072, 3073])
 @pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
 def test_tma_many_allocations(n_allocs, residency):
