@@ -1,0 +1,329 @@
+// The image store: reference counts, completion, host copies of device
+// tables, delta chains, and the image part of the C ABI.
+#include "crac_runtime.h"
+
+using namespace crac;
+
+namespace {
+
+std::mutex g_img_mu;
+std::multimap<std::pair<uint64_t, uint64_t>, crac_image *> g_images;   // (lineage, epoch)
+
+}  // namespace
+
+namespace crac {
+
+void table_add(crac_image *im) {
+    std::lock_guard<std::mutex> lk(g_img_mu);
+    g_images.emplace(std::make_pair(im->lineage, im->epoch), im);
+}
+
+void table_remove(crac_image *im) {
+    std::lock_guard<std::mutex> lk(g_img_mu);
+    auto r = g_images.equal_range(std::make_pair(im->lineage, im->epoch));
+    for (auto it = r.first; it != r.second; ++it) {
+        if (it->second == im) {
+            g_images.erase(it);
+            return;
+        }
+    }
+}
+
+void img_ref(crac_image *im) {
+    if (im) im->refs.fetch_add(1);
+}
+
+crac_status_t img_wait(const crac_image *cim, uint64_t timeout_ns) {
+    crac_image *im = const_cast<crac_image *>(cim);
+    if (im->state.load() == 1) return CRAC_OK;
+    if (im->state.load() < 0) return im->state.load();
+    DeviceGuard g(im->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(im->done);
+        if (e == cudaSuccess) {
+            im->state.store(1);
+            return CRAC_OK;
+        }
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            im->state.store(cuda_status(e));
+            return im->state.load();
+        }
+        if (timeout_ns) {
+            const uint64_t el = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                    std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ns) return CRAC_ERR_TIMEOUT;
+        }
+        std::this_thread::yield();
+    }
+}
+
+void img_unref(crac_image *im) {
+    while (im) {
+        if (im->refs.fetch_sub(1) != 1) return;
+        if (im->done) {
+            DeviceGuard g(im->device);
+            cudaEventSynchronize(im->done);
+            cudaEventDestroy(im->done);
+            cudaGetLastError();
+        }
+        table_remove(im);
+        Arena &pa = pinned_arena();
+        pa.free(im->fp_h);
+        pa.free(im->idx_h);
+        if (im->fp_dev.region >= 0) device_arena(im->device).free(im->fp_dev);
+        for (Piece &p : im->pieces) {
+            pa.free(p.host);
+            if (p.dev.region >= 0 || p.idx_dev.region >= 0 || p.off_dev.region >= 0) {
+                Arena &da = device_arena(im->device);
+                da.free(p.dev);
+                da.free(p.idx_dev);
+                da.free(p.off_dev);
+            }
+        }
+        crac_image *parent = im->parent;
+        delete im;
+        im = parent;
+    }
+}
+
+// Host copies of a device image's fingerprint table and chunk list (made on
+// the first request: serialization, or a restart chain resolved on the host).
+crac_status_t img_host_tables(crac_image *im) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (im->host_tables) return CRAC_OK;
+    TRY(img_wait(im, 0));
+    Arena &pa = pinned_arena();
+    if (im->n_chunks) TRY(pa.alloc(im->n_chunks * 8, &im->fp_h));
+    if (im->k) TRY(pa.alloc(im->k * 8, &im->idx_h));
+    DeviceGuard g(im->device);
+    if (im->n_chunks) CK(cudaMemcpy(im->fp_h.p, im->fp_dev.p, im->n_chunks * 8, cudaMemcpyDeviceToHost));
+    for (const Piece &pc : im->pieces)
+        if (pc.k) CK(cudaMemcpy(im->idx_h.p + pc.k0 * 8, pc.idx_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    im->host_tables = true;
+    return CRAC_OK;
+}
+
+// Parent of a delta: the direct link if set, else a live image with the same
+// lineage and the parent's epoch (deserialized images).
+crac_image *img_parent(crac_image *im) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (im->parent) return im->parent;
+    if (im->parent_epoch == kNoParent) return nullptr;
+    std::lock_guard<std::mutex> lk2(g_img_mu);
+    auto r = g_images.equal_range(std::make_pair(im->lineage, im->parent_epoch));
+    for (auto it = r.first; it != r.second; ++it) {
+        if (it->second != im && it->second->state.load() >= 0) {
+            img_ref(it->second);
+            im->parent = it->second;
+            return im->parent;
+        }
+    }
+    return nullptr;
+}
+
+void free_image_blocks(crac_image *im) {
+    im->refs.store(1);
+    im->parent = nullptr;
+    img_unref(im);
+}
+
+}  // namespace crac
+
+extern "C" {
+
+crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns) {
+    if (!image) return CRAC_ERR_INVALID_ARG;
+    return img_wait(image, timeout_ns);
+}
+
+crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out) {
+    if (!image || !out) return CRAC_ERR_INVALID_ARG;
+    crac_image *im = const_cast<crac_image *>(image);
+    if (im->state.load() == 0 && im->done && cudaEventQuery(im->done) == cudaSuccess) im->state.store(1);
+    cudaGetLastError();
+    std::memset(out, 0, sizeof(*out));
+    out->lineage = im->lineage;
+    out->epoch = im->epoch;
+    out->parent_epoch = im->parent_epoch;
+    out->flags = im->flags;
+    out->chunk_bytes = im->chunk_bytes;
+    out->n_allocs = im->allocs.size();
+    out->n_chunks = im->n_chunks;
+    out->k = im->k;
+    out->payload_bytes = im->payload_bytes;
+    out->serialized_bytes = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
+                            im->payload_bytes;
+    out->residency = im->residency;
+    out->complete = im->state.load() == 1 ? 1u : 0u;
+    return CRAC_OK;
+}
+
+static void put32(uint8_t *&p, uint32_t v) {
+    for (int i = 0; i < 4; ++i) *p++ = (uint8_t)(v >> (8 * i));
+}
+static void put64(uint8_t *&p, uint64_t v) {
+    for (int i = 0; i < 8; ++i) *p++ = (uint8_t)(v >> (8 * i));
+}
+static uint32_t get32(const uint8_t *p) {
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+    return v;
+}
+static uint64_t get64(const uint8_t *p) {
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+namespace {
+// Compact payload of a sparse device piece: its dirty chunks, in list order,
+// taken from their uncompacted offsets.
+crac_status_t sparse_compact(const crac_image *im, const Piece &pc, uint8_t *out) {
+    std::vector<uint8_t> span(pc.span);
+    std::vector<uint64_t> off(pc.k);
+    CK(cudaMemcpy(span.data(), pc.dev.p, pc.span, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(off.data(), pc.off_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    const uint64_t *idx = (const uint64_t *)im->idx_h.p + pc.k0;
+    const uint32_t log2S = log2u(im->chunk_bytes);
+    uint64_t o = 0;
+    size_t a = 0;
+    for (uint64_t j = 0; j < pc.k; ++j) {
+        const uint64_t c = idx[j];   // ascending
+        while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= c) ++a;
+        const uint64_t len = chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+        if (off[j] + len > pc.span || o + len > pc.bytes) return CRAC_ERR_CORRUPT;
+        std::memcpy(out + o, span.data() + off[j], len);
+        o += len;
+    }
+    return o == pc.bytes ? CRAC_OK : CRAC_ERR_CORRUPT;
+}
+}  // namespace
+
+crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
+    if (!image || !need) return CRAC_ERR_INVALID_ARG;
+    crac_image *im = const_cast<crac_image *>(image);
+    const uint64_t total = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
+                           im->payload_bytes;
+    *need = (size_t)total;
+    if (!dst) return CRAC_OK;
+    if (cap < total) return CRAC_ERR_INVALID_ARG;
+    TRY(img_wait(im, 0));
+    TRY(img_host_tables(im));
+    uint8_t *p = (uint8_t *)dst;
+    std::memcpy(p, "CRACIMG1", 8);
+    p += 8;
+    put32(p, 1);
+    put32(p, im->flags);
+    put32(p, im->chunk_bytes);
+    put32(p, 1);
+    put64(p, im->lineage);
+    put64(p, im->epoch);
+    put64(p, im->parent_epoch);
+    put64(p, im->allocs.size());
+    put64(p, im->n_chunks);
+    put64(p, im->k);
+    put64(p, im->payload_bytes);
+    for (const ImgAlloc &a : im->allocs) {
+        put64(p, a.id);
+        put64(p, a.orig_ptr);
+        put64(p, a.bytes);
+        put32(p, a.kind);
+        put32(p, 0);
+        put64(p, a.first_chunk);
+    }
+    if (im->n_chunks) std::memcpy(p, im->fp_h.p, 8 * im->n_chunks);
+    p += 8 * im->n_chunks;
+    if (im->k) std::memcpy(p, im->idx_h.p, 8 * im->k);
+    p += 8 * im->k;
+    for (const Piece &pc : im->pieces) {
+        if (!pc.bytes) continue;
+        if (im->residency == CRAC_RESIDENCY_DEVICE) {
+            DeviceGuard g(im->device);
+            if (pc.span) TRY(sparse_compact(im, pc, p + pc.off0));
+            else CK(cudaMemcpy(p + pc.off0, pc.dev.p, pc.bytes, cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(p + pc.off0, pc.host.p, pc.bytes);
+        }
+    }
+    return CRAC_OK;
+}
+
+crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **out) {
+    if (!src || !out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const uint8_t *b = (const uint8_t *)src;
+    if (n < kHeaderBytes || std::memcmp(b, "CRACIMG1", 8) != 0) return CRAC_ERR_CORRUPT;
+    if (get32(b + 8) != 1 || get32(b + 20) != 1) return CRAC_ERR_CORRUPT;
+    const uint32_t flags = get32(b + 12), chunk = get32(b + 16);
+    if (chunk < 16 || chunk > (1u << 24) || (chunk & (chunk - 1)) || (flags & ~CRAC_IMAGE_FULL)) return CRAC_ERR_CORRUPT;
+    const uint64_t na = get64(b + 48), nc = get64(b + 56), k = get64(b + 64), pb = get64(b + 72);
+    if (na > (n / kAllocEntryBytes) || nc > n / 8 || k > nc || pb > n) return CRAC_ERR_CORRUPT;
+    const uint64_t need = kHeaderBytes + kAllocEntryBytes * na + 8 * nc + 8 * k + pb;
+    if (need != n) return CRAC_ERR_CORRUPT;
+    std::unique_ptr<crac_image> im(new crac_image());
+    cudaGetDevice(&im->device);
+    im->flags = flags;
+    im->chunk_bytes = chunk;
+    im->residency = CRAC_RESIDENCY_HOST;
+    im->lineage = get64(b + 24);
+    im->epoch = get64(b + 32);
+    im->parent_epoch = get64(b + 40);
+    im->n_chunks = nc;
+    im->k = k;
+    im->payload_bytes = pb;
+    const uint32_t log2S = log2u(chunk);
+    const uint8_t *p = b + kHeaderBytes;
+    uint64_t expect_first = 0;
+    im->allocs.resize(na);
+    for (uint64_t a = 0; a < na; ++a, p += kAllocEntryBytes) {
+        ImgAlloc &r = im->allocs[a];
+        r = ImgAlloc{get64(p), get64(p + 8), get64(p + 16), get32(p + 24), get64(p + 32)};
+        if (r.bytes == 0 || r.kind > 1 || r.first_chunk != expect_first) return CRAC_ERR_CORRUPT;
+        expect_first += ((r.bytes - 1) >> log2S) + 1;
+    }
+    if (expect_first != nc || ((flags & CRAC_IMAGE_FULL) != 0) != (k == nc)) return CRAC_ERR_CORRUPT;
+    const uint8_t *fp = p, *idx = p + 8 * nc, *payload = idx + 8 * k;
+    // idx strictly ascending and payload length equal to the listed chunks' lengths
+    uint64_t acc = 0, prev = 0;
+    size_t a = 0;
+    for (uint64_t j = 0; j < k; ++j) {
+        const uint64_t c = get64(idx + 8 * j);
+        if (c >= nc || (j && c <= prev)) return CRAC_ERR_CORRUPT;
+        prev = c;
+        while (a + 1 < na && im->allocs[a + 1].first_chunk <= c) ++a;
+        acc += chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+    }
+    if (acc != pb) return CRAC_ERR_CORRUPT;
+    Arena &pa = pinned_arena();
+    crac_status_t st = CRAC_OK;
+    Piece pc;
+    pc.k = k;
+    pc.bytes = pb;
+    if (nc) st = pa.alloc(8 * nc, &im->fp_h);
+    if (st == CRAC_OK && k) st = pa.alloc(8 * k, &im->idx_h);
+    if (st == CRAC_OK && pb) st = pa.alloc(pb, &pc.host);
+    if (st != CRAC_OK) {
+        im->pieces.push_back(pc);
+        free_image_blocks(im.release());
+        return st;
+    }
+    if (nc) std::memcpy(im->fp_h.p, fp, 8 * nc);
+    if (k) std::memcpy(im->idx_h.p, idx, 8 * k);
+    if (pb) std::memcpy(pc.host.p, payload, pb);
+    im->pieces.push_back(pc);
+    im->state.store(1);
+    crac_image *img = im.release();
+    table_add(img);
+    *out = img;
+    return CRAC_OK;
+}
+
+crac_status_t crac_image_release(crac_image_t *image) {
+    if (!image) return CRAC_ERR_INVALID_ARG;
+    img_unref(image);
+    return CRAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,757 @@
+// Contexts and the checkpoint pass: registry snapshot (A0), managed prefetch
+// (A1), the batched pass launched as one CUDA graph (A2-A4), the drain to
+// pinned host memory (A5) and the commit (A6); also the trial pass the
+// autotuner runs.
+#include "crac_runtime.h"
+
+using namespace crac;
+
+namespace crac {
+
+crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
+    crac_config_default(&c->cfg);
+    if (cfg_in) {
+        if (cfg_in->struct_size && cfg_in->struct_size != sizeof(crac_config_t)) return CRAC_ERR_INVALID_ARG;
+        c->cfg = *cfg_in;
+        c->cfg.struct_size = sizeof(crac_config_t);
+    }
+    crac_config_t &cfg = c->cfg;
+    if (cfg.chunk_bytes == 0) cfg.chunk_bytes = 65536;
+    if (cfg.chunk_bytes < 16 || cfg.chunk_bytes > (1u << 24) || (cfg.chunk_bytes & (cfg.chunk_bytes - 1)))
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.image_residency > CRAC_RESIDENCY_DEVICE || cfg.launch_mode > CRAC_LAUNCH_PER_ALLOC)
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.threads && cfg.threads != 256) return CRAC_ERR_INVALID_ARG;
+    if (cfg.warps_per_chunk && cfg.warps_per_chunk != 1 && cfg.warps_per_chunk != 8)
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
+        return CRAC_ERR_INVALID_ARG;
+    if (cfg.timeout_ns == 0) cfg.timeout_ns = kDefaultTimeoutNs;
+    c->log2S = log2u(cfg.chunk_bytes);
+    c->lineage = cfg.lineage ? cfg.lineage : (g_lineage_counter.fetch_add(1) + 1);
+    return CRAC_OK;
+}
+
+// CUDA resources are created on the first checkpoint or restart, so that the
+// registry works (and can be tested) without touching the device.
+crac_status_t ctx_cuda_ready(crac_ctx *c) {
+    if (c->cuda_ready) return CRAC_OK;
+    int dev = c->cfg.device;
+    if (dev < 0) CK(cudaGetDevice(&dev));
+    c->device = dev;
+    DeviceGuard g(dev);
+    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_last, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_pass, cudaEventDisableTiming));
+    CK(cudaEventCreate(&c->ev_t0));
+    CK(cudaEventCreate(&c->ev_t1));
+    CK(cudaEventCreate(&c->ev_p0));
+    CK(cudaEventCreate(&c->ev_p1));
+    for (cudaEvent_t &e : c->sev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&c->ev_r0));
+    CK(cudaEventCreate(&c->ev_r1));
+    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
+    TRY(ensure_host(c->serr_h, 256));
+    if (c->cfg.reserve_host_bytes) {
+        TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
+        pinned_arena().mark_reserved();
+    }
+    if (c->cfg.reserve_device_bytes) {
+        TRY(device_arena(dev).reserve(c->cfg.reserve_device_bytes));
+        device_arena(dev).mark_reserved();
+    }
+    c->cuda_ready = true;
+    return CRAC_OK;
+}
+
+void ctx_free_all(crac_ctx *c) {
+    tune_clear(c);
+    if (!c->cuda_ready) {
+        img_unref(c->parent);
+        c->parent = nullptr;
+        return;
+    }
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
+                      &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr})
+        if (b->p) cudaFree(b->p);
+    for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h})
+        if (b->p) cudaFreeHost(b->p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->sgexec) cudaGraphExecDestroy(c->sgexec);
+    if (c->sgraph) cudaGraphDestroy(c->sgraph);
+    for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1, c->sev[0], c->sev[1],
+                          c->sev[2], c->sev[3], c->ev_r0, c->ev_r1})
+        if (e) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
+    cudaGetLastError();
+    img_unref(c->parent);
+    c->parent = nullptr;
+}
+
+// Work split of the fused kernel for the context's chunk size.
+void pick_split(const crac_ctx *c, int *wpc, uint32_t *cpt) {
+    const uint64_t S = 1ull << c->log2S;
+    int w = (int)c->cfg.warps_per_chunk;
+    if (!w) w = S >= 16384 ? 8 : 1;
+    uint32_t t = c->cfg.chunks_per_tile;
+    if (!t) {
+        // One chunk per warp: 128 KiB tiles; a CTA per chunk: 256 KiB tiles,
+        // which hide the look-back better (measured at 64 KiB chunks).
+        const uint64_t tile_bytes = w == 8 ? 256ull << 10 : 128ull << 10;
+        t = (uint32_t)std::max<uint64_t>(1, tile_bytes / S);
+        const uint32_t groups = 8 / w;
+        t = std::max(t, groups);
+        t = std::min<uint32_t>(t, 256);
+    }
+    *wpc = w;
+    *cpt = t;
+}
+
+struct Segment {
+    uint64_t c0, c1, bytes;
+};
+
+// Split the global chunk range into segments of at most `cap` bytes.
+std::vector<Segment> make_segments(const std::vector<AllocRec> &allocs, const std::vector<uint64_t> &first,
+                                   uint32_t log2S, uint64_t cap) {
+    std::vector<Segment> out;
+    const uint64_t S = 1ull << log2S;
+    Segment cur{0, 0, 0};
+    for (size_t a = 0; a < allocs.size(); ++a) {
+        const uint64_t nch = first[a + 1] - first[a];
+        uint64_t local = 0;
+        while (local < nch) {
+            const uint64_t rest_bytes = allocs[a].bytes - (local << log2S);
+            const uint64_t room = cap - cur.bytes;
+            uint64_t take, tb;
+            if (rest_bytes <= room) {
+                take = nch - local;
+                tb = rest_bytes;
+            } else {
+                take = room / S;
+                tb = take * S;
+            }
+            if (take == 0) {
+                out.push_back(cur);
+                cur = Segment{cur.c1, cur.c1, 0};
+                continue;
+            }
+            cur.c1 += take;
+            cur.bytes += tb;
+            local += take;
+        }
+    }
+    if (cur.c1 > cur.c0) out.push_back(cur);
+    return out;
+}
+
+// Build (or update) the graph memset -> fused kernel -> ctrl D2H and launch it.
+crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, const void *fn,
+                                 int threads, size_t smem, int grid, cudaStream_t s) {
+    if (!fn) return CRAC_ERR_INVALID_ARG;
+    CkptParams Pc = P;
+    void *args[] = {&Pc};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(threads);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    cudaMemsetParams mp{};
+    mp.dst = c->work.p;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = work_bytes / 4;
+    mp.height = 1;
+    mp.pitch = 0;
+    bool rebuilt = false;
+    if (c->gexec && c->g_fn == fn) {
+        // Width changes of a memset node may be rejected; rebuild then.
+        if (cudaGraphExecMemsetNodeSetParams(c->gexec, c->g_memset, &mp) != cudaSuccess ||
+            cudaGraphExecKernelNodeSetParams(c->gexec, c->g_kernel, &kp) != cudaSuccess ||
+            cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            c->g_fn = nullptr;
+        }
+    }
+    if (!c->gexec || c->g_fn != fn) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->gexec = nullptr;
+        c->graph = nullptr;
+        CK(cudaGraphCreate(&c->graph, 0));
+        CK(cudaGraphAddMemsetNode(&c->g_memset, c->graph, nullptr, 0, &mp));
+        CK(cudaGraphAddKernelNode(&c->g_kernel, c->graph, &c->g_memset, 1, &kp));
+        CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, c->ctrl_h.p, P.ctrl,
+                                    sizeof(CkptCtrl), cudaMemcpyDeviceToHost));
+        CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+        c->g_fn = fn;
+        c->g_threads = threads;
+        rebuilt = true;
+    }
+    (void)rebuilt;
+    CK(cudaEventRecord(c->ev_t0, s));   // after the host-side updates: times the device work only
+    CK(cudaGraphLaunch(c->gexec, s));
+    count_launches(1);
+    return CRAC_OK;
+}
+
+// Build (or update) the split-pass graph and launch it.
+crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
+                                 uint32_t log2Seg, const void *hash_fn, const int grids[3], cudaStream_t s) {
+    const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn()};
+    const int thr[3] = {split_hash_threads(), split_finalize_threads(), split_gather_threads()};
+    CkptParams Pc = P;
+    unsigned long long *accv = acc;
+    uint32_t segv = log2Seg;
+    void *args[] = {&Pc, &accv, &segv};
+    cudaKernelNodeParams kp[3];
+    for (int i = 0; i < 3; ++i) {
+        kp[i] = cudaKernelNodeParams{};
+        kp[i].func = const_cast<void *>(fns[i]);
+        kp[i].gridDim = dim3(grids[i]);
+        kp[i].blockDim = dim3(thr[i]);
+        kp[i].sharedMemBytes = 0;
+        kp[i].kernelParams = args;
+    }
+    cudaMemsetParams mp{};
+    mp.dst = c->work.p;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = work_bytes / 4;
+    mp.height = 1;
+    bool ok = c->sgexec != nullptr && c->s_hash_fn == hash_fn;
+    if (ok) {
+        ok = cudaGraphExecMemsetNodeSetParams(c->sgexec, c->s_memset, &mp) == cudaSuccess;
+        for (int i = 0; ok && i < 3; ++i)
+            ok = cudaGraphExecKernelNodeSetParams(c->sgexec, c->s_k[i], &kp[i]) == cudaSuccess;
+        if (ok)
+            ok = cudaGraphExecMemcpyNodeSetParams1D(c->sgexec, c->s_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    if (!ok) {
+        if (c->sgexec) cudaGraphExecDestroy(c->sgexec);
+        if (c->sgraph) cudaGraphDestroy(c->sgraph);
+        c->sgexec = nullptr;
+        c->sgraph = nullptr;
+        CK(cudaGraphCreate(&c->sgraph, 0));
+        CK(cudaGraphAddMemsetNode(&c->s_memset, c->sgraph, nullptr, 0, &mp));
+        cudaGraphNode_t prev = c->s_memset;
+        cudaGraphNode_t ev;
+        CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &prev, 1, c->sev[0]));
+        prev = ev;
+        for (int i = 0; i < 3; ++i) {
+            CK(cudaGraphAddKernelNode(&c->s_k[i], c->sgraph, &prev, 1, &kp[i]));
+            CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
+            prev = ev;
+        }
+        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+                                    cudaMemcpyDeviceToHost));
+        CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
+        c->s_hash_fn = hash_fn;
+    }
+    CK(cudaEventRecord(c->ev_t0, s));
+    CK(cudaGraphLaunch(c->sgexec, s));
+    count_launches(3);
+    return CRAC_OK;
+}
+
+// One segment of the checkpoint pass; on return the ctrl block is on the host.
+crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_dev,
+                          const std::vector<uint64_t> &first, uint64_t *idx_d, uint64_t *off_d,
+                          uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap,
+                          cudaStream_t s, CkptCtrl *ctrl_out, float *ms) {
+    const uint64_t nseg = sg.c1 - sg.c0;
+    const uint64_t *fp_old = (const uint64_t *)c->fp[c->fp_cur].p;
+    uint64_t *fp_new = (uint64_t *)c->fp[1 - c->fp_cur].p;
+    const bool inject_wait = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
+    if (fault_hit(CRAC_FAULT_PASS)) {
+        t_last_cuda = (int)cudaErrorLaunchFailure;
+        return CRAC_ERR_CUDA;
+    }
+    const bool split = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
+                       (c->cfg.pass_kernel == CRAC_PASS_SPLIT || c->cfg.pass_kernel == CRAC_PASS_AUTO ||
+                        c->cfg.pass_kernel == CRAC_PASS_SPARSE);
+    if (split) {
+        const uint32_t cptF = (uint32_t)split_finalize_threads();
+        const uint64_t n_tiles = (nseg + cptF - 1) / cptF;
+        if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+        const size_t status_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
+        const size_t work_bytes = status_bytes + 8 * nseg;
+        TRY(ensure_dev(c->work, work_bytes));
+        // 512 B..4 KiB chunks: several whole chunks per warp iteration.
+        const bool small = c->log2S >= 9 && c->log2S < 13;
+        const uint32_t log2Seg = std::min<uint32_t>(c->log2S, 13);
+        const void *hash_fn = small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn();
+        CkptParams P{};
+        P.desc = desc_dev;
+        P.n_allocs = (uint32_t)c->allocs.size();
+        P.log2_chunk = c->log2S;
+        P.c_begin = sg.c0;
+        P.c_end = sg.c1;
+        P.cpt = cptF;
+        P.n_tiles = (uint32_t)n_tiles;
+        P.fp_old = fp_old;
+        P.fp_new = fp_new;
+        P.idx_out = idx_d;
+        P.off_out = off_d;
+        P.idx_cap = idx_cap;
+        P.staging = staging;
+        P.staging_cap = staging_cap;
+        P.ctrl = (CkptCtrl *)c->work.p;
+        P.tile_cnt = (uint64_t *)((uint8_t *)c->work.p + sizeof(CkptCtrl));
+        P.tile_bytes = P.tile_cnt + n_tiles;
+        P.timeout_ns = c->cfg.timeout_ns;
+        P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        // FULL pass, or the sparse pass: chunks are written to staging by the
+        // hash kernel, at their uncompacted offsets.
+        P.sparse = c->sparse_ok && staging ? 1u : 0u;
+        P.full_copy = (c->full_copy_ok || P.sparse) && staging ? 1u : 0u;
+        P.alloc_prefix = (const uint64_t *)(desc_dev + c->allocs.size());
+        {
+            const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
+            uint64_t pre = 0;
+            for (size_t a = 0; a < a0; ++a) pre += c->allocs[a].bytes;
+            P.seg_base = pre + ((sg.c0 - first[a0]) << c->log2S);
+        }
+        unsigned long long *acc = (unsigned long long *)((uint8_t *)c->work.p + status_bytes);
+        const uint64_t n_slots = small ? (nseg + (8192u >> c->log2S) - 1) / (8192u >> c->log2S)
+                                       : nseg << (c->log2S - log2Seg);
+        const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>(
+                           (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(hash_fn, split_hash_threads())));
+        const int gf = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2);
+        const int gg = c->sm_count * 8;
+        const int grids[3] = {gh, gf, gg};
+        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, s));
+        c->last.grid = (uint32_t)gh;
+        c->last.chunks_per_tile = cptF;
+        c->last.warps_per_chunk = 0;
+        c->last.kernel_launches += 3;
+        c->last.pass_kernel = P.sparse ? CRAC_PASS_SPARSE : CRAC_PASS_SPLIT;
+    } else if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
+        const uint64_t S = 1ull << c->log2S;
+        const bool tma = c->cfg.pass_kernel == CRAC_PASS_TMA;
+        int wpc;
+        uint32_t cpt;
+        const void *fn;
+        int threads;
+        size_t smem = 0;
+        int per_sm;
+        if (tma) {
+            if (!c->tma_ready) {
+                CK(ckpt_tma_prepare());
+                c->tma_ready = true;
+            }
+            cpt = (uint32_t)(ckpt_tma_slot_bytes() / S);
+            wpc = (int)std::max<uint64_t>(1, 8 * S / ckpt_tma_slot_bytes());
+            fn = ckpt_tma_fn(wpc);
+            threads = ckpt_tma_threads();
+            smem = ckpt_tma_smem((uint32_t)std::min<size_t>(c->allocs.size(), UINT32_MAX));
+            per_sm = 1;
+        } else {
+            pick_split(c, &wpc, &cpt);
+            fn = ckpt_fused_fn(256, wpc);
+            threads = 256;
+            per_sm = (int)c->cfg.ctas_per_sm;
+            if (!per_sm) per_sm = std::max(1, ckpt_fused_max_ctas_per_sm(256, wpc));
+        }
+        const uint64_t n_tiles = (nseg + cpt - 1) / cpt;
+        if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+        const size_t work_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
+        TRY(ensure_dev(c->work, work_bytes));
+        const int grid = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * per_sm);
+        CkptParams P{};
+        P.desc = desc_dev;
+        P.n_allocs = (uint32_t)c->allocs.size();
+        P.log2_chunk = c->log2S;
+        P.c_begin = sg.c0;
+        P.c_end = sg.c1;
+        P.cpt = cpt;
+        P.n_tiles = (uint32_t)n_tiles;
+        P.fp_old = fp_old;
+        P.fp_new = fp_new;
+        P.idx_out = idx_d;
+        P.off_out = off_d;
+        P.idx_cap = idx_cap;
+        P.staging = staging;
+        P.staging_cap = staging_cap;
+        P.ctrl = (CkptCtrl *)c->work.p;
+        P.tile_cnt = (uint64_t *)((uint8_t *)c->work.p + sizeof(CkptCtrl));
+        P.tile_bytes = P.tile_cnt + n_tiles;
+        P.timeout_ns = c->cfg.timeout_ns;
+        P.skip_first_ticket = (inject_wait && n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
+        P.first_cached = tma && c->allocs.size() <= ckpt_tma_cached_allocs() ? 1u : 0u;
+        TRY(launch_fused_graph(c, P, work_bytes, fn, threads, smem, grid, s));
+        c->last.pass_kernel = tma ? CRAC_PASS_TMA : CRAC_PASS_LDG;
+        c->last.grid = (uint32_t)grid;
+        c->last.chunks_per_tile = cpt;
+        c->last.warps_per_chunk = (uint32_t)wpc;
+        c->last.kernel_launches += 1;
+    } else {
+        TRY(ensure_dev(c->work, sizeof(CkptCtrl)));
+        TRY(ensure_dev(c->lens, nseg * sizeof(uint32_t)));
+        TRY(ensure_dev(c->carry, sizeof(PerAllocCarry)));
+        CkptCtrl *ctrl = (CkptCtrl *)c->work.p;
+        CK(cudaEventRecord(c->ev_t0, s));
+        CK(cudaMemsetAsync(ctrl, 0, sizeof(CkptCtrl), s));
+        CK(cudaMemsetAsync(c->carry.p, 0, sizeof(PerAllocCarry), s));
+        const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
+        for (size_t a = a0; a < c->allocs.size() && first[a] < sg.c1; ++a) {
+            const uint64_t u0 = std::max(first[a], sg.c0), u1 = std::min(first[a + 1], sg.c1);
+            if (u1 <= u0) continue;
+            const int g = (int)std::min<uint64_t>(u1 - u0, (uint64_t)c->sm_count * 8);
+            CK(launch_fp_range(desc_dev + a, u0, u1, c->log2S, fp_old, fp_new, (uint32_t *)c->lens.p,
+                               sg.c0, g, s));
+            CK(launch_compact_range((const uint32_t *)c->lens.p, sg.c0, u0, u1, idx_d, off_d, idx_cap,
+                                    (PerAllocCarry *)c->carry.p, ctrl, s));
+            CK(launch_gather_range(desc_dev + a, c->log2S, idx_d, off_d, (PerAllocCarry *)c->carry.p,
+                                   u1 - u0, idx_cap, staging, staging_cap, ctrl, g, s));
+            c->last.kernel_launches += 3;
+        }
+        CK(cudaMemcpyAsync(c->ctrl_h.p, ctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(c->ev_t1, s));
+    CK(cudaEventRecord(c->ev_pass, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1));
+    *ms += t;
+    if (split) {
+        float a = 0, b = 0, d = 0;
+        if (cudaEventElapsedTime(&a, c->sev[0], c->sev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, c->sev[1], c->sev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&d, c->sev[2], c->sev[3]) == cudaSuccess) {
+            c->last.hash_ms += a;
+            c->last.finalize_ms += b;
+            c->last.gather_ms += d;
+        }
+        cudaGetLastError();
+    }
+    *ctrl_out = *(const CkptCtrl *)c->ctrl_h.p;
+    if (ctrl_out->err & kErrTimeout) return CRAC_ERR_TIMEOUT;
+    if (ctrl_out->err) return CRAC_ERR_CORRUPT;
+    return CRAC_OK;
+}
+
+
+crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
+    if (!out) return CRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    DeviceGuard g(c->device);
+    if (!s) CK(cudaDeviceSynchronize());   // the paper's queue drain before a checkpoint
+    const size_t na = c->allocs.size();
+    const uint32_t log2S = c->log2S;
+    const uint64_t S = 1ull << log2S;
+    std::vector<uint64_t> first(na + 1, 0);
+    uint64_t tracked = 0;
+    for (size_t a = 0; a < na; ++a) {
+        first[a + 1] = first[a] + ((c->allocs[a].bytes + S - 1) >> log2S);
+        tracked += c->allocs[a].bytes;
+    }
+    const uint64_t n = first[na];
+    c->last = crac_pass_info_t{};
+    c->last.tracked_bytes = tracked;
+    c->last.n_chunks = n;
+
+    std::unique_ptr<crac_image> im(new crac_image());
+    im->device = c->device;
+    im->chunk_bytes = (uint32_t)S;
+    im->residency = c->cfg.image_residency;
+    im->lineage = c->lineage;
+    im->epoch = c->epoch_max + 1;
+    im->parent_epoch = c->parent_epoch;
+    im->n_chunks = n;
+    im->allocs.resize(na);
+    for (size_t a = 0; a < na; ++a)
+        im->allocs[a] = ImgAlloc{c->allocs[a].id, c->allocs[a].ptr, c->allocs[a].bytes, c->allocs[a].kind, first[a]};
+    CK(cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming));
+
+    Arena &pa = pinned_arena();
+    Arena &da = device_arena(c->device);
+    crac_status_t st = CRAC_OK;
+    auto fail = [&](crac_status_t code) {
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(c->side);
+        cudaGetLastError();
+        free_image_blocks(im.release());
+        return code;
+    };
+
+    const bool dev_res = c->cfg.image_residency == CRAC_RESIDENCY_DEVICE;
+    im->host_tables = !dev_res;
+    if (n > 0) {
+        if (dev_res) {
+            st = da.alloc(n * 8, &im->fp_dev);
+        } else {
+            st = pa.alloc(n * 8, &im->fp_h);
+            if (st == CRAC_OK) st = pa.alloc(n * 8, &im->idx_h);
+        }
+        if (st != CRAC_OK) return fail(st);
+        // fingerprint tables and descriptors
+        // Only the output table may grow: the baseline table keeps the previous
+        // layout, which it still fully holds.
+        st = ensure_dev(c->fp[1 - c->fp_cur], n * 8);
+        if (st == CRAC_OK) st = ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8));
+        if (st == CRAC_OK) st = ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8));
+        if (st != CRAC_OK) return fail(st);
+        CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+        uint64_t *prefix_h = (uint64_t *)(dh + na);   // payload bytes before each allocation
+        bool any_base = false, all16 = true;
+        uint64_t pre = 0;
+        for (size_t a = 0; a < na; ++a) {
+            uint64_t bf = kNoBase;
+            if (c->base_valid) {
+                auto it = c->base_first.find(c->allocs[a].id);
+                if (it != c->base_first.end()) bf = it->second;
+            }
+            any_base |= bf != kNoBase;
+            all16 &= (c->allocs[a].bytes & 15) == 0;
+            dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+            prefix_h[a] = pre;
+            pre += c->allocs[a].bytes;
+        }
+        c->full_copy_ok = !any_base && all16;
+        c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE && dev_res && all16;
+        // Order after the previous operation of this context (drain / restore).
+        if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
+        if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(cuda_status(cudaGetLastError()));
+        // Managed regions migrate to the device before they are read.
+        bool any_managed = false;
+        for (const AllocRec &r : c->allocs) any_managed |= r.kind == CRAC_KIND_MANAGED;
+        if (any_managed) {
+            cudaEventRecord(c->ev_p0, s);
+            cudaMemLocation loc{};
+            loc.type = cudaMemLocationTypeDevice;
+            loc.id = c->device;
+            for (const AllocRec &r : c->allocs) {
+                if (r.kind != CRAC_KIND_MANAGED) continue;
+                cudaError_t e = cudaMemPrefetchAsync((const void *)r.ptr, r.bytes, loc, 0, s);
+                if (e != cudaSuccess) return fail(cuda_status(e));
+            }
+            cudaEventRecord(c->ev_p1, s);
+        }
+        // Segments bounded by the staging capacity.
+        uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
+        cap = std::max(round_up(cap, 256), S);
+        const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
+        uint64_t max_seg_chunks = 0, max_seg_bytes = 0;
+        for (const Segment &sg : segs) {
+            max_seg_chunks = std::max(max_seg_chunks, sg.c1 - sg.c0);
+            max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
+        }
+        const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
+        if (host_res) {
+            st = ensure_dev(c->staging, max_seg_bytes);
+            if (st == CRAC_OK) st = ensure_dev(c->idx, max_seg_chunks * 8);
+            if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
+            if (st != CRAC_OK) return fail(st);
+        }
+        uint64_t k_base = 0, d_base = 0;
+        float ms = 0;
+        for (const Segment &sg : segs) {
+            const uint64_t nseg = sg.c1 - sg.c0;
+            Piece pc;
+            uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
+            uint8_t *stg = (uint8_t *)c->staging.p;
+            if (!host_res) {
+                st = da.alloc(sg.bytes, &pc.dev);
+                if (st == CRAC_OK) st = da.alloc(nseg * 8, &pc.idx_dev);
+                if (st == CRAC_OK) st = da.alloc((nseg + 1) * 8, &pc.off_dev);
+                if (st != CRAC_OK) {
+                    da.free(pc.dev);
+                    da.free(pc.idx_dev);
+                    da.free(pc.off_dev);
+                    return fail(st);
+                }
+                idx_d = (uint64_t *)pc.idx_dev.p;
+                off_d = (uint64_t *)pc.off_dev.p;
+                stg = pc.dev.p;
+            }
+            if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) {
+                im->pieces.push_back(pc);
+                return fail(cuda_status(cudaGetLastError()));
+            }
+            CkptCtrl ctrl{};
+            st = run_segment(c, sg, (const CkptDesc *)c->desc.p, first, idx_d, off_d, nseg, stg, sg.bytes, s,
+                             &ctrl, &ms);
+            if (st != CRAC_OK) {
+                im->pieces.push_back(pc);
+                return fail(st);
+            }
+            pc.k0 = k_base;
+            pc.k = ctrl.k;
+            pc.off0 = d_base;
+            const bool sparse = c->sparse_ok && !host_res;
+            pc.bytes = sparse ? ctrl.payload : ctrl.D;
+            pc.span = sparse ? ctrl.D : 0;
+            if (fault_hit(CRAC_FAULT_DRAIN)) {
+                im->pieces.push_back(pc);
+                t_last_cuda = (int)cudaErrorLaunchFailure;
+                return fail(CRAC_ERR_CUDA);
+            }
+            cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
+            if (host_res) {
+                if (ctrl.D) {
+                    st = pa.alloc(ctrl.D, &pc.host);
+                    if (st != CRAC_OK) {
+                        im->pieces.push_back(pc);
+                        return fail(st);
+                    }
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(pc.host.p, c->staging.p, ctrl.D, cudaMemcpyDeviceToHost, c->side);
+                }
+            } else {
+                da.shrink(pc.dev, ctrl.D);
+                da.shrink(pc.idx_dev, ctrl.k * 8);
+                da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
+            }
+            if (e == cudaSuccess && ctrl.k && host_res)
+                e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+            im->pieces.push_back(pc);
+            if (e != cudaSuccess) return fail(cuda_status(e));
+            k_base += ctrl.k;
+            d_base += pc.bytes;
+        }
+        cudaError_t e;
+        if (host_res) {
+            e = cudaMemcpyAsync(im->fp_h.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        } else {
+            // Device image: its tables stay in device memory; done once the
+            // fingerprint table has its own copy.
+            e = cudaMemcpyAsync(im->fp_dev.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaEventRecord(im->done, s);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, s);
+        }
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        im->k = k_base;
+        im->payload_bytes = d_base;
+        if (host_res) pa.shrink(im->idx_h, k_base * 8);
+        c->last.k = k_base;
+        c->last.payload_bytes = d_base;
+        c->last.segments = (uint32_t)segs.size();
+        c->last.device_ms = ms;
+        if (any_managed) {
+            float pm = 0;
+            cudaEventElapsedTime(&pm, c->ev_p0, c->ev_p1);
+            c->last.prefetch_ms = pm;
+        }
+    } else {
+        CK(cudaEventRecord(im->done, s));
+    }
+
+    // Commit: the new fingerprints become the baseline.
+    im->flags = im->k == n ? CRAC_IMAGE_FULL : 0u;
+    if (!(im->flags & CRAC_IMAGE_FULL) && c->parent) {
+        img_ref(c->parent);
+        im->parent = c->parent;
+    }
+    c->fp_cur = 1 - c->fp_cur;
+    c->base_first.clear();
+    for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
+    c->base_valid = true;
+    c->epoch_max = im->epoch;
+    c->parent_epoch = im->epoch;
+    crac_image *img = im.release();
+    img->refs.store(2);   // the caller's reference and the context's
+    img_unref(c->parent);
+    c->parent = img;
+    table_add(img);
+    *out = img;
+    return CRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Trial passes (the autotuner's observations)
+// ---------------------------------------------------------------------------
+
+// The checkpoint pass without an image: fingerprints, dirty test, compaction
+// and gather into the context's staging, segment by segment.  With commit the
+// new fingerprints become the context's baseline.
+crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms, uint64_t *k_out,
+                             uint64_t *d_out) {
+    TRY(ctx_cuda_ready(c));
+    DeviceGuard g(c->device);
+    const size_t na = c->allocs.size();
+    const uint32_t log2S = c->log2S;
+    const uint64_t S = 1ull << log2S;
+    std::vector<uint64_t> first(na + 1, 0);
+    uint64_t tracked = 0;
+    for (size_t a = 0; a < na; ++a) {
+        first[a + 1] = first[a] + ((c->allocs[a].bytes + S - 1) >> log2S);
+        tracked += c->allocs[a].bytes;
+    }
+    const uint64_t n = first[na];
+    *ms = 0;
+    *k_out = 0;
+    *d_out = 0;
+    c->last = crac_pass_info_t{};
+    if (n == 0) return CRAC_OK;
+    TRY(ensure_dev(c->fp[1 - c->fp_cur], n * 8));
+    TRY(ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8)));
+    TRY(ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8)));
+    CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+    uint64_t *prefix_h = (uint64_t *)(dh + na);
+    bool any_base = false, all16 = true;
+    uint64_t pre = 0;
+    for (size_t a = 0; a < na; ++a) {
+        uint64_t bf = kNoBase;
+        if (c->base_valid) {
+            auto it = c->base_first.find(c->allocs[a].id);
+            if (it != c->base_first.end()) bf = it->second;
+        }
+        any_base |= bf != kNoBase;
+        all16 &= (c->allocs[a].bytes & 15) == 0;
+        dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+        prefix_h[a] = pre;
+        pre += c->allocs[a].bytes;
+    }
+    c->full_copy_ok = !any_base && all16;
+    c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE &&
+                   c->cfg.image_residency == CRAC_RESIDENCY_DEVICE && all16;
+    CK(cudaStreamWaitEvent(s, c->ev_last, 0));
+    CK(cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
+    uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
+    cap = std::max(round_up(cap, 256), S);
+    const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
+    uint64_t max_c = 0, max_b = 0;
+    for (const Segment &sg : segs) {
+        max_c = std::max(max_c, sg.c1 - sg.c0);
+        max_b = std::max(max_b, sg.bytes);
+    }
+    TRY(ensure_dev(c->staging, max_b));
+    TRY(ensure_dev(c->idx, max_c * 8));
+    TRY(ensure_dev(c->off, (max_c + 1) * 8));
+    for (const Segment &sg : segs) {
+        CkptCtrl ctrl{};
+        TRY(run_segment(c, sg, (const CkptDesc *)c->desc.p, first, (uint64_t *)c->idx.p, (uint64_t *)c->off.p,
+                        sg.c1 - sg.c0, (uint8_t *)c->staging.p, sg.bytes, s, &ctrl, ms));
+        *k_out += ctrl.k;
+        *d_out += c->sparse_ok ? ctrl.payload : ctrl.D;
+    }
+    CK(cudaEventRecord(c->ev_last, s));
+    if (commit) {
+        c->prev_base_first = c->base_first;
+        c->prev_base_valid = c->base_valid;
+        c->fp_cur = 1 - c->fp_cur;
+        c->base_first.clear();
+        for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
+        c->base_valid = true;
+    }
+    return CRAC_OK;
+}
+
+}  // namespace crac
