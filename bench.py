@@ -268,7 +268,10 @@ def run_crac(args):
             C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel(), C.CRAC_KIND_DEVICE)
         return ctx
 
-    ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, reserve_device_bytes=8 * B)
+    # The device arena is process-wide: the reservation covers every device-
+    # resident context of this run (their base images and the timed loop's
+    # growing chain), so that no step allocates from CUDA.
+    ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, reserve_device_bytes=16 * B)
     ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=3 * B)
     ctx_pa = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, launch_mode=C.CRAC_LAUNCH_PER_ALLOC)
     ctx_b = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
@@ -317,6 +320,7 @@ def run_crac(args):
     torch.cuda.synchronize()
     barrier()
     launches0 = C.crac_kernel_launches()
+    mem0 = C.crac_memory_stats()
     pass_ms, lat_ms, rst = [], [], []
     torch.cuda.synchronize()
     barrier()
@@ -331,6 +335,9 @@ def run_crac(args):
     bytes_per_step = 2 * B
     t_ms, job_bytes = aggregate_over_ranks(t_ms, bytes_per_step * args.steps, world, dev)
     launches = C.crac_kernel_launches() - launches0 + args.steps   # + one mutator launch per step
+    mem1 = C.crac_memory_stats()
+    arena_growth = {"device_grow_events": mem1["device_grow_events"] - mem0["device_grow_events"],
+                    "host_grow_events": mem1["host_grow_events"] - mem0["host_grow_events"]}
     value = job_bytes / (t_ms / 1e3) / 1e9
 
     # ---- roofline: the dominant kernel is the split pass's streaming hash ------
@@ -413,10 +420,10 @@ def run_crac(args):
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e_pass, e_phase = [], []
+        e_pass, e_phase, e_rst = [], [], []
         e0.record(stream)
         for _ in range(e2e_steps):
-            step(ctx_host, host=True, pass_ms=e_pass, phases=e_phase)
+            step(ctx_host, host=True, pass_ms=e_pass, phases=e_phase, rst=e_rst)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -425,7 +432,11 @@ def run_crac(args):
         k_e = statistics.mean(p[1] for p in e_pass)
         d_e = statistics.mean(p[2] for p in e_pass)
         d2h = int(d_e + 8 * k_e + 8 * n + 64)
-        h2d = int(B + d_e + 16 * k_e + 8 * n + 2 * n + 32 * len(sizes))
+        # The restart reads every restored chunk once from the chain's pinned
+        # images (in place), plus each visited entry's index and offset, and
+        # uploads the fingerprint table and the descriptors.
+        ent = statistics.mean(r.entries_scanned for r in e_rst)
+        h2d = int(B + 16 * ent + 8 * n + 40 * len(sizes) * statistics.mean(r.chain_length for r in e_rst))
         e2e = {"value": bytes_per_step * e2e_steps * world / (te / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "ms_per_step": te / e2e_steps, "link": link,
@@ -463,7 +474,8 @@ def run_crac(args):
                            "step": "mutate 10% + incremental ckpt + full restart (device-resident images)",
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "roofline_ckpt_hash": roofline_hash, "pass": pass_info, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "batched_vs_per_alloc": batched,
+                "gpu_launches": launches, "arena_growth_in_timed_loop": arena_growth,
+                "batched_vs_per_alloc": batched,
                 "ckpt_latency_ms": {"p50": statistics.median(lat_ms),
                                     "p99": float(np.percentile(lat_ms, 99))},
                 "ckpt_pass_gbs": B / (dev_ms / 1e3) / 1e9, "dirty_chunks": k_avg, "dirty_bytes": d_avg}

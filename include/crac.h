@@ -102,9 +102,11 @@ typedef struct crac_image crac_image_t;  /* library-owned, reference counted */
  *                  warps_per_chunk is 1 or 8.
  * timeout_ns:      limit on every device-side spin-wait; 0 = 2 s.
  * reserve_host_bytes, reserve_device_bytes: image memory (pinned host,
- *                  device) reserved when the context first touches the GPU,
- *                  so that steady-state checkpoints allocate nothing from
- *                  CUDA.  The arenas are process-wide and only grow.
+ *                  device) reserved by crac_ctx_create (which then needs the
+ *                  GPU; a context without a reservation touches it only at
+ *                  its first checkpoint or restart), so that no checkpoint
+ *                  allocates from CUDA.  The arenas are process-wide and
+ *                  only grow.
  */
 typedef struct crac_config {
     uint32_t struct_size;
@@ -123,8 +125,18 @@ typedef struct crac_config {
     uint64_t reserve_host_bytes;    /* pinned image memory to reserve up front */
     uint64_t reserve_device_bytes;  /* device image memory to reserve up front */
     uint32_t pass_kernel;           /* CRAC_PASS_* */
-    uint32_t reserved[1];
+    uint32_t flags;                 /* CRAC_FLAG_* */
 } crac_config_t;
+
+/* crac_config_t.flags.
+ * CRAC_FLAG_STAGED_RESTORE: restore host-resident images by copying each
+ *   image's whole payload into device staging (copy engine) and scattering
+ *   from there, window by window.  By default the restore kernels read a host
+ *   image's chunks in place from its pinned memory (mapped into the device's
+ *   address space), so only the chunks that survive into the restored state
+ *   cross the host link and no staging is needed; the staged path is used
+ *   anyway when the device has no unified addressing. */
+#define CRAC_FLAG_STAGED_RESTORE 1u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
 #define CRAC_PASS_AUTO  0  /* the split pass */
@@ -377,7 +389,8 @@ typedef struct crac_restart_info {
     uint32_t images_used;        /* images that still owned at least one chunk */
     uint64_t restored_bytes;     /* bytes written into allocations (= tracked bytes) */
     uint64_t entries_scanned;    /* chunk entries the scatter kernels visited */
-    uint64_t h2d_bytes;          /* host image payload copied to the device */
+    uint64_t h2d_bytes;          /* host image payload copied to the device (staged
+                                    restore; a mapped restore reads in place) */
     uint32_t scatter_launches;
     float device_ms;             /* device time from the first copy/launch to the last */
     uint32_t reserved[4];

@@ -46,6 +46,7 @@ CRAC_PASS_LDG = 1
 CRAC_PASS_TMA = 2
 CRAC_PASS_SPLIT = 3
 CRAC_PASS_SPARSE = 4
+CRAC_FLAG_STAGED_RESTORE = 1
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1
@@ -76,7 +77,7 @@ class CracConfig(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
         ("timeout_ns", ctypes.c_uint64), ("device", ctypes.c_int32), ("pad0", ctypes.c_uint32),
         ("reserve_host_bytes", ctypes.c_uint64), ("reserve_device_bytes", ctypes.c_uint64),
-        ("pass_kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
+        ("pass_kernel", ctypes.c_uint32), ("flags", ctypes.c_uint32),
     ]
 
 

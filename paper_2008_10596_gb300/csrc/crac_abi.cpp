@@ -73,7 +73,9 @@ crac_status_t crac_ctx_create(const crac_config_t *cfg, crac_ctx_t **out) {
     if (!out) return CRAC_ERR_INVALID_ARG;
     *out = nullptr;
     crac_ctx *c = new crac_ctx();
-    const crac_status_t st = ctx_init(c, cfg);
+    crac_status_t st = ctx_init(c, cfg);
+    // A reservation is made now, so that no checkpoint pays for it.
+    if (st == CRAC_OK && (c->cfg.reserve_host_bytes || c->cfg.reserve_device_bytes)) st = ctx_cuda_ready(c);
     if (st != CRAC_OK) {
         ctx_free_all(c);
         delete c;

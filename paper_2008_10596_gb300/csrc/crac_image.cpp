@@ -72,6 +72,7 @@ void img_unref(crac_image *im) {
         Arena &pa = pinned_arena();
         pa.free(im->fp_h);
         pa.free(im->idx_h);
+        pa.free(im->off_h);
         if (im->fp_dev.region >= 0) device_arena(im->device).free(im->fp_dev);
         for (Piece &p : im->pieces) {
             pa.free(p.host);

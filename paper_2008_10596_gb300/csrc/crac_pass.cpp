@@ -26,6 +26,7 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
+    if (cfg.flags & ~CRAC_FLAG_STAGED_RESTORE) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
@@ -45,6 +46,9 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     c->device = dev;
     DeviceGuard g(dev);
     CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    int uva = 0;
+    CK(cudaDeviceGetAttribute(&uva, cudaDevAttrUnifiedAddressing, dev));
+    c->uva = uva != 0;
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_last, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_pass, cudaEventDisableTiming));

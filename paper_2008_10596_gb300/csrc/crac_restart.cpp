@@ -34,13 +34,48 @@ std::vector<int64_t> map_allocs(const crac_image *im, const crac_image *tgt,
     return m;
 }
 
-// Restore from a chain held entirely in device memory, resolved on the device
-// in three launches over every piece of every image of the chain: owner
-// marks (the newest image wins), a coverage check, owner-filtered scatter --
-// no host round trip before them.  An uncovered chunk stops the scatter
-// (memory untouched) and reports IMAGE_MISMATCH.
+// Offset of every entry's bytes inside its piece's payload, for a host image
+// (its payload is compact: the prefix of the entries' chunk lengths).  Made
+// once per image, in pinned memory that the restore kernels read in place.
+crac_status_t img_offsets(crac_image *im) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (im->off_h.p || im->k == 0) return CRAC_OK;
+    Arena &pa = pinned_arena();
+    TRY(pa.alloc(im->k * 8, &im->off_h));
+    uint64_t *off = (uint64_t *)im->off_h.p;
+    const uint64_t *idx = (const uint64_t *)im->idx_h.p;
+    const uint32_t log2S = log2u(im->chunk_bytes);
+    size_t a = 0;
+    for (const Piece &pc : im->pieces) {
+        uint64_t acc = 0;
+        for (uint64_t j = pc.k0; j < pc.k0 + pc.k; ++j) {
+            while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= idx[j]) ++a;
+            off[j] = acc;
+            acc += chunk_len(im->allocs[a].bytes, idx[j] - im->allocs[a].first_chunk, log2S);
+        }
+        if (acc != pc.bytes) {
+            pa.free(im->off_h);
+            return CRAC_ERR_CORRUPT;
+        }
+    }
+    return CRAC_OK;
+}
+
+// Restore a chain on the device, resolved in three launches over every
+// piece of every image of the chain: owner marks (the newest image wins), a
+// coverage check, owner-filtered scatter -- no host round trip before them.
+// A device image's tables and payload are in device memory; a host image's
+// are read in place from pinned memory, which the device addresses directly
+// (unified addressing), so of a host image only the chunks it still owns
+// cross the host link.  An uncovered chunk stops the scatter (memory
+// untouched) and reports IMAGE_MISMATCH.
 crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<crac_image *> &chain, cudaStream_t s) {
     DeviceGuard g(c->device);
+    for (crac_image *im : chain) {
+        if (im->residency == CRAC_RESIDENCY_DEVICE) continue;
+        TRY(img_wait(im, 0));   // the offsets are computed from its chunk list
+        TRY(img_offsets(im));
+    }
     const uint64_t nt = img->n_chunks;
     std::unordered_map<uint64_t, size_t> tpos;
     for (size_t a = 0; a < img->allocs.size(); ++a) tpos[img->allocs[a].id] = a;
@@ -74,15 +109,22 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
             sdh[dpos] = ScatterDesc{im->allocs[a].first_chunk, im->allocs[a].bytes,
                                     m[a] < 0 ? 0 : img->allocs[m[a]].first_chunk, m[a] < 0 ? 0 : c->allocs[m[a]].ptr,
                                     0, {0, 0, 0}};
+        const bool host = im->residency != CRAC_RESIDENCY_DEVICE;
         for (const Piece &pc : im->pieces) {
             if (!pc.k) continue;
-            rph[ppos++] = RestorePiece{(uint64_t)pc.idx_dev.p, (uint64_t)pc.off_dev.p, (uint64_t)pc.dev.p, pc.k,
-                                       entries, pc.span ? pc.span : pc.bytes, (uint32_t)i, (uint32_t)d0,
-                                       (uint32_t)im->allocs.size(), 0};
+            if (host)
+                rph[ppos++] = RestorePiece{(uint64_t)(im->idx_h.p + pc.k0 * 8), (uint64_t)(im->off_h.p + pc.k0 * 8),
+                                           (uint64_t)pc.host.p, pc.k, entries, pc.bytes, (uint32_t)i, (uint32_t)d0,
+                                           (uint32_t)im->allocs.size(), 0};
+            else
+                rph[ppos++] = RestorePiece{(uint64_t)pc.idx_dev.p, (uint64_t)pc.off_dev.p, (uint64_t)pc.dev.p, pc.k,
+                                           entries, pc.span ? pc.span : pc.bytes, (uint32_t)i, (uint32_t)d0,
+                                           (uint32_t)im->allocs.size(), 0};
             entries += pc.k;
         }
     }
-    for (crac_image *im : chain) CK(cudaStreamWaitEvent(s, im->done, 0));
+    for (crac_image *im : chain)   // deserialized images have no event: complete from the start
+        if (im->done) CK(cudaStreamWaitEvent(s, im->done, 0));
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(cudaMemsetAsync(c->serr.p, 0, 256, s));
     if (nt) CK(cudaMemsetAsync(c->owner.p, 0, nt * 4, s));
@@ -107,7 +149,10 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     CK(launch_restore_check(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
     CK(launch_restore_scatter(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 7) / 8, grid)), s));
     CK(cudaEventRecord(c->ev_r1, s));
-    if (nt) CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, img->fp_dev.p, nt * 8, cudaMemcpyDeviceToDevice, s));
+    if (nt) {
+        const void *fp = img->residency == CRAC_RESIDENCY_DEVICE ? (const void *)img->fp_dev.p : (const void *)img->fp_h.p;
+        CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, fp, nt * 8, cudaMemcpyDefault, s));
+    }
     CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
@@ -140,11 +185,17 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
         cur = p;
     }
     std::reverse(chain.begin(), chain.end());
-    bool all_dev = true;
-    for (crac_image *im : chain)
-        all_dev = all_dev && im->residency == CRAC_RESIDENCY_DEVICE && im->device == c->device &&
-                  (im->n_chunks == 0 || im->fp_dev.region >= 0);
-    if (all_dev) return restart_device(c, img, chain, s);
+    // On the device unless an image is on another device, or a host image
+    // must be staged (no unified addressing, or CRAC_FLAG_STAGED_RESTORE).
+    const bool mapped = c->uva && !(c->cfg.flags & CRAC_FLAG_STAGED_RESTORE);
+    bool on_device = true;
+    for (crac_image *im : chain) {
+        const bool dev_ok = im->residency == CRAC_RESIDENCY_DEVICE && im->device == c->device &&
+                            (im->n_chunks == 0 || im->fp_dev.region >= 0);
+        const bool host_ok = im->residency != CRAC_RESIDENCY_DEVICE && mapped;
+        on_device = on_device && (dev_ok || host_ok);
+    }
+    if (on_device) return restart_device(c, img, chain, s);
     for (crac_image *im : chain) {
         TRY(img_wait(im, 0));
         TRY(img_host_tables(im));

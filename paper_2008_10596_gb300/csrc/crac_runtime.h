@@ -312,6 +312,8 @@ struct crac_image {
     uint64_t n_chunks = 0, k = 0, payload_bytes = 0;
     Block fp_h, idx_h;              // pinned: fp[n_chunks], idx[k] (device images: on demand)
     Block fp_dev;                   // device images: fp[n_chunks] in device memory
+    Block off_h;                    // host images: offset of each entry's bytes inside its
+                                    // piece's payload (made by the first mapped restore)
     bool host_tables = true;        // fp_h / idx_h hold the tables
     std::vector<Piece> pieces;
     crac_image *parent = nullptr;   // strong reference, set for delta images
@@ -348,6 +350,7 @@ struct crac_ctx {
     crac_config_t cfg{};
     int device = 0;
     int sm_count = 0;
+    bool uva = false;            // the device addresses pinned host memory directly
     uint32_t log2S = 16;
     std::vector<AllocRec> allocs;
     uint64_t next_id = 0;

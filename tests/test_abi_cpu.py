@@ -50,7 +50,8 @@ def test_config_validation(C):
                 dict(warps_per_chunk=3), dict(chunks_per_tile=1000), dict(pass_kernel=5),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10),
-                dict(pass_kernel=C.CRAC_PASS_SPARSE)):        # needs device-resident images
+                dict(pass_kernel=C.CRAC_PASS_SPARSE),         # needs device-resident images
+                dict(flags=2)):
         with pytest.raises(C.CracError) as e:
             C.crac_ctx_create(C.crac_config_default(**bad))
         assert e.value.code == C.CRAC_ERR_INVALID_ARG

@@ -47,10 +47,12 @@ def test_failed_checkpoint_leaves_state(step, code, kern):
         h.close()
 
 
-@pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
-def test_failed_restart_leaves_memory(residency):
+@pytest.mark.parametrize("residency,flags", [(C.CRAC_RESIDENCY_HOST, 0),
+                                             (C.CRAC_RESIDENCY_HOST, C.CRAC_FLAG_STAGED_RESTORE),
+                                             (C.CRAC_RESIDENCY_DEVICE, 0)])
+def test_failed_restart_leaves_memory(residency, flags):
     S = 4096
-    h = Harness(S, lineage=62, image_residency=residency)
+    h = Harness(S, lineage=62, image_residency=residency, flags=flags)
     try:
         b = h.add(50000, seed=3)
         img, _, _ = h.checkpoint()

@@ -176,7 +176,8 @@ def test_sparse_pass(S, staging, pattern):
         h.close()
 
 
-def test_sparse_pass_fallback_and_mixed_chain():
+@pytest.mark.parametrize("flags", [0, C.CRAC_FLAG_STAGED_RESTORE])
+def test_sparse_pass_fallback_and_mixed_chain(flags):
     """A size that is not a multiple of 16 makes the sparse kernel choice run
     the compacting split pass.  And a chain whose FULL image comes back from
     serialization (host-resident) and whose delta is a sparse device image is
@@ -197,7 +198,7 @@ def test_sparse_pass_fallback_and_mixed_chain():
         h.close()
     sizes = [40000, 12352, 4096 * 3]
     h1 = Harness(S, lineage=712, **dev)
-    h2 = Harness(S, lineage=713, **dev)
+    h2 = Harness(S, lineage=713, flags=flags, **dev)
     try:
         for i, n in enumerate(sizes):
             h1.add(n, seed=10 + i)
@@ -287,13 +288,19 @@ def test_tma_many_allocations(n_allocs, residency):
         C.crac_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("mode", ["per_alloc", "segments", "device", "device_segments"])
+@pytest.mark.parametrize("mode", ["per_alloc", "segments", "device", "device_segments", "staged",
+                                  "staged_segments"])
 def test_launch_modes_and_residency(mode):
+    """Launch modes, staging segments and residencies.  Host images are
+    restored in place from pinned memory unless CRAC_FLAG_STAGED_RESTORE
+    asks for the copy-engine path through staging windows."""
     S = 4 * KIB
     cfg = {}
+    if mode.startswith("staged"):
+        cfg["flags"] = C.CRAC_FLAG_STAGED_RESTORE
     if mode == "per_alloc":
         cfg["launch_mode"] = C.CRAC_LAUNCH_PER_ALLOC
-    if mode in ("segments", "device_segments"):
+    if mode in ("segments", "device_segments", "staged_segments"):
         cfg["staging_bytes"] = 40 * KIB      # forces many segments, allocations split
     if mode.startswith("device"):
         cfg["image_residency"] = C.CRAC_RESIDENCY_DEVICE
