@@ -51,11 +51,25 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_src_sha() -> str:
+    """sha256 prefix over the device sources (every .cu and .cuh of the library
+    in name order, the test mutators excepted): what an ncu summary was
+    captured against."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2008_10596_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        if os.path.basename(f) == "crac_testkit.cu":
+            continue
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic(kernel_tag: str):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches the kernel source."""
-    import hashlib
-    src = os.path.join(ROOT, "paper_2008_10596_gb300", "csrc", "crac_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = kernel_src_sha()
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
         return None

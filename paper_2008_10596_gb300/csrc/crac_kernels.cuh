@@ -1,5 +1,6 @@
-// Internal interface between the host runtime (crac_runtime.cpp) and the
-// device kernels (crac_kernels.cu).  Not part of the public ABI.
+// Internal interface between the host runtime (crac_runtime.h and its units)
+// and the device kernel units (crac_pass_*.cu, crac_restore.cu,
+// crac_noalloc.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

@@ -1,0 +1,194 @@
+// The fused LDG pass: K1 + K2 + K3 in one persistent kernel, and the
+// kernel-launch counter.
+#include "crac_device.cuh"
+
+namespace crac {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Fused batched checkpoint pass: K1 + K2 + K3 in one persistent kernel.
+// ---------------------------------------------------------------------------
+template <int NT, int WPC>
+__global__ void __launch_bounds__(NT) ckpt_fused_kernel(const CkptParams P) {
+    constexpr int W = NT / 32;
+    constexpr int G = W / WPC;        // chunk groups per CTA
+    constexpr int GT = WPC * 32;      // threads per group
+    __shared__ uint32_t s_alloc[kMaxCpt];
+    __shared__ uint32_t s_len[kMaxCpt];    // dirty: chunk length; clean: 0
+    __shared__ uint32_t s_pos[kMaxCpt];    // position among the tile's dirty chunks
+    __shared__ uint64_t s_boff[kMaxCpt];   // byte offset among the tile's dirty bytes
+    __shared__ uint64_t s_part[2][W];
+    __shared__ uint64_t s_k0, s_d0;
+    __shared__ uint32_t s_tile;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = warp / WPC;
+    const int gl = threadIdx.x - g * GT;
+    const uint32_t log2S = P.log2_chunk;
+    const uint64_t S = 1ull << log2S;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t t = atomicAdd(&P.ctrl->ticket, 1u);
+            if (P.skip_first_ticket && t == 0) t = atomicAdd(&P.ctrl->ticket, 1u);
+            s_tile = t;
+        }
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= P.n_tiles) break;
+        const uint64_t c0 = P.c_begin + (uint64_t)tile * P.cpt;
+        const uint32_t nc = (uint32_t)min((uint64_t)P.cpt, P.c_end - c0);
+        for (uint32_t t = threadIdx.x; t < nc; t += NT) s_alloc[t] = find_alloc(P.desc, P.n_allocs, c0 + t);
+        __syncthreads();
+
+        // K1 + K2 per chunk: fingerprint, then compare with the baseline.
+        for (uint32_t r = 0; r * G < nc; ++r) {
+            const uint32_t ci = r * G + g;
+            uint64_t acc = 0;
+            uint32_t len = 0;
+            CkptDesc d{};
+            uint64_t local = 0;
+            if (ci < nc) {
+                d = P.desc[s_alloc[ci]];
+                local = c0 + ci - d.first_chunk;
+                len = (uint32_t)min(S, d.bytes - (local << log2S));
+                acc = hash_partial<GT>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S),
+                                       len, gl);
+            }
+            acc = warp_sum(acc);
+            if (WPC > 1) {
+                if (lane == 0) s_part[r & 1][warp] = acc;
+                __syncthreads();
+                if (ci < nc && gl == 0) {
+                    acc = 0;
+#pragma unroll
+                    for (int w = 0; w < WPC; ++w) acc += s_part[r & 1][g * WPC + w];
+                }
+            }
+            if (ci < nc && gl == 0) {
+                const uint64_t fp = fp_finalize(acc, len);
+                P.fp_new[c0 + ci] = fp;
+                const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
+                s_len[ci] = dirty ? len : 0u;
+            }
+        }
+        __syncthreads();
+
+        // K2 compaction: positions within the tile (ballot + warp scan), then
+        // the tile's global prefix by decoupled look-back.
+        if (warp == 0) {
+            uint32_t cnt = 0;
+            uint64_t bytes = 0;
+            for (uint32_t base = 0; base < nc; base += 32) {
+                const uint32_t i = base + lane;
+                const uint32_t l = i < nc ? s_len[i] : 0u;
+                const unsigned m = __ballot_sync(kFull, l != 0);
+                const uint64_t incl = warp_incl_scan(l, lane);
+                if (i < nc) {
+                    s_pos[i] = cnt + __popc(m & ((1u << lane) - 1u));
+                    s_boff[i] = bytes + incl - l;
+                }
+                cnt += __popc(m);
+                bytes += __shfl_sync(kFull, incl, 31);
+            }
+            uint64_t k0 = 0, d0 = 0;
+            if (tile == 0) {
+                if (lane == 0) {
+                    st_status(P.tile_cnt, kFlagInc | cnt);
+                    st_status(P.tile_bytes, kFlagInc | bytes);
+                }
+            } else {
+                if (lane == 0) {
+                    st_status(P.tile_cnt + tile, kFlagAgg | cnt);
+                    st_status(P.tile_bytes + tile, kFlagAgg | bytes);
+                }
+                lookback(P, tile, lane, &k0, &d0);
+                if (lane == 0) {
+                    st_status(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                    st_status(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                }
+            }
+            if (lane == 0) {
+                s_k0 = k0;
+                s_d0 = d0;
+                if (tile == P.n_tiles - 1) {
+                    P.ctrl->k = k0 + cnt;
+                    P.ctrl->D = d0 + bytes;
+                    if (k0 + cnt <= P.idx_cap) P.off_out[k0 + cnt] = d0 + bytes;
+                    else atomicOr(&P.ctrl->err, kErrBounds);
+                }
+            }
+        }
+        __syncthreads();
+        const uint64_t k0 = s_k0, d0 = s_d0;
+        for (uint32_t t = threadIdx.x; t < nc; t += NT) {
+            if (s_len[t]) {
+                const uint64_t j = k0 + s_pos[t];
+                if (j < P.idx_cap) {
+                    P.idx_out[j] = c0 + t;
+                    P.off_out[j] = d0 + s_boff[t];
+                } else {
+                    atomicOr(&P.ctrl->err, kErrBounds);
+                }
+            }
+        }
+        // K3 gather of this tile's dirty chunks into the staging buffer.
+        for (uint32_t ci = g; ci < nc; ci += G) {
+            const uint32_t len = s_len[ci];
+            if (!len) continue;
+            const CkptDesc d = P.desc[s_alloc[ci]];
+            const uint64_t local = c0 + ci - d.first_chunk;
+            const uint64_t dst = d0 + s_boff[ci];
+            if (dst + len > P.staging_cap) {
+                if (gl == 0) atomicOr(&P.ctrl->err, kErrBounds);
+                continue;
+            }
+            copy_group<GT>(P.staging + dst,
+                           reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S), len, gl);
+        }
+        __syncthreads();
+    }
+}
+
+
+template <int NT, int WPC>
+cudaError_t launch_fused_t(const CkptParams &p, int grid, cudaStream_t s) {
+    ckpt_fused_kernel<NT, WPC><<<grid, NT, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+static uint64_t g_launches = 0;   // guarded by the callers' context lock is not enough
+                                  // across contexts; use an atomic builtin
+void count_launches(uint64_t n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+uint64_t launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+const void *ckpt_fused_fn(int threads, int wpc) {
+    if (threads != 256) return nullptr;
+    if (wpc == 1) return reinterpret_cast<const void *>(&ckpt_fused_kernel<256, 1>);
+    if (wpc == 8) return reinterpret_cast<const void *>(&ckpt_fused_kernel<256, 8>);
+    return nullptr;
+}
+
+int ckpt_fused_max_ctas_per_sm(int threads, int wpc) {
+    const void *fn = ckpt_fused_fn(threads, wpc);
+    if (!fn) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_ckpt_fused(const CkptParams &p, int threads, int wpc, int grid,
+                              cudaStream_t s) {
+    if (p.cpt == 0 || p.cpt > (uint32_t)kMaxCpt || grid <= 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (threads == 256 && wpc == 1) e = launch_fused_t<256, 1>(p, grid, s);
+    else if (threads == 256 && wpc == 8) e = launch_fused_t<256, 8>(p, grid, s);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+}  // namespace crac

@@ -1,0 +1,397 @@
+// The split pass (hash -> finalize + compaction -> gather, one graph) and its
+// sparse variant.
+#include "crac_device.cuh"
+
+namespace crac {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Split pass: H (hash) -> F (finalize + dirty test + compaction) -> G (gather).
+//
+// H streams the tracked bytes with no inter-CTA dependency: every warp takes
+// a contiguous range of segments (8 KiB, or the chunk if smaller), issues all
+// of a segment's 128-bit loads at once (16 per lane), sums the per-word
+// terms, and adds the warp's sum into the chunk's accumulator with one 64-bit
+// atomicAdd.  The CRAC-FP64 sum is taken mod 2^64, so the order of these
+// additions does not change a bit.  F turns each accumulator into the
+// fingerprint, tests it against the baseline, and compacts the dirty chunks
+// (ballot + block scan per 1024-chunk tile, decoupled look-back across
+// tiles).  G copies the listed chunks into staging.  HBM traffic: B + 2D plus
+// small tables, against B + D for the fused kernels, in exchange for three
+// dependency-free streaming phases.
+// ---------------------------------------------------------------------------
+constexpr int kHashNT = 256;
+constexpr int kFinNT = 1024;
+constexpr int kGatherNT = 256;
+
+// Partial CRAC-FP64 sum of a segment (<= 8 KiB) whose first word is word j0
+// of its chunk, over the lanes of one warp.
+__device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, uint32_t len, uint64_t j0,
+                                             int lane, uint4 *__restrict__ copy_to = nullptr) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(src);
+    const uint32_t nv = len >> 4;
+    constexpr int U = 16;
+    uint4 q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t v = lane + 32u * u;
+        if (v < nv) q[u] = __ldg(p + v);
+    }
+    if (copy_to) {   // FULL checkpoint: the vectors also go straight to staging
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t v = lane + 32u * u;
+            if (v < nv) __stcs(copy_to + v, q[u]);
+        }
+    }
+    uint64_t acc = 0;
+    uint64_t key = (j0 + 2ull * (uint64_t)lane + 1ull) * kK1;
+    constexpr uint64_t kStep = 64ull * kK1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t v = lane + 32u * u;
+        if (v < nv) {
+            acc += mixw(((uint64_t)q[u].y << 32) | q[u].x, key);
+            acc += mixw(((uint64_t)q[u].w << 32) | q[u].z, key + kK1);
+        }
+        key += kStep;
+    }
+    const uint32_t rem = len & 15u;
+    if (rem && lane == (int)(nv & 31u)) {
+        const uint8_t *t = src + 16ull * nv;
+        uint64_t w0 = 0, w1 = 0;
+        for (uint32_t b = 0; b < rem; ++b) {
+            const uint64_t byte = t[b];
+            if (b < 8) w0 |= byte << (8 * b);
+            else w1 |= byte << (8 * (b - 8));
+        }
+        const uint64_t kt = (j0 + 2ull * nv + 1ull) * kK1;
+        acc += mixw(w0, kt);
+        if (rem > 8) acc += mixw(w1, kt + kK1);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kHashNT, 2)
+split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t log2Seg) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp_g = ((uint64_t)blockIdx.x * kHashNT + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * kHashNT) >> 5;
+    const uint32_t log2S = P.log2_chunk;
+    const uint32_t spc = log2S - log2Seg;   // log2 of segments per chunk
+    const uint64_t n_slots = (P.c_end - P.c_begin) << spc;
+    const uint64_t per = (n_slots + n_warps - 1) / n_warps;
+    uint64_t q = warp_g * per;
+    const uint64_t q_end = umin64(q + per, n_slots);
+    CkptDesc d{};
+    uint64_t a_next = 0;
+    uint32_t a = 0;
+    bool have = false;
+    for (; q < q_end; ++q) {
+        const uint64_t c = P.c_begin + (q >> spc);
+        if (!have || c >= a_next) {
+            a = find_alloc(P.desc, P.n_allocs, c);
+            d = P.desc[a];
+            a_next = a + 1 < P.n_allocs ? P.desc[a + 1].first_chunk : ~0ull;
+            have = true;
+        }
+        const uint64_t local = c - d.first_chunk;
+        const uint64_t rest = d.bytes - (local << log2S);
+        const uint64_t clen = rest < (1ull << log2S) ? rest : (1ull << log2S);
+        const uint64_t off = (q & ((1ull << spc) - 1)) << log2Seg;
+        if (off >= clen) continue;   // beyond the end of a short last chunk (warp-uniform)
+        const uint32_t len = (uint32_t)umin64(1ull << log2Seg, clen - off);
+        // Direct mode (S <= 8 KiB, the warp sees the whole chunk): the baseline
+        // fingerprint is loaded before the chunk so that both latencies overlap.
+        uint64_t fo = 0;
+        const bool has = d.base_first != kNoBase;
+        if (spc == 0 && lane == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S) + off;
+        uint4 *copy_to = nullptr;
+        if (P.full_copy) {   // FULL checkpoint: the segment's final staging offset is known
+            const uint64_t o = P.alloc_prefix[a] + (local << log2S) + off - P.seg_base;
+            if (o + len <= P.staging_cap) copy_to = reinterpret_cast<uint4 *>(P.staging + o);
+            else if (lane == 0) atomicOr(&P.ctrl->err, kErrBounds);
+        }
+        uint64_t sum = hash_seg(src, len, off >> 3, lane, copy_to);
+        sum = warp_sum(sum);
+        if (lane == 0) {
+            if (spc == 0) {
+                // The warp has seen the whole chunk: finalize here and leave only
+                // the length and the dirty bit for the compaction kernel.
+                const uint64_t fp = fp_finalize(sum, len);
+                P.fp_new[c] = fp;
+                acc[c - P.c_begin] = len | ((!has || fo != fp) ? kAccDirty : 0ull);
+            } else {
+                atomicAdd(acc + (c - P.c_begin), (unsigned long long)sum);
+            }
+        }
+    }
+}
+
+// When log2Seg == log2_chunk the hash kernel has already finalized every
+// chunk and left its length and dirty bit in acc; only the compaction remains.
+// Hash kernel for chunks of 512 B..4 KiB: one warp iteration covers 8 KiB,
+// i.e. 8192/S whole chunks, one group of LPC = 32*S/8192 lanes per chunk (16
+// vectors per lane), so a warp keeps 8 KiB in flight whatever the chunk size.
+// Every chunk is finalized in place (direct mode: acc receives the dirty
+// length).
+template <int LPC>
+__device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned long long *__restrict__ acc,
+                                                uint64_t c, const CkptDesc &d_warp, uint32_t a_warp,
+                                                uint64_t a_next, int li) {
+    const uint32_t log2S = P.log2_chunk;
+    uint64_t sum = 0, fo = 0;
+    uint32_t len = 0;
+    bool has = false;
+    CkptDesc d = d_warp;
+    uint32_t a = a_warp;
+    if (c < P.c_end) {
+        if (c >= a_next) {   // the segment crosses an allocation end
+            a = find_alloc(P.desc, P.n_allocs, c);
+            d = P.desc[a];
+        }
+        const uint64_t local = c - d.first_chunk;
+        const uint64_t rest = d.bytes - (local << log2S);
+        len = (uint32_t)umin64(rest, 1ull << log2S);
+        has = d.base_first != kNoBase;
+        if (li == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
+        const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S));
+        const uint32_t nv = len >> 4;
+        uint4 q[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t v = li + LPC * u;
+            if (v < nv) q[u] = __ldg(p + v);
+        }
+        uint64_t key = (2ull * (uint64_t)li + 1ull) * kK1;
+        constexpr uint64_t kStep = 2ull * LPC * kK1;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t v = li + LPC * u;
+            if (v < nv) {
+                sum += mixw(((uint64_t)q[u].y << 32) | q[u].x, key);
+                sum += mixw(((uint64_t)q[u].w << 32) | q[u].z, key + kK1);
+            }
+            key += kStep;
+        }
+        if (P.full_copy) {   // FULL checkpoint: the chunk goes straight to its staging offset
+            const uint64_t o = P.alloc_prefix[a] + (local << log2S) - P.seg_base;
+            if (o + len <= P.staging_cap) {
+                uint4 *dst = reinterpret_cast<uint4 *>(P.staging + o);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t v = li + LPC * u;
+                    if (v < nv) __stcs(dst + v, q[u]);
+                }
+            } else if (li == 0) {
+                atomicOr(&P.ctrl->err, kErrBounds);
+            }
+        }
+        const uint32_t rem = len & 15u;
+        if (rem && (uint32_t)li == (nv % LPC)) {
+            const uint8_t *t = reinterpret_cast<const uint8_t *>(p + nv);
+            uint64_t w0 = 0, w1 = 0;
+            for (uint32_t b = 0; b < rem; ++b) {
+                const uint64_t byte = t[b];
+                if (b < 8) w0 |= byte << (8 * b);
+                else w1 |= byte << (8 * (b - 8));
+            }
+            const uint64_t kt = (2ull * nv + 1ull) * kK1;
+            sum += mixw(w0, kt);
+            if (rem > 8) sum += mixw(w1, kt + kK1);
+        }
+    }
+#pragma unroll
+    for (int o = LPC / 2; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if (li == 0 && c < P.c_end) {
+        const uint64_t fp = fp_finalize(sum, len);
+        P.fp_new[c] = fp;
+        acc[c - P.c_begin] = len | ((!has || fo != fp) ? kAccDirty : 0ull);
+    }
+}
+
+template <int LPC>
+__global__ void __launch_bounds__(kHashNT, 2)
+split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t) {
+    constexpr int CPS = 32 / LPC;   // chunks per 8 KiB segment
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp_g = ((uint64_t)blockIdx.x * kHashNT + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * kHashNT) >> 5;
+    const uint64_t n_slots = (P.c_end - P.c_begin + CPS - 1) / CPS;
+    const uint64_t per = (n_slots + n_warps - 1) / n_warps;
+    uint64_t q = warp_g * per;
+    const uint64_t q_end = umin64(q + per, n_slots);
+    CkptDesc d{};
+    uint64_t a_next = 0;
+    uint32_t a = 0;
+    bool have = false;
+    for (; q < q_end; ++q) {
+        const uint64_t c0 = P.c_begin + q * CPS;
+        if (!have || c0 >= a_next) {
+            a = find_alloc(P.desc, P.n_allocs, c0);
+            d = P.desc[a];
+            a_next = a + 1 < P.n_allocs ? P.desc[a + 1].first_chunk : ~0ull;
+            have = true;
+        }
+        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a, a_next, lane % LPC);
+    }
+}
+
+__global__ void __launch_bounds__(kFinNT)
+split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t log2Seg) {
+    const bool direct = log2Seg == P.log2_chunk;
+    __shared__ uint32_t s_wcnt[32];
+    __shared__ uint64_t s_wbytes[32];
+    __shared__ uint64_t s_wdirty[32];
+    __shared__ uint64_t s_k0, s_d0;
+    __shared__ uint32_t s_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t log2S = P.log2_chunk;
+    const uint64_t S = 1ull << log2S;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t t = atomicAdd(&P.ctrl->ticket, 1u);
+            if (P.skip_first_ticket && t == 0) t = atomicAdd(&P.ctrl->ticket, 1u);
+            s_tile = t;
+        }
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= P.n_tiles) break;
+        const uint64_t c = P.c_begin + (uint64_t)tile * kFinNT + threadIdx.x;
+        uint32_t dl = 0, len = 0;
+        if (c < P.c_end && direct) {
+            const uint64_t v = acc[c - P.c_begin];
+            len = (uint32_t)v;
+            dl = (v & kAccDirty) ? len : 0u;
+        } else if (c < P.c_end) {
+            const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
+            const uint64_t local = c - d.first_chunk;
+            len = (uint32_t)min(S, d.bytes - (local << log2S));
+            const uint64_t fp = fp_finalize(acc[c - P.c_begin], len);
+            P.fp_new[c] = fp;
+            const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
+            dl = dirty ? len : 0u;
+        }
+        // Bytes that advance the staging offset: the dirty ones, or in the
+        // sparse pass every chunk's (each sits at its uncompacted offset).
+        const uint32_t sv = P.sparse ? len : dl;
+        const unsigned m = __ballot_sync(kFull, dl != 0);
+        const uint64_t incl = warp_incl_scan(sv, lane);
+        if (P.sparse) {
+            const uint64_t wd = warp_sum((uint64_t)dl);
+            if (lane == 0) s_wdirty[warp] = wd;
+        }
+        if (lane == 31) {
+            s_wcnt[warp] = __popc(m);
+            s_wbytes[warp] = incl;
+        }
+        __syncthreads();
+        if (P.sparse && warp == 1) {   // the tile's dirty bytes, one atomic per tile
+            const uint64_t td = warp_sum(s_wdirty[lane]);
+            if (lane == 0 && td) atomicAdd(&P.ctrl->payload, (unsigned long long)td);
+        }
+        if (warp == 0) {
+            const uint32_t wc = s_wcnt[lane];
+            const uint64_t wb = s_wbytes[lane];
+            uint32_t ic = wc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, ic, o);
+                if (lane >= o) ic += t;
+            }
+            const uint64_t ib = warp_incl_scan(wb, lane);
+            const uint32_t cnt = __shfl_sync(kFull, ic, 31);
+            const uint64_t bytes = __shfl_sync(kFull, ib, 31);
+            s_wcnt[lane] = ic - wc;
+            s_wbytes[lane] = ib - wb;
+            uint64_t k0 = 0, d0 = 0;
+            if (tile == 0) {
+                if (lane == 0) {
+                    st_status(P.tile_cnt, kFlagInc | cnt);
+                    st_status(P.tile_bytes, kFlagInc | bytes);
+                }
+            } else {
+                if (lane == 0) {
+                    st_status(P.tile_cnt + tile, kFlagAgg | cnt);
+                    st_status(P.tile_bytes + tile, kFlagAgg | bytes);
+                }
+                lookback(P, tile, lane, &k0, &d0);
+                if (lane == 0) {
+                    st_status(P.tile_cnt + tile, kFlagInc | ((k0 + cnt) & kValMask));
+                    st_status(P.tile_bytes + tile, kFlagInc | ((d0 + bytes) & kValMask));
+                }
+            }
+            if (lane == 0) {
+                s_k0 = k0;
+                s_d0 = d0;
+                if (tile == P.n_tiles - 1) {
+                    P.ctrl->k = k0 + cnt;
+                    P.ctrl->D = d0 + bytes;
+                    if (k0 + cnt <= P.idx_cap) P.off_out[k0 + cnt] = d0 + bytes;
+                    else atomicOr(&P.ctrl->err, kErrBounds);
+                }
+            }
+        }
+        __syncthreads();
+        if (dl) {
+            const uint64_t j = s_k0 + s_wcnt[warp] + __popc(m & ((1u << lane) - 1u));
+            if (j < P.idx_cap) {
+                P.idx_out[j] = c;
+                P.off_out[j] = s_d0 + s_wbytes[warp] + incl - sv;
+            } else {
+                atomicOr(&P.ctrl->err, kErrBounds);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGatherNT)
+split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
+    if (P.full_copy) return;   // the hash kernel has already written every chunk
+    const int lane = threadIdx.x & 31;
+    const uint64_t kd = (uint64_t)P.ctrl->k;
+    const uint64_t k = kd < P.idx_cap ? kd : P.idx_cap;
+    const uint32_t log2S = P.log2_chunk;
+    const uint64_t S = 1ull << log2S;
+    const uint64_t nw = ((uint64_t)gridDim.x * kGatherNT) >> 5;
+    for (uint64_t j = ((uint64_t)blockIdx.x * kGatherNT + threadIdx.x) >> 5; j < k; j += nw) {
+        const uint64_t c = P.idx_out[j];
+        const uint64_t o = P.off_out[j];
+        const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
+        const uint64_t local = c - d.first_chunk;
+        const uint64_t len = min(S, d.bytes - (local << log2S));
+        if (o + len > P.staging_cap) {
+            if (lane == 0) atomicOr(&P.ctrl->err, kErrBounds);
+            continue;
+        }
+        copy_group<32>(P.staging + o, reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S), len, lane);
+    }
+}
+
+}  // namespace
+
+const void *split_hash_fn() { return reinterpret_cast<const void *>(&split_hash_kernel); }
+const void *split_hash_small_fn(int lanes_per_chunk) {
+    switch (lanes_per_chunk) {
+    case 2: return reinterpret_cast<const void *>(&split_hash_small_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&split_hash_small_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&split_hash_small_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&split_hash_small_kernel<16>);
+    default: return nullptr;
+    }
+}
+const void *split_finalize_fn() { return reinterpret_cast<const void *>(&split_finalize_kernel); }
+const void *split_gather_fn() { return reinterpret_cast<const void *>(&split_gather_kernel); }
+int split_hash_threads() { return kHashNT; }
+int split_finalize_threads() { return kFinNT; }
+int split_gather_threads() { return kGatherNT; }
+int split_max_ctas_per_sm(const void *fn, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace crac
