@@ -51,6 +51,12 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def restore_flags(args) -> int:
+    """crac_config_t.flags for host-image restores: in place (default) or staged."""
+    import paper_2008_10596_gb300 as C
+    return C.CRAC_FLAG_STAGED_RESTORE if getattr(args, "staged_restore", False) else 0
+
+
 def kernel_src_sha() -> str:
     """sha256 prefix over the device sources (every .cu and .cuh of the library
     in name order, the test mutators excepted): what an ncu summary was
@@ -286,7 +292,7 @@ def run_crac(args):
     # resident context of this run (their base images and the timed loop's
     # growing chain), so that no step allocates from CUDA.
     ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, reserve_device_bytes=16 * B)
-    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=3 * B)
+    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=3 * B, flags=restore_flags(args))
     ctx_pa = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, launch_mode=C.CRAC_LAUNCH_PER_ALLOC)
     ctx_b = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
@@ -567,7 +573,7 @@ def run_config3(args):
         return len(rows)
 
     ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3, device=0,
-                                                  reserve_host_bytes=int(2.2 * sum(sizes))))
+                                                  reserve_host_bytes=int(2.2 * sum(sizes)), flags=restore_flags(args)))
     for ptr, n, k in zip(ptrs, sizes, kinds):
         C.crac_ctx_register_alloc(ctx, ptr, n, k)
     B = sum(sizes)
@@ -799,7 +805,8 @@ def run_config5(args):
         bufs = [torch.randn(n // 4, generator=g, device=dev).view(torch.uint8) for n in sizes]
         stream = torch.cuda.Stream(dev)
         ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=5000 + i, device=0,
-                                                      reserve_host_bytes=int(2.0 * total) if i == 0 else 0))
+                                                      reserve_host_bytes=int(2.0 * total) if i == 0 else 0,
+                                                      flags=restore_flags(args)))
         for b in bufs:
             C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
         first = W.chunk_layout(sizes, S)
@@ -944,6 +951,8 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes"],
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
+    ap.add_argument("--staged-restore", action="store_true",
+                    help="c2 e2e, c3, c5: restore host images through staging (copy engine) instead of in place")
     ap.add_argument("--chunk-kib", default="4,64", help="passes: chunk sizes in KiB")
     ap.add_argument("--dirty", default="0,0.1,0.5,1", help="passes: fractions of 4 KiB pages rewritten")
     ap.add_argument("--kernels", default="split,ldg,tma,sparse", help="passes: pass kernels")

@@ -143,7 +143,12 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     P.owner = (uint32_t *)c->owner.p;
     P.n_owner = nt;
     P.err = (unsigned int *)c->serr.p;
-    const uint64_t grid = (uint64_t)c->sm_count * 8;
+    // Reads of host images are paced by the host link, which one CTA per SM
+    // already saturates (4 KiB in flight per warp); a bigger grid would only
+    // keep SMs from other streams' work for the length of the transfer.
+    bool any_host = false;
+    for (const crac_image *im : chain) any_host = any_host || im->residency != CRAC_RESIDENCY_DEVICE;
+    const uint64_t grid = (uint64_t)c->sm_count * (any_host ? 1 : 8);
     CK(cudaEventRecord(c->ev_r0, s));
     CK(launch_restore_mark(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 255) / 256, grid)), s));
     CK(launch_restore_check(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
