@@ -433,7 +433,7 @@ def run_crac(args):
         del hbuf, dbuf
 
     # ---- e2e: host images through the C ABI ----------------------------------
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
     e2e = None
     if e2e_steps:
         step(ctx_host, host=True)
