@@ -284,8 +284,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         return CRAC_ERR_CUDA;
     }
     const bool split = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
-                       (c->cfg.pass_kernel == CRAC_PASS_SPLIT || c->cfg.pass_kernel == CRAC_PASS_AUTO ||
-                        c->cfg.pass_kernel == CRAC_PASS_SPARSE);
+                       (c->pass_now == CRAC_PASS_SPLIT || c->pass_now == CRAC_PASS_SPARSE);
     if (split) {
         const uint32_t cptF = (uint32_t)split_finalize_threads();
         const uint64_t n_tiles = (nseg + cptF - 1) / cptF;
@@ -344,7 +343,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         c->last.pass_kernel = P.sparse ? CRAC_PASS_SPARSE : CRAC_PASS_SPLIT;
     } else if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
         const uint64_t S = 1ull << c->log2S;
-        const bool tma = c->cfg.pass_kernel == CRAC_PASS_TMA;
+        const bool tma = c->pass_now == CRAC_PASS_TMA;
         int wpc;
         uint32_t cpt;
         const void *fn;
@@ -448,6 +447,18 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
 }
 
 
+// CRAC_PASS_AUTO: the split pass, unless the last pass with a baseline found
+// more than half of the chunks dirty; then a pass that reads every byte once
+// (at 100% dirty 4 KiB pages and 64 KiB chunks: sparse 0.94, TMA 0.72, LDG
+// 0.69, split 0.66 of the HBM peak), the best one the images and sizes allow.
+uint32_t resolve_pass_kernel(const crac_ctx *c, bool dev_res, bool all16) {
+    if (c->cfg.pass_kernel != CRAC_PASS_AUTO) return c->cfg.pass_kernel;
+    if (!c->delta_frac_valid || c->delta_frac <= 0.5f) return CRAC_PASS_SPLIT;
+    if (dev_res && all16) return CRAC_PASS_SPARSE;
+    if (c->log2S >= 10 && c->log2S <= 16) return CRAC_PASS_TMA;
+    return CRAC_PASS_LDG;
+}
+
 crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
     if (!out) return CRAC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -493,6 +504,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
 
     const bool dev_res = c->cfg.image_residency == CRAC_RESIDENCY_DEVICE;
     im->host_tables = !dev_res;
+    bool had_base = false;   // some chunk had a baseline: the pass measured a dirty fraction
     if (n > 0) {
         if (dev_res) {
             st = da.alloc(n * 8, &im->fp_dev);
@@ -525,7 +537,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             pre += c->allocs[a].bytes;
         }
         c->full_copy_ok = !any_base && all16;
-        c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE && dev_res && all16;
+        c->pass_now = resolve_pass_kernel(c, dev_res, all16);
+        c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && dev_res && all16 &&
+                       c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
+        had_base = any_base;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
         if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -659,6 +674,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
 
     // Commit: the new fingerprints become the baseline.
     im->flags = im->k == n ? CRAC_IMAGE_FULL : 0u;
+    if (had_base) {
+        c->delta_frac = (float)((double)im->k / (double)n);
+        c->delta_frac_valid = true;
+    }
     if (!(im->flags & CRAC_IMAGE_FULL) && c->parent) {
         img_ref(c->parent);
         im->parent = c->parent;
@@ -724,8 +743,11 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
         pre += c->allocs[a].bytes;
     }
     c->full_copy_ok = !any_base && all16;
-    c->sparse_ok = c->cfg.pass_kernel == CRAC_PASS_SPARSE &&
-                   c->cfg.image_residency == CRAC_RESIDENCY_DEVICE && all16;
+    // Trial passes run the configured kernel; AUTO is the split pass here, so
+    // that the tuner's observations of different sizes are comparable.
+    c->pass_now = c->cfg.pass_kernel == CRAC_PASS_AUTO ? (uint32_t)CRAC_PASS_SPLIT : c->cfg.pass_kernel;
+    c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && c->cfg.image_residency == CRAC_RESIDENCY_DEVICE &&
+                   all16 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
     uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);

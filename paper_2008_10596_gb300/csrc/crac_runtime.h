@@ -391,6 +391,9 @@ struct crac_ctx {
     crac_restart_info_t last_restart{};
     bool full_copy_ok = false;   // current pass: no baseline anywhere and 16-byte sizes
     bool sparse_ok = false;      // current pass: CRAC_PASS_SPARSE, device images, 16-byte sizes
+    uint32_t pass_now = CRAC_PASS_SPLIT;   // kernel of the current pass (CRAC_PASS_AUTO resolved)
+    float delta_frac = 0.f;      // dirty chunks / chunks of the last pass that had a baseline
+    bool delta_frac_valid = false;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
     // autotuner session: one shadow context per candidate chunk size

@@ -225,6 +225,65 @@ def test_sparse_pass_fallback_and_mixed_chain(flags):
         h1.close()
 
 
+@pytest.mark.parametrize("residency,S,mostly_dirty_kernel", [
+    (C.CRAC_RESIDENCY_DEVICE, 4 * KIB, C.CRAC_PASS_SPARSE),
+    (C.CRAC_RESIDENCY_HOST, 4 * KIB, C.CRAC_PASS_TMA),
+    (C.CRAC_RESIDENCY_HOST, 256 * KIB, C.CRAC_PASS_LDG)])
+def test_auto_follows_dirty_fraction(residency, S, mostly_dirty_kernel):
+    """CRAC_PASS_AUTO runs the split pass until a pass with a baseline finds
+    more than half of the chunks dirty, then the kernel that reads each byte
+    once (sparse for device images, else TMA, else LDG), and back to split
+    after a sparse delta; every image stays the oracle's."""
+    sizes = [S * 40, S * 3 + 16 * 5, 4096 * 7]
+    h = Harness(S, lineage=720 + S // KIB, image_residency=residency)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=140 + i)
+        kernels = []
+        for pattern in (None, "all", "random10", "random10"):
+            if pattern:
+                h.mutate(pattern_mutations(h.first(), sizes, S, pattern, seed=len(kernels) + 1))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora, pattern
+            kernels.append(C.crac_ctx_last_pass(h.ctx)["pass_kernel"])
+        # FULL (no dirty fraction yet), the all-dirty delta (split), then the
+        # kernel for mostly dirty memory, then split again
+        assert kernels == [C.CRAC_PASS_SPLIT, C.CRAC_PASS_SPLIT, mostly_dirty_kernel, C.CRAC_PASS_SPLIT]
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
+
+
+def test_sparse_kernel_with_per_allocation_launches():
+    """CRAC_PASS_SPARSE under CRAC_LAUNCH_PER_ALLOC: the per-allocation path
+    runs (it compacts) and the images are the oracle's."""
+    S = 4 * KIB
+    sizes = [50000 // 16 * 16, 4096 * 9, 16 * 1000]
+    h = Harness(S, lineage=730, pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE,
+                launch_mode=C.CRAC_LAUNCH_PER_ALLOC)
+    try:
+        for i, n in enumerate(sizes):
+            h.add(n, seed=150 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=3))
+        img, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
+
+
 @pytest.mark.parametrize("n_allocs", [3072, 3073])
 @pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
 def test_tma_many_allocations(n_allocs, residency):
