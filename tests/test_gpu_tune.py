@@ -108,3 +108,43 @@ def test_tune_apply_needs_observations():
         assert e.value.code == C.CRAC_ERR_INVALID_ARG
     finally:
         C.crac_ctx_destroy(ctx)
+
+
+def test_tune_mostly_dirty_device_images_times_every_kernel():
+    """With every page rewritten and device-resident images, apply times the
+    split, LDG, TMA and sparse passes at the chosen size; whichever wins, the
+    retuned context keeps producing the oracle's images."""
+    sizes = [8 * 1024 * KIB, 2 * 1024 * KIB + 16 * 7, 1024 * KIB]
+    bufs = [torch.from_numpy(W.host_contents("u8", n, 600 + i)).to("cuda") for i, n in enumerate(sizes)]
+    ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=64 * KIB, lineage=45,
+                                                  image_residency=C.CRAC_RESIDENCY_DEVICE))
+    stream = torch.cuda.current_stream()
+    imgs = []
+    try:
+        for b, n in zip(bufs, sizes):
+            C.crac_ctx_register_alloc(ctx, b.data_ptr(), n)
+        cands = [4 * KIB, 64 * KIB]
+        C.crac_ctx_tune_observe(ctx, cands, stream)
+        all_pages = [(a, p) for a in range(len(sizes)) for p in range(-(-sizes[a] // PAGE))]
+        for rnd in range(2):
+            _mutate_pages(bufs, sizes, all_pages, 200 + rnd)
+            C.crac_ctx_tune_observe(ctx, cands, stream)
+        res = C.crac_ctx_tune_apply(ctx, 0.0, stream)
+        vm = res["variant_ms"]
+        assert all(vm[k] > 0 for k in (C.CRAC_PASS_SPLIT, C.CRAC_PASS_LDG, C.CRAC_PASS_TMA, C.CRAC_PASS_SPARSE))
+        assert vm[res["chosen_pass_kernel"]] == min(v for v in vm if v > 0)
+        # the context itself has no baseline yet: its next image is FULL at the chosen size
+        ora = O.OracleContext(res["chosen_chunk_bytes"], lineage=45)
+        for b, n in zip(bufs, sizes):
+            ora.register(b.data_ptr(), n)
+        for rnd in range(2):
+            img = C.crac_ctx_checkpoint(ctx, stream)
+            imgs.append(img)
+            C.crac_image_wait(img)
+            assert C.crac_image_serialize(img) == ora.checkpoint([b.cpu().numpy() for b in bufs])
+            _mutate_pages(bufs, sizes, all_pages[::3], 300 + rnd)
+    finally:
+        torch.cuda.synchronize()
+        for i in imgs:
+            C.crac_image_release(i)
+        C.crac_ctx_destroy(ctx)
