@@ -240,6 +240,7 @@ def run_reference(args):
 
 def run_crac(args):
     import torch
+    import torch.cuda.nvtx as nvtx
     import torch.distributed as dist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -298,6 +299,7 @@ def run_crac(args):
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
     ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
     ctx_sparse = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_SPARSE)
+    ctx_inc = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, flags=C.CRAC_FLAG_INCREMENTAL_RESTORE)
 
     def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None, phases=None):
         mutate()
@@ -323,7 +325,7 @@ def run_crac(args):
         return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms) for i in infos]
 
     # Base images (full) for each context.
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc):
         img = C.crac_ctx_checkpoint(ctx, stream)
         C.crac_image_wait(img)
         C.crac_image_release(img)
@@ -346,8 +348,10 @@ def run_crac(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    nvtx.range_push("timed")      # ncu captures select kernels by these ranges
     for _ in range(args.steps):
         step(ctx_dev, pass_ms=pass_ms, lat_ms=lat_ms, rst=rst)
+    nvtx.range_pop()
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -398,6 +402,7 @@ def run_crac(args):
     # ---- batched vs per-allocation launches, and the pass variants -------------
     cmp = {"per_alloc": ([], []), "split": ([], []), "ldg": ([], []), "tma": ([], []), "sparse": ([], [])}
     ctxs = {"per_alloc": ctx_pa, "split": ctx_b, "ldg": ctx_ldg, "tma": ctx_tma, "sparse": ctx_sparse}
+    nvtx.range_push("variants")
     for _ in range(max(3, min(args.steps, 5))):
         mutate()
         for name, ctx in ctxs.items():
@@ -406,6 +411,7 @@ def run_crac(args):
             cmp[name][1].append((time.perf_counter() - t0) * 1e3)
             cmp[name][0].append(C.crac_ctx_last_pass(ctx)["device_ms"])
             C.crac_image_release(img)
+    nvtx.range_pop()
     med = {k: (statistics.median(v[0]), statistics.median(v[1])) for k, v in cmp.items()}
     batched = {"per_alloc_device_ms": med["per_alloc"][0], "batched_device_ms": med["split"][0],
                "speedup_device": med["per_alloc"][0] / med["split"][0],
@@ -413,6 +419,25 @@ def run_crac(args):
                "speedup_wall": med["per_alloc"][1] / med["split"][1],
                "per_alloc_launches": 3 * len(sizes), "batched_graph_launches": 1,
                "variants_device_ms": {k: v[0] for k, v in med.items()}}
+
+    # ---- rollback: incremental restore of the last image after a 10% change ----
+    rb = []
+    nvtx.range_push("rollback")
+    for _ in range(max(3, min(args.steps, 5))):
+        mutate()
+        img = C.crac_ctx_checkpoint(ctx_inc, stream)
+        mutate()                                  # the state diverges from the image again
+        C.crac_ctx_restart(ctx_inc, img, stream)
+        rb.append(C.crac_ctx_last_restart(ctx_inc))
+        C.crac_image_release(img)
+    nvtx.range_pop()
+    rollback = {"device_ms": statistics.median(r["device_ms"] for r in rb),
+                "chunks_rewritten": statistics.median(r["chunks_rewritten"] for r in rb),
+                "chunks": n, "bytes_rewritten": statistics.median(r["restored_bytes"] for r in rb),
+                "full_restore_device_ms": statistics.median(r["device_ms"] for r in rst),
+                "how": "CRAC_FLAG_INCREMENTAL_RESTORE: fingerprint the current memory against the image, "
+                       "rewrite the chunks that differ (device-resident images)"}
+    rollback["speedup_vs_full"] = rollback["full_restore_device_ms"] / rollback["device_ms"]
 
     # ---- host link probe: pinned 1 GiB copies, best of 10 each way ------------
     link = None
@@ -442,8 +467,10 @@ def run_crac(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_pass, e_phase, e_rst = [], [], []
         e0.record(stream)
+        nvtx.range_push("e2e")
         for _ in range(e2e_steps):
             step(ctx_host, host=True, pass_ms=e_pass, phases=e_phase, rst=e_rst)
+        nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -481,7 +508,7 @@ def run_crac(args):
                                    "single thread")
         cpu["nproc"] = os.cpu_count()
 
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc):
         C.crac_ctx_destroy(ctx)
 
     if rank == 0:
@@ -494,7 +521,7 @@ def run_crac(args):
                            "step": "mutate 10% + incremental ckpt + full restart (device-resident images)",
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "roofline_ckpt_hash": roofline_hash, "pass": pass_info, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "arena_growth_in_timed_loop": arena_growth,
+                "gpu_launches": launches, "arena_growth_in_timed_loop": arena_growth, "rollback": rollback,
                 "batched_vs_per_alloc": batched,
                 "ckpt_latency_ms": {"p50": statistics.median(lat_ms),
                                     "p99": float(np.percentile(lat_ms, 99))},

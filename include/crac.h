@@ -137,6 +137,14 @@ typedef struct crac_config {
  *   cross the host link and no staging is needed; the staged path is used
  *   anyway when the device has no unified addressing. */
 #define CRAC_FLAG_STAGED_RESTORE 1u
+/* CRAC_FLAG_INCREMENTAL_RESTORE: before a restart writes anything, the
+ *   current contents of the registered allocations are fingerprinted and
+ *   compared with the target image's fingerprint table; only the chunks that
+ *   differ are restored (the others already hold the image's bytes, up to a
+ *   CRAC-FP64 collision, the same trust as an incremental checkpoint).  A
+ *   rollback to a recent image then costs one read of the tracked bytes plus
+ *   the changed chunks.  Not on the staged path, which restores everything. */
+#define CRAC_FLAG_INCREMENTAL_RESTORE 2u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
 #define CRAC_PASS_AUTO  0  /* the split pass, or, when the last pass with a baseline
@@ -391,13 +399,16 @@ CRAC_API crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out
 typedef struct crac_restart_info {
     uint32_t chain_length;       /* images from the nearest FULL one to the target */
     uint32_t images_used;        /* images that still owned at least one chunk */
-    uint64_t restored_bytes;     /* bytes written into allocations (= tracked bytes) */
+    uint64_t restored_bytes;     /* bytes written into allocations (= tracked bytes,
+                                    or the differing chunks' bytes when incremental) */
     uint64_t entries_scanned;    /* chunk entries the scatter kernels visited */
     uint64_t h2d_bytes;          /* host image payload copied to the device (staged
                                     restore; a mapped restore reads in place) */
     uint32_t scatter_launches;
     float device_ms;             /* device time from the first copy/launch to the last */
-    uint32_t reserved[4];
+    uint64_t chunks_rewritten;   /* chunks written into allocations (incremental restore:
+                                    those that differed from the image; else all) */
+    uint32_t reserved[2];
 } crac_restart_info_t;
 
 CRAC_API crac_status_t crac_ctx_last_restart(crac_ctx_t *ctx, crac_restart_info_t *out);

@@ -47,6 +47,7 @@ CRAC_PASS_TMA = 2
 CRAC_PASS_SPLIT = 3
 CRAC_PASS_SPARSE = 4
 CRAC_FLAG_STAGED_RESTORE = 1
+CRAC_FLAG_INCREMENTAL_RESTORE = 2
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1
@@ -110,7 +111,8 @@ class CracRestartInfo(ctypes.Structure):
     _fields_ = [("chain_length", ctypes.c_uint32), ("images_used", ctypes.c_uint32),
                 ("restored_bytes", ctypes.c_uint64), ("entries_scanned", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("scatter_launches", ctypes.c_uint32),
-                ("device_ms", ctypes.c_float), ("reserved", ctypes.c_uint32 * 4)]
+                ("device_ms", ctypes.c_float), ("chunks_rewritten", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class CracTuneResult(ctypes.Structure):

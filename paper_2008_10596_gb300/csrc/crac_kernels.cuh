@@ -169,12 +169,17 @@ struct RestoreParams {
     uint32_t *owner;              // per target chunk: newest chain position + 1 (0 = none)
     uint64_t n_owner;
     unsigned int *err;
+    // Incremental restore: current and target fingerprints per target chunk.
+    const uint64_t *fp_now, *fp_img;
 };
 // Multi-image restore: mark owners for every entry of every piece (atomicMax,
 // so the newest image wins in any order), check coverage, scatter owned chunks.
 cudaError_t launch_restore_mark(const RestoreParams &p, int grid, cudaStream_t s);
 cudaError_t launch_restore_check(const RestoreParams &p, int grid, cudaStream_t s);
 cudaError_t launch_restore_scatter(const RestoreParams &p, int grid, cudaStream_t s);
+// Incremental restore, between check and scatter: clears the owner of every
+// chunk whose current fingerprint equals the target's, so it is not written.
+cudaError_t launch_restore_unmark(const RestoreParams &p, int grid, cudaStream_t s);
 
 void count_launches(uint64_t n);
 uint64_t launches_so_far();

@@ -26,7 +26,7 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
-    if (cfg.flags & ~CRAC_FLAG_STAGED_RESTORE) return CRAC_ERR_INVALID_ARG;
+    if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE)) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
@@ -83,9 +83,10 @@ void ctx_free_all(crac_ctx *c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
-                      &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr})
+                      &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr,
+                      &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff})
         if (b->p) cudaFree(b->p);
-    for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h})
+    for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h, &c->vdesc_h})
         if (b->p) cudaFreeHost(b->p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
@@ -777,6 +778,70 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
         for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
         c->base_valid = true;
     }
+    return CRAC_OK;
+}
+
+// Fingerprints of the registered allocations' current contents, each tested
+// against fp_ref[global chunk id] (the split pass's hash and finalize kernels
+// over every chunk, without a gather): *fp_out receives the fingerprints,
+// and *ctrl_out is the device control block whose k and D count the chunks
+// that differ and their bytes.  Enqueued on s; the caller reads the results
+// after the stream reaches them.  Incremental restore runs this first.
+crac_status_t fingerprint_against(crac_ctx *c, const uint64_t *fp_ref, cudaStream_t s, const uint64_t **fp_out,
+                                  const CkptCtrl **ctrl_out) {
+    const size_t na = c->allocs.size();
+    const uint32_t log2S = c->log2S;
+    const uint64_t S = 1ull << log2S;
+    std::vector<uint64_t> first(na + 1, 0);
+    for (size_t a = 0; a < na; ++a) first[a + 1] = first[a] + ((c->allocs[a].bytes + S - 1) >> log2S);
+    const uint64_t n = first[na];
+    const uint32_t cptF = (uint32_t)split_finalize_threads();
+    const uint64_t n_tiles = (n + cptF - 1) / cptF;
+    if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+    const size_t status_bytes = sizeof(CkptCtrl) + 16 * n_tiles;
+    const size_t work_bytes = status_bytes + 8 * n;
+    TRY(ensure_dev(c->vdesc, std::max<size_t>(na, 1) * sizeof(CkptDesc)));
+    TRY(ensure_host(c->vdesc_h, std::max<size_t>(na, 1) * sizeof(CkptDesc)));
+    TRY(ensure_dev(c->vwork, work_bytes));
+    TRY(ensure_dev(c->vfp, std::max<uint64_t>(n, 1) * 8));
+    TRY(ensure_dev(c->vidx, std::max<uint64_t>(n, 1) * 8));
+    TRY(ensure_dev(c->voff, (n + 1) * 8));
+    CkptDesc *dh = (CkptDesc *)c->vdesc_h.p;
+    for (size_t a = 0; a < na; ++a)   // the reference table has the same chunk layout
+        dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], first[a]};
+    CK(cudaMemcpyAsync(c->vdesc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->vwork.p, 0, work_bytes, s));
+    const bool small = log2S >= 9 && log2S < 13;
+    uint32_t log2Seg = std::min<uint32_t>(log2S, 13);
+    const void *hash_fn = small ? split_hash_small_fn(1 << (log2S - 8)) : split_hash_fn();
+    CkptParams P{};
+    P.desc = (const CkptDesc *)c->vdesc.p;
+    P.n_allocs = (uint32_t)na;
+    P.log2_chunk = log2S;
+    P.c_begin = 0;
+    P.c_end = n;
+    P.cpt = cptF;
+    P.n_tiles = (uint32_t)n_tiles;
+    P.fp_old = fp_ref;
+    P.fp_new = (uint64_t *)c->vfp.p;
+    P.idx_out = (uint64_t *)c->vidx.p;
+    P.off_out = (uint64_t *)c->voff.p;
+    P.idx_cap = n;
+    P.ctrl = (CkptCtrl *)c->vwork.p;
+    P.tile_cnt = (uint64_t *)((uint8_t *)c->vwork.p + sizeof(CkptCtrl));
+    P.tile_bytes = P.tile_cnt + n_tiles;
+    P.timeout_ns = c->cfg.timeout_ns;
+    unsigned long long *acc = (unsigned long long *)((uint8_t *)c->vwork.p + status_bytes);
+    const uint64_t n_slots = small ? (n + (8192u >> log2S) - 1) / (8192u >> log2S) : n << (log2S - log2Seg);
+    const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>(
+                       (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(hash_fn, split_hash_threads())));
+    const int gf = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2));
+    void *args[] = {&P, &acc, &log2Seg};
+    CK(cudaLaunchKernel(hash_fn, dim3(gh), dim3(split_hash_threads()), args, 0, s));
+    CK(cudaLaunchKernel(split_finalize_fn(), dim3(gf), dim3(split_finalize_threads()), args, 0, s));
+    count_launches(2);
+    *fp_out = (const uint64_t *)c->vfp.p;
+    *ctrl_out = P.ctrl;
     return CRAC_OK;
 }
 

@@ -149,11 +149,22 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     bool any_host = false;
     for (const crac_image *im : chain) any_host = any_host || im->residency != CRAC_RESIDENCY_DEVICE;
     const uint64_t grid = (uint64_t)c->sm_count * (any_host ? 1 : 8);
+    // Incremental: fingerprint the current contents against the target's
+    // table first; chunks that match are then left alone.
+    const bool incremental = (c->cfg.flags & CRAC_FLAG_INCREMENTAL_RESTORE) && nt > 0;
+    const uint64_t *fp_img = img->residency == CRAC_RESIDENCY_DEVICE ? (const uint64_t *)img->fp_dev.p
+                                                                      : (const uint64_t *)img->fp_h.p;
+    const CkptCtrl *vctrl = nullptr;
     CK(cudaEventRecord(c->ev_r0, s));
+    if (incremental) TRY(fingerprint_against(c, fp_img, s, &P.fp_now, &vctrl));
+    P.fp_img = fp_img;
     CK(launch_restore_mark(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 255) / 256, grid)), s));
     CK(launch_restore_check(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
+    if (incremental)
+        CK(launch_restore_unmark(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
     CK(launch_restore_scatter(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 7) / 8, grid)), s));
     CK(cudaEventRecord(c->ev_r1, s));
+    if (incremental) CK(cudaMemcpyAsync(c->ctrl_h.p, vctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
     if (nt) {
         const void *fp = img->residency == CRAC_RESIDENCY_DEVICE ? (const void *)img->fp_dev.p : (const void *)img->fp_h.p;
         CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, fp, nt * 8, cudaMemcpyDefault, s));
@@ -165,6 +176,16 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     if (err & kErrUncovered) return CRAC_ERR_IMAGE_MISMATCH;
     if (err) return CRAC_ERR_CORRUPT;
     cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
+    ri.chunks_rewritten = nt;
+    if (incremental) {
+        // The fingerprints the unmark used are written before the pass's
+        // look-back, so the restore is right even if the counts are not.
+        const CkptCtrl *vc = (const CkptCtrl *)c->ctrl_h.p;
+        if (vc->err == 0) {
+            ri.chunks_rewritten = vc->k;
+            ri.restored_bytes = vc->D;
+        }
+    }
     c->last_restart = ri;
     c->fp_cur = 1 - c->fp_cur;
     restart_commit(c, img);
@@ -418,6 +439,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     CK(cudaEventSynchronize(c->ev_last));
     if (*(const unsigned *)c->serr_h.p) return CRAC_ERR_CORRUPT;
     cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
+    ri.chunks_rewritten = nt;   // the staged path restores every chunk
     c->last_restart = ri;
     c->fp_cur = 1 - c->fp_cur;
     restart_commit(c, img);

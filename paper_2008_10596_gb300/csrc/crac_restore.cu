@@ -87,6 +87,13 @@ __global__ void __launch_bounds__(256) restore_check_kernel(const RestoreParams 
         if (P.owner[i] == 0) atomicOr(P.err, kErrUncovered);
 }
 
+// Incremental restore: a target chunk that already holds the image's bytes
+// (same fingerprint) keeps them; clearing its owner makes the scatter skip it.
+__global__ void __launch_bounds__(256) restore_unmark_kernel(const RestoreParams P) {
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < P.n_owner; i += (uint64_t)gridDim.x * 256)
+        if (P.fp_now[i] == P.fp_img[i]) P.owner[i] = 0;
+}
+
 __global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const RestoreParams P) {
     if (*(volatile unsigned int *)P.err) return;   // uncovered or out of range: memory untouched
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -123,6 +130,14 @@ cudaError_t launch_restore_mark(const RestoreParams &p, int grid, cudaStream_t s
 cudaError_t launch_restore_check(const RestoreParams &p, int grid, cudaStream_t s) {
     if (p.n_owner == 0) return cudaSuccess;
     restore_check_kernel<<<grid, 256, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_restore_unmark(const RestoreParams &p, int grid, cudaStream_t s) {
+    if (p.n_owner == 0) return cudaSuccess;
+    restore_unmark_kernel<<<grid, 256, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(1);
     return e;

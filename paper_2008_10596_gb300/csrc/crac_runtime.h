@@ -370,6 +370,8 @@ struct crac_ctx {
     HostBuf desc_h, ctrl_h;
     // restart scratch
     DevBuf owner, sdesc, sidx, soff, serr;
+    DevBuf vdesc, vwork, vfp, vidx, voff;   // incremental restore: fingerprint pass scratch
+    HostBuf vdesc_h;
     HostBuf owner_h, sdesc_h, soff_h, serr_h;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_last = nullptr, ev_pass = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -415,6 +417,8 @@ void pick_split(const crac_ctx *c, int *wpc, uint32_t *cpt);
 crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out);
 crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms, uint64_t *k_out,
                              uint64_t *d_out);
+crac_status_t fingerprint_against(crac_ctx *c, const uint64_t *fp_ref, cudaStream_t s, const uint64_t **fp_out,
+                                  const CkptCtrl **ctrl_out);
 
 // Restart (crac_restart.cpp).
 crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s);
