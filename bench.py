@@ -52,9 +52,11 @@ def load_peaks():
 
 
 def restore_flags(args) -> int:
-    """crac_config_t.flags for host-image restores: in place (default) or staged."""
+    """crac_config_t.flags for host images: restores in place (default) or
+    staged; drains through staging (default) or direct."""
     import paper_2008_10596_gb300 as C
-    return C.CRAC_FLAG_STAGED_RESTORE if getattr(args, "staged_restore", False) else 0
+    f = C.CRAC_FLAG_STAGED_RESTORE if getattr(args, "staged_restore", False) else 0
+    return f | (C.CRAC_FLAG_DIRECT_DRAIN if getattr(args, "direct_drain", False) else 0)
 
 
 def kernel_src_sha() -> str:
@@ -980,6 +982,8 @@ def main():
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--staged-restore", action="store_true",
                     help="c2 e2e, c3, c5: restore host images through staging (copy engine) instead of in place")
+    ap.add_argument("--direct-drain", action="store_true",
+                    help="c2 e2e, c3, c5: write host images straight into pinned memory instead of staging + D2H")
     ap.add_argument("--chunk-kib", default="4,64", help="passes: chunk sizes in KiB")
     ap.add_argument("--dirty", default="0,0.1,0.5,1", help="passes: fractions of 4 KiB pages rewritten")
     ap.add_argument("--kernels", default="split,ldg,tma,sparse", help="passes: pass kernels")

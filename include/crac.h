@@ -145,6 +145,14 @@ typedef struct crac_config {
  *   rollback to a recent image then costs one read of the tracked bytes plus
  *   the changed chunks.  Not on the staged path, which restores everything. */
 #define CRAC_FLAG_INCREMENTAL_RESTORE 2u
+/* CRAC_FLAG_DIRECT_DRAIN: a checkpoint into host-resident images writes the
+ *   dirty chunks straight into the image's pinned memory through its device
+ *   mapping, instead of into device staging followed by a device-to-host
+ *   copy on the side stream: no staging round trip (2 x dirty bytes of HBM
+ *   traffic, and no staging buffer), but the pass itself then runs at the
+ *   host link's rate, on the caller's stream.  Not for the TMA pass (which
+ *   keeps the staged drain). */
+#define CRAC_FLAG_DIRECT_DRAIN 4u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
 #define CRAC_PASS_AUTO  0  /* the split pass, or, when the last pass with a baseline

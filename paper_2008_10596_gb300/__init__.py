@@ -48,6 +48,7 @@ CRAC_PASS_SPLIT = 3
 CRAC_PASS_SPARSE = 4
 CRAC_FLAG_STAGED_RESTORE = 1
 CRAC_FLAG_INCREMENTAL_RESTORE = 2
+CRAC_FLAG_DIRECT_DRAIN = 4
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1

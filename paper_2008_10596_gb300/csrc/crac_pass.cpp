@@ -26,7 +26,8 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
-    if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE)) return CRAC_ERR_INVALID_ARG;
+    if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE | CRAC_FLAG_DIRECT_DRAIN))
+        return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
@@ -571,8 +572,13 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
         }
         const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
+        // Direct drain: the pass writes the payload straight into the image's
+        // pinned block through its device mapping (not the TMA pass, whose
+        // bulk stores stay within device memory).
+        const bool direct = host_res && c->uva && (c->cfg.flags & CRAC_FLAG_DIRECT_DRAIN) &&
+                            c->pass_now != CRAC_PASS_TMA;
         if (host_res) {
-            st = ensure_dev(c->staging, max_seg_bytes);
+            st = ensure_dev(c->staging, max_seg_bytes);   // also the direct drain's fallback
             if (st == CRAC_OK) st = ensure_dev(c->idx, max_seg_chunks * 8);
             if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
             if (st != CRAC_OK) return fail(st);
@@ -598,6 +604,12 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                 off_d = (uint64_t *)pc.off_dev.p;
                 stg = pc.dev.p;
             }
+            // The worst-case block comes from the pinned regions as they are
+            // (growing them, or starting their background growth, mid-loop
+            // would stall the device); without room this segment drains
+            // through staging.  The unused tail is returned after the pass.
+            const bool direct_seg = direct && pa.try_alloc(sg.bytes, &pc.host);
+            if (direct_seg) stg = pc.host.p;
             if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) {
                 im->pieces.push_back(pc);
                 return fail(cuda_status(cudaGetLastError()));
@@ -621,7 +633,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                 return fail(CRAC_ERR_CUDA);
             }
             cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
-            if (host_res) {
+            if (direct_seg) {
+                if (ctrl.D) pa.shrink(pc.host, ctrl.D);
+                else pa.free(pc.host);
+            } else if (host_res) {
                 if (ctrl.D) {
                     st = pa.alloc(ctrl.D, &pc.host);
                     if (st != CRAC_OK) {

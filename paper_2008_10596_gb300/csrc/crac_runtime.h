@@ -186,6 +186,21 @@ class Arena {
         used_ += len;
         return CRAC_OK;
     }
+    // Carve from the existing regions only: no growth and no background
+    // pre-grow, for temporary worst-case blocks that are shrunk right after.
+    bool try_alloc(uint64_t len, Block *b) {
+        len = round_up(std::max<uint64_t>(len, 1), 256);
+        std::lock_guard<std::mutex> lk(mu_);
+        for (size_t r = 0; r < regions_.size(); ++r) {
+            uint64_t off;
+            if (regions_[r].ra.alloc(len, &off)) {
+                *b = Block{regions_[r].base + off, len, (int)r, off};
+                used_ += len;
+                return true;
+            }
+        }
+        return false;
+    }
     void free(Block &b) {
         if (b.region < 0) return;
         std::lock_guard<std::mutex> lk(mu_);

@@ -51,7 +51,7 @@ def test_config_validation(C):
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10),
                 dict(pass_kernel=C.CRAC_PASS_SPARSE),         # needs device-resident images
-                dict(flags=4)):
+                dict(flags=8)):
         with pytest.raises(C.CracError) as e:
             C.crac_ctx_create(C.crac_config_default(**bad))
         assert e.value.code == C.CRAC_ERR_INVALID_ARG

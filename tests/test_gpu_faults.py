@@ -17,7 +17,7 @@ from tests.gpu_harness import Harness, pattern_mutations
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 
 
-@pytest.mark.parametrize("kern", [C.CRAC_PASS_TMA, C.CRAC_PASS_LDG, C.CRAC_PASS_SPARSE])
+@pytest.mark.parametrize("kern", [C.CRAC_PASS_TMA, C.CRAC_PASS_LDG, C.CRAC_PASS_SPARSE, "direct"])
 @pytest.mark.parametrize("step,code", [(C.CRAC_FAULT_PASS, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_DRAIN, C.CRAC_ERR_CUDA),
                                        (C.CRAC_FAULT_ALLOC, C.CRAC_ERR_OOM),
@@ -25,6 +25,8 @@ pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 def test_failed_checkpoint_leaves_state(step, code, kern):
     S = 4096
     extra = {"image_residency": C.CRAC_RESIDENCY_DEVICE} if kern == C.CRAC_PASS_SPARSE else {}
+    if kern == "direct":   # the split pass writing host images through their device mapping
+        kern, extra = C.CRAC_PASS_SPLIT, {"flags": C.CRAC_FLAG_DIRECT_DRAIN}
     h = Harness(S, lineage=61, timeout_ns=20_000_000, chunks_per_tile=2, pass_kernel=kern, **extra)
     try:
         # > 1024 chunks, so that the split finalize (the sparse pass's

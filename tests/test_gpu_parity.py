@@ -348,7 +348,7 @@ def test_tma_many_allocations(n_allocs, residency):
 
 
 @pytest.mark.parametrize("mode", ["per_alloc", "segments", "device", "device_segments", "staged",
-                                  "staged_segments"])
+                                  "staged_segments", "direct", "direct_segments", "direct_per_alloc"])
 def test_launch_modes_and_residency(mode):
     """Launch modes, staging segments and residencies.  Host images are
     restored in place from pinned memory unless CRAC_FLAG_STAGED_RESTORE
@@ -357,10 +357,14 @@ def test_launch_modes_and_residency(mode):
     cfg = {}
     if mode.startswith("staged"):
         cfg["flags"] = C.CRAC_FLAG_STAGED_RESTORE
+    if mode.startswith("direct"):      # host images written straight into pinned memory
+        cfg["flags"] = C.CRAC_FLAG_DIRECT_DRAIN
     if mode == "per_alloc":
         cfg["launch_mode"] = C.CRAC_LAUNCH_PER_ALLOC
-    if mode in ("segments", "device_segments", "staged_segments"):
+    if mode in ("segments", "device_segments", "staged_segments", "direct_segments"):
         cfg["staging_bytes"] = 40 * KIB      # forces many segments, allocations split
+    if mode == "direct_per_alloc":
+        cfg["launch_mode"] = C.CRAC_LAUNCH_PER_ALLOC
     if mode.startswith("device"):
         cfg["image_residency"] = C.CRAC_RESIDENCY_DEVICE
     sizes = [100000, 4096, 77, 250000, 8192 * 3 + 1]
@@ -387,7 +391,7 @@ def test_launch_modes_and_residency(mode):
         assert lib4 == ora4 and O.parse_image(lib4).k == 0
         info = C.crac_ctx_last_restart(h.ctx)
         assert info["chain_length"] == 3 and info["restored_bytes"] == sum(sizes)
-        if mode == "per_alloc":
+        if mode in ("per_alloc", "direct_per_alloc"):
             info = C.crac_ctx_last_pass(h.ctx)
             assert info["kernel_launches"] == 3 * len(sizes)
     finally:

@@ -29,6 +29,15 @@ def _case(seed):
         cfg["image_residency"] = C.CRAC_RESIDENCY_DEVICE
     if rng.random() < 0.3:
         cfg["staging_bytes"] = int(max(S, rng.integers(S, 64 * S)))
+    flags = 0
+    if cfg.get("image_residency", C.CRAC_RESIDENCY_HOST) == C.CRAC_RESIDENCY_HOST:
+        if rng.random() < 0.4:
+            flags |= C.CRAC_FLAG_DIRECT_DRAIN
+        if rng.random() < 0.3:
+            flags |= C.CRAC_FLAG_STAGED_RESTORE
+    if rng.random() < 0.3:
+        flags |= C.CRAC_FLAG_INCREMENTAL_RESTORE
+    cfg["flags"] = flags
     if kern == C.CRAC_PASS_LDG and rng.random() < 0.5:
         cfg["chunks_per_tile"] = int(rng.integers(1, 40))
     return rng, S, cfg
