@@ -71,7 +71,12 @@ typedef int crac_status_t;
 
 typedef enum {
     CRAC_KIND_DEVICE = 0,   /* cudaMalloc */
-    CRAC_KIND_MANAGED = 1   /* cudaMallocManaged; prefetched to the device before the pass */
+    CRAC_KIND_MANAGED = 1,  /* cudaMallocManaged; prefetched to the device before the pass */
+    CRAC_KIND_HOST = 2      /* page-locked host memory (cudaMallocHost / cudaHostAlloc), which
+                               the paper also tracks (Sec. 3.2); the pass and the restore
+                               read and write it in place through its device mapping, at
+                               the host link's rate (needs unified addressing, else a
+                               checkpoint returns CRAC_ERR_UNSUPPORTED) */
 } crac_kind_t;
 
 /* Where a checkpoint image keeps its payload. */

@@ -54,6 +54,7 @@ FLAG_FULL = 1
 NO_PARENT = (1 << 64) - 1
 KIND_DEVICE = 0
 KIND_MANAGED = 1
+KIND_HOST = 2     # page-locked host memory (Sec. 3.2 lists cudaMallocHost / cudaHostAlloc)
 
 HEADER = struct.Struct("<8sIIIIQQQQQQQ")
 ALLOC = struct.Struct("<QQQIIQ")
@@ -211,7 +212,7 @@ class OracleContext:
 
     # -- registry (the cudaMalloc-family log of active mallocs, Sec. 3.2) ---
     def register(self, ptr: int, nbytes: int, kind: int = KIND_DEVICE) -> int:
-        if nbytes <= 0 or ptr == 0 or ptr % 16 or kind not in (KIND_DEVICE, KIND_MANAGED):
+        if nbytes <= 0 or ptr == 0 or ptr % 16 or kind not in (KIND_DEVICE, KIND_MANAGED, KIND_HOST):
             raise InvalidArg("bad registration")
         for a in self.allocs:
             if ptr < a.ptr + a.bytes and a.ptr < ptr + nbytes:

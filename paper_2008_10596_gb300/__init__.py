@@ -36,6 +36,7 @@ CRAC_ERR_CORRUPT = -10
 
 CRAC_KIND_DEVICE = 0
 CRAC_KIND_MANAGED = 1
+CRAC_KIND_HOST = 2
 CRAC_RESIDENCY_HOST = 0
 CRAC_RESIDENCY_DEVICE = 1
 CRAC_LAUNCH_BATCHED = 0

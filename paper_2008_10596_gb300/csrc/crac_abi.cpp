@@ -98,7 +98,7 @@ crac_status_t crac_ctx_destroy(crac_ctx_t *ctx) {
 
 crac_status_t crac_ctx_register_alloc(crac_ctx_t *ctx, void *ptr, size_t bytes, crac_kind_t kind) {
     if (!ctx || !ptr || bytes == 0 || ((uintptr_t)ptr & 15u) ||
-        (kind != CRAC_KIND_DEVICE && kind != CRAC_KIND_MANAGED))
+        (kind != CRAC_KIND_DEVICE && kind != CRAC_KIND_MANAGED && kind != CRAC_KIND_HOST))
         return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
     const uint64_t p = (uint64_t)(uintptr_t)ptr;

@@ -281,7 +281,7 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
     for (uint64_t a = 0; a < na; ++a, p += kAllocEntryBytes) {
         ImgAlloc &r = im->allocs[a];
         r = ImgAlloc{get64(p), get64(p + 8), get64(p + 16), get32(p + 24), get64(p + 32)};
-        if (r.bytes == 0 || r.kind > 1 || r.first_chunk != expect_first) return CRAC_ERR_CORRUPT;
+        if (r.bytes == 0 || r.kind > CRAC_KIND_HOST || r.first_chunk != expect_first) return CRAC_ERR_CORRUPT;
         expect_first += ((r.bytes - 1) >> log2S) + 1;
     }
     if (expect_first != nc || ((flags & CRAC_IMAGE_FULL) != 0) != (k == nc)) return CRAC_ERR_CORRUPT;

@@ -493,6 +493,11 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         im->allocs[a] = ImgAlloc{c->allocs[a].id, c->allocs[a].ptr, c->allocs[a].bytes, c->allocs[a].kind, first[a]};
     CK(cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming));
 
+    for (const AllocRec &r : c->allocs)   // host memory is read through its device mapping
+        if (r.kind == CRAC_KIND_HOST && !c->uva) {
+            cudaEventDestroy(im->done);
+            return CRAC_ERR_UNSUPPORTED;
+        }
     Arena &pa = pinned_arena();
     Arena &da = device_arena(c->device);
     crac_status_t st = CRAC_OK;
@@ -737,6 +742,8 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     *ms = 0;
     *k_out = 0;
     *d_out = 0;
+    for (const AllocRec &r : c->allocs)
+        if (r.kind == CRAC_KIND_HOST && !c->uva) return CRAC_ERR_UNSUPPORTED;
     c->last = crac_pass_info_t{};
     if (n == 0) return CRAC_OK;
     TRY(ensure_dev(c->fp[1 - c->fp_cur], n * 8));

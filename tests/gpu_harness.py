@@ -23,7 +23,11 @@ class Buf:
 
     def read(self) -> np.ndarray:
         if self.tensor is not None:
-            return self.tensor[: self.nbytes].cpu().numpy()
+            t = self.tensor[: self.nbytes]
+            if t.device.type == "cpu":     # pinned host memory: copy, do not alias it
+                torch.cuda.synchronize()
+                return t.numpy().copy()
+            return t.cpu().numpy()
         torch.cuda.synchronize()
         return np.frombuffer(ctypes.string_at(self.ptr, self.nbytes), dtype=np.uint8).copy()
 
@@ -56,6 +60,8 @@ class Harness:
             seed: int = 1) -> Buf:
         if kind == C.CRAC_KIND_DEVICE:
             b = Buf(nbytes, kind, tensor=torch.empty(nbytes, dtype=torch.uint8, device="cuda"))
+        elif kind == C.CRAC_KIND_HOST:    # page-locked host memory (cudaHostAlloc)
+            b = Buf(nbytes, kind, tensor=torch.empty(nbytes, dtype=torch.uint8, pin_memory=True))
         else:
             p = C.crac_alloc_managed(nbytes)
             self._managed.append(p)

@@ -76,6 +76,11 @@ def test_registry_host_logic(C):
         C.crac_ctx_register_alloc(ctx, base + 4096, 16, 5)
     assert e.value.code == C.CRAC_ERR_INVALID_ARG
     with pytest.raises(C.CracError) as e:
+        C.crac_ctx_register_alloc(ctx, base + 4096, 16, 3)
+    assert e.value.code == C.CRAC_ERR_INVALID_ARG
+    C.crac_ctx_register_alloc(ctx, base + 4096, 16, C.CRAC_KIND_HOST)   # page-locked host memory
+    C.crac_ctx_free(ctx, base + 4096)
+    with pytest.raises(C.CracError) as e:
         C.crac_ctx_free(ctx, base + 4096)
     assert e.value.code == C.CRAC_ERR_UNKNOWN_PTR
     C.crac_ctx_free(ctx, base)

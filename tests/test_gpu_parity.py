@@ -284,6 +284,40 @@ def test_sparse_kernel_with_per_allocation_launches():
         h.close()
 
 
+@pytest.mark.parametrize("kern,residency,flags", [
+    (C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_HOST, 0),
+    (C.CRAC_PASS_LDG, C.CRAC_RESIDENCY_DEVICE, C.CRAC_FLAG_INCREMENTAL_RESTORE),
+    (C.CRAC_PASS_TMA, C.CRAC_RESIDENCY_HOST, C.CRAC_FLAG_STAGED_RESTORE),
+    (C.CRAC_PASS_SPARSE, C.CRAC_RESIDENCY_DEVICE, 0),
+    (C.CRAC_PASS_SPLIT, C.CRAC_RESIDENCY_HOST, C.CRAC_FLAG_DIRECT_DRAIN | C.CRAC_FLAG_INCREMENTAL_RESTORE)])
+def test_host_kind_allocations(kern, residency, flags):
+    """Page-locked host allocations (CRAC_KIND_HOST) next to device and
+    managed ones: the pass hashes and gathers them through their device
+    mapping and the restore writes them back the same way."""
+    S = 4 * KIB
+    h = Harness(S, lineage=740 + kern, pass_kernel=kern, image_residency=residency, flags=flags)
+    try:
+        kinds = [C.CRAC_KIND_HOST, C.CRAC_KIND_DEVICE, C.CRAC_KIND_HOST, C.CRAC_KIND_MANAGED]
+        sizes = [S * 20, S * 7 + 32, 100000 // 16 * 16, S * 3]
+        for i, (n, k) in enumerate(zip(sizes, kinds)):
+            h.add(n, kind=k, seed=160 + i)
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        assert [a[3] for a in O.parse_image(lib1).allocs] == kinds
+        for seed, pattern in ((1, "random10"), (2, "alternating")):
+            h.mutate(pattern_mutations(h.first(), sizes, S, pattern, seed=seed))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
+
+
 @pytest.mark.parametrize("n_allocs", [3072, 3073])
 @pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
 def test_tma_many_allocations(n_allocs, residency):

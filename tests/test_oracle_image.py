@@ -194,6 +194,30 @@ def test_registry_errors():
     ctx.register(4096, 100)
 
 
+def test_allocation_kinds_are_recorded():
+    """Device, managed and page-locked host allocations (Sec. 3.2 lists
+    cudaMalloc, cudaMallocManaged and cudaMallocHost / cudaHostAlloc) are
+    saved alike; the image's allocation table records each one's kind, and
+    a restart into a registry whose kinds differ is refused."""
+    sizes = [100, 5000, 64]
+    kinds = [O.KIND_HOST, O.KIND_DEVICE, O.KIND_MANAGED]
+    ctx = O.OracleContext(4096, lineage=9)
+    for i, (n, k) in enumerate(zip(sizes, kinds)):
+        ctx.register((1 << 40) + i * 8192, n, k)
+    bufs = _mk(sizes)
+    raw = ctx.checkpoint(bufs)
+    img = O.parse_image(raw)
+    assert [a[3] for a in img.allocs] == kinds
+    assert bytes(img.payload) == b"".join(b.tobytes() for b in bufs)
+    other = O.OracleContext(4096, lineage=9)
+    for i, n in enumerate(sizes):
+        other.register((1 << 41) + i * 8192, n, O.KIND_DEVICE)
+    with pytest.raises(O.ImageMismatch):
+        other.restart([raw])
+    with pytest.raises(O.InvalidArg):
+        other.register(1 << 42, 16, 3)
+
+
 def test_offsets_and_counts_invariants():
     sizes = [123457, 4096, 65536 + 17]
     bufs = _mk(sizes, seed=21)
