@@ -295,13 +295,16 @@ def run_crac(args):
     # resident context of this run (their base images and the timed loop's
     # growing chain), so that no step allocates from CUDA.
     ctx_dev = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, reserve_device_bytes=16 * B)
-    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=3 * B, flags=restore_flags(args))
+    # The pinned arena is process-wide too: the reservation covers both host-
+    # image contexts' chains (the e2e leg's and the rollback leg's).
+    ctx_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, reserve_host_bytes=6 * B, flags=restore_flags(args))
     ctx_pa = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, launch_mode=C.CRAC_LAUNCH_PER_ALLOC)
     ctx_b = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE)
     ctx_ldg = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_LDG)
     ctx_tma = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_TMA)
     ctx_sparse = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, pass_kernel=C.CRAC_PASS_SPARSE)
     ctx_inc = make_ctx(image_residency=C.CRAC_RESIDENCY_DEVICE, flags=C.CRAC_FLAG_INCREMENTAL_RESTORE)
+    ctx_inc_host = make_ctx(image_residency=C.CRAC_RESIDENCY_HOST, flags=C.CRAC_FLAG_INCREMENTAL_RESTORE)
 
     def step(ctx, host=False, pass_ms=None, lat_ms=None, rst=None, phases=None):
         mutate()
@@ -327,7 +330,7 @@ def run_crac(args):
         return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms) for i in infos]
 
     # Base images (full) for each context.
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc, ctx_inc_host):
         img = C.crac_ctx_checkpoint(ctx, stream)
         C.crac_image_wait(img)
         C.crac_image_release(img)
@@ -423,23 +426,35 @@ def run_crac(args):
                "variants_device_ms": {k: v[0] for k, v in med.items()}}
 
     # ---- rollback: incremental restore of the last image after a 10% change ----
-    rb = []
-    nvtx.range_push("rollback")
-    for _ in range(max(3, min(args.steps, 5))):
-        mutate()
-        img = C.crac_ctx_checkpoint(ctx_inc, stream)
-        mutate()                                  # the state diverges from the image again
-        C.crac_ctx_restart(ctx_inc, img, stream)
-        rb.append(C.crac_ctx_last_restart(ctx_inc))
-        C.crac_image_release(img)
-    nvtx.range_pop()
-    rollback = {"device_ms": statistics.median(r["device_ms"] for r in rb),
+    def rollback_leg(ctx, host):
+        rb, wall = [], []
+        for _ in range(max(3, min(args.steps, 5))):
+            mutate()
+            img = C.crac_ctx_checkpoint(ctx, stream)
+            if host:
+                C.crac_image_wait(img)
+            mutate()                                  # the state diverges from the image again
+            t0 = time.perf_counter()
+            C.crac_ctx_restart(ctx, img, stream)
+            wall.append((time.perf_counter() - t0) * 1e3)
+            rb.append(C.crac_ctx_last_restart(ctx))
+            C.crac_image_release(img)
+        return {"device_ms": statistics.median(r["device_ms"] for r in rb),
+                "call_ms": statistics.median(wall),
                 "chunks_rewritten": statistics.median(r["chunks_rewritten"] for r in rb),
-                "chunks": n, "bytes_rewritten": statistics.median(r["restored_bytes"] for r in rb),
-                "full_restore_device_ms": statistics.median(r["device_ms"] for r in rst),
-                "how": "CRAC_FLAG_INCREMENTAL_RESTORE: fingerprint the current memory against the image, "
-                       "rewrite the chunks that differ (device-resident images)"}
+                "chunks": n, "bytes_rewritten": statistics.median(r["restored_bytes"] for r in rb)}
+
+    nvtx.range_push("rollback")
+    rollback = rollback_leg(ctx_inc, False)
+    rollback_host = rollback_leg(ctx_inc_host, True)
+    nvtx.range_pop()
+    rollback["full_restore_device_ms"] = statistics.median(r["device_ms"] for r in rst)
     rollback["speedup_vs_full"] = rollback["full_restore_device_ms"] / rollback["device_ms"]
+    rollback["host_images"] = rollback_host
+    rollback["how"] = ("CRAC_FLAG_INCREMENTAL_RESTORE: fingerprint the current memory against the image, "
+                       "rewrite the chunks that differ; device-resident images, and host-resident ones "
+                       "(host_images: only the differing chunks cross the host link; compare with the e2e "
+                       "restart_call of a full restore)")
 
     # ---- host link probe: pinned 1 GiB copies, best of 10 each way ------------
     link = None
@@ -468,6 +483,7 @@ def run_crac(args):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_pass, e_phase, e_rst = [], [], []
+        emem0 = C.crac_memory_stats()
         e0.record(stream)
         nvtx.range_push("e2e")
         for _ in range(e2e_steps):
@@ -477,6 +493,7 @@ def run_crac(args):
         torch.cuda.synchronize()
         barrier()
         te = e0.elapsed_time(e1)
+        emem1 = C.crac_memory_stats()
         e_pass = pass_rows(e_pass)
         k_e = statistics.mean(p[1] for p in e_pass)
         d_e = statistics.mean(p[2] for p in e_pass)
@@ -489,6 +506,8 @@ def run_crac(args):
         e2e = {"value": bytes_per_step * e2e_steps * world / (te / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "ms_per_step": te / e2e_steps, "link": link,
+               "arena_growth": {"host_grow_events": emem1["host_grow_events"] - emem0["host_grow_events"],
+                                "device_grow_events": emem1["device_grow_events"] - emem0["device_grow_events"]},
                "phases_ms": {"checkpoint_call": statistics.median(p[0] for p in e_phase),
                              "drain_wait": statistics.median(p[1] for p in e_phase),
                              "restart_call": statistics.median(p[2] for p in e_phase)}}
@@ -510,7 +529,7 @@ def run_crac(args):
                                    "single thread")
         cpu["nproc"] = os.cpu_count()
 
-    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc):
+    for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc, ctx_inc_host):
         C.crac_ctx_destroy(ctx)
 
     if rank == 0:
