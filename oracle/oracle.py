@@ -10,9 +10,10 @@ What it computes, in the paper's terms:
     made by the cudaMalloc family and not yet freed (Sec. 3.2, "Saving the
     library-allocated arena"), in the order they were allocated (Sec. 3.1,
     log-and-replay restores regions "in the same order as when they were
-    allocated").  Device (cudaMalloc) and unified (cudaMallocManaged)
-    regions are both saved (Sec. 3.2, "restoring the CUDA
-    library-allocated regions").
+    allocated").  Device (cudaMalloc), unified (cudaMallocManaged) and
+    page-locked host (cudaMallocHost / cudaHostAlloc) regions are all
+    saved (Sec. 3.2, "restoring the CUDA library-allocated regions"); the
+    kind is recorded with each allocation.
   * Restart copies the saved bytes back into the allocations (same
     subsection), after which the device state equals the checkpointed one.
   * Before the copy, pending device work is drained (Sec. 2.2, CheCUDA
