@@ -38,6 +38,9 @@ Image byte layout (all integers little-endian):
   u64 fp[n_chunks]          fingerprints of every chunk at this epoch
   u64 idx[k]                ascending global ids of the chunks present
   payload                   those chunks' bytes, concatenated, tails unpadded
+A coded image (flags bit1 CODED, chosen per context) stores each chunk as
+its CRZ1 stream (crz.py): u64 zlen[k] follows idx, and the payload is the
+streams in idx order, each zero-padded to a multiple of 16 bytes.
 """
 from __future__ import annotations
 
@@ -48,10 +51,13 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from oracle import crz
+
 MAGIC = b"CRACIMG1"
 VERSION = 1
 HASH_ID = 1
 FLAG_FULL = 1
+FLAG_CODED = 2
 NO_PARENT = (1 << 64) - 1
 KIND_DEVICE = 0
 KIND_MANAGED = 1
@@ -146,6 +152,7 @@ class Image:
     fp: np.ndarray
     idx: np.ndarray
     payload: memoryview
+    zlen: np.ndarray | None = None   # coded images: stream length of each chunk
 
     @property
     def full(self) -> bool:
@@ -154,6 +161,10 @@ class Image:
     @property
     def k(self) -> int:
         return int(self.idx.size)
+
+    @property
+    def coded(self) -> bool:
+        return bool(self.flags & FLAG_CODED)
 
 
 def parse_image(buf: bytes) -> Image:
@@ -164,7 +175,8 @@ def parse_image(buf: bytes) -> Image:
      payload_bytes) = HEADER.unpack_from(mv, 0)
     if magic != MAGIC or version != VERSION or hash_id != HASH_ID:
         raise Corrupt("bad magic/version/hash id")
-    need = HEADER.size + ALLOC.size * n_allocs + 8 * n_chunks + 8 * k + payload_bytes
+    coded = bool(flags & FLAG_CODED)
+    need = HEADER.size + ALLOC.size * n_allocs + 8 * n_chunks + 8 * k * (2 if coded else 1) + payload_bytes
     if len(mv) != need:
         raise Corrupt(f"size {len(mv)} != {need}")
     allocs = []
@@ -177,8 +189,12 @@ def parse_image(buf: bytes) -> Image:
     o += 8 * n_chunks
     idx = np.frombuffer(mv[o:o + 8 * k], dtype="<u8").astype(np.uint64)
     o += 8 * k
+    zlen = None
+    if coded:
+        zlen = np.frombuffer(mv[o:o + 8 * k], dtype="<u8").astype(np.uint64)
+        o += 8 * k
     return Image(flags, chunk, lineage, epoch, parent, allocs, n_chunks, fp, idx,
-                 mv[o:o + payload_bytes])
+                 mv[o:o + payload_bytes], zlen)
 
 
 def chunk_len(alloc_bytes: int, local: int, chunk_bytes: int) -> int:
@@ -200,10 +216,11 @@ class _Alloc:
 class OracleContext:
     """One simulated process: its active-allocation table and last fingerprints."""
 
-    def __init__(self, chunk_bytes: int, lineage: int = 1):
+    def __init__(self, chunk_bytes: int, lineage: int = 1, coded: bool = False):
         if chunk_bytes < 16 or chunk_bytes & (chunk_bytes - 1):
             raise InvalidArg("chunk_bytes must be a power of two >= 16")
         self.S = int(chunk_bytes)
+        self.coded = bool(coded)   # images store CRZ1 streams (crz.py)
         self.lineage = int(lineage)
         self.allocs: list[_Alloc] = []
         self.next_id = 0
@@ -267,10 +284,16 @@ class OracleContext:
             local = c - int(first[a])
             lo = local * S
             pieces.append(bufs[a][lo:lo + chunk_len(self.allocs[a].bytes, local, S)].tobytes())
-        # 5: payload = dirty chunk bytes in idx order.
+        # 5: payload = dirty chunk bytes in idx order (coded: their CRZ1
+        # streams, each zero-padded to 16 bytes).
+        zlen = None
+        if self.coded:
+            streams = [crz.encode(np.frombuffer(c, dtype=np.uint8)) for c in pieces]
+            zlen = np.array([len(z) for z in streams], dtype=np.uint64)
+            pieces = [z + bytes(crz.padded(len(z)) - len(z)) for z in streams]
         payload = b"".join(pieces)
         k = int(idx.size)
-        flags = FLAG_FULL if k == n else 0
+        flags = (FLAG_FULL if k == n else 0) | (FLAG_CODED if self.coded else 0)
         epoch = self.epoch + 1
         # 6: serialize.
         out = [HEADER.pack(MAGIC, VERSION, flags, S, HASH_ID, self.lineage, epoch,
@@ -279,6 +302,8 @@ class OracleContext:
             out.append(ALLOC.pack(a.id, a.ptr, a.bytes, a.kind, 0, int(first[i])))
         out.append(fp_new.astype("<u8").tobytes())
         out.append(idx.astype("<u8").tobytes())
+        if zlen is not None:
+            out.append(zlen.astype("<u8").tobytes())
         out.append(payload)
         # 7: commit the new baseline.
         self.fp_valid = {a.id: fp_new[int(first[i]):int(first[i + 1])].copy()
@@ -318,17 +343,27 @@ class OracleContext:
         for img in imgs:
             firsts = np.array([t[4] for t in img.allocs] + [img.n_chunks], dtype=np.int64)
             off = 0
-            for c in img.idx.tolist():
+            for e, c in enumerate(img.idx.tolist()):
                 a = int(np.searchsorted(firsts, c, side="right") - 1)
                 aid, _p, nbytes, _k, first = img.allocs[a]
                 local = c - first
                 ln = chunk_len(nbytes, local, S)
+                # coded: the stream's length, and the 16-byte padded step
+                zl = int(img.zlen[e]) if img.coded else ln
+                step = crz.padded(zl) if img.coded else ln
+                if off + step > len(img.payload):
+                    raise Corrupt("payload shorter than its chunk list")
                 pos = pos_of_id.get(aid)
                 if pos is not None:
-                    mem[pos][local * S:local * S + ln] = np.frombuffer(
-                        img.payload[off:off + ln], dtype=np.uint8)
+                    raw = img.payload[off:off + zl]
+                    if img.coded:
+                        try:
+                            raw = crz.decode(raw, ln)
+                        except crz.CodecError as err:
+                            raise Corrupt(str(err)) from err
+                    mem[pos][local * S:local * S + ln] = np.frombuffer(raw, dtype=np.uint8)
                     covered[pos][local] = True
-                off += ln
+                off += step
             if off != len(img.payload):
                 raise Corrupt("payload length does not match the chunk list")
         if not all(cv.all() for cv in covered):
