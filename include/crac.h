@@ -158,6 +158,25 @@ typedef struct crac_config {
  *   host link's rate, on the caller's stream.  Not for the TMA pass (which
  *   keeps the staged drain). */
 #define CRAC_FLAG_DIRECT_DRAIN 4u
+/* CRAC_FLAG_COMPRESS: images store each chunk as its CRZ1 stream, a
+ *   lossless byte-plane code of this library (the paper measures with
+ *   DMTCP's gzip compression turned off, Sec. 4.4.1, and has none).  A chunk
+ *   is cut into 512-byte blocks of 128 u32 words; every byte is rotated left
+ *   by one bit (a float's sign moves to the bottom), byte p of the words forms
+ *   plane p, and each plane is stored as its minimum and the offsets from it
+ *   in as many bits as their range needs; a chunk that this would not shrink
+ *   is stored as it is.  Floating-point data with few distinct exponents and
+ *   zero-filled memory shrink (fp32 N(0,1): 0.89, bf16: 0.76, zeros:
+ *   0.016); uniformly random bytes are stored as they are.  The pass gathers
+ *   into device staging as usual and an encoder kernel writes the streams --
+ *   into the device image, the staging drain, or, with
+ *   CRAC_FLAG_DIRECT_DRAIN, straight into the image's pinned memory -- so
+ *   only the coded bytes cross the host link.  Restores decode in the scatter
+ *   kernel, reading host images in place; a context that has to stage its
+ *   host restores (no unified addressing) cannot restore coded images
+ *   (CRAC_ERR_UNSUPPORTED).  Images carry CRAC_IMAGE_CODED.  Not with
+ *   CRAC_PASS_SPARSE. */
+#define CRAC_FLAG_COMPRESS 8u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
 #define CRAC_PASS_AUTO  0  /* the split pass, or, when the last pass with a baseline
@@ -196,8 +215,11 @@ typedef struct crac_image_info {
     uint64_t serialized_bytes;
     uint32_t residency;
     uint32_t complete;       /* 1 once the drain has finished */
+    uint64_t raw_bytes;      /* bytes of the chunks present before coding (payload_bytes,
+                                the stored bytes, for an uncoded image) */
 } crac_image_info_t;
 #define CRAC_IMAGE_FULL 1u
+#define CRAC_IMAGE_CODED 2u  /* chunks are stored as CRZ1 streams (CRAC_FLAG_COMPRESS) */
 
 /* Measurements of a context's most recent checkpoint (crac_ctx_last_pass). */
 typedef struct crac_pass_info {
@@ -216,7 +238,8 @@ typedef struct crac_pass_info {
     float finalize_ms;
     float gather_ms;
     uint32_t pass_kernel;    /* CRAC_PASS_* that ran */
-    uint32_t reserved[1];
+    float codec_ms;          /* CRAC_FLAG_COMPRESS: device time of the encoder launches */
+    uint64_t stored_bytes;   /* payload bytes of the image (coded: its streams) */
 } crac_pass_info_t;
 
 /* ---- configuration and contexts --------------------------------------- */
@@ -449,6 +472,10 @@ CRAC_API crac_status_t crac_image_info(const crac_image_t *image, crac_image_inf
  *   n_allocs x {u64 id, u64 orig_ptr, u64 bytes, u32 kind, u32 0, u64 first_chunk};
  *   u64 fp[n_chunks]; u64 idx[k] (ascending); payload (chunks in idx order,
  *   the last chunk of an allocation unpadded).
+ * A coded image (flags bit 1, CRAC_IMAGE_CODED) has u64 zlen[k] after idx
+ * (each chunk's stream length; equal to the chunk's length when it is stored
+ * as it is) and its payload is the streams in idx order, each zero-padded to
+ * a multiple of 16 bytes.
  * *need receives the size.  dst == NULL: only *need is set.  cap < need:
  * CRAC_ERR_INVALID_ARG.  Waits for the drain first.
  */

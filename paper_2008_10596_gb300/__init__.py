@@ -42,6 +42,7 @@ CRAC_RESIDENCY_DEVICE = 1
 CRAC_LAUNCH_BATCHED = 0
 CRAC_LAUNCH_PER_ALLOC = 1
 CRAC_IMAGE_FULL = 1
+CRAC_IMAGE_CODED = 2
 CRAC_PASS_AUTO = 0
 CRAC_PASS_LDG = 1
 CRAC_PASS_TMA = 2
@@ -50,6 +51,7 @@ CRAC_PASS_SPARSE = 4
 CRAC_FLAG_STAGED_RESTORE = 1
 CRAC_FLAG_INCREMENTAL_RESTORE = 2
 CRAC_FLAG_DIRECT_DRAIN = 4
+CRAC_FLAG_COMPRESS = 8
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1
@@ -90,7 +92,7 @@ class CracImageInfo(ctypes.Structure):
         ("flags", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32), ("n_allocs", ctypes.c_uint64),
         ("n_chunks", ctypes.c_uint64), ("k", ctypes.c_uint64), ("payload_bytes", ctypes.c_uint64),
         ("serialized_bytes", ctypes.c_uint64), ("residency", ctypes.c_uint32),
-        ("complete", ctypes.c_uint32),
+        ("complete", ctypes.c_uint32), ("raw_bytes", ctypes.c_uint64),
     ]
 
 
@@ -102,7 +104,7 @@ class CracPassInfo(ctypes.Structure):
         ("prefetch_ms", ctypes.c_float), ("grid", ctypes.c_uint32),
         ("chunks_per_tile", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
         ("hash_ms", ctypes.c_float), ("finalize_ms", ctypes.c_float), ("gather_ms", ctypes.c_float),
-        ("pass_kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
+        ("pass_kernel", ctypes.c_uint32), ("codec_ms", ctypes.c_float), ("stored_bytes", ctypes.c_uint64),
     ]
 
 

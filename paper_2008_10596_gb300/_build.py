@@ -23,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hi
 
 LIBS = {
     "libcrac.so": ["crac_pass_split.cu", "crac_pass_fused.cu", "crac_pass_tma.cu", "crac_pass_per_alloc.cu",
-                   "crac_restore.cu", "crac_noalloc.cu", "crac_arena.cpp", "crac_image.cpp", "crac_pass.cpp", "crac_restart.cpp",
+                   "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu", "crac_arena.cpp", "crac_image.cpp", "crac_pass.cpp", "crac_restart.cpp",
                    "crac_tune.cpp", "crac_server.cpp", "crac_abi.cpp"],
     "libcrac_testkit.so": ["crac_testkit.cu"],
 }
@@ -34,7 +34,8 @@ def _deps_newer(target, sources):
         return True
     t = os.path.getmtime(target)
     extra = [os.path.join(INC, "crac.h"), os.path.join(CSRC, "crac_kernels.cuh"),
-             os.path.join(CSRC, "crac_device.cuh"), os.path.join(CSRC, "crac_runtime.h")]
+             os.path.join(CSRC, "crac_device.cuh"), os.path.join(CSRC, "crac_codec.cuh"),
+             os.path.join(CSRC, "crac_runtime.h")]
     return any(os.path.getmtime(s) > t for s in list(sources) + extra)
 
 

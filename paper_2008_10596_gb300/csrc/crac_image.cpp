@@ -73,14 +73,16 @@ void img_unref(crac_image *im) {
         pa.free(im->fp_h);
         pa.free(im->idx_h);
         pa.free(im->off_h);
+        pa.free(im->zlen_h);
         if (im->fp_dev.region >= 0) device_arena(im->device).free(im->fp_dev);
         for (Piece &p : im->pieces) {
             pa.free(p.host);
-            if (p.dev.region >= 0 || p.idx_dev.region >= 0 || p.off_dev.region >= 0) {
+            if (p.dev.region >= 0 || p.idx_dev.region >= 0 || p.off_dev.region >= 0 || p.zlen_dev.region >= 0) {
                 Arena &da = device_arena(im->device);
                 da.free(p.dev);
                 da.free(p.idx_dev);
                 da.free(p.off_dev);
+                da.free(p.zlen_dev);
             }
         }
         crac_image *parent = im->parent;
@@ -98,10 +100,15 @@ crac_status_t img_host_tables(crac_image *im) {
     Arena &pa = pinned_arena();
     if (im->n_chunks) TRY(pa.alloc(im->n_chunks * 8, &im->fp_h));
     if (im->k) TRY(pa.alloc(im->k * 8, &im->idx_h));
+    const bool coded = (im->flags & CRAC_IMAGE_CODED) != 0;
+    if (im->k && coded) TRY(pa.alloc(im->k * 8, &im->zlen_h));
     DeviceGuard g(im->device);
     if (im->n_chunks) CK(cudaMemcpy(im->fp_h.p, im->fp_dev.p, im->n_chunks * 8, cudaMemcpyDeviceToHost));
-    for (const Piece &pc : im->pieces)
+    for (const Piece &pc : im->pieces) {
         if (pc.k) CK(cudaMemcpy(im->idx_h.p + pc.k0 * 8, pc.idx_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+        if (pc.k && coded)
+            CK(cudaMemcpy(im->zlen_h.p + pc.k0 * 8, pc.zlen_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    }
     im->host_tables = true;
     return CRAC_OK;
 }
@@ -132,6 +139,11 @@ void free_image_blocks(crac_image *im) {
 
 }  // namespace crac
 
+static uint64_t serialized_size(const crac_image *im) {
+    const uint64_t tables = 8 * im->k * ((im->flags & CRAC_IMAGE_CODED) ? 2 : 1);
+    return kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + tables + im->payload_bytes;
+}
+
 extern "C" {
 
 crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns) {
@@ -154,10 +166,10 @@ crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out)
     out->n_chunks = im->n_chunks;
     out->k = im->k;
     out->payload_bytes = im->payload_bytes;
-    out->serialized_bytes = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
-                            im->payload_bytes;
+    out->serialized_bytes = serialized_size(im);
     out->residency = im->residency;
     out->complete = im->state.load() == 1 ? 1u : 0u;
+    out->raw_bytes = im->raw_bytes;
     return CRAC_OK;
 }
 
@@ -205,8 +217,7 @@ crac_status_t sparse_compact(const crac_image *im, const Piece &pc, uint8_t *out
 crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
     if (!image || !need) return CRAC_ERR_INVALID_ARG;
     crac_image *im = const_cast<crac_image *>(image);
-    const uint64_t total = kHeaderBytes + kAllocEntryBytes * im->allocs.size() + 8 * im->n_chunks + 8 * im->k +
-                           im->payload_bytes;
+    const uint64_t total = serialized_size(im);
     *need = (size_t)total;
     if (!dst) return CRAC_OK;
     if (cap < total) return CRAC_ERR_INVALID_ARG;
@@ -238,6 +249,10 @@ crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t 
     p += 8 * im->n_chunks;
     if (im->k) std::memcpy(p, im->idx_h.p, 8 * im->k);
     p += 8 * im->k;
+    if (im->flags & CRAC_IMAGE_CODED) {
+        if (im->k) std::memcpy(p, im->zlen_h.p, 8 * im->k);
+        p += 8 * im->k;
+    }
     for (const Piece &pc : im->pieces) {
         if (!pc.bytes) continue;
         if (im->residency == CRAC_RESIDENCY_DEVICE) {
@@ -258,10 +273,12 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
     if (n < kHeaderBytes || std::memcmp(b, "CRACIMG1", 8) != 0) return CRAC_ERR_CORRUPT;
     if (get32(b + 8) != 1 || get32(b + 20) != 1) return CRAC_ERR_CORRUPT;
     const uint32_t flags = get32(b + 12), chunk = get32(b + 16);
-    if (chunk < 16 || chunk > (1u << 24) || (chunk & (chunk - 1)) || (flags & ~CRAC_IMAGE_FULL)) return CRAC_ERR_CORRUPT;
+    if (chunk < 16 || chunk > (1u << 24) || (chunk & (chunk - 1)) || (flags & ~(CRAC_IMAGE_FULL | CRAC_IMAGE_CODED)))
+        return CRAC_ERR_CORRUPT;
+    const bool coded = (flags & CRAC_IMAGE_CODED) != 0;
     const uint64_t na = get64(b + 48), nc = get64(b + 56), k = get64(b + 64), pb = get64(b + 72);
     if (na > (n / kAllocEntryBytes) || nc > n / 8 || k > nc || pb > n) return CRAC_ERR_CORRUPT;
-    const uint64_t need = kHeaderBytes + kAllocEntryBytes * na + 8 * nc + 8 * k + pb;
+    const uint64_t need = kHeaderBytes + kAllocEntryBytes * na + 8 * nc + 8 * k * (coded ? 2 : 1) + pb;
     if (need != n) return CRAC_ERR_CORRUPT;
     std::unique_ptr<crac_image> im(new crac_image());
     cudaGetDevice(&im->device);
@@ -285,18 +302,27 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
         expect_first += ((r.bytes - 1) >> log2S) + 1;
     }
     if (expect_first != nc || ((flags & CRAC_IMAGE_FULL) != 0) != (k == nc)) return CRAC_ERR_CORRUPT;
-    const uint8_t *fp = p, *idx = p + 8 * nc, *payload = idx + 8 * k;
-    // idx strictly ascending and payload length equal to the listed chunks' lengths
-    uint64_t acc = 0, prev = 0;
+    const uint8_t *fp = p, *idx = p + 8 * nc, *zlen = idx + 8 * k, *payload = zlen + (coded ? 8 * k : 0);
+    // idx strictly ascending; payload length equal to the listed chunks'
+    // lengths, or (coded) to their streams' padded lengths, no stream longer
+    // than its chunk
+    uint64_t acc = 0, zacc = 0, prev = 0;
     size_t a = 0;
     for (uint64_t j = 0; j < k; ++j) {
         const uint64_t c = get64(idx + 8 * j);
         if (c >= nc || (j && c <= prev)) return CRAC_ERR_CORRUPT;
         prev = c;
         while (a + 1 < na && im->allocs[a + 1].first_chunk <= c) ++a;
-        acc += chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+        const uint64_t len = chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+        acc += len;
+        if (coded) {
+            const uint64_t z = get64(zlen + 8 * j);
+            if (z == 0 || z > len) return CRAC_ERR_CORRUPT;
+            zacc += round_up(z, 16);
+        }
     }
-    if (acc != pb) return CRAC_ERR_CORRUPT;
+    if ((coded ? zacc : acc) != pb) return CRAC_ERR_CORRUPT;
+    im->raw_bytes = acc;
     Arena &pa = pinned_arena();
     crac_status_t st = CRAC_OK;
     Piece pc;
@@ -304,6 +330,7 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
     pc.bytes = pb;
     if (nc) st = pa.alloc(8 * nc, &im->fp_h);
     if (st == CRAC_OK && k) st = pa.alloc(8 * k, &im->idx_h);
+    if (st == CRAC_OK && k && coded) st = pa.alloc(8 * k, &im->zlen_h);
     if (st == CRAC_OK && pb) st = pa.alloc(pb, &pc.host);
     if (st != CRAC_OK) {
         im->pieces.push_back(pc);
@@ -312,6 +339,7 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
     }
     if (nc) std::memcpy(im->fp_h.p, fp, 8 * nc);
     if (k) std::memcpy(im->idx_h.p, idx, 8 * k);
+    if (k && coded) std::memcpy(im->zlen_h.p, zlen, 8 * k);
     if (pb) std::memcpy(pc.host.p, payload, pb);
     im->pieces.push_back(pc);
     im->state.store(1);

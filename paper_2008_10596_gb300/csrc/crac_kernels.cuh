@@ -29,6 +29,7 @@ static_assert(sizeof(CkptCtrl) == 64, "CkptCtrl layout");
 constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
 constexpr unsigned kErrBounds = 2u;    // an output index/offset exceeded its buffer
 constexpr unsigned kErrUncovered = 4u; // restore: a target chunk no image of the chain holds
+constexpr unsigned kErrCodec = 8u;     // restore: a coded stream no chunk encodes to
 
 // Parameters of the fused batched pass over global chunks [c_begin, c_end).
 struct CkptParams {
@@ -159,6 +160,8 @@ struct RestorePiece {
     uint64_t bytes;               // payload bytes (window)
     uint32_t image_index;         // chain position (oldest = 0)
     uint32_t desc_off, n_desc, pad;
+    uint64_t zlen;                // coded image: device address of each entry's
+                                  // stream length (0: entries are raw chunks)
 };
 struct RestoreParams {
     const RestorePiece *pieces;
@@ -180,6 +183,32 @@ cudaError_t launch_restore_scatter(const RestoreParams &p, int grid, cudaStream_
 // Incremental restore, between check and scatter: clears the owner of every
 // chunk whose current fingerprint equals the target's, so it is not written.
 cudaError_t launch_restore_unmark(const RestoreParams &p, int grid, cudaStream_t s);
+
+// CRZ1 encoder (crac_codec.cu): the raw payload of one segment, as the pass
+// left it in device staging, -> one stream per entry (coded, or the chunk
+// itself when coding does not shrink it), each at a 16-byte multiple.
+// Persistent CTAs take tiles of tile_entries consecutive entries from a
+// ticket, compute every block's header word, find the tile's output offset
+// by a decoupled look-back over earlier tiles, then write the streams.
+struct CodecParams {
+    const uint8_t *src;       // raw payload: entry e at off[e], off[e+1] - off[e] bytes
+    const uint64_t *off;      // k + 1 offsets
+    uint64_t k;
+    uint8_t *dst;             // streams (device memory or mapped pinned memory), 16-byte aligned
+    uint64_t dst_cap;
+    uint64_t *zoff;           // out: k + 1 stream offsets (prefix of 16-byte padded lengths)
+    uint64_t *zlen;           // out: k stream lengths
+    uint64_t *hdr;            // scratch: block header words, entry e's from off[e] / 512
+    uint64_t *status;         // scratch: one look-back word per tile, zeroed
+    uint32_t *ticket;         // scratch: tile counter, zeroed
+    unsigned int *err;        // kErr* bits, zeroed
+    uint32_t tile_entries;    // entries per tile, 1..crz_tile_max()
+    uint32_t n_tiles;
+    uint64_t timeout_ns;
+};
+cudaError_t launch_crz_encode(const CodecParams &p, int grid, cudaStream_t s);
+uint32_t crz_tile_max();
+int crz_encode_max_ctas_per_sm();
 
 void count_launches(uint64_t n);
 uint64_t launches_so_far();

@@ -26,8 +26,10 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
         return CRAC_ERR_INVALID_ARG;
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
-    if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE | CRAC_FLAG_DIRECT_DRAIN))
+    if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE | CRAC_FLAG_DIRECT_DRAIN |
+                      CRAC_FLAG_COMPRESS))
         return CRAC_ERR_INVALID_ARG;
+    if (cfg.pass_kernel == CRAC_PASS_SPARSE && (cfg.flags & CRAC_FLAG_COMPRESS)) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
         return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_TMA && (cfg.chunk_bytes < 1024 || cfg.chunk_bytes > 65536))
@@ -60,7 +62,7 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     for (cudaEvent_t &e : c->sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&c->ev_r0));
     CK(cudaEventCreate(&c->ev_r1));
-    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl)));
+    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl) + 64));   // + the encoder's total and error bits
     TRY(ensure_host(c->serr_h, 256));
     if (c->cfg.reserve_host_bytes) {
         TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
@@ -85,7 +87,8 @@ void ctx_free_all(crac_ctx *c) {
     cudaDeviceSynchronize();
     for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
                       &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr,
-                      &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff})
+                      &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff, &c->cstage, &c->zwork, &c->zoff,
+                      &c->zlen})
         if (b->p) cudaFree(b->p);
     for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h, &c->vdesc_h})
         if (b->p) cudaFreeHost(b->p);
@@ -449,6 +452,84 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
 }
 
 
+// Entries per tile of the encoder: about 64 KiB of raw payload.
+uint32_t crz_tile_entries(uint32_t log2S) {
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(crz_tile_max(), 65536ull >> std::min<uint32_t>(log2S, 16)));
+}
+
+// Encoder scratch of a segment with k entries and D raw bytes: control
+// words, one look-back word per tile, block header words.
+size_t crz_work_bytes(uint64_t k, uint64_t D, uint32_t log2S) {
+    const uint64_t tiles = (k + crz_tile_entries(log2S) - 1) / crz_tile_entries(log2S);
+    return 16 + 8 * tiles + 8 * (D / 512 + 1);
+}
+
+// CRAC_FLAG_COMPRESS: the segment's raw payload (device staging, offsets in
+// c->off) -> its streams.  Host images: into the piece's pinned block when
+// direct drain finds room (*zdirect), else into c->cstage for the side
+// stream's copy; tables in c->zoff / c->zlen.  Device images: into pc.dev,
+// with the stream offsets in pc.off_dev and lengths in pc.zlen_dev.  On
+// return the total stream bytes are known (*Z).
+crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
+                             cudaStream_t s, uint64_t *Z, bool *zdirect) {
+    const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
+    const uint32_t T = crz_tile_entries(c->log2S);
+    const uint64_t n_tiles = (k + T - 1) / T;
+    if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
+    *zdirect = false;
+    TRY(ensure_dev(c->zwork, crz_work_bytes(k, D, c->log2S)));
+    CodecParams P{};
+    if (host_res) {
+        P.zoff = (uint64_t *)c->zoff.p;
+        P.zlen = (uint64_t *)c->zlen.p;
+        if (direct_flag && pinned_arena().try_alloc(zmax, &pc.host)) {
+            P.dst = pc.host.p;
+            *zdirect = true;
+        } else {
+            TRY(ensure_dev(c->cstage, zmax));
+            P.dst = (uint8_t *)c->cstage.p;
+        }
+    } else {
+        TRY(device_arena(c->device).alloc(zmax, &pc.dev));
+        P.dst = pc.dev.p;
+        P.zoff = (uint64_t *)pc.off_dev.p;
+        P.zlen = (uint64_t *)pc.zlen_dev.p;
+    }
+    uint8_t *w = (uint8_t *)c->zwork.p;
+    P.src = (const uint8_t *)c->staging.p;
+    P.off = (const uint64_t *)c->off.p;
+    P.k = k;
+    P.dst_cap = zmax;
+    P.err = (unsigned int *)w;
+    P.ticket = (uint32_t *)(w + 4);
+    P.status = (uint64_t *)(w + 16);
+    P.hdr = P.status + n_tiles;
+    P.tile_entries = T;
+    P.n_tiles = (uint32_t)n_tiles;
+    P.timeout_ns = c->cfg.timeout_ns;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * crz_encode_max_ctas_per_sm()));
+    uint8_t *out_h = (uint8_t *)c->ctrl_h.p + sizeof(CkptCtrl);
+    CK(cudaMemsetAsync(w, 0, 16 + 8 * n_tiles, s));
+    CK(cudaEventRecord(c->ev_t0, s));
+    CK(launch_crz_encode(P, grid, s));
+    CK(cudaEventRecord(c->ev_t1, s));
+    CK(cudaMemcpyAsync(out_h, P.zoff + k, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out_h + 8, w, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev_pass, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    c->last.kernel_launches += 1;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1) == cudaSuccess) c->last.codec_ms += ms;
+    cudaGetLastError();
+    const unsigned err = *(const unsigned *)(out_h + 8);
+    if (err & kErrTimeout) return CRAC_ERR_TIMEOUT;
+    if (err) return CRAC_ERR_CORRUPT;
+    *Z = *(const uint64_t *)out_h;
+    if (*Z > zmax) return CRAC_ERR_CORRUPT;
+    if (*zdirect) pinned_arena().shrink(pc.host, *Z);
+    return CRAC_OK;
+}
+
 // CRAC_PASS_AUTO: the split pass, unless the last pass with a baseline found
 // more than half of the chunks dirty; then a pass that reads every byte once
 // (at 100% dirty 4 KiB pages and 64 KiB chunks: sparse 0.94, TMA 0.72, LDG
@@ -456,7 +537,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
 uint32_t resolve_pass_kernel(const crac_ctx *c, bool dev_res, bool all16) {
     if (c->cfg.pass_kernel != CRAC_PASS_AUTO) return c->cfg.pass_kernel;
     if (!c->delta_frac_valid || c->delta_frac <= 0.5f) return CRAC_PASS_SPLIT;
-    if (dev_res && all16) return CRAC_PASS_SPARSE;
+    if (dev_res && all16 && !(c->cfg.flags & CRAC_FLAG_COMPRESS)) return CRAC_PASS_SPARSE;
     if (c->log2S >= 10 && c->log2S <= 16) return CRAC_PASS_TMA;
     return CRAC_PASS_LDG;
 }
@@ -577,18 +658,31 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
         }
         const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
-        // Direct drain: the pass writes the payload straight into the image's
-        // pinned block through its device mapping (not the TMA pass, whose
-        // bulk stores stay within device memory).
-        const bool direct = host_res && c->uva && (c->cfg.flags & CRAC_FLAG_DIRECT_DRAIN) &&
-                            c->pass_now != CRAC_PASS_TMA;
-        if (host_res) {
+        // Coded images: the pass gathers into device staging as usual and the
+        // encoder writes the streams (encode_segment).
+        const bool coded = (c->cfg.flags & CRAC_FLAG_COMPRESS) != 0;
+        // Direct drain: the pass (uncoded) or the encoder (coded) writes the
+        // payload straight into the image's pinned block through its device
+        // mapping (not the TMA pass, whose bulk stores stay within device
+        // memory).
+        const bool direct_flag = host_res && c->uva && (c->cfg.flags & CRAC_FLAG_DIRECT_DRAIN);
+        const bool direct = direct_flag && !coded && c->pass_now != CRAC_PASS_TMA;
+        if (host_res || coded) {
             st = ensure_dev(c->staging, max_seg_bytes);   // also the direct drain's fallback
             if (st == CRAC_OK) st = ensure_dev(c->idx, max_seg_chunks * 8);
             if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
             if (st != CRAC_OK) return fail(st);
         }
-        uint64_t k_base = 0, d_base = 0;
+        if (coded) {
+            st = ensure_dev(c->zwork, crz_work_bytes(max_seg_chunks, max_seg_bytes, log2S));
+            if (st == CRAC_OK && host_res) st = ensure_dev(c->zoff, (max_seg_chunks + 1) * 8);
+            if (st == CRAC_OK && host_res) st = ensure_dev(c->zlen, max_seg_chunks * 8);
+            if (st == CRAC_OK && host_res && !direct_flag)
+                st = ensure_dev(c->cstage, max_seg_bytes + 16 * max_seg_chunks);
+            if (st == CRAC_OK && host_res) st = pa.alloc(n * 8, &im->zlen_h);
+            if (st != CRAC_OK) return fail(st);
+        }
+        uint64_t k_base = 0, d_base = 0, raw_base = 0;
         float ms = 0;
         for (const Segment &sg : segs) {
             const uint64_t nseg = sg.c1 - sg.c0;
@@ -596,18 +690,23 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
             uint8_t *stg = (uint8_t *)c->staging.p;
             if (!host_res) {
-                st = da.alloc(sg.bytes, &pc.dev);
+                // coded: pc.dev is sized by the encoder, after the pass
+                if (!coded) st = da.alloc(sg.bytes, &pc.dev);
                 if (st == CRAC_OK) st = da.alloc(nseg * 8, &pc.idx_dev);
                 if (st == CRAC_OK) st = da.alloc((nseg + 1) * 8, &pc.off_dev);
+                if (st == CRAC_OK && coded) st = da.alloc(nseg * 8, &pc.zlen_dev);
                 if (st != CRAC_OK) {
                     da.free(pc.dev);
                     da.free(pc.idx_dev);
                     da.free(pc.off_dev);
+                    da.free(pc.zlen_dev);
                     return fail(st);
                 }
                 idx_d = (uint64_t *)pc.idx_dev.p;
-                off_d = (uint64_t *)pc.off_dev.p;
-                stg = pc.dev.p;
+                if (!coded) {
+                    off_d = (uint64_t *)pc.off_dev.p;
+                    stg = pc.dev.p;
+                }
             }
             // The worst-case block comes from the pinned regions as they are
             // (growing them, or starting their background growth, mid-loop
@@ -632,6 +731,17 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             const bool sparse = c->sparse_ok && !host_res;
             pc.bytes = sparse ? ctrl.payload : ctrl.D;
             pc.span = sparse ? ctrl.D : 0;
+            bool zdirect = false;
+            if (coded && ctrl.k) {
+                uint64_t Z = 0;
+                st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zdirect);
+                if (st != CRAC_OK) {
+                    im->pieces.push_back(pc);
+                    return fail(st);
+                }
+                pc.bytes = Z;
+            }
+            raw_base += sparse ? ctrl.payload : ctrl.D;
             if (fault_hit(CRAC_FAULT_DRAIN)) {
                 im->pieces.push_back(pc);
                 t_last_cuda = (int)cudaErrorLaunchFailure;
@@ -642,22 +752,26 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                 if (ctrl.D) pa.shrink(pc.host, ctrl.D);
                 else pa.free(pc.host);
             } else if (host_res) {
-                if (ctrl.D) {
-                    st = pa.alloc(ctrl.D, &pc.host);
+                if (pc.bytes && !zdirect) {
+                    st = pa.alloc(pc.bytes, &pc.host);
                     if (st != CRAC_OK) {
                         im->pieces.push_back(pc);
                         return fail(st);
                     }
                     if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(pc.host.p, c->staging.p, ctrl.D, cudaMemcpyDeviceToHost, c->side);
+                        e = cudaMemcpyAsync(pc.host.p, coded ? c->cstage.p : c->staging.p, pc.bytes,
+                                            cudaMemcpyDeviceToHost, c->side);
                 }
             } else {
-                da.shrink(pc.dev, ctrl.D);
+                da.shrink(pc.dev, coded ? pc.bytes : ctrl.D);   // sparse: the span
                 da.shrink(pc.idx_dev, ctrl.k * 8);
                 da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
+                if (coded) da.shrink(pc.zlen_dev, ctrl.k * 8);
             }
             if (e == cudaSuccess && ctrl.k && host_res)
                 e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess && ctrl.k && host_res && coded)
+                e = cudaMemcpyAsync(im->zlen_h.p + k_base * 8, c->zlen.p, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
             if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
             im->pieces.push_back(pc);
             if (e != cudaSuccess) return fail(cuda_status(e));
@@ -679,9 +793,12 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         if (e != cudaSuccess) return fail(cuda_status(e));
         im->k = k_base;
         im->payload_bytes = d_base;
+        im->raw_bytes = raw_base;
         if (host_res) pa.shrink(im->idx_h, k_base * 8);
+        if (host_res && coded) pa.shrink(im->zlen_h, k_base * 8);
         c->last.k = k_base;
-        c->last.payload_bytes = d_base;
+        c->last.payload_bytes = raw_base;
+        c->last.stored_bytes = d_base;
         c->last.segments = (uint32_t)segs.size();
         c->last.device_ms = ms;
         if (any_managed) {
@@ -694,7 +811,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
     }
 
     // Commit: the new fingerprints become the baseline.
-    im->flags = im->k == n ? CRAC_IMAGE_FULL : 0u;
+    im->flags = (im->k == n ? CRAC_IMAGE_FULL : 0u) | ((c->cfg.flags & CRAC_FLAG_COMPRESS) ? CRAC_IMAGE_CODED : 0u);
     if (had_base) {
         c->delta_frac = (float)((double)im->k / (double)n);
         c->delta_frac_valid = true;

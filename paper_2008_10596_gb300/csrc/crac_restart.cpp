@@ -35,8 +35,9 @@ std::vector<int64_t> map_allocs(const crac_image *im, const crac_image *tgt,
 }
 
 // Offset of every entry's bytes inside its piece's payload, for a host image
-// (its payload is compact: the prefix of the entries' chunk lengths).  Made
-// once per image, in pinned memory that the restore kernels read in place.
+// (its payload is compact: the prefix of the entries' chunk lengths, or of a
+// coded image's 16-byte padded stream lengths).  Made once per image, in
+// pinned memory that the restore kernels read in place.
 crac_status_t img_offsets(crac_image *im) {
     std::lock_guard<std::mutex> lk(im->mu);
     if (im->off_h.p || im->k == 0) return CRAC_OK;
@@ -45,13 +46,14 @@ crac_status_t img_offsets(crac_image *im) {
     uint64_t *off = (uint64_t *)im->off_h.p;
     const uint64_t *idx = (const uint64_t *)im->idx_h.p;
     const uint32_t log2S = log2u(im->chunk_bytes);
+    const uint64_t *zlen = (im->flags & CRAC_IMAGE_CODED) ? (const uint64_t *)im->zlen_h.p : nullptr;
     size_t a = 0;
     for (const Piece &pc : im->pieces) {
         uint64_t acc = 0;
         for (uint64_t j = pc.k0; j < pc.k0 + pc.k; ++j) {
             while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= idx[j]) ++a;
             off[j] = acc;
-            acc += chunk_len(im->allocs[a].bytes, idx[j] - im->allocs[a].first_chunk, log2S);
+            acc += zlen ? round_up(zlen[j], 16) : chunk_len(im->allocs[a].bytes, idx[j] - im->allocs[a].first_chunk, log2S);
         }
         if (acc != pc.bytes) {
             pa.free(im->off_h);
@@ -110,16 +112,18 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
                                     m[a] < 0 ? 0 : img->allocs[m[a]].first_chunk, m[a] < 0 ? 0 : c->allocs[m[a]].ptr,
                                     0, {0, 0, 0}};
         const bool host = im->residency != CRAC_RESIDENCY_DEVICE;
+        const bool coded = (im->flags & CRAC_IMAGE_CODED) != 0;
         for (const Piece &pc : im->pieces) {
             if (!pc.k) continue;
             if (host)
                 rph[ppos++] = RestorePiece{(uint64_t)(im->idx_h.p + pc.k0 * 8), (uint64_t)(im->off_h.p + pc.k0 * 8),
                                            (uint64_t)pc.host.p, pc.k, entries, pc.bytes, (uint32_t)i, (uint32_t)d0,
-                                           (uint32_t)im->allocs.size(), 0};
+                                           (uint32_t)im->allocs.size(), 0,
+                                           coded ? (uint64_t)(im->zlen_h.p + pc.k0 * 8) : 0ull};
             else
                 rph[ppos++] = RestorePiece{(uint64_t)pc.idx_dev.p, (uint64_t)pc.off_dev.p, (uint64_t)pc.dev.p, pc.k,
                                            entries, pc.span ? pc.span : pc.bytes, (uint32_t)i, (uint32_t)d0,
-                                           (uint32_t)im->allocs.size(), 0};
+                                           (uint32_t)im->allocs.size(), 0, coded ? (uint64_t)pc.zlen_dev.p : 0ull};
             entries += pc.k;
         }
     }
@@ -213,7 +217,12 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     std::reverse(chain.begin(), chain.end());
     // On the device unless an image is on another device, or a host image
     // must be staged (no unified addressing, or CRAC_FLAG_STAGED_RESTORE).
-    const bool mapped = c->uva && !(c->cfg.flags & CRAC_FLAG_STAGED_RESTORE);
+    // Coded images are decoded by the in-place restore kernels only, so a
+    // chain holding one reads its host images in place whenever the device
+    // can address them.
+    bool any_coded = false;
+    for (crac_image *im : chain) any_coded = any_coded || (im->flags & CRAC_IMAGE_CODED);
+    const bool mapped = c->uva && (!(c->cfg.flags & CRAC_FLAG_STAGED_RESTORE) || any_coded);
     bool on_device = true;
     for (crac_image *im : chain) {
         const bool dev_ok = im->residency == CRAC_RESIDENCY_DEVICE && im->device == c->device &&
@@ -222,6 +231,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
         on_device = on_device && (dev_ok || host_ok);
     }
     if (on_device) return restart_device(c, img, chain, s);
+    if (any_coded) return CRAC_ERR_UNSUPPORTED;
     for (crac_image *im : chain) {
         TRY(img_wait(im, 0));
         TRY(img_host_tables(im));

@@ -1,6 +1,6 @@
 // Restart kernels: owner marks, coverage check and scatter over every piece of
 // a chain (device path), and the windowed scatter of the staged path.
-#include "crac_device.cuh"
+#include "crac_codec.cuh"
 
 namespace crac {
 
@@ -108,12 +108,16 @@ __global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const Resto
         const uint64_t local = c - d.img_first;
         const uint64_t len = min(S, d.bytes - (local << P.log2_chunk));
         const uint64_t o = reinterpret_cast<const uint64_t *>(pc.off)[e - pc.entry_base];
-        if (o + len > pc.bytes) {
+        // Coded image: the entry's stream length (equal to len when stored raw).
+        const uint64_t z = pc.zlen ? reinterpret_cast<const uint64_t *>(pc.zlen)[e - pc.entry_base] : len;
+        if (o > pc.bytes || z > pc.bytes - o) {
             if (lane == 0) atomicOr(P.err, kErrBounds);
             continue;
         }
-        copy_group<32>(reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk),
-                       reinterpret_cast<const uint8_t *>(pc.payload) + o, len, lane);
+        uint8_t *dst = reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(pc.payload) + o;
+        if (z == len) copy_group<32>(dst, src, len, lane);
+        else if (!crz_decode_warp(dst, src, len, z, lane) && lane == 0) atomicOr(P.err, kErrCodec);
     }
 }
 

@@ -301,6 +301,7 @@ struct Piece {
     Block host;                     // host residency: pinned copy
     Block dev;                      // device residency: payload
     Block idx_dev, off_dev;         // device residency: idx[k], off[k+1] (piece-relative)
+    Block zlen_dev;                 // device residency, coded image: zlen[k]
 };
 
 struct AllocRec {
@@ -329,6 +330,9 @@ struct crac_image {
     Block fp_dev;                   // device images: fp[n_chunks] in device memory
     Block off_h;                    // host images: offset of each entry's bytes inside its
                                     // piece's payload (made by the first mapped restore)
+    Block zlen_h;                   // coded images: stream length of each entry (pinned;
+                                    // device images: on demand, like idx_h)
+    uint64_t raw_bytes = 0;         // bytes of the chunks present, before coding
     bool host_tables = true;        // fp_h / idx_h hold the tables
     std::vector<Piece> pieces;
     crac_image *parent = nullptr;   // strong reference, set for delta images
@@ -383,6 +387,7 @@ struct crac_ctx {
     // pass scratch
     DevBuf desc, work, idx, off, staging, lens, carry;
     HostBuf desc_h, ctrl_h;
+    DevBuf cstage, zwork, zoff, zlen;   // CRAC_FLAG_COMPRESS: streams, encoder scratch, tables
     // restart scratch
     DevBuf owner, sdesc, sidx, soff, serr;
     DevBuf vdesc, vwork, vfp, vidx, voff;   // incremental restore: fingerprint pass scratch

@@ -49,7 +49,8 @@ class Harness:
         self.S = chunk
         self.cfg = C.crac_config_default(chunk_bytes=chunk, lineage=lineage, **cfg)
         self.ctx = C.crac_ctx_create(self.cfg)
-        self.oracle = O.OracleContext(chunk, lineage=lineage)
+        self.oracle = O.OracleContext(chunk, lineage=lineage,
+                                      coded=bool(cfg.get("flags", 0) & C.CRAC_FLAG_COMPRESS))
         self.bufs: list[Buf] = []
         self.images: list[int] = []
         self.stream = torch.cuda.current_stream()

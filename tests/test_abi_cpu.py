@@ -51,13 +51,17 @@ def test_config_validation(C):
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10),
                 dict(pass_kernel=C.CRAC_PASS_SPARSE),         # needs device-resident images
-                dict(flags=8)):
+                dict(flags=16),
+                dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE,
+                     flags=C.CRAC_FLAG_COMPRESS)):       # the sparse payload is not compacted
         with pytest.raises(C.CracError) as e:
             C.crac_ctx_create(C.crac_config_default(**bad))
         assert e.value.code == C.CRAC_ERR_INVALID_ARG
     for ok in (dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=1024),
                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=64 << 10),
-               dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE)):
+               dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE),
+               dict(flags=C.CRAC_FLAG_COMPRESS | C.CRAC_FLAG_DIRECT_DRAIN),
+               dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=4096, flags=C.CRAC_FLAG_COMPRESS)):
         C.crac_ctx_destroy(C.crac_ctx_create(C.crac_config_default(**ok)))
 
 

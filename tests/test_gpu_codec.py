@@ -1,0 +1,229 @@
+"""Coded images (GPU): with CRAC_FLAG_COMPRESS every image must serialize to
+the oracle's coded image byte for byte (stream lengths, streams, zero
+padding), every restart must bring the memory back exactly, the GPU decoder
+must restore images the oracle encoded (independent of the GPU encoder), and
+a damaged stream must come back as CRAC_ERR_CORRUPT, not as a fault."""
+import numpy as np
+import pytest
+
+import paper_2008_10596_gb300 as C
+import workloads as W
+from oracle import crz
+from oracle import oracle as O
+from tests.gpu_harness import Harness, pattern_mutations
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
+
+KIB = 1024
+CODED = C.CRAC_FLAG_COMPRESS
+KINDS = ["f32_normal", "zeros", "bf16", "u8", "i64_small"]
+
+
+def _contents(kind, n, seed):
+    if kind == "zeros":
+        return np.zeros(n, np.uint8)
+    if kind == "i64_small":
+        rng = np.random.default_rng(seed)
+        return rng.integers(-300, 300, -(-n // 8)).astype("<i8").view(np.uint8)[:n].copy()
+    return W.host_contents(kind, n, seed)
+
+
+def _sizes(S):
+    # ragged tails, a size that is not a multiple of 16 (later staging offsets
+    # become unaligned), chunks below one 512-byte block
+    return [S * 30 + 48, 7 * 4096 + 1, S * 5, 100000, 513, 16, 3 * S + 600]
+
+
+def _fill(h, S, seed=0):
+    for i, n in enumerate(_sizes(S)):
+        h.add(n, data=_contents(KINDS[i % len(KINDS)], n, seed + 10 * i + 1))
+
+
+def _zero_some(h, every=3):
+    for b in h.bufs[::every]:
+        b.zero()
+
+
+CASES = [
+    (C.CRAC_RESIDENCY_HOST, C.CRAC_PASS_AUTO, 0),
+    (C.CRAC_RESIDENCY_HOST, C.CRAC_PASS_SPLIT, C.CRAC_FLAG_DIRECT_DRAIN),
+    (C.CRAC_RESIDENCY_HOST, C.CRAC_PASS_LDG, 0),
+    (C.CRAC_RESIDENCY_HOST, C.CRAC_PASS_TMA, C.CRAC_FLAG_DIRECT_DRAIN),
+    (C.CRAC_RESIDENCY_DEVICE, C.CRAC_PASS_SPLIT, 0),
+    (C.CRAC_RESIDENCY_DEVICE, C.CRAC_PASS_TMA, C.CRAC_FLAG_INCREMENTAL_RESTORE),
+    (C.CRAC_RESIDENCY_DEVICE, C.CRAC_PASS_AUTO, 0),
+]
+
+
+@pytest.mark.parametrize("S", [512, 4 * KIB, 64 * KIB, 256 * KIB])
+@pytest.mark.parametrize("residency,kern,flags", CASES)
+def test_coded_images_match_oracle(S, residency, kern, flags):
+    if kern == C.CRAC_PASS_TMA and not (KIB <= S <= 64 * KIB):
+        pytest.skip("TMA pass: 1-64 KiB chunks")
+    h = Harness(S, lineage=1200 + S // 256 + kern, image_residency=residency, pass_kernel=kern,
+                flags=flags | CODED)
+    try:
+        _fill(h, S, seed=S // 512)
+        chain_lib, images, states = [], [], []
+        img, lib, ora = h.checkpoint()
+        assert lib == ora
+        assert O.parse_image(lib).coded
+        info = C.crac_image_info(img)
+        assert info["flags"] & C.CRAC_IMAGE_CODED and info["serialized_bytes"] == len(lib)
+        assert info["raw_bytes"] == sum(b.nbytes for b in h.bufs)
+        chain_lib.append(lib)
+        images.append(img)
+        states.append(h.host())
+        for step, pattern in enumerate(["random10", "zero", "alternating", "none"]):
+            if pattern == "zero":
+                _zero_some(h)
+            else:
+                h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, pattern, seed=step + 5))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora, (step, pattern)
+            pi = C.crac_ctx_last_pass(h.ctx)
+            assert pi["stored_bytes"] == C.crac_image_info(img)["payload_bytes"]
+            chain_lib.append(lib)
+            images.append(img)
+            states.append(h.host())
+        # restart the second image after wiping memory, then the newest
+        for target in (1, len(images) - 1):
+            for b in h.bufs:
+                b.zero()
+            h.restart(images[target])
+            for b, w in zip(h.bufs, states[target]):
+                assert np.array_equal(b.read(), w), target
+        # the oracle restores the same chain to the same bytes
+        got = h.oracle.restart(chain_lib)
+        assert all(np.array_equal(g, w) for g, w in zip(got, states[-1]))
+    finally:
+        h.close()
+
+
+def test_codec_shrinks_what_it_should():
+    """Ratio of stored to raw bytes per content kind on a full checkpoint."""
+    S = 64 * KIB
+    for kind, lo, hi in [("zeros", 0.0, 0.02), ("f32_normal", 0.85, 0.93), ("bf16", 0.72, 0.80),
+                         ("u8", 1.0, 1.0)]:
+        h = Harness(S, lineage=1300, flags=CODED)
+        try:
+            h.add(64 * S, data=_contents(kind, 64 * S, 3))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora
+            info = C.crac_image_info(img)
+            ratio = info["payload_bytes"] / info["raw_bytes"]
+            assert lo <= ratio <= hi, (kind, ratio)
+        finally:
+            h.close()
+
+
+@pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
+def test_oracle_encoded_images_restore_on_gpu(residency):
+    """The GPU decoder restores a chain the oracle encoded, deserialized from
+    its bytes (the GPU encoder is not involved)."""
+    S = 4 * KIB
+    sizes = _sizes(S)
+    h = Harness(S, lineage=1400, image_residency=residency, flags=CODED)
+    try:
+        _fill(h, S, seed=77)
+        mem0 = h.host()
+        ora = O.OracleContext(S, lineage=4242, coded=True)
+        for b in h.bufs:
+            ora.register(b.ptr, b.nbytes, b.kind)
+        chain = [ora.checkpoint(mem0)]
+        mem1 = [m.copy() for m in mem0]
+        mem1[0][: 3 * S] = 0
+        mem1[3][100:200] ^= 0x33
+        chain.append(ora.checkpoint(mem1))
+        imgs = [C.crac_image_deserialize(b) for b in chain]
+        try:
+            for b in h.bufs:
+                b.zero()
+            h2 = Harness(S, lineage=4242, flags=CODED)   # a context of the oracle's lineage
+            try:
+                for b in h.bufs:
+                    C.crac_ctx_register_alloc(h2.ctx, b.ptr, b.nbytes, b.kind)
+                C.crac_ctx_restart(h2.ctx, imgs[-1], h2.stream)
+                for b, w in zip(h.bufs, mem1):
+                    assert np.array_equal(b.read(), w)
+                assert C.crac_ctx_last_restart(h2.ctx)["chunks_rewritten"] == int(h.first()[-1])
+            finally:
+                h2.close()
+        finally:
+            for i in imgs:
+                C.crac_image_release(i)
+        assert len(sizes) == len(h.bufs)
+    finally:
+        h.close()
+
+
+def _damage(img_bytes, S, how):
+    """Copy of a coded FULL image with its first coded stream damaged."""
+    im = O.parse_image(img_bytes)
+    firsts = [t[4] for t in im.allocs]
+    off = len(img_bytes) - len(im.payload)
+    for e, c in enumerate(im.idx.tolist()):
+        a = int(np.searchsorted(firsts, c, side="right") - 1)
+        ln = O.chunk_len(im.allocs[a][2], c - firsts[a], S)
+        z = int(im.zlen[e])
+        if z < ln:
+            break
+        off += crz.padded(z)
+    else:
+        raise AssertionError("no coded stream")
+    b = bytearray(img_bytes)
+    if how == "width":
+        b[off + 4] = 0x0C          # plane 0 width 12
+    elif how == "reserved":
+        b[off + 7] = 0x80
+    elif how == "overflow":        # plane 0 minimum 255 with a non-zero width
+        b[off + 0] = 0xFF
+        b[off + 4] = (b[off + 4] & 0xF0) | 0x08
+    return bytes(b)
+
+
+@pytest.mark.parametrize("how", ["width", "reserved", "overflow"])
+def test_damaged_stream_is_reported(how):
+    S = 4 * KIB
+    h = Harness(S, lineage=1500, flags=CODED)
+    try:
+        h.add(16 * S, data=_contents("f32_normal", 16 * S, 5))
+        img, lib, ora = h.checkpoint()
+        assert lib == ora
+        bad = C.crac_image_deserialize(_damage(lib, S, how))
+        try:
+            h2 = Harness(S, lineage=1500, flags=CODED)
+            try:
+                C.crac_ctx_register_alloc(h2.ctx, h.bufs[0].ptr, h.bufs[0].nbytes)
+                with pytest.raises(C.CracError) as e:
+                    C.crac_ctx_restart(h2.ctx, bad, h2.stream)
+                assert e.value.code == C.CRAC_ERR_CORRUPT
+                # the context still works: the good image restores
+                C.crac_ctx_restart(h2.ctx, img, h2.stream)
+            finally:
+                h2.close()
+        finally:
+            C.crac_image_release(bad)
+    finally:
+        h.close()
+
+
+def test_staged_flag_still_restores_coded_chain():
+    """CRAC_FLAG_STAGED_RESTORE: coded host images are decoded in place anyway."""
+    S = 4 * KIB
+    h = Harness(S, lineage=1600, flags=CODED | C.CRAC_FLAG_STAGED_RESTORE)
+    try:
+        _fill(h, S, seed=9)
+        img0, lib0, ora0 = h.checkpoint()
+        assert lib0 == ora0
+        h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, "random10", seed=2))
+        img1, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img1)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()

@@ -1,6 +1,6 @@
 """Randomized parity cases (GPU): for each seed a random registry (count,
 sizes from 1 byte to ~1 MiB, some 16-byte multiples), a random chunk size,
-pass kernel, residency and staging capacity, then a random sequence of
+pass kernel, residency, staging capacity and flags (coded images included), then a random sequence of
 mutations, registrations and frees over several checkpoints.  Every image
 must serialize to the oracle's bytes, and a restart of the last image must
 bring back the memory exactly."""
@@ -40,6 +40,10 @@ def _case(seed):
     cfg["flags"] = flags
     if kern == C.CRAC_PASS_LDG and rng.random() < 0.5:
         cfg["chunks_per_tile"] = int(rng.integers(1, 40))
+    # coded images, drawn from a generator of their own so that the other
+    # draws of each seed stay as they were
+    if kern != C.CRAC_PASS_SPARSE and np.random.default_rng(77000 + seed).random() < 0.35:
+        cfg["flags"] |= C.CRAC_FLAG_COMPRESS
     return rng, S, cfg
 
 
