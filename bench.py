@@ -824,6 +824,145 @@ def run_passes(args):
     return 0
 
 
+def run_codec(args):
+    """Coded images (CRAC_FLAG_COMPRESS) against plain ones on the config-2
+    layout (256 allocations, 4 GiB, 64 KiB chunks, the same 10% hot set),
+    filled in turn with fp32 N(0,1) (config 2's contents), bf16 N(0,1)
+    (config 3's rewritten pages), zeros and uniform bytes.  Per content and
+    image kind: a full checkpoint, delta checkpoints after the 10% XOR
+    mutation, and a restart of the resulting chain; calls are timed on the
+    wall clock including the drain wait, and the library's CUDA-event times
+    of the pass, encoder and restore kernels are reported beside them."""
+    import torch
+    import torch.cuda.nvtx as nvtx
+    import paper_2008_10596_gb300 as C
+    from paper_2008_10596_gb300 import testkit
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = W.config2(total=args.total_mib << 20)
+    S, sizes = wl.chunk_bytes, wl.sizes
+    B = wl.total_bytes
+    first = W.chunk_layout(sizes, S)
+    n = int(first[-1])
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_src = load_peaks()
+    g = torch.Generator(device=dev)
+    bufs = [torch.empty(s, dtype=torch.uint8, device=dev) for s in sizes]
+
+    def fill(kind):
+        g.manual_seed(wl.seed)
+        for b in bufs:
+            s = b.numel()
+            if kind == "f32_normal":
+                b.copy_(torch.randn((s + 3) // 4, generator=g, device=dev).view(torch.uint8)[:s])
+            elif kind == "bf16_normal":
+                b.copy_(torch.randn((s + 1) // 2, generator=g, device=dev).to(torch.bfloat16).view(torch.uint8)[:s])
+            elif kind == "zeros":
+                b.zero_()
+            else:
+                b.copy_(torch.randint(0, 256, (s,), generator=g, device=dev, dtype=torch.uint8))
+        torch.cuda.synchronize()
+
+    muts = W.choose_mutations(wl.seed, n, wl.dirty_fraction)
+    ent = np.zeros((len(muts), 3), dtype=np.uint64)
+    for i, m in enumerate(muts):
+        a = int(np.searchsorted(first, m.chunk, side="right") - 1)
+        lo = (m.chunk - int(first[a])) * S
+        ent[i] = (bufs[a].data_ptr() + lo, min(S, sizes[a] - lo), m.mask)
+    ent_dev = torch.from_numpy(ent.view(np.int64)).to(dev)
+
+    variants = {
+        "host": dict(image_residency=C.CRAC_RESIDENCY_HOST),
+        "host_coded": dict(image_residency=C.CRAC_RESIDENCY_HOST, flags=C.CRAC_FLAG_COMPRESS),
+        "host_coded_direct": dict(image_residency=C.CRAC_RESIDENCY_HOST,
+                                  flags=C.CRAC_FLAG_COMPRESS | C.CRAC_FLAG_DIRECT_DRAIN),
+        "device": dict(image_residency=C.CRAC_RESIDENCY_DEVICE),
+        "device_coded": dict(image_residency=C.CRAC_RESIDENCY_DEVICE, flags=C.CRAC_FLAG_COMPRESS),
+    }
+    reserve = dict(reserve_host_bytes=3 * B, reserve_device_bytes=3 * B)
+    steps = max(3, min(args.steps, 5))
+    sampler = ClockSampler(None)
+    sampler.start()
+    launches0 = C.crac_kernel_launches()
+    rows = []
+    enc = []   # encoder launches into device memory: (raw bytes, stored bytes, entries, ms)
+    for kind in ("f32_normal", "bf16_normal", "zeros", "u8_uniform"):
+        fill(kind)
+        for name, cfg in variants.items():
+            ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3000, device=0, **cfg, **reserve))
+            reserve = {}
+            for b in bufs:
+                C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
+            host = cfg["image_residency"] == C.CRAC_RESIDENCY_HOST
+            imgs, full, deltas = [], None, []
+            for r in range(steps + 1):
+                if r:
+                    testkit.mutate_xor(ent_dev.data_ptr(), len(muts), stream)
+                torch.cuda.synchronize()
+                nvtx.range_push(f"codec_{name}")
+                t0 = time.perf_counter()
+                img = C.crac_ctx_checkpoint(ctx, stream)
+                C.crac_image_wait(img)
+                wall = (time.perf_counter() - t0) * 1e3
+                nvtx.range_pop()
+                imgs.append(img)
+                pi = C.crac_ctx_last_pass(ctx)
+                rec = {"wall_ms": wall, "device_ms": pi["device_ms"], "codec_ms": pi["codec_ms"],
+                       "raw_bytes": pi["payload_bytes"], "stored_bytes": pi["stored_bytes"], "k": pi["k"]}
+                if r == 0:
+                    full = rec
+                else:
+                    deltas.append(rec)
+                if pi["codec_ms"] > 0 and name != "host_coded_direct":
+                    enc.append((kind, r == 0, pi["payload_bytes"], pi["stored_bytes"], pi["k"], pi["codec_ms"]))
+            want = [bufs[i][:4096].clone() for i in (0, len(bufs) // 2, len(bufs) - 1)]
+            for b in bufs[::17]:
+                b.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C.crac_ctx_restart(ctx, imgs[-1], stream)
+            torch.cuda.synchronize()
+            rwall = (time.perf_counter() - t0) * 1e3
+            ri = C.crac_ctx_last_restart(ctx)
+            ok = all(torch.equal(bufs[i][:4096], w) for i, w in zip((0, len(bufs) // 2, len(bufs) - 1), want))
+            for img in imgs:
+                C.crac_image_release(img)
+            C.crac_ctx_destroy(ctx)
+            med = lambda key: statistics.median(d[key] for d in deltas)   # noqa: E731
+            rows.append({
+                "content": kind, "images": name,
+                "full": dict(full, ratio=full["stored_bytes"] / full["raw_bytes"]),
+                "delta": {"wall_ms": med("wall_ms"), "device_ms": med("device_ms"), "codec_ms": med("codec_ms"),
+                          "raw_bytes": med("raw_bytes"), "stored_bytes": med("stored_bytes"),
+                          "ratio": med("stored_bytes") / med("raw_bytes")},
+                "restart": {"wall_ms": rwall, "device_ms": ri["device_ms"], "chain_length": ri["chain_length"],
+                            "tracked_gbs": B / (rwall / 1e3) / 1e9, "sampled_restore_ok": ok}})
+    launches = C.crac_kernel_launches() - launches0
+    clocks = sampler.stop()
+    # The encoder's roofline: it reads the raw payload from staging once from
+    # HBM (its second read hits L2) and writes the streams, plus 16 B of
+    # stream offset and length per entry: alg = D + Z + 16 k per launch.
+    full_f32 = [e for e in enc if e[0] == "f32_normal" and e[1]]
+    kind, _, D, Z, k, ms = full_f32[0]
+    alg = D + Z + 16 * k
+    roofline = {"bound": "hbm", "kernel": "crz_encode_kernel (full checkpoint, fp32 N(0,1), device images)",
+                "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": profile_traffic("crz_encode_c2_f32"),
+                "alg_bytes_per_launch": int(alg), "avg_launch_ms": ms, "raw_gbs": D / (ms / 1e3) / 1e9,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
+    encoder = [{"content": e[0], "checkpoint": "full" if e[1] else "delta", "raw_bytes": e[2],
+                "stored_bytes": e[3], "k": e[4], "ms": e[5], "raw_gbs": e[2] / (e[5] / 1e3) / 1e9,
+                "hbm_frac": (e[2] + e[3] + 16 * e[4]) / (e[5] / 1e3) / 1e9 / peak} for e in enc]
+    line = {"workload": "codec: c2 layout (256 allocs = 4 GiB, 64 KiB chunks, 10% hot set), contents "
+                        "fp32 N(0,1) / bf16 N(0,1) / zeros / uniform bytes; plain vs CRZ1-coded images",
+            "tracked_bytes": B, "n_chunks": n, "steps": steps, "roofline": roofline, "rows": rows,
+            "encoder_launches": encoder, "gpu_launches": launches, "clocks": clocks,
+            "note": "wall_ms includes the drain wait; delta rows are medians over the steps; the restart "
+                    "restores the chain of 1 full + steps deltas after zeroing every 17th allocation"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # Config 5: serving loop over 64 simulated process contexts
 # ---------------------------------------------------------------------------
@@ -997,7 +1136,7 @@ def main():
                     help="tracked bytes of the config-2 workload (default 4096 = the full config)")
     ap.add_argument("--requests", type=int, default=1200, help="c5: requests in the serving loop")
     ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes", "codec"],
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--staged-restore", action="store_true",
                     help="c2 e2e, c3, c5: restore host images through staging (copy engine) instead of in place")
@@ -1021,6 +1160,8 @@ def main():
         return run_config5(args)
     if args.workload == "passes":
         return run_passes(args)
+    if args.workload == "codec":
+        return run_codec(args)
     return run_crac(args)
 
 

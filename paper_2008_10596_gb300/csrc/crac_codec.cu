@@ -8,7 +8,7 @@ namespace {
 
 constexpr int kCodecNT = 256;
 constexpr int kCodecWarps = kCodecNT / 32;
-constexpr uint32_t kCodecTileMax = kCodecNT;   // one entry per thread in the tile bookkeeping
+constexpr uint32_t kCodecTileMax = 128;   // entries per tile (a 64 KiB tile of 512-byte chunks)
 
 // Exclusive prefix over the CTA of one value per thread, and the total.
 // Every thread calls it; s_warp holds kCodecWarps values.
@@ -68,31 +68,123 @@ __device__ uint64_t lookback1(uint64_t *status, uint32_t tile, int lane, uint64_
     }
 }
 
-__global__ void __launch_bounds__(kCodecNT) crz_encode_kernel(const CodecParams P) {
+// ---- shared-memory staging of the raw payload --------------------------
+// A tile's raw bytes (at most one 64 KiB window; a chunk above 64 KiB is
+// taken window by window) are brought into shared memory by one bulk async
+// copy completing on an mbarrier, so both passes over them (headers, then
+// units) read shared memory and the staging buffer is read from HBM once.
+constexpr uint32_t kWin = 65536;
+constexpr uint32_t kWinBlocks = kWin / 512;
+constexpr size_t kEncSmem = kWin + 32 + 16;   // window (+ alignment slack), mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the mbarrier phase `par`; false if it does not complete
+// within the time limit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t par, uint64_t timeout_ns) {
+    if (mbar_try(bar, par)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, par)) return true;
+        if ((i & 63u) == 0 && (globaltimer() - t0 > timeout_ns || i > (1u << 28))) return false;
+    }
+}
+
+// Staging bytes [wa, wb) -> shared memory (whole CTA, after every thread is
+// done with the previous window).  *sb receives where byte wa landed.
+// Returns false on every thread if the copy did not complete in time: then
+// kErrTimeout is set, the copy has been waited for once more (bounded), and
+// the CTA must stop.
+__device__ bool load_window(const CodecParams &P, uint8_t *sdata, uint64_t *bar, uint32_t *phase, uint64_t wa,
+                            uint64_t wb, const uint8_t **sb) {
+    const uint64_t a0 = wa & ~15ull, a1 = (wb + 15) & ~15ull;   // 16-byte aligned, inside the staging slack
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                     "r"((uint32_t)(a1 - a0))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(sdata)),
+            "l"(P.src + a0), "r"((uint32_t)(a1 - a0)), "r"(smem_addr(bar))
+            : "memory");
+    }
+    const uint32_t par = *phase;
+    *phase ^= 1u;
+    const bool ok = mbar_wait_bounded(bar, par, P.timeout_ns);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(P.err, kErrTimeout);
+            mbar_wait_bounded(bar, par, P.timeout_ns);   // the copy may still land in this CTA's memory
+        }
+        __syncthreads();
+        return false;
+    }
+    *sb = sdata + (wa - a0);
+    return true;
+}
+
+// 16 bytes at p (generic, any alignment) to a 16-byte aligned q.
+__device__ __forceinline__ void copy_bytes_cta(uint8_t *q, const uint8_t *p, uint64_t len, int tid) {
+    const uint64_t nv = len >> 4;
+    for (uint64_t v = tid; v < nv; v += kCodecNT) *reinterpret_cast<uint4 *>(q + 16 * v) = load16_any(p + 16 * v);
+    for (uint64_t i = 16 * nv + tid; i < len; i += kCodecNT) q[i] = p[i];
+}
+
+__global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecParams P) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    uint8_t *sdata = dsm;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(dsm + kWin + 32);
     __shared__ uint32_t s_tile, s_skip;
     __shared__ uint32_t s_nbp[kCodecTileMax + 1];    // tile-local prefix of block counts
     __shared__ uint32_t s_wsum[kCodecTileMax];       // per entry: sum of its blocks' widths
     __shared__ uint32_t s_z[kCodecTileMax];          // per entry: stream length
     __shared__ uint64_t s_zpre[kCodecTileMax + 1];   // tile-local prefix of padded stream lengths
     __shared__ uint64_t s_base;                      // the tile's output offset
-    __shared__ uint32_t s_boff[kCodecNT];            // units before each block of a batch
+    __shared__ uint32_t s_boff[kWinBlocks];          // prefix of unit counts over a window's blocks
+    __shared__ __align__(16) uint8_t s_units[kCodecWarps][512];   // per warp: a block's units
+    __shared__ uint64_t s_off[kCodecTileMax + 1];    // the tile's entry offsets in staging
+    __shared__ uint64_t s_hdr[kWinBlocks];           // header words of the window's blocks
     __shared__ uint32_t s_w32[kCodecWarps];
     __shared__ uint64_t s_w64[kCodecWarps];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const CrzLane LT = crz_lane(lane);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;
     for (;;) {
-        __syncthreads();   // the previous tile's shared state is consumed
+        __syncthreads();   // the previous tile's shared state (and window) is consumed
         if (tid == 0) s_tile = atomicAdd(P.ticket, 1u);
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= P.n_tiles) return;
         const uint64_t e0 = (uint64_t)tile * P.tile_entries;
         const uint32_t ne = (uint32_t)umin64(P.tile_entries, P.k - e0);   // 1 .. kCodecTileMax
+        const uint64_t r0 = P.off[e0], r1 = P.off[e0 + ne];
+        // One window, or (a single chunk above 64 KiB) several.
+        const uint32_t n_win = r1 - r0 <= kWin ? 1u : (uint32_t)((r1 - r0 + kWin - 1) / kWin);
 
         // Entry lengths and block counts.
         uint64_t L_t = 0;
         uint32_t nb_t = 0;
         if ((uint32_t)tid < ne) {
-            L_t = P.off[e0 + tid + 1] - P.off[e0 + tid];
+            const uint64_t a = P.off[e0 + tid], b = P.off[e0 + tid + 1];
+            s_off[tid] = a;
+            if ((uint32_t)tid == ne - 1) s_off[ne] = b;
+            L_t = b - a;
             nb_t = (uint32_t)(L_t >> 9);
             s_wsum[tid] = 0;
         }
@@ -102,25 +194,38 @@ __global__ void __launch_bounds__(kCodecNT) crz_encode_kernel(const CodecParams 
         if (tid == 0) s_nbp[ne] = nb_all;
         __syncthreads();
 
-        // Phase 1: the header word of every block of the tile (a warp per block).
-        for (uint32_t fb = warp; fb < nb_all; fb += kCodecWarps) {
-            uint32_t lo = 0, hi = ne;   // last entry whose first block is <= fb
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_nbp[mid] <= fb) lo = mid;
-                else hi = mid;
+        // Phase 1: every block's header word, from shared memory.
+        bool dead = false;
+        for (uint32_t w = 0; w < n_win; ++w) {
+            const uint64_t wa = r0 + (uint64_t)w * kWin, wb = umin64(r1, wa + kWin);
+            const uint8_t *sb = nullptr;
+            if (!load_window(P, sdata, bar, &phase, wa, wb, &sb)) {
+                dead = true;   // uniform across the CTA
+                break;
             }
-            const uint32_t b = fb - s_nbp[lo];
-            const uint64_t o = P.off[e0 + lo];
-            const uint4 w = load16_any(P.src + o + 512ull * b + 16u * lane);
-            const uint32_t r[4] = {crz_rot(w.x), crz_rot(w.y), crz_rot(w.z), crz_rot(w.w)};
-            const uint64_t h = crz_block_header(r);
-            if (lane == 0) {
-                P.hdr[(o >> 9) + b] = h;
-                atomicAdd(&s_wsum[lo], crz_width_sum(h));
+            // blocks of this window, as tile-flattened ids [f0, f1)
+            const uint32_t f0 = n_win == 1 ? 0u : w * kWinBlocks;
+            const uint32_t f1 = n_win == 1 ? nb_all : (uint32_t)umin64(nb_all, (uint64_t)(w + 1) * kWinBlocks);
+            for (uint32_t fb = f0 + warp; fb < f1; fb += kCodecWarps) {
+                uint32_t lo = 0, hi = ne;   // last entry whose first block is <= fb
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_nbp[mid] <= fb) lo = mid;
+                    else hi = mid;
+                }
+                const uint32_t b = fb - s_nbp[lo];
+                const uint64_t o = s_off[lo];
+                const uint4 v = load16_any(sb + (o - wa) + 512ull * b + 16u * lane);
+                const uint32_t r[4] = {crz_rot(v.x), crz_rot(v.y), crz_rot(v.z), crz_rot(v.w)};
+                const uint64_t h = crz_block_header(r);
+                if (lane == 0) {
+                    s_hdr[fb - f0] = h;
+                    if (n_win > 1) P.hdr[(o >> 9) + b] = h;   // for the second pass over the windows
+                    atomicAdd(&s_wsum[lo], crz_width_sum(h));
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
 
         // Stream lengths: coded when that is shorter, else the chunk itself.
         uint64_t pz = 0;
@@ -157,45 +262,98 @@ __global__ void __launch_bounds__(kCodecNT) crz_encode_kernel(const CodecParams 
         const uint64_t base = s_base;
         if ((uint32_t)tid < ne) P.zoff[e0 + tid] = base + s_zpre[tid];
         if (tid == 0 && e0 + ne == P.k) P.zoff[P.k] = base + tile_bytes;
+        if (dead) return;   // a copy that never completed: this CTA stops (error reported)
         if (s_skip) continue;
 
-        // Phase 2: each entry's stream, entry by entry with the whole CTA.
-        for (uint32_t t = 0; t < ne; ++t) {
-            const uint64_t o = P.off[e0 + t];
-            const uint64_t L = P.off[e0 + t + 1] - o;
-            const uint64_t z = s_z[t];
-            const uint64_t zpad = (z + 15) & ~15ull;
+        // Phase 2: headers and padding of every coded entry, then the units
+        // and raw bytes window by window.
+        for (uint32_t fb = tid; fb < nb_all; fb += kCodecNT) {
+            uint32_t lo = 0, hi = ne;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_nbp[mid] <= fb) lo = mid;
+                else hi = mid;
+            }
+            const uint64_t o = s_off[lo], L = s_off[lo + 1] - o;
+            if (s_z[lo] == L) continue;   // raw entry
+            const uint32_t b = fb - s_nbp[lo];
+            reinterpret_cast<uint64_t *>(P.dst + base + s_zpre[lo])[b] = n_win == 1 ? s_hdr[fb] : P.hdr[(o >> 9) + b];
+        }
+        for (uint32_t t = tid; t < ne; t += kCodecNT) {
+            const uint64_t L = s_off[t + 1] - s_off[t], z = s_z[t];
             uint8_t *d = P.dst + base + s_zpre[t];
-            const uint8_t *sp = P.src + o;
-            if (z == L) {
-                copy_group<kCodecNT>(d, sp, L, tid);
-                for (uint64_t i = L + tid; i < zpad; i += kCodecNT) d[i] = 0;
-                continue;
-            }
-            const uint64_t nb = L >> 9, head = crz_head_bytes(nb);
-            const uint64_t *hb = P.hdr + (o >> 9);
-            uint64_t *dh = reinterpret_cast<uint64_t *>(d);
-            for (uint64_t b = tid; b < nb; b += kCodecNT) dh[b] = hb[b];
-            if ((nb & 1) && tid == 0) dh[nb] = 0;
-            uint32_t carry = 0;   // units of the blocks before this batch
-            for (uint64_t B = 0; B < nb; B += kCodecNT) {
-                const uint32_t ws = B + tid < nb ? crz_width_sum(hb[B + tid]) : 0u;
-                uint32_t batch_units;
-                s_boff[tid] = carry + cta_excl_scan<uint32_t>(ws, s_w32, &batch_units);
+            const uint32_t nb = s_nbp[t + 1] - s_nbp[t];
+            if (z != L && (nb & 1)) reinterpret_cast<uint64_t *>(d)[nb] = 0;   // header pad
+            for (uint64_t i = z; i < ((z + 15) & ~15ull); ++i) d[i] = 0;            // stream pad
+        }
+        uint32_t carry = 0;   // multi-window chunk: units of the earlier windows' blocks
+        for (uint32_t w = 0; w < n_win; ++w) {
+            const uint64_t wa = r0 + (uint64_t)w * kWin, wb = umin64(r1, wa + kWin);
+            const uint8_t *sb = sdata + (wa & 15u);
+            const uint32_t f0 = n_win == 1 ? 0u : w * kWinBlocks;
+            const uint32_t f1 = n_win == 1 ? nb_all : (uint32_t)umin64(nb_all, (uint64_t)(w + 1) * kWinBlocks);
+            if (n_win > 1) {
+                __syncthreads();   // every thread is done with the previous window
+                if (!load_window(P, sdata, bar, &phase, wa, wb, &sb)) return;   // uniform; error reported
+                // one entry: its header words of this window, back from global scratch
+                if (f0 + tid < f1) s_hdr[tid] = P.hdr[(s_off[0] >> 9) + f0 + tid];
                 __syncthreads();
-                const uint32_t nbatch = (uint32_t)umin64(kCodecNT, nb - B);
-                for (uint32_t bb = warp; bb < nbatch; bb += kCodecWarps) {
-                    const uint64_t blk = B + bb;
-                    const uint4 w = load16_any(sp + 512ull * blk + 16u * lane);
-                    const uint32_t r[4] = {crz_rot(w.x), crz_rot(w.y), crz_rot(w.z), crz_rot(w.w)};
-                    crz_block_units(hb[blk], r, d + head + 16ull * s_boff[bb], lane);
-                }
-                carry += batch_units;
-                __syncthreads();   // s_boff is rewritten by the next batch
             }
-            const uint64_t tl = L & 511u, tail_at = head + 16ull * carry;
-            for (uint64_t i = tid; i < tl; i += kCodecNT) d[tail_at + i] = sp[512ull * nb + i];
-            for (uint64_t i = z + tid; i < zpad; i += kCodecNT) d[i] = 0;
+            // unit offsets: prefix of the blocks' unit counts over the window
+            uint32_t wcount = 0;
+            {
+                uint32_t v = 0;
+                if (f0 + tid < f1) {
+                    const uint32_t fb = f0 + tid;
+                    uint32_t lo = 0, hi = ne;
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (s_nbp[mid] <= fb) lo = mid;
+                        else hi = mid;
+                    }
+                    v = crz_width_sum(s_hdr[fb - f0]);
+                }
+                const uint32_t ex = cta_excl_scan<uint32_t>(v, s_w32, &wcount);
+                if ((uint32_t)tid < kWinBlocks) s_boff[tid] = ex;
+            }
+            __syncthreads();
+            for (uint32_t fb = f0 + warp; fb < f1; fb += kCodecWarps) {
+                uint32_t lo = 0, hi = ne;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_nbp[mid] <= fb) lo = mid;
+                    else hi = mid;
+                }
+                const uint64_t o = s_off[lo], L = s_off[lo + 1] - o;
+                if (s_z[lo] == L) continue;   // raw entry: copied below
+                const uint32_t b = fb - s_nbp[lo];
+                // units before this block within its entry
+                const uint32_t before = n_win == 1 ? s_boff[fb] - s_boff[s_nbp[lo]] : carry + s_boff[fb - f0];
+                const uint4 v = load16_any(sb + (o - wa) + 512ull * b + 16u * lane);
+                const uint32_t r[4] = {crz_rot(v.x), crz_rot(v.y), crz_rot(v.z), crz_rot(v.w)};
+                uint32_t pw[4];
+                crz_bytes_transpose(r, pw);
+                uint8_t *d = P.dst + base + s_zpre[lo] + crz_head_bytes(L >> 9) + 16ull * before;
+                crz_block_units(s_hdr[fb - f0], pw, d, lane, LT, s_units[warp]);
+            }
+            carry += wcount;
+            // raw entries, and the tails of coded ones, where they overlap the window
+            for (uint32_t t = 0; t < ne; ++t) {
+                const uint64_t o = s_off[t], L = s_off[t + 1] - o;
+                uint8_t *d = P.dst + base + s_zpre[t];
+                uint64_t lo_b, hi_b, to;   // entry bytes [lo_b, hi_b) go to d + to + (x - lo_b)
+                if (s_z[t] == L) {
+                    lo_b = 0;
+                    hi_b = L;
+                    to = 0;
+                } else {
+                    lo_b = L & ~511ull;
+                    hi_b = L;
+                    to = s_z[t] - (L & 511u);
+                }
+                const uint64_t x0 = o + lo_b > wa ? o + lo_b : wa, x1 = umin64(o + hi_b, wb);
+                if (x1 > x0) copy_bytes_cta(d + to + (x0 - o - lo_b), sb + (x0 - wa), x1 - x0, tid);
+            }
         }
     }
 }
@@ -209,7 +367,9 @@ int crz_encode_max_ctas_per_sm() {
     static std::once_flag once;
     std::call_once(once, [] {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, crz_encode_kernel, kCodecNT, 0) != cudaSuccess)
+        if (cudaFuncSetAttribute(crz_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEncSmem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, crz_encode_kernel, kCodecNT, kEncSmem) != cudaSuccess)
             n = 1;
         cudaGetLastError();
         v = n > 0 ? n : 1;
@@ -219,7 +379,8 @@ int crz_encode_max_ctas_per_sm() {
 
 cudaError_t launch_crz_encode(const CodecParams &p, int grid, cudaStream_t s) {
     if (p.k == 0) return cudaSuccess;
-    crz_encode_kernel<<<grid, kCodecNT, 0, s>>>(p);
+    crz_encode_max_ctas_per_sm();   // sets the dynamic shared memory limit once
+    crz_encode_kernel<<<grid, kCodecNT, kEncSmem, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(1);
     return e;

@@ -14,8 +14,10 @@
 // bytes), the blocks' units in order, then the tail; a chunk whose stream
 // would not be shorter than L is stored as itself.
 //
-// Warp layout: lane l holds words 4l .. 4l+3 of a block (one 16-byte load),
-// so unit (p, j) word q is __ballot_sync of bit j of the lane's value q.
+// Warp layout: lane l holds words 4l .. 4l+3 of a block (one 16-byte load).
+// Gathering byte p of its four words gives the lane's plane-p word (byte q =
+// value 4l + q); the 32 plane words form a 32x32 bit matrix whose transpose
+// across the warp is exactly the plane's units (lane 8q + j: unit j, word q).
 #pragma once
 
 #include "crac_device.cuh"
@@ -74,50 +76,125 @@ __device__ __forceinline__ void store16_any(uint8_t *p, uint4 v) {
         for (int b = 0; b < 4; ++b) p[4 * i + b] = (uint8_t)(w[i] >> (8 * b));
 }
 
-// Header word of the block whose words 4*lane .. 4*lane+3 the calling lane
-// holds (rotated).  Whole warp.
+// 4x4 byte transpose: byte q of out[p] = byte p of in[q].  Turns a lane's
+// four rotated words into its four plane words (byte q = value 4*lane+q of
+// the plane), and back.
+__device__ __forceinline__ void crz_bytes_transpose(const uint32_t in[4], uint32_t out[4]) {
+    const uint32_t t01 = __byte_perm(in[0], in[1], 0x5140), t23 = __byte_perm(in[2], in[3], 0x5140);
+    const uint32_t u01 = __byte_perm(in[0], in[1], 0x7362), u23 = __byte_perm(in[2], in[3], 0x7362);
+    out[0] = __byte_perm(t01, t23, 0x5410);
+    out[1] = __byte_perm(t01, t23, 0x7632);
+    out[2] = __byte_perm(u01, u23, 0x5410);
+    out[3] = __byte_perm(u01, u23, 0x7632);
+}
+
+// Per-lane constants of the warp bit transpose: for each butterfly stage
+// (distance s = 16, 8, 4, 2, 1) the rotation that brings the partner's bit
+// groups into place and the mask of the groups this lane keeps.
+struct CrzLane {
+    uint32_t amt[5], keep[5];
+};
+
+__device__ __forceinline__ CrzLane crz_lane(int lane) {
+    constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+    CrzLane L;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t s = 16u >> i;
+        const bool hi = (lane & s) != 0;
+        L.amt[i] = hi ? 32u - s : s;   // rotate left by s, or right by s
+        L.keep[i] = hi ? ~kMask[i] : kMask[i];
+    }
+    return L;
+}
+
+// 32x32 bit transpose across the warp: on entry lane r holds row r (bit c =
+// column c), on return lane c holds column c (bit r = row r's bit c).  Five
+// butterfly stages, each swapping the off-diagonal halves of every 2s x 2s
+// block: the partner's word rotated by s towards this lane's half, merged
+// under the keep mask (a shuffle, a funnel shift and one three-input logic
+// operation per stage).
+__device__ __forceinline__ uint32_t crz_warp_transpose(uint32_t v, const CrzLane &L) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t x = __shfl_xor_sync(kFull, v, 16 >> i);
+        const uint32_t r = __funnelshift_l(x, x, L.amt[i]);
+        v = (v & L.keep[i]) | (r & ~L.keep[i]);
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Header word of the block whose rotated words 4*lane .. 4*lane+3 the calling
+// lane holds.  Planes 0 and 2 (the even bytes) and 1 and 3 (the odd bytes)
+// are reduced in pairs as 16-bit lanes, then across the warp.  Whole warp.
 __device__ __forceinline__ uint64_t crz_block_header(const uint32_t r[4]) {
+    uint32_t e[4], o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        e[q] = r[q] & 0x00FF00FFu;                   // bytes 0, 2 -> 16-bit lanes
+        o[q] = __byte_perm(r[q], 0u, 0x4341);        // bytes 1, 3 -> 16-bit lanes
+    }
+    const uint32_t emin = min_u16x2(min_u16x2(e[0], e[1]), min_u16x2(e[2], e[3]));
+    const uint32_t emax = max_u16x2(max_u16x2(e[0], e[1]), max_u16x2(e[2], e[3]));
+    const uint32_t omin = min_u16x2(min_u16x2(o[0], o[1]), min_u16x2(o[2], o[3]));
+    const uint32_t omax = max_u16x2(max_u16x2(o[0], o[1]), max_u16x2(o[2], o[3]));
+    const uint32_t lo[4] = {emin & 0xFFFFu, omin & 0xFFFFu, emin >> 16, omin >> 16};
+    const uint32_t hi[4] = {emax & 0xFFFFu, omax & 0xFFFFu, emax >> 16, omax >> 16};
     uint64_t h = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        const uint32_t v0 = (r[0] >> (8 * p)) & 255u, v1 = (r[1] >> (8 * p)) & 255u;
-        const uint32_t v2 = (r[2] >> (8 * p)) & 255u, v3 = (r[3] >> (8 * p)) & 255u;
-        const uint32_t lo = min(min(v0, v1), min(v2, v3)), hi = max(max(v0, v1), max(v2, v3));
-        const uint32_t m = __reduce_min_sync(kFull, lo), M = __reduce_max_sync(kFull, hi);
-        const uint32_t W = M == m ? 0u : 32u - (uint32_t)__clz(M - m);
+        const uint32_t m = __reduce_min_sync(kFull, lo[p]), M = __reduce_max_sync(kFull, hi[p]);
+        const uint32_t W = 32u - (uint32_t)__clz(M - m);   // bit length; 0 when M == m
         h |= ((uint64_t)m << (8 * p)) | ((uint64_t)W << (32 + 4 * p));
     }
     return h;
 }
 
-// Units of one block: lanes 0 .. sum(W)-1 each store one 16-byte unit at
-// out + 16 * lane (out 16-byte aligned).  Whole warp.
-__device__ __forceinline__ void crz_block_units(uint64_t h, const uint32_t r[4], uint8_t *out, int lane) {
-    uint4 mine = make_uint4(0u, 0u, 0u, 0u);
+// Units of one block: unit (p, j) word q is column 8q + j of the 32x32 bit
+// matrix whose row l is lane l's plane word minus the plane minimum (every
+// byte is at least the minimum, so the subtraction borrows across no byte).
+// After the transpose lane 8q + j holds it and parks it in the warp's
+// 512-byte shared scratch at 16 * (u_p + j) + 4q when j < W_p; lanes
+// 0 .. sum(W)-1 then store one 16-byte unit each at out + 16 * lane (out
+// 16-byte aligned): one coalesced store per block, which matters most when
+// out is mapped host memory.  Whole warp.
+__device__ __forceinline__ void crz_block_units(uint64_t h, const uint32_t P[4], uint8_t *out, int lane,
+                                                const CrzLane &L, uint8_t *scratch) {
+    const uint32_t j = (uint32_t)lane & 7u, q = (uint32_t)lane >> 3;
     uint32_t u = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t m = (uint32_t)(h >> (8 * p)) & 255u, W = crz_width(h, p);
-        const uint32_t d0 = ((r[0] >> (8 * p)) & 255u) - m, d1 = ((r[1] >> (8 * p)) & 255u) - m;
-        const uint32_t d2 = ((r[2] >> (8 * p)) & 255u) - m, d3 = ((r[3] >> (8 * p)) & 255u) - m;
-        for (uint32_t j = 0; j < W; ++j) {
-            const uint32_t b0 = __ballot_sync(kFull, (d0 >> j) & 1u);
-            const uint32_t b1 = __ballot_sync(kFull, (d1 >> j) & 1u);
-            const uint32_t b2 = __ballot_sync(kFull, (d2 >> j) & 1u);
-            const uint32_t b3 = __ballot_sync(kFull, (d3 >> j) & 1u);
-            if ((uint32_t)lane == u + j) mine = make_uint4(b0, b1, b2, b3);
+        if (W) {
+            const uint32_t col = crz_warp_transpose(P[p] - m * 0x01010101u, L);
+            if (j < W) *reinterpret_cast<uint32_t *>(scratch + 16u * (u + j) + 4u * q) = col;
         }
         u += W;
     }
-    if ((uint32_t)lane < u) *reinterpret_cast<uint4 *>(out + 16u * lane) = mine;
+    __syncwarp();
+    if ((uint32_t)lane < u)
+        *reinterpret_cast<uint4 *>(out + 16u * lane) = *reinterpret_cast<const uint4 *>(scratch + 16u * lane);
+    __syncwarp();   // the scratch is rewritten by the next block
 }
 
 // Decode the z-byte stream at src (16-byte aligned) into the len bytes at
-// dst (16-byte aligned).  Whole warp.  Every read stays inside [src, src+z)
-// and every write inside [dst, dst+len).  Returns false for a stream that
-// no chunk of len bytes encodes to: nothing is written when its lengths or
-// headers are inconsistent, and the chunk may be partly written when a
-// plane value overflows a byte.
+// dst.  Whole warp.  Every read stays inside [src, src+z) and every write
+// inside [dst, dst+len).  Returns false for a stream that no chunk of len
+// bytes encodes to: nothing is written when its lengths or headers are
+// inconsistent, and the chunk may be partly written when a plane value
+// overflows a byte.
 __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src, uint64_t len, uint64_t z,
                                                 int lane) {
     const uint64_t nb = len >> 9, tl = len & 511u, head = crz_head_bytes(nb);
@@ -136,6 +213,8 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
     tot = __reduce_add_sync(kFull, tot);   // <= 32 per block, nb <= 2^15
     if (bad || head + 16ull * tot + tl != z) return false;
     const uint8_t *units = src + head;
+    const uint32_t j = (uint32_t)lane & 7u, q = (uint32_t)lane >> 3;
+    const CrzLane LT = crz_lane(lane);
     uint32_t carry = 0;
     bool over = false;
     for (uint64_t b0 = 0; b0 < nb; b0 += 32) {
@@ -151,38 +230,53 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
         const uint32_t excl = carry + incl - ws;
         carry += __shfl_sync(kFull, incl, 31);
         const int nblk = (int)umin64(32, nb - b0);
-        for (int i = 0; i < nblk; ++i) {
-            const uint64_t hb = __shfl_sync(kFull, h, i);
-            const uint32_t ub = __shfl_sync(kFull, excl, i);
-            const uint32_t wsb = crz_width_sum(hb);
-            uint4 u = make_uint4(0u, 0u, 0u, 0u);
-            if ((uint32_t)lane < wsb) u = *reinterpret_cast<const uint4 *>(units + 16ull * (ub + lane));
-            uint32_t o[4] = {0u, 0u, 0u, 0u};
-            uint32_t uu = 0;
+        // Groups of kG blocks: every unit word of the group is requested before
+        // any is used, so a host image read in place has kG * 4 loads in
+        // flight per lane instead of one round trip per plane.
+        constexpr int kG = 4;
+        for (int i = 0; i < nblk; i += kG) {
+            uint64_t hb[kG];
+            uint32_t col[kG][4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const uint32_t m = (uint32_t)(hb >> (8 * p)) & 255u, W = crz_width(hb, p);
-                uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-                for (uint32_t j = 0; j < W; ++j) {
-                    const int sl = (int)(uu + j);
-                    v0 |= ((__shfl_sync(kFull, u.x, sl) >> lane) & 1u) << j;
-                    v1 |= ((__shfl_sync(kFull, u.y, sl) >> lane) & 1u) << j;
-                    v2 |= ((__shfl_sync(kFull, u.z, sl) >> lane) & 1u) << j;
-                    v3 |= ((__shfl_sync(kFull, u.w, sl) >> lane) & 1u) << j;
+            for (int g = 0; g < kG; ++g) {
+                const bool valid = i + g < nblk;
+                hb[g] = __shfl_sync(kFull, h, (i + g) & 31);
+                uint32_t u = __shfl_sync(kFull, excl, (i + g) & 31);
+                if (!valid) hb[g] = 0;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t W = crz_width(hb[g], p);
+                    // lane 8q + j fetches unit (p, j) word q
+                    col[g][p] = j < W ? *reinterpret_cast<const uint32_t *>(units + 16ull * (u + j) + 4u * q) : 0u;
+                    u += W;
                 }
-                uu += W;
-                v0 += m;
-                v1 += m;
-                v2 += m;
-                v3 += m;
-                over |= ((v0 | v1 | v2 | v3) > 255u);
-                o[0] |= (v0 & 255u) << (8 * p);
-                o[1] |= (v1 & 255u) << (8 * p);
-                o[2] |= (v2 & 255u) << (8 * p);
-                o[3] |= (v3 & 255u) << (8 * p);
             }
-            store16_any(dst + 512ull * (b0 + i) + 16u * lane,
-                        make_uint4(crz_unrot(o[0]), crz_unrot(o[1]), crz_unrot(o[2]), crz_unrot(o[3])));
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                if (i + g >= nblk) break;
+                uint32_t P[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t m = (uint32_t)(hb[g] >> (8 * p)) & 255u, W = crz_width(hb[g], p);
+                    // the transpose hands lane l its four values' offsets from the minimum
+                    const uint32_t d = W ? crz_warp_transpose(col[g][p], LT) : 0u;
+                    const uint32_t m4 = m * 0x01010101u;
+                    if (m + (1u << W) - 1u <= 255u) {
+                        P[p] = d + m4;   // no byte can pass 255: a plain add carries nowhere
+                    } else {
+                        // bytewise d + m: the sum without carries between bytes,
+                        // and the bytes whose sum passes 255
+                        const uint32_t s7 = (d & 0x7F7F7F7Fu) + (m4 & 0x7F7F7F7Fu);
+                        const uint32_t sum = s7 ^ ((d ^ m4) & 0x80808080u);
+                        over |= (((d & m4) | ((d | m4) & ~sum)) & 0x80808080u) != 0;
+                        P[p] = sum;
+                    }
+                }
+                uint32_t r[4];
+                crz_bytes_transpose(P, r);
+                store16_any(dst + 512ull * (b0 + i + g) + 16u * lane,
+                            make_uint4(crz_unrot(r[0]), crz_unrot(r[1]), crz_unrot(r[2]), crz_unrot(r[3])));
+            }
         }
     }
     for (uint64_t i = lane; i < tl; i += 32) dst[512ull * nb + i] = units[16ull * tot + i];

@@ -174,6 +174,7 @@ struct RestoreParams {
     unsigned int *err;
     // Incremental restore: current and target fingerprints per target chunk.
     const uint64_t *fp_now, *fp_img;
+    uint32_t coded;               // some piece has a zlen table (coded image)
 };
 // Multi-image restore: mark owners for every entry of every piece (atomicMax,
 // so the newest image wins in any order), check coverage, scatter owned chunks.

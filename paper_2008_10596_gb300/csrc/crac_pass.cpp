@@ -668,7 +668,8 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         const bool direct_flag = host_res && c->uva && (c->cfg.flags & CRAC_FLAG_DIRECT_DRAIN);
         const bool direct = direct_flag && !coded && c->pass_now != CRAC_PASS_TMA;
         if (host_res || coded) {
-            st = ensure_dev(c->staging, max_seg_bytes);   // also the direct drain's fallback
+            // coded: + the 16-byte slack of the encoder's aligned bulk reads
+            st = ensure_dev(c->staging, max_seg_bytes + (coded ? 16 : 0));   // also the direct drain's fallback
             if (st == CRAC_OK) st = ensure_dev(c->idx, max_seg_chunks * 8);
             if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
             if (st != CRAC_OK) return fail(st);

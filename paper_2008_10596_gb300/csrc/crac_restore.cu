@@ -94,7 +94,11 @@ __global__ void __launch_bounds__(256) restore_unmark_kernel(const RestoreParams
         if (P.fp_now[i] == P.fp_img[i]) P.owner[i] = 0;
 }
 
-__global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const RestoreParams P) {
+// kCoded: some piece of the chain is coded (its decoder needs registers the
+// plain copy does not, so chains without coded images keep the lean build,
+// restore_scatter_kernel; coded chains run restore_scatter_coded_kernel).
+template <bool kCoded>
+__device__ __forceinline__ void restore_scatter_body(const RestoreParams &P) {
     if (*(volatile unsigned int *)P.err) return;   // uncovered or out of range: memory untouched
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t S = 1ull << P.log2_chunk;
@@ -109,16 +113,24 @@ __global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const Resto
         const uint64_t len = min(S, d.bytes - (local << P.log2_chunk));
         const uint64_t o = reinterpret_cast<const uint64_t *>(pc.off)[e - pc.entry_base];
         // Coded image: the entry's stream length (equal to len when stored raw).
-        const uint64_t z = pc.zlen ? reinterpret_cast<const uint64_t *>(pc.zlen)[e - pc.entry_base] : len;
+        const uint64_t z = (kCoded && pc.zlen) ? reinterpret_cast<const uint64_t *>(pc.zlen)[e - pc.entry_base] : len;
         if (o > pc.bytes || z > pc.bytes - o) {
             if (lane == 0) atomicOr(P.err, kErrBounds);
             continue;
         }
         uint8_t *dst = reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk);
         const uint8_t *src = reinterpret_cast<const uint8_t *>(pc.payload) + o;
-        if (z == len) copy_group<32>(dst, src, len, lane);
+        if (!kCoded || z == len) copy_group<32>(dst, src, len, lane);
         else if (!crz_decode_warp(dst, src, len, z, lane) && lane == 0) atomicOr(P.err, kErrCodec);
     }
+}
+
+__global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const RestoreParams P) {
+    restore_scatter_body<false>(P);
+}
+
+__global__ void __launch_bounds__(kScatterNT, 3) restore_scatter_coded_kernel(const RestoreParams P) {
+    restore_scatter_body<true>(P);
 }
 
 }  // namespace
@@ -149,7 +161,8 @@ cudaError_t launch_restore_unmark(const RestoreParams &p, int grid, cudaStream_t
 
 cudaError_t launch_restore_scatter(const RestoreParams &p, int grid, cudaStream_t s) {
     if (p.n_entries == 0) return cudaSuccess;
-    restore_scatter_kernel<<<grid, kScatterNT, 0, s>>>(p);
+    if (p.coded) restore_scatter_coded_kernel<<<grid, kScatterNT, 0, s>>>(p);
+    else restore_scatter_kernel<<<grid, kScatterNT, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(1);
     return e;
