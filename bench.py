@@ -879,11 +879,15 @@ def run_codec(args):
         "device": dict(image_residency=C.CRAC_RESIDENCY_DEVICE),
         "device_coded": dict(image_residency=C.CRAC_RESIDENCY_DEVICE, flags=C.CRAC_FLAG_COMPRESS),
     }
-    reserve = dict(reserve_host_bytes=3 * B, reserve_device_bytes=3 * B)
+    # Every variant's chain (a first image, a full one, the deltas: ~2.5 B)
+    # must stay under the pinned arena's 80% mark, where its background
+    # growth (pinning a new region while the timed copies run) would start.
+    reserve = dict(reserve_host_bytes=5 * B, reserve_device_bytes=4 * B)
     steps = max(3, min(args.steps, 5))
     sampler = ClockSampler(None)
     sampler.start()
     launches0 = C.crac_kernel_launches()
+    mem0 = None
     rows = []
     enc = []   # encoder launches into device memory: (raw bytes, stored bytes, entries, ms)
     for kind in ("f32_normal", "bf16_normal", "zeros", "u8_uniform"):
@@ -891,6 +895,8 @@ def run_codec(args):
             fill("u8_uniform", wl.seed + 7)   # the untimed first image: other bytes everywhere
             ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3000, device=0, **cfg, **reserve))
             reserve = {}
+            if mem0 is None:
+                mem0 = C.crac_memory_stats()   # after the reservation
             for b in bufs:
                 C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
             # A first full checkpoint (of other bytes) sizes the context's
@@ -943,6 +949,7 @@ def run_codec(args):
                 "restart": {"wall_ms": rwall, "device_ms": ri["device_ms"], "chain_length": ri["chain_length"],
                             "tracked_gbs": B / (rwall / 1e3) / 1e9, "sampled_restore_ok": ok}})
     launches = C.crac_kernel_launches() - launches0
+    mem1 = C.crac_memory_stats()
     clocks = sampler.stop()
     # The encoder's roofline: it reads the raw payload from staging once (bulk
     # copies into shared memory, where both of its passes read it) and writes
@@ -963,6 +970,7 @@ def run_codec(args):
                         "fp32 N(0,1) / bf16 N(0,1) / zeros / uniform bytes; plain vs CRZ1-coded images",
             "tracked_bytes": B, "n_chunks": n, "steps": steps, "roofline": roofline, "rows": rows,
             "encoder_launches": encoder, "gpu_launches": launches, "clocks": clocks,
+            "arena_growth": {k: mem1[k] - mem0[k] for k in ("host_grow_events", "device_grow_events")},
             "note": "wall_ms includes the drain wait; full = a steady-state full checkpoint (every chunk "
                     "rewritten after a first, untimed one of uniform bytes); delta rows are medians over the steps; the restart "
                     "restores the chain of 2 full + steps deltas after zeroing every 17th allocation"}

@@ -600,6 +600,7 @@ CRAC_API crac_status_t crac_pass_noalloc(const crac_region_t *regions_dev, uint3
 #define CRAC_FAULT_H2D          3  /* restart H2D enqueue */
 #define CRAC_FAULT_ALLOC        4  /* staging / image memory allocation */
 #define CRAC_FAULT_DEVICE_WAIT  5  /* look-back wait times out on the device */
+#define CRAC_FAULT_ENCODE_WAIT  6  /* the CRZ1 encoder's look-back wait times out (CRAC_FLAG_COMPRESS) */
 CRAC_API void crac_debug_inject_fault(int step, int count);
 
 #ifdef __cplusplus

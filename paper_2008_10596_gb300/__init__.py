@@ -59,6 +59,7 @@ CRAC_FAULT_DRAIN = 2
 CRAC_FAULT_H2D = 3
 CRAC_FAULT_ALLOC = 4
 CRAC_FAULT_DEVICE_WAIT = 5
+CRAC_FAULT_ENCODE_WAIT = 6
 
 EXPORTED = [
     "crac_config_default", "crac_ctx_create", "crac_ctx_destroy", "crac_ctx_register_alloc",

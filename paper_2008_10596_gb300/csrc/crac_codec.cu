@@ -42,7 +42,8 @@ __device__ uint64_t lookback1(uint64_t *status, uint32_t tile, int lane, uint64_
     uint64_t acc = 0;
     int64_t j = (int64_t)tile - 1;
     const uint64_t t0 = globaltimer();
-    bool gave_up = false;
+    // once a wait has run out anywhere, later tiles give up at once
+    bool gave_up = (*(volatile unsigned int *)err & kErrTimeout) != 0;
     for (;;) {
         const int64_t t = j - lane;
         uint64_t w = kFlagInc;   // tiles before 0: inclusive 0
@@ -167,7 +168,13 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
     uint32_t phase = 0;
     for (;;) {
         __syncthreads();   // the previous tile's shared state (and window) is consumed
-        if (tid == 0) s_tile = atomicAdd(P.ticket, 1u);
+        if (tid == 0) {
+            uint32_t t = atomicAdd(P.ticket, 1u);
+            // fault injection: tile 0 is never processed, so the wait of the
+            // tiles after it runs out (bounded) and the launch reports kErrTimeout
+            if (P.skip_first_ticket && t == 0) t = atomicAdd(P.ticket, 1u);
+            s_tile = t;
+        }
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= P.n_tiles) return;

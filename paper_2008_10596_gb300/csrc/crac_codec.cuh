@@ -152,14 +152,15 @@ __device__ __forceinline__ uint64_t crz_block_header(const uint32_t r[4]) {
     const uint32_t omax = max_u16x2(max_u16x2(o[0], o[1]), max_u16x2(o[2], o[3]));
     const uint32_t lo[4] = {emin & 0xFFFFu, omin & 0xFFFFu, emin >> 16, omin >> 16};
     const uint32_t hi[4] = {emax & 0xFFFFu, omax & 0xFFFFu, emax >> 16, omax >> 16};
-    uint64_t h = 0;
+    uint32_t mins = 0, widths = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t m = __reduce_min_sync(kFull, lo[p]), M = __reduce_max_sync(kFull, hi[p]);
         const uint32_t W = 32u - (uint32_t)__clz(M - m);   // bit length; 0 when M == m
-        h |= ((uint64_t)m << (8 * p)) | ((uint64_t)W << (32 + 4 * p));
+        mins |= m << (8 * p);
+        widths |= W << (4 * p);
     }
-    return h;
+    return ((uint64_t)widths << 32) | mins;
 }
 
 // Units of one block: unit (p, j) word q is column 8q + j of the 32x32 bit
@@ -172,15 +173,18 @@ __device__ __forceinline__ uint64_t crz_block_header(const uint32_t r[4]) {
 // out is mapped host memory.  Whole warp.
 __device__ __forceinline__ void crz_block_units(uint64_t h, const uint32_t P[4], uint8_t *out, int lane,
                                                 const CrzLane &L, uint8_t *scratch) {
+    if ((uint32_t)(h >> 32) == 0) return;   // every plane constant: no units
     const uint32_t j = (uint32_t)lane & 7u, q = (uint32_t)lane >> 3;
+    // All four transposes run unconditionally (a plane of width 0 stores
+    // nothing), so their dependency chains interleave.
+    uint32_t col[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) col[p] = crz_warp_transpose(P[p] - ((uint32_t)(h >> (8 * p)) & 255u) * 0x01010101u, L);
     uint32_t u = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        const uint32_t m = (uint32_t)(h >> (8 * p)) & 255u, W = crz_width(h, p);
-        if (W) {
-            const uint32_t col = crz_warp_transpose(P[p] - m * 0x01010101u, L);
-            if (j < W) *reinterpret_cast<uint32_t *>(scratch + 16u * (u + j) + 4u * q) = col;
-        }
+        const uint32_t W = crz_width(h, p);
+        if (j < W) *reinterpret_cast<uint32_t *>(scratch + 16u * (u + j) + 4u * q) = col[p];
         u += W;
     }
     __syncwarp();
@@ -233,7 +237,7 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
         // Groups of kG blocks: every unit word of the group is requested before
         // any is used, so a host image read in place has kG * 4 loads in
         // flight per lane instead of one round trip per plane.
-        constexpr int kG = 4;
+        constexpr int kG = 3;
         for (int i = 0; i < nblk; i += kG) {
             uint64_t hb[kG];
             uint32_t col[kG][4];
@@ -255,21 +259,29 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
             for (int g = 0; g < kG; ++g) {
                 if (i + g >= nblk) break;
                 uint32_t P[4];
+                if ((uint32_t)(hb[g] >> 32) == 0) {
+                    // every plane constant: each byte is its plane's minimum
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const uint32_t m = (uint32_t)(hb[g] >> (8 * p)) & 255u, W = crz_width(hb[g], p);
-                    // the transpose hands lane l its four values' offsets from the minimum
-                    const uint32_t d = W ? crz_warp_transpose(col[g][p], LT) : 0u;
-                    const uint32_t m4 = m * 0x01010101u;
-                    if (m + (1u << W) - 1u <= 255u) {
-                        P[p] = d + m4;   // no byte can pass 255: a plain add carries nowhere
-                    } else {
-                        // bytewise d + m: the sum without carries between bytes,
-                        // and the bytes whose sum passes 255
-                        const uint32_t s7 = (d & 0x7F7F7F7Fu) + (m4 & 0x7F7F7F7Fu);
-                        const uint32_t sum = s7 ^ ((d ^ m4) & 0x80808080u);
-                        over |= (((d & m4) | ((d | m4) & ~sum)) & 0x80808080u) != 0;
-                        P[p] = sum;
+                    for (int p = 0; p < 4; ++p) P[p] = ((uint32_t)(hb[g] >> (8 * p)) & 255u) * 0x01010101u;
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const uint32_t m = (uint32_t)(hb[g] >> (8 * p)) & 255u, W = crz_width(hb[g], p);
+                        // the transpose hands lane l its four values' offsets from the
+                        // minimum (unconditionally: a width-0 plane transposes zeros, and
+                        // the four planes' chains interleave)
+                        const uint32_t d = crz_warp_transpose(col[g][p], LT);
+                        const uint32_t m4 = m * 0x01010101u;
+                        if (m + (1u << W) - 1u <= 255u) {
+                            P[p] = d + m4;   // no byte can pass 255: a plain add carries nowhere
+                        } else {
+                            // bytewise d + m: the sum without carries between bytes,
+                            // and the bytes whose sum passes 255
+                            const uint32_t s7 = (d & 0x7F7F7F7Fu) + (m4 & 0x7F7F7F7Fu);
+                            const uint32_t sum = s7 ^ ((d ^ m4) & 0x80808080u);
+                            over |= (((d & m4) | ((d | m4) & ~sum)) & 0x80808080u) != 0;
+                            P[p] = sum;
+                        }
                     }
                 }
                 uint32_t r[4];

@@ -206,6 +206,7 @@ struct CodecParams {
     uint32_t tile_entries;    // entries per tile, 1..crz_tile_max()
     uint32_t n_tiles;
     uint64_t timeout_ns;
+    uint32_t skip_first_ticket;   // fault injection: tile 0 is never processed
 };
 cudaError_t launch_crz_encode(const CodecParams &p, int grid, cudaStream_t s);
 uint32_t crz_tile_max();

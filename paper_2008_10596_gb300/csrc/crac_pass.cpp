@@ -507,6 +507,7 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
     P.tile_entries = T;
     P.n_tiles = (uint32_t)n_tiles;
     P.timeout_ns = c->cfg.timeout_ns;
+    P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_ENCODE_WAIT)) ? 1u : 0u;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * crz_encode_max_ctas_per_sm()));
     uint8_t *out_h = (uint8_t *)c->ctrl_h.p + sizeof(CkptCtrl);
     CK(cudaMemsetAsync(w, 0, 16 + 8 * n_tiles, s));

@@ -227,3 +227,37 @@ def test_staged_flag_still_restores_coded_chain():
             assert np.array_equal(b.read(), w)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("residency,flags", [(C.CRAC_RESIDENCY_HOST, 0),
+                                             (C.CRAC_RESIDENCY_HOST, C.CRAC_FLAG_DIRECT_DRAIN),
+                                             (C.CRAC_RESIDENCY_DEVICE, 0)])
+def test_encoder_wait_runs_out_cleanly(residency, flags):
+    """The encoder is launched so that its first tile is never processed: the
+    later tiles' bounded look-back waits run out, the checkpoint reports
+    CRAC_ERR_TIMEOUT, and the context's baseline is untouched (the next
+    checkpoint equals the oracle's, which never saw the failed one)."""
+    S = 4 * KIB
+    h = Harness(S, lineage=1700, image_residency=residency, flags=flags | CODED, timeout_ns=20_000_000)
+    try:
+        for i, n in enumerate([64 * S + 100, 40 * S]):   # more than one 16-chunk tile
+            h.add(n, data=_contents("f32_normal", n, 40 + i))
+        _, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, "alternating", seed=3))
+        C.crac_debug_inject_fault(C.CRAC_FAULT_ENCODE_WAIT, 1)
+        with pytest.raises(C.CracError) as e:
+            C.crac_ctx_checkpoint(h.ctx, h.stream)
+        assert e.value.code == C.CRAC_ERR_TIMEOUT
+        C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
+        _, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(h.images[-1])
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
+        h.close()
