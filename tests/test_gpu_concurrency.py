@@ -1,6 +1,7 @@
 """Concurrent contexts (GPU): several host threads, each with its own
 context, stream and allocations, checkpoint and restart at the same time,
-sharing the process-wide arenas, the image table and the launch counter.
+sharing the process-wide arenas, the image table and the launch counter
+(plain and coded images).
 Every image must equal the oracle's and every restart must bring back its
 memory exactly."""
 import threading
@@ -19,19 +20,20 @@ pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 KIB = 1024
 
 
-def _worker(idx, kern, residency, out, errors):
+def _worker(idx, kern, residency, flags, out, errors):
     try:
         S = 4 * KIB
         stream = torch.cuda.Stream()
         rng = np.random.default_rng(idx)
         sizes = [int(x) // 16 * 16 + 16 for x in rng.integers(1, 200000, size=6)]
         with torch.cuda.stream(stream):
-            bufs = [torch.from_numpy(W.host_contents("u8", n, 900 + 10 * idx + i)).to("cuda", non_blocking=False)
+            kind = "f32_normal" if flags & C.CRAC_FLAG_COMPRESS else "u8"   # coded: content that shrinks
+        bufs = [torch.from_numpy(W.host_contents(kind, n, 900 + 10 * idx + i)).to("cuda", non_blocking=False)
                     for i, n in enumerate(sizes)]
         stream.synchronize()
         ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=8000 + idx, pass_kernel=kern,
-                                                      image_residency=residency))
-        ora = O.OracleContext(S, lineage=8000 + idx)
+                                                      image_residency=residency, flags=flags))
+        ora = O.OracleContext(S, lineage=8000 + idx, coded=bool(flags & C.CRAC_FLAG_COMPRESS))
         imgs = []
         try:
             for b, n in zip(bufs, sizes):
@@ -75,11 +77,15 @@ def _worker(idx, kern, residency, out, errors):
 
 
 def test_concurrent_contexts():
-    plans = [(C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_HOST), (C.CRAC_PASS_SPLIT, C.CRAC_RESIDENCY_DEVICE),
-             (C.CRAC_PASS_LDG, C.CRAC_RESIDENCY_HOST), (C.CRAC_PASS_TMA, C.CRAC_RESIDENCY_DEVICE),
-             (C.CRAC_PASS_SPARSE, C.CRAC_RESIDENCY_DEVICE), (C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_DEVICE)]
+    coded = C.CRAC_FLAG_COMPRESS
+    plans = [(C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_HOST, 0), (C.CRAC_PASS_SPLIT, C.CRAC_RESIDENCY_DEVICE, 0),
+             (C.CRAC_PASS_LDG, C.CRAC_RESIDENCY_HOST, 0), (C.CRAC_PASS_TMA, C.CRAC_RESIDENCY_DEVICE, 0),
+             (C.CRAC_PASS_SPARSE, C.CRAC_RESIDENCY_DEVICE, 0), (C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_DEVICE, 0),
+             (C.CRAC_PASS_SPLIT, C.CRAC_RESIDENCY_HOST, coded),
+             (C.CRAC_PASS_AUTO, C.CRAC_RESIDENCY_HOST, coded | C.CRAC_FLAG_DIRECT_DRAIN),
+             (C.CRAC_PASS_TMA, C.CRAC_RESIDENCY_DEVICE, coded)]
     out, errors = {}, []
-    threads = [threading.Thread(target=_worker, args=(i, k, r, out, errors)) for i, (k, r) in enumerate(plans)]
+    threads = [threading.Thread(target=_worker, args=(i, k, r, f, out, errors)) for i, (k, r, f) in enumerate(plans)]
     launches0 = C.crac_kernel_launches()
     for t in threads:
         t.start()
