@@ -26,6 +26,8 @@ namespace crac {
 namespace {
 
 constexpr uint32_t kCrzBlock = 512;
+constexpr int kCrzDecodeGroup = 3;                           // blocks decoded per step
+constexpr int kCrzDecodeScratch = 512 * kCrzDecodeGroup;     // shared bytes per decoding warp
 
 __device__ __forceinline__ uint32_t crz_rot(uint32_t w) {
     return ((w << 1) & 0xFEFEFEFEu) | ((w >> 7) & 0x01010101u);
@@ -194,13 +196,14 @@ __device__ __forceinline__ void crz_block_units(uint64_t h, const uint32_t P[4],
 }
 
 // Decode the z-byte stream at src (16-byte aligned) into the len bytes at
-// dst.  Whole warp.  Every read stays inside [src, src+z) and every write
+// dst.  Whole warp; scratch is the warp's kCrzDecodeScratch bytes of shared
+// memory (16-byte aligned).  Every read stays inside [src, src+z) and every write
 // inside [dst, dst+len).  Returns false for a stream that no chunk of len
 // bytes encodes to: nothing is written when its lengths or headers are
 // inconsistent, and the chunk may be partly written when a plane value
 // overflows a byte.
 __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src, uint64_t len, uint64_t z,
-                                                int lane) {
+                                                int lane, uint8_t *scratch) {
     const uint64_t nb = len >> 9, tl = len & 511u, head = crz_head_bytes(nb);
     if (nb == 0 || z >= len || z < head || ((uintptr_t)src & 15u)) return false;
     const uint64_t *H = reinterpret_cast<const uint64_t *>(src);
@@ -234,27 +237,26 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
         const uint32_t excl = carry + incl - ws;
         carry += __shfl_sync(kFull, incl, 31);
         const int nblk = (int)umin64(32, nb - b0);
-        // Groups of kG blocks: every unit word of the group is requested before
-        // any is used, so a host image read in place has kG * 4 loads in
-        // flight per lane instead of one round trip per plane.
-        constexpr int kG = 3;
+        // Groups of kCrzDecodeGroup blocks: each block's units arrive with one
+        // coalesced 16-byte load per lane (lane k: unit k), all of the group's
+        // before any is used, and are parked in the warp's shared scratch,
+        // from which lane 8q + j takes word q of each plane's unit j.
+        constexpr int kG = kCrzDecodeGroup;
         for (int i = 0; i < nblk; i += kG) {
             uint64_t hb[kG];
-            uint32_t col[kG][4];
+            uint4 raw[kG];
 #pragma unroll
             for (int g = 0; g < kG; ++g) {
-                const bool valid = i + g < nblk;
-                hb[g] = __shfl_sync(kFull, h, (i + g) & 31);
-                uint32_t u = __shfl_sync(kFull, excl, (i + g) & 31);
-                if (!valid) hb[g] = 0;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const uint32_t W = crz_width(hb[g], p);
-                    // lane 8q + j fetches unit (p, j) word q
-                    col[g][p] = j < W ? *reinterpret_cast<const uint32_t *>(units + 16ull * (u + j) + 4u * q) : 0u;
-                    u += W;
-                }
+                hb[g] = i + g < nblk ? __shfl_sync(kFull, h, (i + g) & 31) : 0ull;
+                const uint32_t u = __shfl_sync(kFull, excl, (i + g) & 31);
+                if ((uint32_t)lane < crz_width_sum(hb[g]))
+                    raw[g] = *reinterpret_cast<const uint4 *>(units + 16ull * (u + lane));
             }
+#pragma unroll
+            for (int g = 0; g < kG; ++g)
+                if ((uint32_t)lane < crz_width_sum(hb[g]))
+                    *reinterpret_cast<uint4 *>(scratch + 512 * g + 16 * lane) = raw[g];
+            __syncwarp();
 #pragma unroll
             for (int g = 0; g < kG; ++g) {
                 if (i + g >= nblk) break;
@@ -264,13 +266,22 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
 #pragma unroll
                     for (int p = 0; p < 4; ++p) P[p] = ((uint32_t)(hb[g] >> (8 * p)) & 255u) * 0x01010101u;
                 } else {
+                    uint32_t col[4];   // lane 8q + j: word q of the plane's unit j
+                    uint32_t u = 0;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const uint32_t W = crz_width(hb[g], p);
+                        col[p] = j < W ? *reinterpret_cast<const uint32_t *>(scratch + 512 * g + 16 * (u + j) + 4 * q)
+                                       : 0u;
+                        u += W;
+                    }
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
                         const uint32_t m = (uint32_t)(hb[g] >> (8 * p)) & 255u, W = crz_width(hb[g], p);
                         // the transpose hands lane l its four values' offsets from the
                         // minimum (unconditionally: a width-0 plane transposes zeros, and
                         // the four planes' chains interleave)
-                        const uint32_t d = crz_warp_transpose(col[g][p], LT);
+                        const uint32_t d = crz_warp_transpose(col[p], LT);
                         const uint32_t m4 = m * 0x01010101u;
                         if (m + (1u << W) - 1u <= 255u) {
                             P[p] = d + m4;   // no byte can pass 255: a plain add carries nowhere
@@ -289,6 +300,7 @@ __device__ __forceinline__ bool crz_decode_warp(uint8_t *dst, const uint8_t *src
                 store16_any(dst + 512ull * (b0 + i + g) + 16u * lane,
                             make_uint4(crz_unrot(r[0]), crz_unrot(r[1]), crz_unrot(r[2]), crz_unrot(r[3])));
             }
+            __syncwarp();   // the scratch is rewritten by the next group
         }
     }
     for (uint64_t i = lane; i < tl; i += 32) dst[512ull * nb + i] = units[16ull * tot + i];

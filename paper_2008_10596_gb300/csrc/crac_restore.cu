@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) restore_unmark_kernel(const RestoreParams
 // plain copy does not, so chains without coded images keep the lean build,
 // restore_scatter_kernel; coded chains run restore_scatter_coded_kernel).
 template <bool kCoded>
-__device__ __forceinline__ void restore_scatter_body(const RestoreParams &P) {
+__device__ __forceinline__ void restore_scatter_body(const RestoreParams &P, uint8_t *scratch) {
     if (*(volatile unsigned int *)P.err) return;   // uncovered or out of range: memory untouched
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t S = 1ull << P.log2_chunk;
@@ -121,16 +121,18 @@ __device__ __forceinline__ void restore_scatter_body(const RestoreParams &P) {
         uint8_t *dst = reinterpret_cast<uint8_t *>(d.dst) + (local << P.log2_chunk);
         const uint8_t *src = reinterpret_cast<const uint8_t *>(pc.payload) + o;
         if (!kCoded || z == len) copy_group<32>(dst, src, len, lane);
-        else if (!crz_decode_warp(dst, src, len, z, lane) && lane == 0) atomicOr(P.err, kErrCodec);
+        else if (!crz_decode_warp(dst, src, len, z, lane, scratch + kCrzDecodeScratch * warp) && lane == 0)
+            atomicOr(P.err, kErrCodec);
     }
 }
 
 __global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const RestoreParams P) {
-    restore_scatter_body<false>(P);
+    restore_scatter_body<false>(P, nullptr);
 }
 
 __global__ void __launch_bounds__(kScatterNT, 3) restore_scatter_coded_kernel(const RestoreParams P) {
-    restore_scatter_body<true>(P);
+    __shared__ __align__(16) uint8_t scratch[kCrzDecodeScratch * (kScatterNT / 32)];
+    restore_scatter_body<true>(P, scratch);
 }
 
 }  // namespace
