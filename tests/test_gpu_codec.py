@@ -261,3 +261,28 @@ def test_encoder_wait_runs_out_cleanly(residency, flags):
     finally:
         C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
         h.close()
+
+
+@pytest.mark.parametrize("S", [16, 64, 256, 1 << 20])
+@pytest.mark.parametrize("residency", [C.CRAC_RESIDENCY_HOST, C.CRAC_RESIDENCY_DEVICE])
+def test_coded_extreme_chunk_sizes(S, residency):
+    """Chunks below one block (every stream raw, up to 128 entries a tile) and
+    1 MiB chunks (sixteen shared-memory windows each, a ragged last one)."""
+    h = Harness(S, lineage=1800 + S.bit_length(), image_residency=residency, flags=CODED)
+    try:
+        sizes = [3 * S + 5, 2 * S, 4100] if S >= 1 << 20 else [5000, 777, 64 * S + 48]
+        for i, n in enumerate(sizes):
+            h.add(n, data=_contents(["f32_normal", "zeros", "bf16"][i % 3], n, 60 + i))
+        img, lib, ora = h.checkpoint()
+        assert lib == ora
+        h.mutate(pattern_mutations(h.first(), sizes, S, "alternating", seed=4))
+        img2, lib2, ora2 = h.checkpoint()
+        assert lib2 == ora2
+        want = h.host()
+        for b in h.bufs:
+            b.zero()
+        h.restart(img2)
+        for b, w in zip(h.bufs, want):
+            assert np.array_equal(b.read(), w)
+    finally:
+        h.close()
