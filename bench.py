@@ -951,6 +951,33 @@ def run_codec(args):
     launches = C.crac_kernel_launches() - launches0
     mem1 = C.crac_memory_stats()
     clocks = sampler.stop()
+    # The oracle's CRZ1 code on the host cores, on a bounded sample of the
+    # fp32 content (the first allocations, up to 64 MiB, 64 KiB chunks).
+    cpu = None
+    if not args.no_cpu:
+        from oracle import crz
+        fill("f32_normal", wl.seed)
+        sample, got = [], 0
+        for b in bufs:
+            if got >= 64 << 20:
+                break
+            sample.append(b.cpu().numpy())
+            got += b.numel()
+        chunks = [a[i:i + S] for a in sample for i in range(0, a.size, S)]
+        t0 = time.perf_counter()
+        streams = [crz.encode(ch) for ch in chunks]
+        t_enc = time.perf_counter() - t0
+        nd = max(1, len(chunks) // 4)
+        t0 = time.perf_counter()
+        for ch, z in zip(chunks[:nd], streams[:nd]):
+            crz.decode(z, ch.size)
+        t_dec = time.perf_counter() - t0
+        raw = sum(ch.size for ch in chunks)
+        raw_d = sum(ch.size for ch in chunks[:nd])
+        cpu = {"value": raw / t_enc / 1e9, "unit": "GB/s (raw bytes encoded)", "cores": 1, "kind": "oracle",
+               "decode_gbs": raw_d / t_dec / 1e9, "ratio": sum(len(z) for z in streams) / raw,
+               "sample": f"{len(sample)} allocations, {raw / 2**20:.0f} MiB of the fp32 content in 64 KiB chunks "
+                         f"(decode: the first {raw_d / 2**20:.0f} MiB); numpy, single thread"}
     # The encoder's roofline: it reads the raw payload from staging once (bulk
     # copies into shared memory, where both of its passes read it) and writes
     # the streams, plus 16 B of stream offset and length per entry:
@@ -969,7 +996,7 @@ def run_codec(args):
     line = {"workload": "codec: c2 layout (256 allocs = 4 GiB, 64 KiB chunks, 10% hot set), contents "
                         "fp32 N(0,1) / bf16 N(0,1) / zeros / uniform bytes; plain vs CRZ1-coded images",
             "tracked_bytes": B, "n_chunks": n, "steps": steps, "roofline": roofline, "rows": rows,
-            "encoder_launches": encoder, "gpu_launches": launches, "clocks": clocks,
+            "encoder_launches": encoder, "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu,
             "arena_growth": {k: mem1[k] - mem0[k] for k in ("host_grow_events", "device_grow_events")},
             "note": "wall_ms includes the drain wait; full = a steady-state full checkpoint (every chunk "
                     "rewritten after a first, untimed one of uniform bytes); delta rows are medians over the steps; the restart "
