@@ -286,3 +286,40 @@ def test_coded_extreme_chunk_sizes(S, residency):
             assert np.array_equal(b.read(), w)
     finally:
         h.close()
+
+
+def test_deserialize_rejects_bad_coded_tables():
+    """Host-side checks of a coded image's tables: a stream longer than its
+    chunk, an empty stream, a payload that does not match the padded stream
+    lengths, an unknown flag bit."""
+    S = 4 * KIB
+    ora = O.OracleContext(S, lineage=1900, coded=True)
+    mem = [_contents("f32_normal", 9 * S + 100, 1), np.zeros(3 * S, np.uint8)]
+    for i, m in enumerate(mem):
+        ora.register(0x100000 * (i + 1), m.size)
+    good = ora.checkpoint(mem)
+    im = O.parse_image(good)
+    zoff = len(good) - len(im.payload) - 8 * im.k   # start of zlen[]
+
+    def patched(e, value):
+        b = bytearray(good)
+        b[zoff + 8 * e:zoff + 8 * e + 8] = int(value).to_bytes(8, "little")
+        return bytes(b)
+
+    lens = [O.chunk_len(im.allocs[int(np.searchsorted([t[4] for t in im.allocs], c, side="right") - 1)][2],
+                        c - im.allocs[int(np.searchsorted([t[4] for t in im.allocs], c, side="right") - 1)][4], S)
+            for c in im.idx.tolist()]
+    coded_e = next(e for e, z in enumerate(im.zlen.tolist()) if z < lens[e])
+    bad = [patched(0, lens[0] + 1),                      # longer than the chunk
+           patched(0, 0),                                # empty
+           patched(coded_e, int(im.zlen[coded_e]) + 16)]  # padded lengths no longer add up to the payload
+    flags = bytearray(good)
+    flags[12] |= 4                                       # unknown flag bit
+    bad.append(bytes(flags))
+    for b in bad:
+        with pytest.raises(C.CracError) as e:
+            C.crac_image_deserialize(b)
+        assert e.value.code == C.CRAC_ERR_CORRUPT
+    img = C.crac_image_deserialize(good)                 # the untouched image is accepted
+    assert C.crac_image_info(img)["raw_bytes"] == sum(lens)
+    C.crac_image_release(img)
