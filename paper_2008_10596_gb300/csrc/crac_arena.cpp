@@ -29,6 +29,7 @@ Arena &pinned_arena() {
 crac_status_t ensure_dev(DevBuf &b, size_t bytes) {
     bytes = std::max<size_t>(bytes, 256);
     if (b.cap >= bytes) return CRAC_OK;
+    if (b.borrowed) return CRAC_ERR_OOM;   // a lease cannot grow (and is not ours to free)
     if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
     if (b.p) {
         CK(cudaDeviceSynchronize());

@@ -652,6 +652,11 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         // Segments bounded by the staging capacity.
         uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
         cap = std::max(round_up(cap, 256), S);
+        // Coded images: the encoder's aligned bulk reads may pass the end of
+        // the payload by up to 15 bytes, so with a given staging capacity (a
+        // configured one, or a server lease that cannot grow) the segments
+        // leave 256 bytes of it free.
+        if ((c->cfg.flags & CRAC_FLAG_COMPRESS) && c->cfg.staging_bytes && cap >= S + 256) cap -= 256;
         const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
         uint64_t max_seg_chunks = 0, max_seg_bytes = 0;
         for (const Segment &sg : segs) {

@@ -277,6 +277,7 @@ Arena &pinned_arena();
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    bool borrowed = false;   // a server lease: never freed or replaced by ensure_dev
 };
 crac_status_t ensure_dev(DevBuf &b, size_t bytes);
 

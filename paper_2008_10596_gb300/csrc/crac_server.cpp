@@ -16,7 +16,7 @@ crac_status_t with_staging(crac_ctx *c, void *p, uint64_t bytes, F &&op) {
     const DevBuf saved = c->staging;
     const uint64_t saved_cfg = c->cfg.staging_bytes;
     if (p) {
-        c->staging = DevBuf{p, (size_t)bytes};
+        c->staging = DevBuf{p, (size_t)bytes, true};
         c->cfg.staging_bytes = bytes;
     }
     const crac_status_t st = op();
@@ -222,6 +222,9 @@ crac_status_t crac_server_submit(crac_server_t *sv, crac_ctx_t *ctx, uint32_t ty
             lease = q->r.tracked_bytes;
         if (type == CRAC_REQ_RESTART && image->residency == CRAC_RESIDENCY_HOST) lease = q->r.tracked_bytes;
         if (lease) lease = std::max(round_up(std::min(lease, sv->max_lease), 256), round_up(S, 256));
+        // coded images: a segment leaves 256 bytes of the lease for the
+        // encoder's aligned reads, so the lease holds at least a chunk more
+        if (lease && (ctx->cfg.flags & CRAC_FLAG_COMPRESS)) lease = std::max(lease, round_up(S, 256) + 256);
         if (lease > sv->budget) {
             delete q;
             return CRAC_ERR_INVALID_ARG;

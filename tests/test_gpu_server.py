@@ -4,7 +4,8 @@ the same request sequence twice -- once alone (each request waited for
 before the next is submitted, one context at a time) and once in the mix
 (all contexts at once, four workers, a staging budget that forces requests
 to wait for leases) -- and every image and the restored memory must be
-identical byte for byte, and equal to the oracle's."""
+identical byte for byte, and equal to the oracle's.  Two of the contexts
+make coded images (CRAC_FLAG_COMPRESS) of fp32 contents."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +22,7 @@ S = 64 * KIB
 SIZES = [[3 * 1024 * KIB + 5, 700 * KIB], [8 * 1024 * KIB], [123457, 2 * 1024 * KIB, 64 * KIB],
          [5 * 1024 * KIB + 64 * KIB], [1024 * KIB, 1024 * KIB + 7, 300 * KIB, 4096]]
 PLAN = ["c", "c", "c", "r", "c"]     # checkpoints, restart from the latest image, one more checkpoint
+CODED = (1, 3)                       # contexts whose images are coded
 
 
 class Proc:
@@ -29,11 +31,14 @@ class Proc:
     def __init__(self, i, sizes):
         self.i = i
         self.sizes = sizes
-        self.bufs = [torch.from_numpy(W.host_contents("u32_xorshift", n, 700 + 10 * i + j)).to("cuda")
+        coded = i in CODED
+        kind = "f32_normal" if coded else "u32_xorshift"
+        self.bufs = [torch.from_numpy(W.host_contents(kind, n, 700 + 10 * i + j)).to("cuda")
                      for j, n in enumerate(sizes)]
         self.stream = torch.cuda.Stream()
-        self.ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=600 + i))
-        self.ora = O.OracleContext(S, lineage=600 + i)
+        self.ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=600 + i,
+                                                          flags=C.CRAC_FLAG_COMPRESS if coded else 0))
+        self.ora = O.OracleContext(S, lineage=600 + i, coded=coded)
         for b, n in zip(self.bufs, sizes):
             C.crac_ctx_register_alloc(self.ctx, b.data_ptr(), n)
             self.ora.register(b.data_ptr(), n)
@@ -129,8 +134,9 @@ def test_server_results_alone_equal_mixed_and_oracle():
             assert np.array_equal(x, y)
     # the images of the mixed run against the oracle, replaying the same plan
     for i, sizes in enumerate(SIZES):
-        ora = O.OracleContext(S, lineage=600 + i)
-        host = [W.host_contents("u32_xorshift", n, 700 + 10 * i + j) for j, n in enumerate(sizes)]
+        ora = O.OracleContext(S, lineage=600 + i, coded=i in CODED)
+        kind_i = "f32_normal" if i in CODED else "u32_xorshift"
+        host = [W.host_contents(kind_i, n, 700 + 10 * i + j) for j, n in enumerate(sizes)]
         for j, n in enumerate(sizes):
             ora.register((i + 1) << 40 | (j << 32), n)
         first = W.chunk_layout(sizes, S)
@@ -144,6 +150,9 @@ def test_server_results_alone_equal_mixed_and_oracle():
                 want = O.parse_image(imgs[-1])
                 assert got.fp.tolist() == want.fp.tolist() and got.idx.tolist() == want.idx.tolist()
                 assert bytes(got.payload) == bytes(want.payload) and got.epoch == want.epoch
+                assert got.coded == want.coded == (i in CODED)
+                if got.coded:
+                    assert got.zlen.tolist() == want.zlen.tolist()
                 k += 1
             else:
                 host = ora.restart(imgs)
