@@ -536,9 +536,12 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
 // (at 100% dirty 4 KiB pages and 64 KiB chunks: sparse 0.94, TMA 0.72, LDG
 // 0.69, split 0.66 of the HBM peak), the best one the images and sizes allow.
 uint32_t resolve_pass_kernel(const crac_ctx *c, bool dev_res, bool all16) {
+    const bool coded = (c->cfg.flags & CRAC_FLAG_COMPRESS) != 0;
+    // the encoder reads a compact payload, which the sparse pass does not leave
+    if (c->cfg.pass_kernel == CRAC_PASS_SPARSE && coded) return CRAC_PASS_SPLIT;
     if (c->cfg.pass_kernel != CRAC_PASS_AUTO) return c->cfg.pass_kernel;
     if (!c->delta_frac_valid || c->delta_frac <= 0.5f) return CRAC_PASS_SPLIT;
-    if (dev_res && all16 && !(c->cfg.flags & CRAC_FLAG_COMPRESS)) return CRAC_PASS_SPARSE;
+    if (dev_res && all16 && !coded) return CRAC_PASS_SPARSE;
     if (c->log2S >= 10 && c->log2S <= 16) return CRAC_PASS_TMA;
     return CRAC_PASS_LDG;
 }

@@ -132,6 +132,7 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
                        (uint32_t)CRAC_PASS_SPARSE}) {
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
         if (v == CRAC_PASS_SPARSE && t->cfg.image_residency != CRAC_RESIDENCY_DEVICE) continue;
+        if (v == CRAC_PASS_SPARSE && (t->cfg.flags & CRAC_FLAG_COMPRESS)) continue;   // needs a compact payload
         t->cfg.pass_kernel = v;
         float bestm = 0;
         const bool ldg_tiles = v == CRAC_PASS_LDG && saved_cpt == 0;

@@ -148,3 +148,43 @@ def test_tune_mostly_dirty_device_images_times_every_kernel():
         for i in imgs:
             C.crac_image_release(i)
         C.crac_ctx_destroy(ctx)
+
+
+def test_tune_coded_context_never_picks_sparse():
+    """A coded context (CRAC_FLAG_COMPRESS, device images, mostly dirty pages,
+    where the sparse pass would otherwise be a candidate): apply times the
+    other kernels only, and the retuned context's coded images equal the
+    oracle's."""
+    sizes = [4 * 1024 * KIB, 2 * 1024 * KIB + 16 * 7]
+    bufs = [torch.from_numpy(W.host_contents("f32_normal", n, 650 + i)).to("cuda") for i, n in enumerate(sizes)]
+    ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=64 * KIB, lineage=46,
+                                                  image_residency=C.CRAC_RESIDENCY_DEVICE,
+                                                  flags=C.CRAC_FLAG_COMPRESS))
+    stream = torch.cuda.current_stream()
+    imgs = []
+    try:
+        for b, n in zip(bufs, sizes):
+            C.crac_ctx_register_alloc(ctx, b.data_ptr(), n)
+        cands = [4 * KIB, 64 * KIB]
+        C.crac_ctx_tune_observe(ctx, cands, stream)
+        all_pages = [(a, p) for a in range(len(sizes)) for p in range(-(-sizes[a] // PAGE))]
+        for rnd in range(2):
+            _mutate_pages(bufs, sizes, all_pages, 210 + rnd)
+            C.crac_ctx_tune_observe(ctx, cands, stream)
+        res = C.crac_ctx_tune_apply(ctx, 0.0, stream)
+        assert res["variant_ms"][C.CRAC_PASS_SPARSE] == 0
+        assert res["chosen_pass_kernel"] != C.CRAC_PASS_SPARSE
+        ora = O.OracleContext(res["chosen_chunk_bytes"], lineage=46, coded=True)
+        for b, n in zip(bufs, sizes):
+            ora.register(b.data_ptr(), n)
+        for rnd in range(2):
+            img = C.crac_ctx_checkpoint(ctx, stream)
+            imgs.append(img)
+            C.crac_image_wait(img)
+            assert C.crac_image_serialize(img) == ora.checkpoint([b.cpu().numpy() for b in bufs])
+            _mutate_pages(bufs, sizes, all_pages[::3], 310 + rnd)
+    finally:
+        torch.cuda.synchronize()
+        for i in imgs:
+            C.crac_image_release(i)
+        C.crac_ctx_destroy(ctx)
