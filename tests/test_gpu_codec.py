@@ -323,3 +323,43 @@ def test_deserialize_rejects_bad_coded_tables():
     img = C.crac_image_deserialize(good)                 # the untouched image is accepted
     assert C.crac_image_info(img)["raw_bytes"] == sum(lens)
     C.crac_image_release(img)
+
+
+@pytest.mark.parametrize("base_coded", [True, False])
+def test_mixed_coded_and_plain_chain(base_coded):
+    """A chain whose base is coded and delta plain (or the reverse), written
+    by the oracle and deserialized: the restore decodes the coded pieces and
+    copies the plain ones in the same launch."""
+    S = 4 * KIB
+    h = Harness(S, lineage=2000 + base_coded)
+    try:
+        _fill(h, S, seed=90)
+        mem0 = h.host()
+        ora = O.OracleContext(S, lineage=7000 + base_coded, coded=base_coded)
+        for b in h.bufs:
+            ora.register(b.ptr, b.nbytes, b.kind)
+        chain = [ora.checkpoint(mem0)]
+        ora.coded = not base_coded
+        mem1 = [m.copy() for m in mem0]
+        mem1[0][: 2 * S] = 0
+        mem1[2][S:S + 100] ^= 0x77
+        chain.append(ora.checkpoint(mem1))
+        assert O.parse_image(chain[0]).coded == base_coded and O.parse_image(chain[1]).coded != base_coded
+        imgs = [C.crac_image_deserialize(b) for b in chain]
+        try:
+            for b in h.bufs:
+                b.zero()
+            h2 = Harness(S, lineage=7000 + base_coded)
+            try:
+                for b in h.bufs:
+                    C.crac_ctx_register_alloc(h2.ctx, b.ptr, b.nbytes, b.kind)
+                C.crac_ctx_restart(h2.ctx, imgs[-1], h2.stream)
+                for b, w in zip(h.bufs, mem1):
+                    assert np.array_equal(b.read(), w)
+            finally:
+                h2.close()
+        finally:
+            for i in imgs:
+                C.crac_image_release(i)
+    finally:
+        h.close()
