@@ -4,6 +4,7 @@ import os
 import numpy as np
 import pytest
 
+from oracle import crz
 from oracle import fp_bigint
 from oracle import oracle as O
 from tests.golden import make_golden as G
@@ -41,3 +42,18 @@ def _flip_mask():
     m[36] = 0x80
     m[37 + 70] = 0x01
     return m
+
+
+def test_crz_vectors():
+    rows = [line.split() for line in open(os.path.join(HERE, "crz_vectors.txt")).read().splitlines()]
+    assert [(c, int(s), int(n)) for c, s, n, _ in rows] == G.CRZ_CASES
+    for content, seed, n, hexz in rows:
+        raw = G.crz_input(content, int(seed), int(n))
+        z = bytes.fromhex(hexz)
+        assert crz.encode(raw) == z
+        assert crz.decode(z, int(n)) == raw
+        if content in ("u32_xorshift",):
+            assert z == raw            # incompressible: stored as itself
+        if content == "zeros":             # zero header words, padded, then the zero tail
+            nb = int(n) // 512
+            assert z == bytes(16 * (-(-nb // 2)) + int(n) % 512)
