@@ -175,7 +175,9 @@ typedef struct crac_config {
  *   kernel, reading host images in place; a context that has to stage its
  *   host restores (no unified addressing) cannot restore coded images
  *   (CRAC_ERR_UNSUPPORTED).  Images carry CRAC_IMAGE_CODED.  Not with
- *   CRAC_PASS_SPARSE. */
+ *   CRAC_PASS_SPARSE, whose payload is not compacted (rejected at creation;
+ *   the autotuner never picks it for a coded context).  Under the request
+ *   server a coded context's lease is at least one chunk plus 256 bytes. */
 #define CRAC_FLAG_COMPRESS 8u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
