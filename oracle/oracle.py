@@ -126,13 +126,34 @@ def fp64(chunk) -> int:
     return int(_load().oracle_fp64(a.ctypes.data, a.size))
 
 
-def fp_chunks(buf: np.ndarray, chunk_bytes: int) -> np.ndarray:
-    """Fingerprints of every chunk of one allocation's bytes."""
+def fp_chunks(buf: np.ndarray, chunk_bytes: int, workers: int = 1) -> np.ndarray:
+    """Fingerprints of every chunk of one allocation's bytes.
+
+    Chunks are independent, so with workers > 1 the chunk list is cut into
+    that many contiguous runs of whole chunks and each run goes through the
+    same C loop on its own thread (the C call releases the GIL); the result
+    is the same array."""
     a = np.ascontiguousarray(buf, dtype=np.uint8)
     n = -(-a.size // chunk_bytes)
     out = np.empty(n, dtype=np.uint64)
-    if n:
-        _load().oracle_fp_chunks(a.ctypes.data, a.size, chunk_bytes, out.ctypes.data)
+    if n == 0:
+        return out
+    lib = _load()
+    workers = max(1, min(int(workers), n))
+    if workers == 1:
+        lib.oracle_fp_chunks(a.ctypes.data, a.size, chunk_bytes, out.ctypes.data)
+        return out
+    bounds = [n * w // workers for w in range(workers + 1)]
+
+    def run(w):
+        c0, c1 = bounds[w], bounds[w + 1]
+        lo, hi = c0 * chunk_bytes, min(c1 * chunk_bytes, a.size)
+        if c1 > c0:
+            lib.oracle_fp_chunks(a.ctypes.data + lo, hi - lo, chunk_bytes, out.ctypes.data + 8 * c0)
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(run, range(workers)))
     return out
 
 
@@ -216,10 +237,11 @@ class _Alloc:
 class OracleContext:
     """One simulated process: its active-allocation table and last fingerprints."""
 
-    def __init__(self, chunk_bytes: int, lineage: int = 1, coded: bool = False):
+    def __init__(self, chunk_bytes: int, lineage: int = 1, coded: bool = False, workers: int = 1):
         if chunk_bytes < 16 or chunk_bytes & (chunk_bytes - 1):
             raise InvalidArg("chunk_bytes must be a power of two >= 16")
         self.S = int(chunk_bytes)
+        self.workers = int(workers)   # threads for the per-chunk fingerprint loop
         self.coded = bool(coded)   # images store CRZ1 streams (crz.py)
         self.lineage = int(lineage)
         self.allocs: list[_Alloc] = []
@@ -257,60 +279,91 @@ class OracleContext:
         """Image of the active allocations; contents[i] = bytes of allocs[i]."""
         if len(contents) != len(self.allocs):
             raise InvalidArg("one content buffer per registered allocation")
+        fps, idxs, zlens, pieces = [], [], [], []
+
+        def keep(i, fa, ids, chunk_pieces, zlen):
+            fps.append(fa)
+            idxs.append(ids)
+            pieces.extend(chunk_pieces)
+            if zlen is not None:
+                zlens.append(zlen)
+
+        head = self.checkpoint_by_alloc(lambda i: contents[i], keep)
+        # 6: header and allocation table, fingerprints, chunk list, (stream
+        # lengths), payload.
+        out = [head, np.concatenate(fps + [np.empty(0, np.uint64)]).astype("<u8").tobytes(),
+               np.concatenate(idxs + [np.empty(0, np.uint64)]).astype("<u8").tobytes()]
+        if self.coded:
+            out.append(np.concatenate(zlens + [np.empty(0, np.uint64)]).astype("<u8").tobytes())
+        out.append(b"".join(pieces))
+        return b"".join(out)
+
+    def checkpoint_by_alloc(self, read, visit) -> bytes:
+        """The checkpoint, one allocation at a time, in registration order.
+
+        read(i) returns the bytes of allocs[i]; each allocation is read once.
+        For each one, visit(i, fp, ids, pieces, zlen) receives its
+        fingerprints, the global ids of its dirty chunks (ascending), those
+        chunks' payload pieces in that order, and (coded images) their
+        stream lengths, else None.  The image is the header and allocation
+        table this method returns, followed by the concatenation over
+        allocations of every fp, then of every ids, (then of every zlen),
+        then of every piece; checkpoint() assembles exactly that.  The new
+        baseline is committed only after the last allocation.
+        """
         S = self.S
         first = self.layout()
         n = int(first[-1])
-        fp_new = np.empty(n, dtype=np.uint64)
-        dirty = np.empty(n, dtype=bool)
-        bufs = []
-        # 1-3: fingerprint every chunk, compare with the previous table of the
-        # same allocation id; an allocation with no valid table is all dirty.
+        fp_next = {}
+        k = 0
+        payload_bytes = 0
         for i, a in enumerate(self.allocs):
-            buf = np.ascontiguousarray(np.asarray(contents[i]).view(np.uint8).reshape(-1))
+            buf = np.ascontiguousarray(np.asarray(read(i)).view(np.uint8).reshape(-1))
             if buf.size != a.bytes:
                 raise InvalidArg("content size differs from registered size")
-            bufs.append(buf)
-            lo, hi = int(first[i]), int(first[i + 1])
-            fa = fp_chunks(buf, S)
-            fp_new[lo:hi] = fa
+            # 1-3: fingerprint every chunk, compare with the previous table of
+            # the same allocation id; an allocation with no valid table is all
+            # dirty.
+            fa = fp_chunks(buf, S, self.workers)
             prev = self.fp_valid.get(a.id)
-            dirty[lo:hi] = True if prev is None else (fa != prev)
-        # 4: ascending dirty ids; byte offsets are the exclusive prefix sum of
-        # the chunks' actual (unpadded) lengths.
-        idx = np.flatnonzero(dirty).astype(np.uint64)
-        alloc_of = np.searchsorted(first, idx.astype(np.int64), side="right") - 1
-        pieces = []
-        for c, a in zip(idx.tolist(), alloc_of.tolist()):
-            local = c - int(first[a])
-            lo = local * S
-            pieces.append(bufs[a][lo:lo + chunk_len(self.allocs[a].bytes, local, S)].tobytes())
-        # 5: payload = dirty chunk bytes in idx order (coded: their CRZ1
-        # streams, each zero-padded to 16 bytes).
-        zlen = None
-        if self.coded:
-            streams = [crz.encode(np.frombuffer(c, dtype=np.uint8)) for c in pieces]
-            zlen = np.array([len(z) for z in streams], dtype=np.uint64)
-            pieces = [z + bytes(crz.padded(len(z)) - len(z)) for z in streams]
-        payload = b"".join(pieces)
-        k = int(idx.size)
+            dirty = np.ones(fa.size, dtype=bool) if prev is None else (fa != prev)
+            # 4: ascending dirty ids (global ids are consecutive across
+            # allocations); byte offsets are the running sum of the chunks'
+            # actual (unpadded) lengths.
+            local = np.flatnonzero(dirty)
+            ids = (int(first[i]) + local).astype(np.uint64)
+            # 5: payload = dirty chunk bytes in id order (coded: their CRZ1
+            # streams, each zero-padded to 16 bytes).
+            chunk_pieces = [buf[c * S:c * S + chunk_len(a.bytes, c, S)].tobytes() for c in local.tolist()]
+            zlen = None
+            if self.coded:
+                streams = [crz.encode(np.frombuffer(c, dtype=np.uint8)) for c in chunk_pieces]
+                zlen = np.array([len(z) for z in streams], dtype=np.uint64)
+                chunk_pieces = [z + bytes(crz.padded(len(z)) - len(z)) for z in streams]
+            visit(i, fa, ids, chunk_pieces, zlen)
+            fp_next[a.id] = fa
+            k += int(local.size)
+            payload_bytes += sum(len(c) for c in chunk_pieces)
         flags = (FLAG_FULL if k == n else 0) | (FLAG_CODED if self.coded else 0)
         epoch = self.epoch + 1
-        # 6: serialize.
+        # 6: header and allocation table.
         out = [HEADER.pack(MAGIC, VERSION, flags, S, HASH_ID, self.lineage, epoch,
-                           self.last_epoch, len(self.allocs), n, k, len(payload))]
+                           self.last_epoch, len(self.allocs), n, k, payload_bytes)]
         for i, a in enumerate(self.allocs):
             out.append(ALLOC.pack(a.id, a.ptr, a.bytes, a.kind, 0, int(first[i])))
-        out.append(fp_new.astype("<u8").tobytes())
-        out.append(idx.astype("<u8").tobytes())
-        if zlen is not None:
-            out.append(zlen.astype("<u8").tobytes())
-        out.append(payload)
         # 7: commit the new baseline.
-        self.fp_valid = {a.id: fp_new[int(first[i]):int(first[i + 1])].copy()
-                         for i, a in enumerate(self.allocs)}
+        self.fp_valid = fp_next
         self.epoch = epoch
         self.last_epoch = epoch
         return b"".join(out)
+
+    def set_chunk_bytes(self, chunk_bytes: int) -> None:
+        """Switch to another chunk size.  The previous fingerprints describe
+        other chunks, so they are dropped: the next image is FULL."""
+        if chunk_bytes < 16 or chunk_bytes & (chunk_bytes - 1):
+            raise InvalidArg("chunk_bytes must be a power of two >= 16")
+        self.S = int(chunk_bytes)
+        self.fp_valid = {}
 
     # -- restart ------------------------------------------------------------
     def restart(self, chain: list) -> list:

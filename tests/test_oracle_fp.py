@@ -135,3 +135,16 @@ def test_zero_word_term_is_not_zero():
     t = fp_bigint.word_terms(b"\0" * 16)
     assert all(v != 0 for v in t)
     assert fp_bigint.fp64(b"\0" * 8) != fp_bigint.finalize(sum(t) % (1 << 64), 8)
+
+
+@pytest.mark.parametrize("workers", [2, 3, 7, 64])
+def test_fp_chunks_split_over_threads_is_the_same_table(workers):
+    """The per-chunk loop cut into runs over threads: every fingerprint is
+    still the one-chunk definition (brute force, chunk by chunk, through the
+    big-integer restatement), ragged tail included, also with more threads
+    than chunks."""
+    for n, S in [(10 * 64 + 13, 64), (5 * 256, 256), (40, 16), (3, 4096)]:
+        buf = np.random.default_rng(4000 + n).integers(0, 256, size=n, dtype=np.uint8)
+        got = O.fp_chunks(buf, S, workers=workers)
+        want = [fp_bigint.fp64(buf[c * S:(c + 1) * S].tobytes()) for c in range(-(-n // S))]
+        assert got.tolist() == want

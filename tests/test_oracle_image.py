@@ -233,3 +233,66 @@ def test_offsets_and_counts_invariants():
     assert sum(lens) == len(img.payload)
     assert img.n_chunks == int(first[-1])
     assert np.all(np.diff(img.idx.astype(np.int64)) > 0)
+
+
+def test_by_alloc_reads_each_allocation_once_and_commits_last():
+    """checkpoint_by_alloc reads every allocation once, in registration
+    order, and hands out per-allocation parts that line up with the image's
+    sections; a failure part way leaves the baseline as it was (the next
+    image is still a delta against the last committed one)."""
+    sizes = [5000, 1, 4096 * 3, 777]
+    S = 1024
+    bufs = _mk(sizes, seed=11)
+    ref = _ctx(sizes, S)
+    ctx = _ctx(sizes, S)
+    img0 = O.parse_image(ref.checkpoint(bufs))
+    reads, parts = [], []
+    head = ctx.checkpoint_by_alloc(lambda i: (reads.append(i), bufs[i])[1],
+                                   lambda i, fa, ids, pcs, zl: parts.append((i, fa, ids, pcs, zl)))
+    assert reads == list(range(len(sizes)))
+    assert head == ref_head(img0, sizes, S)
+    first = W.chunk_layout(sizes, S)
+    assert np.concatenate([p[1] for p in parts]).tolist() == img0.fp.tolist()
+    for i, fa, ids, pcs, zl in parts:
+        assert fa.size == first[i + 1] - first[i] and zl is None
+        assert ids.tolist() == list(range(int(first[i]), int(first[i + 1])))   # first image: every chunk
+        assert b"".join(pcs) == bufs[i].tobytes()
+    # mutate one chunk; fail while reading allocation 2: nothing committed
+    bufs[3] = bufs[3].copy()
+    bufs[3][5] ^= 1
+
+    def bad(i):
+        if i == 2:
+            raise RuntimeError("read failed")
+        return bufs[i]
+    with pytest.raises(RuntimeError):
+        ctx.checkpoint_by_alloc(bad, lambda *a: None)
+    img1 = O.parse_image(ctx.checkpoint(bufs))
+    assert img1.epoch == 2 and img1.parent_epoch == 1
+    assert img1.idx.tolist() == [int(first[3])]
+
+
+def ref_head(img, sizes, S):
+    """Header and allocation table of a parsed image, re-packed field by field."""
+    out = [O.HEADER.pack(O.MAGIC, 1, img.flags, S, 1, img.lineage, img.epoch, img.parent_epoch,
+                         len(img.allocs), img.n_chunks, img.k, len(img.payload))]
+    for a in img.allocs:
+        out.append(O.ALLOC.pack(a[0], a[1], a[2], a[3], 0, a[4]))
+    return b"".join(out)
+
+
+def test_chunk_size_switch_makes_the_next_image_full():
+    """After set_chunk_bytes the previous fingerprints describe other chunks:
+    the next image holds every chunk (closed form: the concatenation of the
+    allocations) at the new size, and the epoch chain continues."""
+    sizes = [70000, 3000]
+    bufs = _mk(sizes, seed=21)
+    ctx = _ctx(sizes, 4096)
+    ctx.checkpoint(bufs)
+    ctx.set_chunk_bytes(65536)
+    img = O.parse_image(ctx.checkpoint(bufs))
+    assert img.full and img.chunk_bytes == 65536 and img.epoch == 2 and img.parent_epoch == 1
+    assert img.n_chunks == 2 + 1
+    assert bytes(img.payload) == b"".join(b.tobytes() for b in bufs)
+    again = O.parse_image(ctx.checkpoint(bufs))
+    assert again.k == 0
