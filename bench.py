@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -59,35 +60,68 @@ def restore_flags(args) -> int:
     return f | (C.CRAC_FLAG_DIRECT_DRAIN if getattr(args, "direct_drain", False) else 0)
 
 
-def kernel_src_sha() -> str:
-    """sha256 prefix over the device sources (every .cu and .cuh of the library
-    in name order, the test mutators excepted): what an ncu summary was
-    captured against."""
+KERNEL_UNITS = ("crac_pass_split.cu", "crac_pass_fused.cu", "crac_pass_tma.cu", "crac_pass_per_alloc.cu",
+                "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu")
+
+
+def kernel_src_sha(unit: str | None = None, read=None) -> str:
+    """sha256 prefix over device sources: with `unit` (a .cu file of the
+    library), that file and the device headers it includes; without, every
+    .cu and .cuh of the library in name order, the test mutators excepted.
+    It is what an ncu summary was captured against.  `read(name)` returns a
+    source file's bytes (default: the working tree)."""
     import glob
     import hashlib
-    h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2008_10596_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        if os.path.basename(f) == "crac_testkit.cu":
-            continue
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    if read is None:
+        def read(name):
+            return open(os.path.join(csrc, name), "rb").read()
+    if unit is None:
+        names = sorted(os.path.basename(f) for f in glob.glob(os.path.join(csrc, "*.cu")) +
+                       glob.glob(os.path.join(csrc, "*.cuh")))
+        names = [f for f in names if f != "crac_testkit.cu"]
+    else:
+        names, todo = set(), [unit]
+        while todo:
+            f = todo.pop()
+            if f in names:
+                continue
+            names.add(f)
+            todo += [x.decode() for x in re.findall(rb'#include "([^"]+\.cuh)"', read(f))]
+        names = sorted(names)
+    h = hashlib.sha256()
+    for f in names:
+        h.update(f.encode())
+        h.update(read(f))
     return h.hexdigest()[:16]
+
+
+SHA_LINE = re.compile(r"Kernel source sha256 prefix at capture: `([0-9a-f]+)`(?: \(([\w.]+\.cu) and the device headers it includes\))?")
+
+
+def summary_sha_ok(text: str):
+    """(captured sha, current sha) of an ncu summary: per translation unit
+    where the summary names one, else over every device source."""
+    m = SHA_LINE.search(text)
+    if not m:
+        return None
+    return m.group(1), kernel_src_sha(m.group(2))
 
 
 def profile_traffic(kernel_tag: str):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches the kernel source."""
-    sha = kernel_src_sha()
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
         return None
+    text = open(path).read()
+    shas = summary_sha_ok(text)
+    if shas is None or shas[0] != shas[1]:
+        return None
     fields = {}
-    for line in open(path):
+    for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_src_sha") != sha:
-        return None
     try:
         return int(fields["traffic_bytes_per_launch"])
     except (KeyError, ValueError):

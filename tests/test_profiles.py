@@ -27,12 +27,28 @@ def test_every_summary_gives_its_command():
 
 
 def test_summaries_match_the_kernel_sources():
-    sha = bench.kernel_src_sha()
+    """Each summary names the translation unit it was captured from, and its
+    hash equals that unit's (and its device headers') current hash."""
     for f in _summaries():
         s = open(os.path.join(PROFILES, f)).read()
-        m = re.search(r"Kernel source sha256 prefix at capture: `([0-9a-f]+)`", s)
-        if m:
-            assert m.group(1) == sha, f"{f} was captured from other kernel sources"
+        shas = bench.summary_sha_ok(s)
+        if shas is None:
+            continue
+        unit = bench.SHA_LINE.search(s).group(2)
+        assert unit in bench.KERNEL_UNITS, f"{f} names no kernel translation unit"
+        assert shas[0] == shas[1], f"{f} was captured from other {unit} sources"
+
+
+def test_unit_hash_follows_its_headers():
+    """A unit's hash covers the headers it includes: every kernel unit's hash
+    differs from the hash of the unit's own file alone."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2008_10596_gb300", "csrc")
+    for u in bench.KERNEL_UNITS:
+        h = hashlib.sha256()
+        h.update(u.encode())
+        h.update(open(os.path.join(csrc, u), "rb").read())
+        assert bench.kernel_src_sha(u) != h.hexdigest()[:16], u
 
 
 def test_traffic_read_by_the_bench():
