@@ -357,6 +357,10 @@ class OracleContext:
         self.last_epoch = epoch
         return b"".join(out)
 
+    def invalidate(self) -> None:
+        """Forget the baseline: the next image holds every chunk (FULL)."""
+        self.fp_valid = {}
+
     def set_chunk_bytes(self, chunk_bytes: int) -> None:
         """Switch to another chunk size.  The previous fingerprints describe
         other chunks, so they are dropped: the next image is FULL."""

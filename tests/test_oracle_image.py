@@ -296,3 +296,18 @@ def test_chunk_size_switch_makes_the_next_image_full():
     assert bytes(img.payload) == b"".join(b.tobytes() for b in bufs)
     again = O.parse_image(ctx.checkpoint(bufs))
     assert again.k == 0
+
+
+def test_invalidate_makes_the_next_image_full():
+    """Without a baseline every chunk is saved again: the payload is the
+    concatenation of the allocations (closed form), and the epoch chain
+    continues from the last image."""
+    sizes = [9000, 4096]
+    bufs = _mk(sizes, seed=31)
+    ctx = _ctx(sizes, 4096)
+    ctx.checkpoint(bufs)
+    assert O.parse_image(ctx.checkpoint(bufs)).k == 0
+    ctx.invalidate()
+    img = O.parse_image(ctx.checkpoint(bufs))
+    assert img.full and img.epoch == 3 and img.parent_epoch == 2
+    assert bytes(img.payload) == b"".join(b.tobytes() for b in bufs)
