@@ -284,6 +284,11 @@ CRAC_API crac_status_t crac_ctx_free(crac_ctx_t *ctx, void *ptr);
  * The first checkpoint of an allocation carries all of its chunks; later
  * ones carry only chunks whose fingerprint changed.  *image_out receives a
  * new reference that the caller releases with crac_image_release.
+ * A device wait that runs out gives CRAC_ERR_TIMEOUT with the baseline
+ * untouched.  If a kernel reports that a bulk copy into its shared memory
+ * never completed, even after it waited for it in bounded rounds, the
+ * device's state is unspecified: the call returns CRAC_ERR_CUDA and the
+ * context refuses every later checkpoint and restart with CRAC_ERR_CUDA.
  */
 CRAC_API crac_status_t crac_ctx_checkpoint(crac_ctx_t *ctx, crac_stream_t stream,
                                            crac_image_t **image_out);
@@ -296,11 +301,19 @@ CRAC_API crac_status_t crac_ctx_checkpoint(crac_ctx_t *ctx, crac_stream_t stream
  * the image's allocation table in count, sizes, kinds and order, and the
  * context's chunk size must equal the image's; otherwise
  * CRAC_ERR_IMAGE_MISMATCH and device memory is untouched.  Work is enqueued
- * on `stream` (NULL: device-wide sync first); the call returns after
- * enqueueing.  The images stay referenced by the context until that work has
- * completed.  Afterwards the image's fingerprints are the baseline for the
- * next checkpoint (so an unmodified checkpoint is empty), and the registered
- * allocations take the image's allocation identities.
+ * on `stream` (NULL: device-wide sync first), after all work enqueued there
+ * before the call.  The call then waits on the host until that work has
+ * finished: the registry adopts the image (its fingerprints become the
+ * baseline, its allocation identities the registry's) only once the
+ * restore's error word says it succeeded, so a failed restore never leaves
+ * a baseline that does not describe memory.  Afterwards an unmodified
+ * checkpoint is empty.
+ * Errors found on the device: a chunk of the target no chain image holds
+ * (CRAC_ERR_IMAGE_MISMATCH; memory untouched, the scatter does not start);
+ * a coded stream whose plane values pass 255, which only decoding finds
+ * (CRAC_ERR_CORRUPT; the allocations' contents are then unspecified, the
+ * context's baseline is unchanged).  Coded streams of deserialized images
+ * are checked for impossible headers when they are deserialized.
  */
 CRAC_API crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image,
                                         crac_stream_t stream);
@@ -430,6 +443,18 @@ CRAC_API crac_status_t crac_ctx_tune_apply(crac_ctx_t *ctx, crac_stream_t stream
  * (a FULL image, which cuts the delta chain). */
 CRAC_API crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx);
 
+/* Let go of the context's own reference to its newest image (a checkpoint's
+ * image, or the image a restart restored), keeping the fingerprint baseline:
+ * the next checkpoint is still a delta against the state that image holds,
+ * but it no longer keeps that image alive.  Such a delta finds its parent by
+ * (lineage, parent_epoch) among loaded images when it is restored, as a
+ * deserialized delta does, so its chain restores only while the parent (or a
+ * deserialized copy of it) is loaded.  For callers that write each image out
+ * (crac_image_read, crac_image_serialize) and release it, so that memory
+ * holds only the newest image -- the paper's images are files on disk
+ * (Sec. 3.2), not kept in memory. */
+CRAC_API crac_status_t crac_ctx_drop_history(crac_ctx_t *ctx);
+
 /* Measurements of the context's most recent checkpoint pass. */
 CRAC_API crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out);
 
@@ -484,8 +509,22 @@ CRAC_API crac_status_t crac_image_info(const crac_image_t *image, crac_image_inf
 CRAC_API crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap,
                                             size_t *need);
 
+/*
+ * Copy bytes [offset, offset + n) of the serialized form (the layout above)
+ * into host memory dst, without building the whole of it: a caller can write
+ * an image out piece by piece (the paper's checkpoint is a file that the
+ * saved regions are written into, Sec. 3.2 "Saving the library-allocated
+ * arena"), or check a multi-GiB image section by section.  Reading every
+ * range once gives exactly the bytes crac_image_serialize writes.  Waits for
+ * the drain first.  CRAC_ERR_INVALID_ARG if the range passes the end
+ * (crac_image_info's serialized_bytes) or dst is NULL with n > 0.
+ */
+CRAC_API crac_status_t crac_image_read(const crac_image_t *image, uint64_t offset, void *dst, size_t n);
+
 /* Parse a serialized image into a new host-resident image (CRAC_ERR_CORRUPT if
- * malformed).  A delta's parent is found among live images by (lineage,
+ * malformed: sizes, chunk list, stream lengths, or a coded stream whose block
+ * headers have reserved bits set, a plane width above 8, or a length that
+ * does not match them).  A delta's parent is found among live images by (lineage,
  * parent_epoch) when it is restored. */
 CRAC_API crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **out);
 
@@ -574,7 +613,8 @@ typedef struct crac_pass_totals {
  *
  * Works on the current device.  Inputs: regions_dev (n_regions entries,
  * device memory), n_chunks (their total chunk count), chunk_bytes (power of
- * two in [16, 2^24]), fp_old_dev (read where base_first != UINT64_MAX).
+ * two in [16, 2^24]), fp_old_dev (read where base_first != UINT64_MAX; may
+ * be NULL, and then no region has a baseline and every chunk is dirty).
  * Outputs (device memory): fp_new_dev[n_chunks]; idx_dev[idx_cap] ascending
  * dirty chunk ids; off_dev[idx_cap + 1] their byte offsets in staging (off[k]
  * = payload bytes); staging_dev[staging_cap]; *totals_dev.  Enqueued on

@@ -63,9 +63,9 @@ CRAC_FAULT_ENCODE_WAIT = 6
 
 EXPORTED = [
     "crac_config_default", "crac_ctx_create", "crac_ctx_destroy", "crac_ctx_register_alloc",
-    "crac_ctx_free", "crac_ctx_checkpoint", "crac_ctx_restart", "crac_ctx_invalidate",
+    "crac_ctx_free", "crac_ctx_checkpoint", "crac_ctx_restart", "crac_ctx_invalidate", "crac_ctx_drop_history",
     "crac_ctx_last_pass", "crac_register_alloc", "crac_free", "crac_checkpoint", "crac_restart",
-    "crac_image_wait", "crac_image_info", "crac_image_serialize", "crac_image_deserialize",
+    "crac_image_wait", "crac_image_info", "crac_image_serialize", "crac_image_read", "crac_image_deserialize",
     "crac_image_release", "crac_status_str", "crac_last_cuda_error", "crac_kernel_launches",
     "crac_alloc_managed", "crac_free_managed", "crac_debug_inject_fault", "crac_pass_noalloc",
     "crac_ctx_tune_observe", "crac_ctx_tune_apply", "crac_ctx_last_restart", "crac_time_now", "crac_server_create",
@@ -185,6 +185,7 @@ _sigs = {
     "crac_ctx_checkpoint": (_st, [_vp, _vp, ctypes.POINTER(_vp)]),
     "crac_ctx_restart": (_st, [_vp, _vp, _vp]),
     "crac_ctx_invalidate": (_st, [_vp]),
+    "crac_ctx_drop_history": (_st, [_vp]),
     "crac_ctx_last_pass": (_st, [_vp, ctypes.POINTER(CracPassInfo)]),
     "crac_register_alloc": (_st, [_vp, ctypes.c_size_t, ctypes.c_int]),
     "crac_free": (_st, [_vp]),
@@ -193,6 +194,7 @@ _sigs = {
     "crac_image_wait": (_st, [_vp, ctypes.c_uint64]),
     "crac_image_info": (_st, [_vp, ctypes.POINTER(CracImageInfo)]),
     "crac_image_serialize": (_st, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "crac_image_read": (_st, [_vp, ctypes.c_uint64, _vp, ctypes.c_size_t]),
     "crac_image_deserialize": (_st, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "crac_image_release": (_st, [_vp]),
     "crac_status_str": (ctypes.c_char_p, [_st]),
@@ -363,6 +365,10 @@ def crac_ctx_invalidate(ctx: int) -> None:
     _check(_lib.crac_ctx_invalidate(ctx), "crac_ctx_invalidate")
 
 
+def crac_ctx_drop_history(ctx: int) -> None:
+    _check(_lib.crac_ctx_drop_history(ctx), "crac_ctx_drop_history")
+
+
 def crac_ctx_last_pass(ctx: int, out: "CracPassInfo | None" = None):
     """The last pass's statistics as a dict; given `out` (a CracPassInfo), fills
     it and returns it unconverted (no per-field Python work, for timed loops)."""
@@ -413,6 +419,22 @@ def crac_image_serialize(image: int) -> bytes:
     buf = ctypes.create_string_buffer(need.value)
     _check(_lib.crac_image_serialize(image, buf, need.value, ctypes.byref(need)), "crac_image_serialize")
     return buf.raw
+
+
+def crac_image_read(image: int, offset: int, n: int, out=None):
+    """Bytes [offset, offset + n) of the serialized image.  With `out` (a
+    writable buffer of n bytes: bytearray, numpy array) fills it and returns
+    it; else returns bytes."""
+    if out is None:
+        buf = ctypes.create_string_buffer(max(n, 1))
+        _check(_lib.crac_image_read(image, offset, buf, n), "crac_image_read")
+        return buf.raw[:n]
+    mv = memoryview(out).cast("B")
+    if mv.nbytes != n or mv.readonly:
+        raise ValueError("out must be a writable buffer of n bytes")
+    addr = ctypes.addressof(ctypes.c_char.from_buffer(mv)) if n else None
+    _check(_lib.crac_image_read(image, offset, addr, n), "crac_image_read")
+    return out
 
 
 def crac_image_deserialize(data: bytes) -> int:

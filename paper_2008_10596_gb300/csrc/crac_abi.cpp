@@ -145,6 +145,14 @@ crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx) {
     return CRAC_OK;
 }
 
+crac_status_t crac_ctx_drop_history(crac_ctx_t *ctx) {
+    if (!ctx) return CRAC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    img_unref(ctx->parent);
+    ctx->parent = nullptr;
+    return CRAC_OK;
+}
+
 crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out) {
     if (!ctx || !out) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);

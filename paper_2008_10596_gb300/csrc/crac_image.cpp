@@ -191,39 +191,11 @@ static uint64_t get64(const uint8_t *p) {
 }
 
 namespace {
-// Compact payload of a sparse device piece: its dirty chunks, in list order,
-// taken from their uncompacted offsets.
-crac_status_t sparse_compact(const crac_image *im, const Piece &pc, uint8_t *out) {
-    std::vector<uint8_t> span(pc.span);
-    std::vector<uint64_t> off(pc.k);
-    CK(cudaMemcpy(span.data(), pc.dev.p, pc.span, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(off.data(), pc.off_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
-    const uint64_t *idx = (const uint64_t *)im->idx_h.p + pc.k0;
-    const uint32_t log2S = log2u(im->chunk_bytes);
-    uint64_t o = 0;
-    size_t a = 0;
-    for (uint64_t j = 0; j < pc.k; ++j) {
-        const uint64_t c = idx[j];   // ascending
-        while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= c) ++a;
-        const uint64_t len = chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
-        if (off[j] + len > pc.span || o + len > pc.bytes) return CRAC_ERR_CORRUPT;
-        std::memcpy(out + o, span.data() + off[j], len);
-        o += len;
-    }
-    return o == pc.bytes ? CRAC_OK : CRAC_ERR_CORRUPT;
-}
-}  // namespace
 
-crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
-    if (!image || !need) return CRAC_ERR_INVALID_ARG;
-    crac_image *im = const_cast<crac_image *>(image);
-    const uint64_t total = serialized_size(im);
-    *need = (size_t)total;
-    if (!dst) return CRAC_OK;
-    if (cap < total) return CRAC_ERR_INVALID_ARG;
-    TRY(img_wait(im, 0));
-    TRY(img_host_tables(im));
-    uint8_t *p = (uint8_t *)dst;
+// Header and allocation table of the serialized form.
+std::vector<uint8_t> image_prefix(const crac_image *im) {
+    std::vector<uint8_t> v(kHeaderBytes + kAllocEntryBytes * im->allocs.size());
+    uint8_t *p = v.data();
     std::memcpy(p, "CRACIMG1", 8);
     p += 8;
     put32(p, 1);
@@ -245,25 +217,138 @@ crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t 
         put32(p, 0);
         put64(p, a.first_chunk);
     }
-    if (im->n_chunks) std::memcpy(p, im->fp_h.p, 8 * im->n_chunks);
-    p += 8 * im->n_chunks;
-    if (im->k) std::memcpy(p, im->idx_h.p, 8 * im->k);
-    p += 8 * im->k;
-    if (im->flags & CRAC_IMAGE_CODED) {
-        if (im->k) std::memcpy(p, im->zlen_h.p, 8 * im->k);
-        p += 8 * im->k;
+    return v;
+}
+
+// A sparse device piece's host tables (span offset and compact offset of
+// every entry), made once per piece.
+crac_status_t sparse_tables(crac_image *im, Piece &pc) {
+    std::lock_guard<std::mutex> lk(im->mu);
+    if (!pc.sp_cum.empty()) return CRAC_OK;
+    std::vector<uint64_t> off(pc.k), cum(pc.k + 1);
+    if (pc.k) CK(cudaMemcpy(off.data(), pc.off_dev.p, pc.k * 8, cudaMemcpyDeviceToHost));
+    const uint64_t *idx = (const uint64_t *)im->idx_h.p + pc.k0;
+    const uint32_t log2S = log2u(im->chunk_bytes);
+    size_t a = 0;
+    cum[0] = 0;
+    for (uint64_t j = 0; j < pc.k; ++j) {
+        const uint64_t c = idx[j];   // ascending
+        while (a + 1 < im->allocs.size() && im->allocs[a + 1].first_chunk <= c) ++a;
+        const uint64_t len = chunk_len(im->allocs[a].bytes, c - im->allocs[a].first_chunk, log2S);
+        if (off[j] > pc.span || len > pc.span - off[j]) return CRAC_ERR_CORRUPT;
+        cum[j + 1] = cum[j] + len;
     }
-    for (const Piece &pc : im->pieces) {
+    if (cum[pc.k] != pc.bytes) return CRAC_ERR_CORRUPT;
+    pc.sp_off.swap(off);
+    pc.sp_cum.swap(cum);
+    return CRAC_OK;
+}
+
+// Bytes [a, b) of a sparse piece's compact payload (its entries' chunks in
+// list order, taken from their uncompacted offsets): one copy per run of
+// entries that lie back to back in the span.
+crac_status_t sparse_range(crac_image *im, Piece &pc, uint64_t a, uint64_t b, uint8_t *out) {
+    TRY(sparse_tables(im, pc));
+    const std::vector<uint64_t> &off = pc.sp_off, &cum = pc.sp_cum;
+    uint64_t j = (uint64_t)(std::upper_bound(cum.begin(), cum.end(), a) - cum.begin()) - 1;
+    uint64_t pos = a;
+    while (pos < b && j < pc.k) {
+        const uint64_t src = off[j] + (pos - cum[j]);
+        uint64_t jj = j;
+        while (cum[jj + 1] < b && jj + 1 < pc.k && off[jj + 1] == off[jj] + (cum[jj + 1] - cum[jj])) ++jj;
+        const uint64_t take = std::min(cum[jj + 1], b) - pos;
+        CK(cudaMemcpy(out + (pos - a), pc.dev.p + src, take, cudaMemcpyDeviceToHost));
+        pos += take;
+        j = jj + 1;
+    }
+    return pos == b ? CRAC_OK : CRAC_ERR_CORRUPT;
+}
+
+// Bytes [offset, offset + n) of the serialized form into host memory dst.
+// Serialization is the whole range; ranged reads let a caller stream an
+// image out (to a file, or to a checker) without holding it whole.
+crac_status_t read_range(crac_image *im, uint64_t offset, uint8_t *dst, uint64_t n) {
+    const uint64_t total = serialized_size(im);
+    if (offset > total || n > total - offset) return CRAC_ERR_INVALID_ARG;
+    if (n == 0) return CRAC_OK;
+    TRY(img_wait(im, 0));
+    TRY(img_host_tables(im));
+    const uint64_t end = offset + n;
+    // Copy the part of section [s0, s0 + len) that the range covers.
+    auto part = [&](uint64_t s0, uint64_t len, const std::function<crac_status_t(uint64_t, uint64_t, uint8_t *)> &copy) {
+        const uint64_t a = std::max(offset, s0), b = std::min(end, s0 + len);
+        return a < b ? copy(a - s0, b - a, dst + (a - offset)) : CRAC_OK;
+    };
+    auto from_host = [](const uint8_t *src) {
+        return [src](uint64_t o, uint64_t l, uint8_t *out) {
+            std::memcpy(out, src + o, l);
+            return CRAC_OK;
+        };
+    };
+    const std::vector<uint8_t> pre = image_prefix(im);
+    uint64_t pos = 0;
+    TRY(part(pos, pre.size(), from_host(pre.data())));
+    pos += pre.size();
+    TRY(part(pos, 8 * im->n_chunks, from_host(im->fp_h.p)));
+    pos += 8 * im->n_chunks;
+    TRY(part(pos, 8 * im->k, from_host(im->idx_h.p)));
+    pos += 8 * im->k;
+    if (im->flags & CRAC_IMAGE_CODED) {
+        TRY(part(pos, 8 * im->k, from_host(im->zlen_h.p)));
+        pos += 8 * im->k;
+    }
+    DeviceGuard g(im->device);
+    for (Piece &pc : im->pieces) {
         if (!pc.bytes) continue;
-        if (im->residency == CRAC_RESIDENCY_DEVICE) {
-            DeviceGuard g(im->device);
-            if (pc.span) TRY(sparse_compact(im, pc, p + pc.off0));
-            else CK(cudaMemcpy(p + pc.off0, pc.dev.p, pc.bytes, cudaMemcpyDeviceToHost));
-        } else {
-            std::memcpy(p + pc.off0, pc.host.p, pc.bytes);
-        }
+        TRY(part(pos + pc.off0, pc.bytes, [&](uint64_t o, uint64_t l, uint8_t *out) -> crac_status_t {
+            if (im->residency != CRAC_RESIDENCY_DEVICE) {
+                std::memcpy(out, pc.host.p + o, l);
+                return CRAC_OK;
+            }
+            if (pc.span) return sparse_range(im, pc, o, o + l, out);
+            CK(cudaMemcpy(out, pc.dev.p + o, l, cudaMemcpyDeviceToHost));
+            return CRAC_OK;
+        }));
     }
     return CRAC_OK;
+}
+
+}  // namespace
+
+crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
+    if (!image || !need) return CRAC_ERR_INVALID_ARG;
+    crac_image *im = const_cast<crac_image *>(image);
+    const uint64_t total = serialized_size(im);
+    *need = (size_t)total;
+    if (!dst) return CRAC_OK;
+    if (cap < total) return CRAC_ERR_INVALID_ARG;
+    return read_range(im, 0, (uint8_t *)dst, total);
+}
+
+crac_status_t crac_image_read(const crac_image_t *image, uint64_t offset, void *dst, size_t n) {
+    if (!image || (!dst && n)) return CRAC_ERR_INVALID_ARG;
+    return read_range(const_cast<crac_image *>(image), offset, (uint8_t *)dst, n);
+}
+
+// A coded CRZ1 stream of z bytes for a chunk of L bytes (z < L): every block
+// header has its reserved bits (48..63) clear and plane widths of at most 8,
+// and the header-padded length plus 16 bytes per unit plus the tail is z.
+// What only decoding can find (a plane value above 255) is left to the
+// restore.
+static bool crz_stream_header_ok(const uint8_t *s, uint64_t z, uint64_t L) {
+    const uint64_t nb = L / 512, tail = L % 512, head = 16 * ((nb + 1) / 2);
+    if (nb == 0 || z < head) return false;
+    uint64_t units = 0;
+    for (uint64_t b = 0; b < nb; ++b) {
+        const uint64_t h = get64(s + 8 * b);
+        if (h >> 48) return false;
+        for (int p = 0; p < 4; ++p) {
+            const uint64_t w = (h >> (32 + 4 * p)) & 0xF;
+            if (w > 8) return false;
+            units += w;
+        }
+    }
+    return head + 16 * units + tail == z;
 }
 
 crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **out) {
@@ -317,7 +402,8 @@ crac_status_t crac_image_deserialize(const void *src, size_t n, crac_image_t **o
         acc += len;
         if (coded) {
             const uint64_t z = get64(zlen + 8 * j);
-            if (z == 0 || z > len) return CRAC_ERR_CORRUPT;
+            if (z == 0 || z > len || zacc > pb || z > pb - zacc) return CRAC_ERR_CORRUPT;
+            if (z < len && !crz_stream_header_ok(payload + zacc, z, len)) return CRAC_ERR_CORRUPT;
             zacc += round_up(z, 16);
         }
     }

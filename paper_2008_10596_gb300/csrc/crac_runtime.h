@@ -25,9 +25,10 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
-#include <deque>
 #include <climits>
 #include <cstring>
+#include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -303,6 +304,10 @@ struct Piece {
     Block dev;                      // device residency: payload
     Block idx_dev, off_dev;         // device residency: idx[k], off[k+1] (piece-relative)
     Block zlen_dev;                 // device residency, coded image: zlen[k]
+    // Sparse piece, made on the first ranged read: host copies of the
+    // entries' span offsets and of the running sum of their chunk lengths
+    // (the compact offsets, k + 1 values).
+    std::vector<uint64_t> sp_off, sp_cum;
 };
 
 struct AllocRec {
@@ -419,6 +424,7 @@ struct crac_ctx {
     bool delta_frac_valid = false;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
+    bool lost = false;   // a kernel reported kErrLostCopy: no further device work on this context
     // autotuner session: one shadow context per candidate chunk size
     std::vector<crac_ctx *> tune_ctx;
     std::vector<double> tune_sum_ms, tune_sum_bytes;
