@@ -105,8 +105,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t par, u
 // Staging bytes [wa, wb) -> shared memory (whole CTA, after every thread is
 // done with the previous window).  *sb receives where byte wa landed.
 // Returns false on every thread if the copy did not complete in time: then
-// kErrTimeout is set, the copy has been waited for once more (bounded), and
-// the CTA must stop.
+// kErrTimeout is set and the CTA must stop.  Before that the CTA stays
+// resident while the copy may still land in its shared memory (in bounded
+// rounds), so that no later CTA is given that memory while it is written;
+// a copy that never lands also sets kErrLostCopy.
 __device__ bool load_window(const CodecParams &P, uint8_t *sdata, uint64_t *bar, uint32_t *phase, uint64_t wa,
                             uint64_t wb, const uint8_t **sb) {
     const uint64_t a0 = wa & ~15ull, a1 = (wb + 15) & ~15ull;   // 16-byte aligned, inside the staging slack
@@ -127,7 +129,9 @@ __device__ bool load_window(const CodecParams &P, uint8_t *sdata, uint64_t *bar,
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
             atomicOr(P.err, kErrTimeout);
-            mbar_wait_bounded(bar, par, P.timeout_ns);   // the copy may still land in this CTA's memory
+            bool landed = false;
+            for (int r = 0; r < kCopyDrainRounds && !landed; ++r) landed = mbar_wait_bounded(bar, par, P.timeout_ns);
+            if (!landed) atomicOr(P.err, kErrLostCopy);
         }
         __syncthreads();
         return false;

@@ -30,6 +30,10 @@ constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
 constexpr unsigned kErrBounds = 2u;    // an output index/offset exceeded its buffer
 constexpr unsigned kErrUncovered = 4u; // restore: a target chunk no image of the chain holds
 constexpr unsigned kErrCodec = 8u;     // restore: a coded stream no chunk encodes to
+constexpr unsigned kErrLostCopy = 16u; // a bulk copy into shared memory never completed, even
+                                       // after the CTA waited for it in bounded rounds: the
+                                       // device's state is unspecified
+constexpr int kCopyDrainRounds = 8;    // bounded waits for an in-flight bulk copy before a CTA exits
 
 // Parameters of the fused batched pass over global chunks [c_begin, c_end).
 struct CkptParams {

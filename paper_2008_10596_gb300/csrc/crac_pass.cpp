@@ -43,6 +43,7 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
 // CUDA resources are created on the first checkpoint or restart, so that the
 // registry works (and can be tested) without touching the device.
 crac_status_t ctx_cuda_ready(crac_ctx *c) {
+    if (c->lost) return CRAC_ERR_CUDA;
     if (c->cuda_ready) return CRAC_OK;
     int dev = c->cfg.device;
     if (dev < 0) CK(cudaGetDevice(&dev));
@@ -446,6 +447,10 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         cudaGetLastError();
     }
     *ctrl_out = *(const CkptCtrl *)c->ctrl_h.p;
+    if (ctrl_out->err & kErrLostCopy) {
+        c->lost = true;
+        return CRAC_ERR_CUDA;
+    }
     if (ctrl_out->err & kErrTimeout) return CRAC_ERR_TIMEOUT;
     if (ctrl_out->err) return CRAC_ERR_CORRUPT;
     return CRAC_OK;
@@ -523,6 +528,10 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
     if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1) == cudaSuccess) c->last.codec_ms += ms;
     cudaGetLastError();
     const unsigned err = *(const unsigned *)(out_h + 8);
+    if (err & kErrLostCopy) {
+        c->lost = true;
+        return CRAC_ERR_CUDA;
+    }
     if (err & kErrTimeout) return CRAC_ERR_TIMEOUT;
     if (err) return CRAC_ERR_CORRUPT;
     *Z = *(const uint64_t *)out_h;

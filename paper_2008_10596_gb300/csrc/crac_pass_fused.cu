@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(NT) ckpt_fused_kernel(const CkptParams P) {
             if (ci < nc && gl == 0) {
                 const uint64_t fp = fp_finalize(acc, len);
                 P.fp_new[c0 + ci] = fp;
-                const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
+                // no baseline table at all (fp_old NULL) reads as no baseline
+                const bool dirty = d.base_first == kNoBase || P.fp_old == nullptr ||
+                                   P.fp_old[d.base_first + local] != fp;
                 s_len[ci] = dirty ? len : 0u;
             }
         }

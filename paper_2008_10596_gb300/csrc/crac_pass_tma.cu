@@ -456,10 +456,16 @@ __global__ void __launch_bounds__(tma::kThreads, 1) ckpt_tma_kernel(const CkptPa
     else tma_store(P, slots, meta, scanned, empty, lane);
     __syncthreads();
     // Bulk loads still in flight (only after a role stopped on a timeout):
-    // wait for the last phase armed on each slot before the CTA exits.
+    // wait, in bounded rounds, for the last phase armed on each slot before
+    // the CTA exits, so that no later CTA is given shared memory that a copy
+    // is still writing; a copy that never lands sets kErrLostCopy.
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kNSlot; ++s)
-            if (armed[s] & 2u) mbar_wait(&full[s], armed[s] & 1u, P);
+        for (int s = 0; s < kNSlot; ++s) {
+            if (!(armed[s] & 2u)) continue;
+            bool landed = false;
+            for (int r = 0; r < kCopyDrainRounds && !landed; ++r) landed = mbar_wait(&full[s], armed[s] & 1u, P);
+            if (!landed) atomicOr(&P.ctrl->err, kErrLostCopy);
+        }
     }
 }
 

@@ -4,6 +4,7 @@ padding), every restart must bring the memory back exactly, the GPU decoder
 must restore images the oracle encoded (independent of the GPU encoder), and
 a damaged stream must come back as CRAC_ERR_CORRUPT, not as a fault."""
 import numpy as np
+import torch
 import pytest
 
 import paper_2008_10596_gb300 as C
@@ -182,15 +183,36 @@ def _damage(img_bytes, S, how):
     return bytes(b)
 
 
-@pytest.mark.parametrize("how", ["width", "reserved", "overflow"])
-def test_damaged_stream_is_reported(how):
+@pytest.mark.parametrize("how", ["width", "reserved"])
+def test_damaged_stream_header_is_refused_at_deserialize(how):
+    """A stream whose headers no chunk encodes to (a width above 8, a
+    reserved bit) is refused when the image is deserialized, before any
+    restore can touch memory."""
     S = 4 * KIB
     h = Harness(S, lineage=1500, flags=CODED)
     try:
         h.add(16 * S, data=_contents("f32_normal", 16 * S, 5))
         img, lib, ora = h.checkpoint()
         assert lib == ora
-        bad = C.crac_image_deserialize(_damage(lib, S, how))
+        with pytest.raises(C.CracError) as e:
+            C.crac_image_deserialize(_damage(lib, S, how))
+        assert e.value.code == C.CRAC_ERR_CORRUPT
+    finally:
+        h.close()
+
+
+def test_plane_overflow_is_reported_at_restart():
+    """A header that lets a plane value pass 255 is only found by decoding:
+    the restart reports CRAC_ERR_CORRUPT (the allocations' contents are then
+    unspecified), and the context still restores a good image."""
+    S = 4 * KIB
+    h = Harness(S, lineage=1500, flags=CODED)
+    try:
+        h.add(16 * S, data=_contents("f32_normal", 16 * S, 5))
+        img, lib, ora = h.checkpoint()
+        assert lib == ora
+        want = h.host()
+        bad = C.crac_image_deserialize(_damage(lib, S, "overflow"))
         try:
             h2 = Harness(S, lineage=1500, flags=CODED)
             try:
@@ -198,8 +220,9 @@ def test_damaged_stream_is_reported(how):
                 with pytest.raises(C.CracError) as e:
                     C.crac_ctx_restart(h2.ctx, bad, h2.stream)
                 assert e.value.code == C.CRAC_ERR_CORRUPT
-                # the context still works: the good image restores
                 C.crac_ctx_restart(h2.ctx, img, h2.stream)
+                torch.cuda.synchronize()
+                assert np.array_equal(h.bufs[0].read(), want[0])
             finally:
                 h2.close()
         finally:
