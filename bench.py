@@ -206,12 +206,14 @@ def _sample_prefix(sizes, budget):
     return out
 
 
-def oracle_step_timer(host_bufs, S, seed):
-    """Returns (setup, step) for the oracle: step() = mutate 10% + incremental
-    checkpoint + full restart of the chain, on host byte arrays."""
+def oracle_step_timer(host_bufs, S, seed, workers=1):
+    """Returns step() for the oracle: step() = mutate 10% + incremental
+    checkpoint + full restart of the chain, on host byte arrays; the
+    fingerprint loop runs on `workers` threads.  Building the FULL base image
+    is set-up, outside the steps."""
     from oracle import oracle as O
     sizes = [b.size for b in host_bufs]
-    ctx = O.OracleContext(S, lineage=1)
+    ctx = O.OracleContext(S, lineage=1, workers=workers)
     for i, n in enumerate(sizes):
         ctx.register((i + 1) << 36, n)
     first = W.chunk_layout(sizes, S)
@@ -227,16 +229,31 @@ def oracle_step_timer(host_bufs, S, seed):
     return step
 
 
-def cpu_baseline_measure(host_bufs, S, seed, label, target_s=10.0, max_steps=20):
-    step = oracle_step_timer(host_bufs, S, seed)
+def cpu_baseline_measure(host_bufs, S, seed, label, target_s=10.0, max_steps=20, workers=1):
+    step = oracle_step_timer(host_bufs, S, seed, workers)
     t0 = time.perf_counter()
     nbytes, steps = 0, 0
     while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < target_s):
         nbytes += step()
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": workers, "kind": "oracle",
             "sample": f"{label}; {steps} steps", "seconds": round(dt, 3)}
+
+
+def cpu_baseline_both(host_bufs, S, seed, label, same_config):
+    """The oracle on one thread and with its per-chunk fingerprint loop split
+    over every host core, on the same bytes.  The line's value is the
+    all-cores one."""
+    cores = os.cpu_count() or 1
+    one = cpu_baseline_measure(host_bufs, S, seed, label + "; single thread", target_s=8.0, max_steps=3)
+    allc = cpu_baseline_measure(host_bufs, S, seed, label + f"; fingerprint loop on {cores} threads",
+                                target_s=8.0, max_steps=5, workers=cores)
+    return {"value": allc["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": allc["sample"], "seconds": allc["seconds"], "same_config": same_config,
+            "single_thread": {"value": one["value"], "cores": 1, "seconds": one["seconds"], "sample": one["sample"]},
+            "all_cores": {"value": allc["value"], "cores": cores, "seconds": allc["seconds"]},
+            "nproc": cores}
 
 
 def run_reference(args):
@@ -246,10 +263,11 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     wl = W.config2()
-    budget = int(os.environ.get("CRAC_REF_SAMPLE_BYTES", str(1 << 30)))
+    budget = int(os.environ.get("CRAC_REF_SAMPLE_BYTES", str(wl.total_bytes)))
     sizes = _sample_prefix(wl.sizes, budget)
     host = [W.host_contents("f32_normal", n, wl.seed + i) for i, n in enumerate(sizes)]
-    step = oracle_step_timer(host, wl.chunk_bytes, wl.seed)
+    cores = os.cpu_count() or 1
+    step = oracle_step_timer(host, wl.chunk_bytes, wl.seed, workers=cores)
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -258,13 +276,16 @@ def run_reference(args):
         nbytes += step()
     dt = time.perf_counter() - t0
     v = nbytes / dt / 1e9
-    label = (f"first {len(sizes)} of 256 c2 allocations ({sum(sizes) / 2**20:.0f} MiB), numpy N(0,1); "
-             "per step: 10% mutate + incremental ckpt + full chain restart; single thread")
+    whole = len(sizes) == len(wl.sizes)
+    label = ((f"all 256 c2 allocations ({sum(sizes) / 2**20:.0f} MiB)" if whole else
+              f"first {len(sizes)} of 256 c2 allocations ({sum(sizes) / 2**20:.0f} MiB)") +
+             f", numpy N(0,1); per step: 10% mutate + incremental ckpt + full chain restart; "
+             f"fingerprint loop on {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_bytes": sum(sizes)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": label},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_bytes": sum(sizes), "same_config": whole},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": label},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -554,17 +575,31 @@ def run_crac(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import build as ob
         ob.build()
-        budget = int(os.environ.get("CRAC_CPU_SAMPLE_BYTES", str(1 << 30)))
+        budget = int(os.environ.get("CRAC_CPU_SAMPLE_BYTES", str(B)))
         ssz = _sample_prefix(sizes, budget)
         host = [bufs[i].cpu().numpy().copy() for i in range(len(ssz))]
-        cpu = cpu_baseline_measure(host, S, wl.seed,
-                                   f"first {len(ssz)} of 256 allocations ({sum(ssz) / 2**20:.0f} MiB) of this "
-                                   "workload read back to host; 10% mutate + incremental ckpt + full restart; "
-                                   "single thread")
-        cpu["nproc"] = os.cpu_count()
+        whole = len(ssz) == len(sizes)
+        cpu = cpu_baseline_both(host, S, wl.seed,
+                                (f"all {len(ssz)} allocations" if whole else
+                                 f"first {len(ssz)} of {len(sizes)} allocations") +
+                                f" ({sum(ssz) / 2**20:.0f} MiB) of this workload read back to host; "
+                                "10% mutate + incremental ckpt + full restart", whole)
+        del host
 
     for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc, ctx_inc_host):
         C.crac_ctx_destroy(ctx)
+
+    # ---- serving: config 5's request loop, short (N=1 only) -------------------
+    serving = None
+    if world == 1 and not args.no_serving:
+        total5 = args.serving_gib * W.GIB
+        sr = ServingRun(dev, total=total5)
+        sr.base_images()
+        serving = sr.run(args.serving_requests, args.rate)
+        sr.close()
+        serving["workload"] = (f"c5 shape: 64 contexts, {args.serving_gib} GiB total (log-uniform 0.5-8 GiB scaled "
+                               f"by {total5 / (173 * W.GIB):.3f}), {args.serving_requests} requests Poisson "
+                               f"{args.rate}/s, 75% ckpt / 25% restart, 24 GiB staging budget, 8 slots, host images")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -580,6 +615,10 @@ def run_crac(args):
                 "batched_vs_per_alloc": batched,
                 "ckpt_latency_ms": {"p50": statistics.median(lat_ms),
                                     "p99": float(np.percentile(lat_ms, 99))},
+                "serving_latency_ms": None if serving is None else {
+                    "checkpoint": serving["latency_ms"]["checkpoint"], "restart": serving["latency_ms"]["restart"],
+                    "all": serving["latency_all_ms"]},
+                "serving": serving,
                 "ckpt_pass_gbs": B / (dev_ms / 1e3) / 1e9, "dirty_chunks": k_avg, "dirty_bytes": d_avg}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -591,68 +630,18 @@ def run_crac(args):
 # Config 3: device + managed memory, 4-stream mutator, 3 checkpoints + restart
 # ---------------------------------------------------------------------------
 
-def _rewrite_entries(torch, dev, rows):
-    arr = np.asarray(rows, dtype=np.uint64).reshape(-1, 3)
-    return torch.from_numpy(arr.view(np.int64)).to(dev)
-
-
 def run_config3(args):
     import torch
     import paper_2008_10596_gb300 as C
     from paper_2008_10596_gb300 import testkit
+    from workloads.device import C3Memory, rows_tensor
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     scale = args.total_mib / 4096.0 if args.total_mib != 4096 else 1.0
-    wl = W.config3(device_total=int(12 * W.GIB * scale) // (64 * W.KIB) * (64 * W.KIB),
-                   managed_total=int(4 * W.GIB * scale) // (64 * W.KIB) * (64 * W.KIB))
-    S = wl.chunk_bytes
-    g = torch.Generator(device=dev)
-    g.manual_seed(wl.seed)
-    pool = torch.randn(64 << 20, generator=g, device=dev, dtype=torch.float32).to(torch.bfloat16)  # 128 MiB
-    pool_u8 = pool.view(torch.uint8)
-    bufs, kinds, managed = [], [], []
-    for n in wl.sizes:
-        bufs.append((torch.empty(n, dtype=torch.uint8, device=dev), n))
-        kinds.append(C.CRAC_KIND_DEVICE)
-    for n in wl.managed_sizes:
-        p = C.crac_alloc_managed(n)
-        managed.append(p)
-        bufs.append((p, n))
-        kinds.append(C.CRAC_KIND_MANAGED)
-    ptrs = [b.data_ptr() if hasattr(b, "data_ptr") else b for b, _ in bufs]
-    sizes = [n for _, n in bufs]
-    rng = np.random.default_rng(wl.seed)
-    # initial contents: bf16 N(0,1) copied from the pool at random offsets
-    rows = []
-    for ptr, n in zip(ptrs, sizes):
-        for o in range(0, n, 64 << 20):
-            ln = min(64 << 20, n - o)
-            src = pool_u8.data_ptr() + int(rng.integers(0, (pool_u8.numel() - ln) // 16 + 1)) * 16
-            rows.append((ptr + o, src, ln))
-    e = _rewrite_entries(torch, dev, rows)
-    testkit.rewrite(e.data_ptr(), len(rows), torch.cuda.current_stream())
-    torch.cuda.synchronize()
-    pages = [(a, o) for a, n in enumerate(sizes) for o in range(0, n, S)]
-    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    mem = C3Memory(dev, device_total=int(12 * W.GIB * scale), managed_total=int(4 * W.GIB * scale))
+    wl, S, ptrs, sizes, kinds = mem.wl, mem.S, mem.ptrs, mem.sizes, mem.kinds
     main = torch.cuda.current_stream(dev)
-
-    def mutate(seed):
-        r = np.random.default_rng(seed)
-        pick = r.choice(len(pages), size=len(pages) // 4, replace=False)
-        rows = []
-        for i in pick:
-            a, o = pages[i]
-            ln = min(S, sizes[a] - o)
-            src = pool_u8.data_ptr() + int(r.integers(0, (pool_u8.numel() - ln) // 16 + 1)) * 16
-            rows.append((ptrs[a] + o, src, ln))
-        parts = np.array_split(np.asarray(rows, dtype=np.uint64), 4)
-        ents = [torch.from_numpy(pp.view(np.int64)).to(dev) for pp in parts]
-        torch.cuda.synchronize()
-        for st, en, pp in zip(streams, ents, parts):
-            testkit.rewrite(en.data_ptr(), len(pp), st)
-        for st in streams:           # the checkpoint is stream-synced: join the mutator streams
-            main.wait_stream(st)
-        return len(rows)
+    mutate = mem.mutate
 
     ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=3, device=0,
                                                   reserve_host_bytes=int(2.2 * sum(sizes)), flags=restore_flags(args)))
@@ -679,12 +668,12 @@ def run_config3(args):
                       "e2e_payload_gbs": ii["payload_bytes"] / max(t2 - t0, 1e-9) / 1e9})
     # restart from the third image into zeroed memory, compare with a copy
     keep = [torch.empty(n, dtype=torch.uint8, device=dev) for n in sizes]
-    rows = [(k.data_ptr(), p, n) for k, p, n in zip(keep, ptrs, sizes)]
-    e = _rewrite_entries(torch, dev, rows)
+    rows = mem.copy_rows([k.data_ptr() for k in keep])
+    e = rows_tensor(rows, dev)
     testkit.rewrite(e.data_ptr(), len(rows), main)
     zero = torch.zeros(64 << 20, dtype=torch.uint8, device=dev)
     rows = [(p + o, zero.data_ptr(), min(64 << 20, n - o)) for p, n in zip(ptrs, sizes) for o in range(0, n, 64 << 20)]
-    e = _rewrite_entries(torch, dev, rows)
+    e = rows_tensor(rows, dev)
     testkit.rewrite(e.data_ptr(), len(rows), main)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -692,16 +681,15 @@ def run_config3(args):
     torch.cuda.synchronize()
     t_restart = time.perf_counter() - t0
     back = [torch.empty(n, dtype=torch.uint8, device=dev) for n in sizes]
-    rows = [(b.data_ptr(), p, n) for b, p, n in zip(back, ptrs, sizes)]
-    e = _rewrite_entries(torch, dev, rows)
+    rows = mem.copy_rows([b.data_ptr() for b in back])
+    e = rows_tensor(rows, dev)
     testkit.rewrite(e.data_ptr(), len(rows), main)
     torch.cuda.synchronize()
     exact = all(torch.equal(a, b) for a, b in zip(keep, back))
     for img in imgs:
         C.crac_image_release(img)
     C.crac_ctx_destroy(ctx)
-    for p in managed:
-        C.crac_free_managed(p)
+    mem.free()
     line = {"workload": f"c3: {len(wl.sizes)} device ({sum(wl.sizes) / 2**30:.1f} GiB) + {len(wl.managed_sizes)} "
                         f"managed ({sum(wl.managed_sizes) / 2**30:.1f} GiB) allocations, 64 KiB chunks, 25% of pages "
                         "rewritten (bf16) on 4 streams between checkpoints",
@@ -716,53 +704,13 @@ def run_config3(args):
 # Config 4: 120 GiB / 2048 allocations, dirty sweep, autotuned chunk size
 # ---------------------------------------------------------------------------
 
-def c4_memory(total: int, n: int, dev):
-    """Config-4-shaped device memory (Zipf sizes, uint8 / fp32 / int64 contents)
-    and a mutator that rewrites a fraction of its 4 KiB pages."""
-    import torch
-    from paper_2008_10596_gb300 import testkit
-    wl = W.config4(total=total, n=n)
-    sizes = wl.sizes
-    g = torch.Generator(device=dev)
-    g.manual_seed(wl.seed)
-    bufs = []
-    for i, nb in enumerate(sizes):     # uint8 / fp32 N(0,1) / int64 uniform, cycling
-        if i % 3 == 0:
-            t = torch.randint(0, 256, (nb,), generator=g, device=dev, dtype=torch.uint8)
-        elif i % 3 == 1:
-            t = torch.randn(nb // 4, generator=g, device=dev, dtype=torch.float32).view(torch.uint8)
-        else:
-            t = torch.randint(-(1 << 62), 1 << 62, (nb // 8,), generator=g, device=dev, dtype=torch.int64).view(torch.uint8)
-        bufs.append(t)
-    page_counts = torch.tensor([n // 4096 for n in sizes], device=dev, dtype=torch.int64)
-    page_first = torch.cumsum(page_counts, 0) - page_counts
-    bases = torch.tensor([b.data_ptr() for b in bufs], device=dev, dtype=torch.int64)
-    n_pages = int(page_counts.sum().item())
-
-    def mutate(frac, seed):
-        k = int(round(frac * n_pages))
-        if k == 0:
-            return 0
-        gg = torch.Generator(device=dev)
-        gg.manual_seed(seed)
-        pid = torch.randperm(n_pages, generator=gg, device=dev)[:k]
-        a = torch.searchsorted(page_first, pid, right=True) - 1
-        ptr = bases[a] + (pid - page_first[a]) * 4096
-        mask = (torch.randint(0, 1 << 31, (k,), generator=gg, device=dev, dtype=torch.int64) * 2 + 1) & 0xFFFFFFFF
-        ent = torch.stack([ptr, torch.full_like(ptr, 4096), mask], dim=1).contiguous()
-        testkit.mutate_xor(ent.data_ptr(), k, torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        return k
-
-    return sizes, bufs, mutate
-
-
 def run_config4(args):
     import torch
     import paper_2008_10596_gb300 as C
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     total = (args.total_mib << 20) if args.total_mib != 4096 else 120 * W.GIB
+    from workloads.device import c4_memory
     sizes, bufs, mutate = c4_memory(total, 2048, dev)
     B = sum(sizes)
     peak, _ = load_peaks()
@@ -820,6 +768,7 @@ def run_passes(args):
     torch.cuda.set_device(dev)
     total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
     n_allocs = max(16, int(512 * total / (32 * W.GIB)))
+    from workloads.device import c4_memory
     sizes, bufs, mutate = c4_memory(total, n_allocs, dev)
     B = sum(sizes)
     peak, _ = load_peaks()
@@ -1043,161 +992,221 @@ def run_codec(args):
 # Config 5: serving loop over 64 simulated process contexts
 # ---------------------------------------------------------------------------
 
+class ServingRun:
+    """Config 5's serving loop: n_ctx simulated process contexts (log-uniform
+    0.5-8 GiB images scaled to `total`, 4-64 allocations each, fp32 N(0,1)),
+    checkpoint / restart requests arriving Poisson at `rate` (75% / 25%),
+    admitted by a request server with 8 worker slots and a 24 GiB staging
+    budget.  Before each checkpoint the request's prepare callback XORs a
+    seeded 10% of the context's chunks; every 4th checkpoint of a context is
+    FULL (the baseline is dropped first).  A restart targets the context's
+    newest committed image.  Latency runs from the scheduled arrival to the
+    request's completion event.
+
+    on_result(j, i, kind, result, plan), when given, is called in submission
+    order (so in each context's own order) from the collecting thread, with
+    plan = {"mut": index into procs[i]["mut_lists"], "full": bool} for a
+    checkpoint and {"image": handle, "epoch": its epoch} for a restart (the
+    handle may have been released by then; the epoch names the image)."""
+
+    def __init__(self, dev, n_ctx=64, total=32 * W.GIB, seed=W.SEED_BASE + 5, flags=0, host_reserve=2.0):
+        import torch
+        import paper_2008_10596_gb300 as C
+        self.torch, self.C, self.dev = torch, C, dev
+        self.seed = seed
+        self.rng = np.random.default_rng(seed)
+        self.n_ctx = n_ctx
+        self.total = total
+        self.S = S = 64 * W.KIB
+        raw = W.log_uniform(self.rng, n_ctx, 0.5 * W.GIB, 8 * W.GIB)
+        scale = total / (173 * W.GIB)
+        ctx_bytes = W.water_fill(raw, total, int(0.5 * W.GIB * scale), int(8 * W.GIB * scale) + 1, 64 * W.KIB)
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        self.procs = []
+        for i, cb in enumerate(ctx_bytes):
+            na = int(round(np.exp(self.rng.uniform(np.log(4), np.log(64)))))
+            w = self.rng.dirichlet(np.ones(na))
+            sizes = [max(64 * W.KIB, int(x * cb) // (64 * W.KIB) * (64 * W.KIB)) for x in w]
+            bufs = [torch.randn(n // 4, generator=g, device=dev).view(torch.uint8) for n in sizes]
+            ctx = C.crac_ctx_create(C.crac_config_default(
+                chunk_bytes=S, lineage=5000 + i, device=dev.index or 0,
+                reserve_host_bytes=int(host_reserve * total) if i == 0 else 0, flags=flags))
+            for b in bufs:
+                C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
+            first = W.chunk_layout(sizes, S)
+            mut_lists, muts = [], []
+            for r in range(4):
+                ms = W.choose_mutations(seed * 131 + i * 7 + r, int(first[-1]), 0.10)
+                rows = []
+                for m in ms:
+                    a = int(np.searchsorted(first, m.chunk, side="right") - 1)
+                    lo = (m.chunk - int(first[a])) * S
+                    rows.append((bufs[a].data_ptr() + lo, min(S, sizes[a] - lo), m.mask))
+                mut_lists.append(ms)
+                muts.append(torch.from_numpy(np.array(rows, dtype=np.uint64).view(np.int64)).to(dev))
+            self.procs.append({"ctx": ctx, "bufs": bufs, "sizes": sizes, "first": first,
+                               "stream": torch.cuda.Stream(dev), "muts": muts, "mut_lists": mut_lists,
+                               "bytes": sum(sizes), "ckpts": 0, "images": [], "latest": None})
+        torch.cuda.synchronize(dev)
+
+    def base_images(self, on_base=None):
+        """The FULL base image of every context, before the measured loop."""
+        for i, p in enumerate(self.procs):
+            img = self.C.crac_ctx_checkpoint(p["ctx"], p["stream"])
+            self.C.crac_image_wait(img)
+            p["latest"] = img
+            p["images"].append(img)
+            if on_base is not None:
+                on_base(i, img)
+        self.torch.cuda.synchronize(self.dev)
+
+    def run(self, n_req, rate, on_result=None, workers=8, budget=24 * W.GIB, max_lease=4 * W.GIB):
+        import queue as _q
+        import threading
+        C, torch = self.C, self.torch
+        procs = self.procs
+        server = C.crac_server_create(workers=workers, staging_budget=budget, max_lease=max_lease)
+        rng = self.rng
+        inter = rng.exponential(1.0 / rate, size=n_req)
+        arrivals = np.cumsum(inter)
+        targets = rng.integers(0, self.n_ctx, size=n_req)
+        kinds = np.where(rng.uniform(size=n_req) < 0.75, C.CRAC_REQ_CHECKPOINT, C.CRAC_REQ_RESTART)
+        lock = threading.Lock()
+        callbacks = []
+        results = {}
+        errors = []
+
+        def make_prep(p, k_mut, full):
+            def prep(stream, arg):
+                m = p["muts"][k_mut]
+                from paper_2008_10596_gb300 import testkit
+                testkit.mutate_xor(m.data_ptr(), m.shape[0], stream)
+                if full:
+                    C.crac_ctx_invalidate(p["ctx"])
+            return C.PREPARE_FN(prep)
+
+        qq = _q.Queue()
+
+        def collect():
+            for j, t, i, kind, plan in iter(qq.get, None):
+                r = C.crac_server_wait(server, t)
+                p = procs[i]
+                if on_result is not None and not errors:
+                    try:
+                        on_result(j, i, int(kind), r, plan)
+                    except Exception as e:   # reported after the loop
+                        errors.append(e)
+                with lock:
+                    if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
+                        # keep only the newest image: its chain holds what a
+                        # restart needs, and each FULL image frees the history
+                        for old in p["images"]:
+                            C.crac_image_release(old)
+                        p["images"] = [r["image"]]
+                        p["latest"] = r["image"]
+                    results[t] = (int(kind), r, p["bytes"])
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = C.crac_time_now() + 0.05
+        for j in range(n_req):
+            i = int(targets[j])
+            p = procs[i]
+            t_arr = t0 + float(arrivals[j])
+            while C.crac_time_now() < t_arr:
+                time.sleep(min(0.002, max(0.0, t_arr - C.crac_time_now())))
+            if kinds[j] == C.CRAC_REQ_CHECKPOINT:
+                p["ckpts"] += 1
+                plan = {"mut": p["ckpts"] % 4, "full": p["ckpts"] % 4 == 0}
+                cb = make_prep(p, plan["mut"], plan["full"])
+                callbacks.append(cb)
+                t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_CHECKPOINT, None, p["stream"], cb, None, t_arr)
+            else:
+                with lock:   # the collector releases superseded images under the lock
+                    img = p["latest"]
+                    plan = {"image": img, "epoch": C.crac_image_info(img)["epoch"]}
+                    t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_RESTART, img, p["stream"], None, None,
+                                             t_arr)
+            qq.put((j, t, i, int(kinds[j]), plan))
+        qq.put(None)
+        th.join()
+        t_end = max(r["t_done"] for _, r, _ in results.values())
+        stats = C.crac_server_stats(server)
+        C.crac_server_destroy(server)
+        if errors:
+            raise errors[0]
+        return self._summary(results, stats, t0, t_end, arrivals, targets, n_req, rate, workers, budget)
+
+    def _summary(self, results, stats, t0, t_end, arrivals, targets, n_req, rate, workers, budget):
+        C = self.C
+        lat = {"checkpoint": [], "restart": []}
+        wait = {"checkpoint": [], "restart": []}
+        serv = {"checkpoint": [], "restart": []}
+        full_serv, full_wait = [], []
+        scanned = payload = 0
+        fails = 0
+        for kind, r, nb in results.values():
+            if r["status"] != 0:
+                fails += 1
+                continue
+            key = "checkpoint" if kind == C.CRAC_REQ_CHECKPOINT else "restart"
+            lat[key].append((r["t_done"] - r["t_arrival"]) * 1e3)
+            wait[key].append((r["t_admit"] - r["t_arrival"]) * 1e3)
+            serv[key].append((r["t_done"] - r["t_admit"]) * 1e3)
+            if kind == C.CRAC_REQ_CHECKPOINT and r["payload_bytes"] >= nb:
+                full_serv.append((r["t_done"] - r["t_admit"]) * 1e3)
+                full_wait.append((r["t_admit"] - r["t_arrival"]) * 1e3)
+            scanned += nb
+            payload += r["payload_bytes"]
+        wall = t_end - t0
+        allv = lat["checkpoint"] + lat["restart"]
+
+        def pct(v, q):
+            return float(np.percentile(v, q)) if v else None
+
+        def dist(v):
+            return {"p50": pct(v, 50), "p99": pct(v, 99), "max": max(v) if v else None, "n": len(v)}
+
+        return {"contexts": self.n_ctx, "tracked_bytes": sum(p["bytes"] for p in self.procs),
+                "requests": n_req, "rate_per_s": rate, "workers": workers, "staging_budget": budget,
+                "failed": fails, "wall_s": wall,
+                "latency_ms": {k: dist(v) for k, v in lat.items()},
+                "latency_all_ms": {"p50": pct(allv, 50), "p99": pct(allv, 99)},
+                "queue_wait_ms": {k: dist(v) for k, v in wait.items()},
+                "service_ms": {k: dist(v) for k, v in serv.items()},
+                "full_checkpoint_ms": {"service": dist(full_serv), "queue_wait": dist(full_wait)},
+                "memory": C.crac_memory_stats(),
+                "offered_gbs": sum(self.procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
+                "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
+                "server": stats}
+
+    def close(self):
+        self.torch.cuda.synchronize(self.dev)
+        for p in self.procs:
+            for img in p["images"]:
+                self.C.crac_image_release(img)
+            p["images"] = []
+            self.C.crac_ctx_destroy(p["ctx"])
+        self.procs = []
+
+
 def run_config5(args):
-    import threading
     import torch
-    import paper_2008_10596_gb300 as C
-    from paper_2008_10596_gb300 import testkit
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    seed = W.SEED_BASE + 5
-    rng = np.random.default_rng(seed)
-    n_ctx = 64
     total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
-    raw = W.log_uniform(rng, n_ctx, 0.5 * W.GIB, 8 * W.GIB)
-    ctx_bytes = W.water_fill(raw, total, int(0.5 * W.GIB * total / (173 * W.GIB)),
-                             int(8 * W.GIB * total / (173 * W.GIB)) + 1, 64 * W.KIB)
-    S = 64 * W.KIB
-    g = torch.Generator(device=dev)
-    g.manual_seed(seed)
-    procs = []
-    for i, cb in enumerate(ctx_bytes):
-        na = int(round(np.exp(rng.uniform(np.log(4), np.log(64)))))
-        w = rng.dirichlet(np.ones(na))
-        sizes = [max(64 * W.KIB, int(x * cb) // (64 * W.KIB) * (64 * W.KIB)) for x in w]
-        bufs = [torch.randn(n // 4, generator=g, device=dev).view(torch.uint8) for n in sizes]
-        stream = torch.cuda.Stream(dev)
-        ctx = C.crac_ctx_create(C.crac_config_default(chunk_bytes=S, lineage=5000 + i, device=0,
-                                                      reserve_host_bytes=int(2.0 * total) if i == 0 else 0,
-                                                      flags=restore_flags(args)))
-        for b in bufs:
-            C.crac_ctx_register_alloc(ctx, b.data_ptr(), b.numel())
-        first = W.chunk_layout(sizes, S)
-        muts = []
-        for r in range(4):
-            ms = W.choose_mutations(seed * 131 + i * 7 + r, int(first[-1]), 0.10)
-            rows = []
-            for m in ms:
-                a = int(np.searchsorted(first, m.chunk, side="right") - 1)
-                lo = (m.chunk - int(first[a])) * S
-                rows.append((bufs[a].data_ptr() + lo, min(S, sizes[a] - lo), m.mask))
-            muts.append(torch.from_numpy(np.array(rows, dtype=np.uint64).view(np.int64)).to(dev))
-        procs.append({"ctx": ctx, "bufs": bufs, "stream": stream, "muts": muts, "bytes": sum(sizes),
-                      "ckpts": 0, "images": [], "latest": None})
-    torch.cuda.synchronize()
-    # base (FULL) image of every context, before the measured loop
-    for p in procs:
-        img = C.crac_ctx_checkpoint(p["ctx"], p["stream"])
-        C.crac_image_wait(img)
-        p["latest"] = img
-        p["images"].append(img)
-    torch.cuda.synchronize()
-    server = C.crac_server_create(workers=8, staging_budget=24 * W.GIB, max_lease=4 * W.GIB)
-    n_req = args.requests
-    inter = rng.exponential(1.0 / args.rate, size=n_req)
-    arrivals = np.cumsum(inter)
-    targets = rng.integers(0, n_ctx, size=n_req)
-    kinds = np.where(rng.uniform(size=n_req) < 0.75, C.CRAC_REQ_CHECKPOINT, C.CRAC_REQ_RESTART)
-    lock = threading.Lock()
-    callbacks = []
-
-    def make_prep(p, k_mut, full):
-        def prep(stream, arg):
-            m = p["muts"][k_mut]
-            testkit.mutate_xor(m.data_ptr(), m.shape[0], stream)
-            if full:
-                C.crac_ctx_invalidate(p["ctx"])   # every 4th checkpoint of a context is FULL
-        return C.PREPARE_FN(prep)
-
-    tickets = []
-    results = {}
-
-    def collect():
-        for t, i, kind in iter(queue_get, None):
-            r = C.crac_server_wait(server, t)
-            p = procs[i]
-            with lock:
-                if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
-                    # keep only the latest image: its chain holds what a restart
-                    # needs, and each FULL checkpoint frees the older history
-                    for old in p["images"]:
-                        C.crac_image_release(old)
-                    p["images"] = [r["image"]]
-                    p["latest"] = r["image"]
-                results[t] = (kind, r, p["bytes"])
-
-    import queue as _q
-    qq = _q.Queue()
-    queue_get = qq.get
-    th = threading.Thread(target=collect)
-    th.start()
-    t0 = C.crac_time_now() + 0.05
-    for j in range(n_req):
-        i = int(targets[j])
-        p = procs[i]
-        t_arr = t0 + float(arrivals[j])
-        while C.crac_time_now() < t_arr:
-            time.sleep(min(0.002, max(0.0, t_arr - C.crac_time_now())))
-        if kinds[j] == C.CRAC_REQ_CHECKPOINT:
-            p["ckpts"] += 1
-            cb = make_prep(p, p["ckpts"] % 4, p["ckpts"] % 4 == 0)
-            callbacks.append(cb)
-            t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_CHECKPOINT, None, p["stream"], cb, None, t_arr)
-        else:
-            with lock:
-                img = p["latest"]
-            t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_RESTART, img, p["stream"], None, None, t_arr)
-        tickets.append(t)
-        qq.put((t, i, int(kinds[j])))
-    qq.put(None)
-    th.join()
-    t_end = max(r["t_done"] for _, r, _ in results.values())
-    stats = C.crac_server_stats(server)
-    C.crac_server_destroy(server)
-    lat = {"checkpoint": [], "restart": []}
-    wait = {"checkpoint": [], "restart": []}
-    serv = {"checkpoint": [], "restart": []}
-    full_serv = []
-    scanned = payload = 0
-    fails = 0
-    for kind, r, nb in results.values():
-        if r["status"] != 0:
-            fails += 1
-            continue
-        key = "checkpoint" if kind == 0 else "restart"
-        lat[key].append((r["t_done"] - r["t_arrival"]) * 1e3)
-        wait[key].append((r["t_admit"] - r["t_arrival"]) * 1e3)
-        serv[key].append((r["t_done"] - r["t_admit"]) * 1e3)
-        if kind == 0 and r["payload_bytes"] >= nb:
-            full_serv.append((r["t_done"] - r["t_admit"]) * 1e3)
-        scanned += nb
-        payload += r["payload_bytes"]
-    wall = t_end - t0
-    allv = lat["checkpoint"] + lat["restart"]
-
-    def pct(v, q):
-        return float(np.percentile(v, q)) if v else None
-
-    line = {"workload": f"c5: {n_ctx} contexts, {total / 2**30:.0f} GiB total (log-uniform 0.5-8 GiB scaled by "
-                        f"{total / (173 * W.GIB):.3f}), {n_req} requests Poisson {args.rate}/s, 75% ckpt / 25% restart, "
-                        "10% of chunks mutated before each checkpoint, 24 GiB staging budget, 8 slots",
-            "requests": n_req, "failed": fails, "wall_s": wall,
-            "latency_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)} for k, v in lat.items()},
-            "latency_all_ms": {"p50": pct(allv, 50), "p99": pct(allv, 99)},
-            "queue_wait_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99)} for k, v in wait.items()},
-            "service_ms": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "max": max(v) if v else None}
-                           for k, v in serv.items()},
-            "full_checkpoint_service_ms": {"p50": pct(full_serv, 50), "p99": pct(full_serv, 99), "n": len(full_serv)},
-            "memory": C.crac_memory_stats(),
-            "offered_gbs": sum(procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
-            "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
-            "server": stats}
-    for p in procs:
-        for img in p["images"]:
-            C.crac_image_release(img)
-        C.crac_ctx_destroy(p["ctx"])
+    sr = ServingRun(dev, total=total, flags=restore_flags(args))
+    sr.base_images()
+    out = sr.run(args.requests, args.rate)
+    sr.close()
+    line = {"workload": f"c5: 64 contexts, {total / 2**30:.0f} GiB total (log-uniform 0.5-8 GiB scaled by "
+                        f"{total / (173 * W.GIB):.3f}), {args.requests} requests Poisson {args.rate}/s, "
+                        "75% ckpt / 25% restart, 10% of chunks mutated before each checkpoint, "
+                        "24 GiB staging budget, 8 slots"}
+    line.update(out)
     print(json.dumps(line), flush=True)
-    return 0 if fails == 0 else 1
+    return 0 if out["failed"] == 0 else 1
 
 
 def main():
@@ -1212,6 +1221,9 @@ def main():
                     help="tracked bytes of the config-2 workload (default 4096 = the full config)")
     ap.add_argument("--requests", type=int, default=1200, help="c5: requests in the serving loop")
     ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
+    ap.add_argument("--no-serving", action="store_true", help="c2: skip the short serving leg")
+    ap.add_argument("--serving-gib", type=int, default=8, help="c2: total context memory of the serving leg")
+    ap.add_argument("--serving-requests", type=int, default=200, help="c2: requests of the serving leg")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes", "codec"],
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--staged-restore", action="store_true",
