@@ -57,11 +57,12 @@ def restore_flags(args) -> int:
     staged; drains through staging (default) or direct."""
     import paper_2008_10596_gb300 as C
     f = C.CRAC_FLAG_STAGED_RESTORE if getattr(args, "staged_restore", False) else 0
+    f |= C.CRAC_FLAG_WAIT_PASS if getattr(args, "wait_pass", False) else 0
     return f | (C.CRAC_FLAG_DIRECT_DRAIN if getattr(args, "direct_drain", False) else 0)
 
 
 KERNEL_UNITS = ("crac_pass_split.cu", "crac_pass_fused.cu", "crac_pass_tma.cu", "crac_pass_per_alloc.cu",
-                "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu")
+                "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu", "crac_drain.cu")
 
 
 def kernel_src_sha(unit: str | None = None, read=None) -> str:
@@ -1107,6 +1108,10 @@ class ServingRun:
                         p["latest"] = r["image"]
                     results[t] = (int(kind), r, p["bytes"])
 
+        # The prepare callbacks (the application's mutator launches) run on the
+        # server's worker threads and need the GIL: hand it over quickly.
+        switch = sys.getswitchinterval()
+        sys.setswitchinterval(0.0002)
         th = threading.Thread(target=collect)
         th.start()
         t0 = C.crac_time_now() + 0.05
@@ -1131,6 +1136,7 @@ class ServingRun:
             qq.put((j, t, i, int(kinds[j]), plan))
         qq.put(None)
         th.join()
+        sys.setswitchinterval(switch)
         t_end = max(r["t_done"] for _, r, _ in results.values())
         stats = C.crac_server_stats(server)
         C.crac_server_destroy(server)
@@ -1228,6 +1234,8 @@ def main():
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--staged-restore", action="store_true",
                     help="c2 e2e, c3, c5: restore host images through staging (copy engine) instead of in place")
+    ap.add_argument("--wait-pass", action="store_true",
+                    help="host contexts: every checkpoint call waits for its pass (CRAC_FLAG_WAIT_PASS)")
     ap.add_argument("--direct-drain", action="store_true",
                     help="c2 e2e, c3, c5: write host images straight into pinned memory instead of staging + D2H")
     ap.add_argument("--chunk-kib", default="4,64", help="passes: chunk sizes in KiB")

@@ -179,6 +179,12 @@ typedef struct crac_config {
  *   the autotuner never picks it for a coded context).  Under the request
  *   server a coded context's lease is at least one chunk plus 256 bytes. */
 #define CRAC_FLAG_COMPRESS 8u
+/* CRAC_FLAG_WAIT_PASS: every checkpoint call waits for its pass, so the
+ *   image's dirty count and payload size are known when it returns and its
+ *   blocks are sized to them (no worst-case blocks while it runs); the
+ *   single-segment passes that otherwise return once enqueued behave like
+ *   the others.  A pass failure is then reported by the call. */
+#define CRAC_FLAG_WAIT_PASS 16u
 
 /* Kernel of the batched pass (crac_config_t.pass_kernel). */
 #define CRAC_PASS_AUTO  0  /* the split pass, or, when the last pass with a baseline
@@ -278,14 +284,28 @@ CRAC_API crac_status_t crac_ctx_free(crac_ctx_t *ctx, void *ptr);
  * (other streams must be joined by the caller); stream == NULL first
  * synchronizes the whole device.  Managed allocations are prefetched to the
  * device on `stream` before the pass.
- * The call returns once the device pass has finished (it needs the dirty
- * byte count to size the image); the drain of the payload to host memory
- * may still be running -- crac_image_wait blocks until it is done.
+ * The call returns after enqueueing (Sec. 2.2's drain of pending work
+ * becomes stream order) when the pass is one batched launch into uncoded
+ * images whose tracked bytes fit the staging capacity: the image's dirty
+ * count and payload size are then known, and settle, once its pass has run
+ * (crac_image_wait, crac_image_info, crac_image_serialize and a restart wait
+ * for that).  Until then the image holds worst-case blocks (the tracked
+ * bytes, from the device arena or the pinned regions as they are).  Up to
+ * two such checkpoints of a context may be unsettled; a third call, and
+ * every other kind of pass, first waits for the earlier ones.  The other
+ * passes (several staging segments, coded images, per-allocation launches)
+ * wait for each segment's dirty counts, and return once the pass has
+ * finished; the drain to host memory may still be running.  A call that has
+ * to grow the context's tables (more chunks than before) may synchronize
+ * the device while it allocates.
  * The first checkpoint of an allocation carries all of its chunks; later
  * ones carry only chunks whose fingerprint changed.  *image_out receives a
  * new reference that the caller releases with crac_image_release.
  * A device wait that runs out gives CRAC_ERR_TIMEOUT with the baseline
- * untouched.  If a kernel reports that a bulk copy into its shared memory
+ * untouched: from this call, or, for a pass it did not wait for, from the
+ * image (crac_image_wait); the context's baseline then returns to its last
+ * good image before its next operation, and an image taken meanwhile, whose
+ * pass compared against the failed one, fails with the same error.  If a kernel reports that a bulk copy into its shared memory
  * never completed, even after it waited for it in bounded rounds, the
  * device's state is unspecified: the call returns CRAC_ERR_CUDA and the
  * context refuses every later checkpoint and restart with CRAC_ERR_CUDA.
@@ -485,10 +505,17 @@ CRAC_API crac_status_t crac_restart(const crac_image_t *image, crac_stream_t str
 
 /* ---- images ----------------------------------------------------------- */
 
-/* Block until the image's drain has completed, at most timeout_ns
- * (0 = no limit).  CRAC_ERR_TIMEOUT if the limit passes first. */
+/* Block until the image's pass and drain have completed, at most timeout_ns
+ * (0 = no limit).  CRAC_ERR_TIMEOUT if the limit passes first.  For a
+ * checkpoint whose call returned before its pass finished, this is where a
+ * device-side failure of the pass is reported (CRAC_ERR_TIMEOUT for a device
+ * wait that ran out, CRAC_ERR_CORRUPT, CRAC_ERR_CUDA), and again on every
+ * later call that needs the image. */
 CRAC_API crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns);
 
+/* The image's header fields.  For an image whose pass may still be running
+ * (crac_ctx_checkpoint returned before it finished) this first waits for it,
+ * since k and the payload size come from the pass. */
 CRAC_API crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out);
 
 /*
@@ -504,7 +531,9 @@ CRAC_API crac_status_t crac_image_info(const crac_image_t *image, crac_image_inf
  * as it is) and its payload is the streams in idx order, each zero-padded to
  * a multiple of 16 bytes.
  * *need receives the size.  dst == NULL: only *need is set.  cap < need:
- * CRAC_ERR_INVALID_ARG.  Waits for the drain first.
+ * CRAC_ERR_INVALID_ARG.  Waits for the image's pass and drain first (also
+ * when only the size is asked for), and returns the image's error if they
+ * failed.
  */
 CRAC_API crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap,
                                             size_t *need);

@@ -52,6 +52,7 @@ CRAC_FLAG_STAGED_RESTORE = 1
 CRAC_FLAG_INCREMENTAL_RESTORE = 2
 CRAC_FLAG_DIRECT_DRAIN = 4
 CRAC_FLAG_COMPRESS = 8
+CRAC_FLAG_WAIT_PASS = 16
 
 CRAC_FAULT_NONE = 0
 CRAC_FAULT_PASS = 1

@@ -23,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hi
 
 LIBS = {
     "libcrac.so": ["crac_pass_split.cu", "crac_pass_fused.cu", "crac_pass_tma.cu", "crac_pass_per_alloc.cu",
-                   "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu", "crac_arena.cpp", "crac_image.cpp", "crac_pass.cpp", "crac_restart.cpp",
+                   "crac_restore.cu", "crac_codec.cu", "crac_noalloc.cu", "crac_drain.cu", "crac_arena.cpp", "crac_image.cpp", "crac_pass.cpp", "crac_restart.cpp",
                    "crac_tune.cpp", "crac_server.cpp", "crac_abi.cpp"],
     "libcrac_testkit.so": ["crac_testkit.cu"],
 }

@@ -137,9 +137,18 @@ crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *image, crac_
     return ctx_restart(ctx, const_cast<crac_image *>(image), (cudaStream_t)stream);
 }
 
+// Settle the context's unsettled checkpoints (their failure would revert the
+// baseline these calls change or report on).
+static void settle_all(crac_ctx *c) {
+    if (!c->cuda_ready || c->pending.empty()) return;
+    DeviceGuard g(c->device);
+    ctx_settle(c, true);
+}
+
 crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx) {
     if (!ctx) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    settle_all(ctx);
     ctx->base_valid = false;
     ctx->base_first.clear();
     return CRAC_OK;
@@ -148,6 +157,7 @@ crac_status_t crac_ctx_invalidate(crac_ctx_t *ctx) {
 crac_status_t crac_ctx_drop_history(crac_ctx_t *ctx) {
     if (!ctx) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    settle_all(ctx);
     img_unref(ctx->parent);
     ctx->parent = nullptr;
     return CRAC_OK;
@@ -156,6 +166,7 @@ crac_status_t crac_ctx_drop_history(crac_ctx_t *ctx) {
 crac_status_t crac_ctx_last_pass(crac_ctx_t *ctx, crac_pass_info_t *out) {
     if (!ctx || !out) return CRAC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    settle_all(ctx);
     *out = ctx->last;
     return CRAC_OK;
 }

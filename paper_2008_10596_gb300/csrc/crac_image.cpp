@@ -42,8 +42,10 @@ crac_status_t img_wait(const crac_image *cim, uint64_t timeout_ns) {
     for (;;) {
         cudaError_t e = cudaEventQuery(im->done);
         if (e == cudaSuccess) {
-            im->state.store(1);
-            return CRAC_OK;
+            const crac_status_t st = img_resolve(im);   // an unsettled pass: its counts, its errors
+            int zero = 0;
+            if (st == CRAC_OK) im->state.compare_exchange_strong(zero, 1);
+            return im->state.load() < 0 ? im->state.load() : CRAC_OK;
         }
         if (e != cudaErrorNotReady) {
             cudaGetLastError();
@@ -69,7 +71,9 @@ void img_unref(crac_image *im) {
             cudaGetLastError();
         }
         table_remove(im);
+        if (im->dep) img_unref(im->dep);
         Arena &pa = pinned_arena();
+        pa.free(im->ctrl_b);
         pa.free(im->fp_h);
         pa.free(im->idx_h);
         pa.free(im->off_h);
@@ -93,6 +97,81 @@ void img_unref(crac_image *im) {
 
 // Host copies of a device image's fingerprint table and chunk list (made on
 // the first request: serialization, or a restart chain resolved on the host).
+// A checkpoint that returned before its pass finished, once `done` has
+// completed: the pass's control block gives the dirty count and bytes, which
+// become the image's k, payload size, FULL flag and block sizes; an error bit
+// (or the failure of the context's previous unsettled image, whose
+// fingerprints this pass compared against) fails the image.  Idempotent;
+// the failure is stored in `state`.
+crac_status_t img_resolve(crac_image *im) {
+    crac_image *dep = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(im->mu);
+        if (!im->deferred) return im->state.load() < 0 ? im->state.load() : CRAC_OK;
+        dep = im->dep;
+        im->dep = nullptr;
+    }
+    crac_status_t st = CRAC_OK;
+    if (dep) {
+        st = img_wait(dep, 0);
+        img_unref(dep);
+    }
+    crac_image *drop = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(im->mu);
+        if (!im->deferred) return im->state.load() < 0 ? im->state.load() : CRAC_OK;
+        const CkptCtrl ctrl = *(const CkptCtrl *)im->ctrl_b.p;
+        if (st == CRAC_OK) {
+            if (ctrl.err & kErrLostCopy) {
+                im->lost = true;
+                st = CRAC_ERR_CUDA;
+            } else if (ctrl.err & kErrTimeout) {
+                st = CRAC_ERR_TIMEOUT;
+            } else if (ctrl.err) {
+                st = CRAC_ERR_CORRUPT;
+            }
+        }
+        Piece &pc = im->pieces[0];
+        const bool host = im->residency != CRAC_RESIDENCY_DEVICE;
+        const uint64_t bytes = im->sparse_pass ? ctrl.payload : ctrl.D;
+        uint64_t total = 0;
+        for (const ImgAlloc &a : im->allocs) total += a.bytes;
+        if (st == CRAC_OK && (ctrl.k > im->n_chunks || ctrl.D > total ||
+                              (im->predicted_full && (ctrl.k != im->n_chunks || ctrl.D != total))))
+            st = CRAC_ERR_CORRUPT;
+        if (st == CRAC_OK) {
+            pc.k = ctrl.k;
+            pc.bytes = bytes;
+            pc.span = im->sparse_pass ? ctrl.D : 0;
+            im->k = ctrl.k;
+            im->payload_bytes = bytes;
+            im->raw_bytes = bytes;
+            if (host) {
+                Arena &pa = pinned_arena();
+                if (bytes) pa.shrink(pc.host, bytes);
+                else pa.free(pc.host);
+                pa.shrink(im->idx_h, ctrl.k * 8);
+            } else {
+                Arena &da = device_arena(im->device);
+                da.shrink(pc.dev, ctrl.D);   // sparse: the span
+                da.shrink(pc.idx_dev, ctrl.k * 8);
+                da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
+            }
+            im->flags = (im->flags & ~CRAC_IMAGE_FULL) | (ctrl.k == im->n_chunks ? CRAC_IMAGE_FULL : 0u);
+            if ((im->flags & CRAC_IMAGE_FULL) && im->parent) {   // a FULL image needs no parent
+                drop = im->parent;
+                im->parent = nullptr;
+            }
+        } else {
+            im->state.store(st);
+        }
+        pinned_arena().free(im->ctrl_b);
+        im->deferred = false;
+    }
+    img_unref(drop);
+    return st;
+}
+
 crac_status_t img_host_tables(crac_image *im) {
     std::lock_guard<std::mutex> lk(im->mu);
     if (im->host_tables) return CRAC_OK;
@@ -154,7 +233,16 @@ crac_status_t crac_image_wait(const crac_image_t *image, uint64_t timeout_ns) {
 crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out) {
     if (!image || !out) return CRAC_ERR_INVALID_ARG;
     crac_image *im = const_cast<crac_image *>(image);
-    if (im->state.load() == 0 && im->done && cudaEventQuery(im->done) == cudaSuccess) im->state.store(1);
+    bool unsettled;
+    {
+        std::lock_guard<std::mutex> lk(im->mu);
+        unsettled = im->deferred;
+    }
+    if (unsettled) {
+        img_wait(im, 0);   // its counts are known once its pass has finished
+    } else if (im->state.load() == 0 && im->done && cudaEventQuery(im->done) == cudaSuccess) {
+        im->state.store(1);
+    }
     cudaGetLastError();
     std::memset(out, 0, sizeof(*out));
     out->lineage = im->lineage;
@@ -268,10 +356,10 @@ crac_status_t sparse_range(crac_image *im, Piece &pc, uint64_t a, uint64_t b, ui
 // Serialization is the whole range; ranged reads let a caller stream an
 // image out (to a file, or to a checker) without holding it whole.
 crac_status_t read_range(crac_image *im, uint64_t offset, uint8_t *dst, uint64_t n) {
+    TRY(img_wait(im, 0));   // an unsettled pass's sizes are known once it has finished
     const uint64_t total = serialized_size(im);
     if (offset > total || n > total - offset) return CRAC_ERR_INVALID_ARG;
     if (n == 0) return CRAC_OK;
-    TRY(img_wait(im, 0));
     TRY(img_host_tables(im));
     const uint64_t end = offset + n;
     // Copy the part of section [s0, s0 + len) that the range covers.
@@ -318,6 +406,7 @@ crac_status_t read_range(crac_image *im, uint64_t offset, uint8_t *dst, uint64_t
 crac_status_t crac_image_serialize(const crac_image_t *image, void *dst, size_t cap, size_t *need) {
     if (!image || !need) return CRAC_ERR_INVALID_ARG;
     crac_image *im = const_cast<crac_image *>(image);
+    TRY(img_wait(im, 0));
     const uint64_t total = serialized_size(im);
     *need = (size_t)total;
     if (!dst) return CRAC_OK;

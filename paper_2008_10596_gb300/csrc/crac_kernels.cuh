@@ -154,6 +154,12 @@ cudaError_t launch_gather_range(const CkptDesc *d, uint32_t log2_chunk, const ui
                                 CkptCtrl *ctrl, int grid, cudaStream_t s);
 
 cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s);
+
+// Side-stream drain of a delta pass into host images, sized on the device
+// from the pass's control block (crac_drain.cu); prepare_drain loads it.
+cudaError_t prepare_drain();
+cudaError_t launch_drain(const CkptCtrl *ctrl, const uint8_t *src, uint8_t *dst, uint64_t cap,
+                         const uint64_t *idx_src, uint64_t *idx_dst, uint64_t idx_cap, int grid, cudaStream_t s);
 // One piece of a device-resident image in a multi-image restore: its chunk
 // list, offsets and payload, where its entries start in the combined entry
 // space, its image's position in the chain and its descriptor range.

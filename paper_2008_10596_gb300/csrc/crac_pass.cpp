@@ -27,7 +27,7 @@ crac_status_t ctx_init(crac_ctx *c, const crac_config_t *cfg_in) {
     if (cfg.chunks_per_tile > 256) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel > CRAC_PASS_SPARSE) return CRAC_ERR_INVALID_ARG;
     if (cfg.flags & ~(CRAC_FLAG_STAGED_RESTORE | CRAC_FLAG_INCREMENTAL_RESTORE | CRAC_FLAG_DIRECT_DRAIN |
-                      CRAC_FLAG_COMPRESS))
+                      CRAC_FLAG_COMPRESS | CRAC_FLAG_WAIT_PASS))
         return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && (cfg.flags & CRAC_FLAG_COMPRESS)) return CRAC_ERR_INVALID_ARG;
     if (cfg.pass_kernel == CRAC_PASS_SPARSE && cfg.image_residency != CRAC_RESIDENCY_DEVICE)
@@ -63,6 +63,7 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     for (cudaEvent_t &e : c->sev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&c->ev_r0));
     CK(cudaEventCreate(&c->ev_r1));
+    CK(prepare_drain());
     TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl) + 64));   // + the encoder's total and error bits
     TRY(ensure_host(c->serr_h, 256));
     if (c->cfg.reserve_host_bytes) {
@@ -85,13 +86,16 @@ void ctx_free_all(crac_ctx *c) {
         return;
     }
     DeviceGuard g(c->device);
+    ctx_settle(c, true);
+    img_unref(c->settled.parent);
+    c->settled.parent = nullptr;
     cudaDeviceSynchronize();
-    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
+    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->fp[2], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
                       &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr,
                       &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff, &c->cstage, &c->zwork, &c->zoff,
                       &c->zlen})
         if (b->p) cudaFree(b->p);
-    for (HostBuf *b : {&c->desc_h, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h, &c->vdesc_h})
+    for (HostBuf *b : {&c->desc_h, &c->desc_h2, &c->ctrl_h, &c->owner_h, &c->sdesc_h, &c->soff_h, &c->serr_h, &c->vdesc_h})
         if (b->p) cudaFreeHost(b->p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
@@ -165,7 +169,7 @@ std::vector<Segment> make_segments(const std::vector<AllocRec> &allocs, const st
 
 // Build (or update) the graph memset -> fused kernel -> ctrl D2H and launch it.
 crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, const void *fn,
-                                 int threads, size_t smem, int grid, cudaStream_t s) {
+                                 int threads, size_t smem, int grid, void *ctrl_dst, cudaStream_t s) {
     if (!fn) return CRAC_ERR_INVALID_ARG;
     CkptParams Pc = P;
     void *args[] = {&Pc};
@@ -187,7 +191,7 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         // Width changes of a memset node may be rejected; rebuild then.
         if (cudaGraphExecMemsetNodeSetParams(c->gexec, c->g_memset, &mp) != cudaSuccess ||
             cudaGraphExecKernelNodeSetParams(c->gexec, c->g_kernel, &kp) != cudaSuccess ||
-            cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+            cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
                                                cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
             c->g_fn = nullptr;
@@ -201,7 +205,7 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         CK(cudaGraphCreate(&c->graph, 0));
         CK(cudaGraphAddMemsetNode(&c->g_memset, c->graph, nullptr, 0, &mp));
         CK(cudaGraphAddKernelNode(&c->g_kernel, c->graph, &c->g_memset, 1, &kp));
-        CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, c->ctrl_h.p, P.ctrl,
+        CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, ctrl_dst, P.ctrl,
                                     sizeof(CkptCtrl), cudaMemcpyDeviceToHost));
         CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
         c->g_fn = fn;
@@ -217,7 +221,8 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
 
 // Build (or update) the split-pass graph and launch it.
 crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
-                                 uint32_t log2Seg, const void *hash_fn, const int grids[3], cudaStream_t s) {
+                                 uint32_t log2Seg, const void *hash_fn, const int grids[3], void *ctrl_dst,
+                                 cudaStream_t s) {
     const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn()};
     const int thr[3] = {split_hash_threads(), split_finalize_threads(), split_gather_threads()};
     CkptParams Pc = P;
@@ -245,7 +250,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         for (int i = 0; ok && i < 3; ++i)
             ok = cudaGraphExecKernelNodeSetParams(c->sgexec, c->s_k[i], &kp[i]) == cudaSuccess;
         if (ok)
-            ok = cudaGraphExecMemcpyNodeSetParams1D(c->sgexec, c->s_copy, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+            ok = cudaGraphExecMemcpyNodeSetParams1D(c->sgexec, c->s_copy, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
                                                     cudaMemcpyDeviceToHost) == cudaSuccess;
         if (!ok) cudaGetLastError();
     }
@@ -265,7 +270,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
             CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
             prev = ev;
         }
-        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, c->ctrl_h.p, P.ctrl, sizeof(CkptCtrl),
+        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
                                     cudaMemcpyDeviceToHost));
         CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
         c->s_hash_fn = hash_fn;
@@ -276,14 +281,16 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     return CRAC_OK;
 }
 
-// One segment of the checkpoint pass; on return the ctrl block is on the host.
-crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_dev,
-                          const std::vector<uint64_t> &first, uint64_t *idx_d, uint64_t *off_d,
-                          uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap,
-                          cudaStream_t s, CkptCtrl *ctrl_out, float *ms) {
+// Enqueue one segment of the checkpoint pass on s, reading the baseline
+// fp[fp_cur] and writing fingerprints to fp[out_fp]; the control block is
+// copied to the host at ctrl_dst after the pass, and ev_pass is recorded.
+crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_dev,
+                             const std::vector<uint64_t> &first, uint64_t *idx_d, uint64_t *off_d,
+                             uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap, int out_fp,
+                             void *ctrl_dst, cudaStream_t s) {
     const uint64_t nseg = sg.c1 - sg.c0;
     const uint64_t *fp_old = (const uint64_t *)c->fp[c->fp_cur].p;
-    uint64_t *fp_new = (uint64_t *)c->fp[1 - c->fp_cur].p;
+    uint64_t *fp_new = (uint64_t *)c->fp[out_fp].p;
     const bool inject_wait = c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
     if (fault_hit(CRAC_FAULT_PASS)) {
         t_last_cuda = (int)cudaErrorLaunchFailure;
@@ -341,7 +348,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         const int gf = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2);
         const int gg = c->sm_count * 8;
         const int grids[3] = {gh, gf, gg};
-        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, s));
+        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, ctrl_dst, s));
         c->last.grid = (uint32_t)gh;
         c->last.chunks_per_tile = cptF;
         c->last.warps_per_chunk = 0;
@@ -400,7 +407,7 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         P.timeout_ns = c->cfg.timeout_ns;
         P.skip_first_ticket = (inject_wait && n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
         P.first_cached = tma && c->allocs.size() <= ckpt_tma_cached_allocs() ? 1u : 0u;
-        TRY(launch_fused_graph(c, P, work_bytes, fn, threads, smem, grid, s));
+        TRY(launch_fused_graph(c, P, work_bytes, fn, threads, smem, grid, ctrl_dst, s));
         c->last.pass_kernel = tma ? CRAC_PASS_TMA : CRAC_PASS_LDG;
         c->last.grid = (uint32_t)grid;
         c->last.chunks_per_tile = cpt;
@@ -427,15 +434,21 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
                                    u1 - u0, idx_cap, staging, staging_cap, ctrl, g, s));
             c->last.kernel_launches += 3;
         }
-        CK(cudaMemcpyAsync(c->ctrl_h.p, ctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctrl_dst, ctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
     }
+    c->split_now = split;
     CK(cudaEventRecord(c->ev_t1, s));
     CK(cudaEventRecord(c->ev_pass, s));
-    CK(cudaEventSynchronize(c->ev_pass));
+    return CRAC_OK;
+}
+
+// The timings of the pass just enqueued (its events must have completed):
+// device time added to *ms, the split pass's per-kernel times to c->last.
+void pass_timings(crac_ctx *c, float *ms) {
     float t = 0;
-    CK(cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1));
-    *ms += t;
-    if (split) {
+    if (cudaEventElapsedTime(&t, c->ev_t0, c->ev_t1) == cudaSuccess) *ms += t;
+    cudaGetLastError();
+    if (c->split_now) {
         float a = 0, b = 0, d = 0;
         if (cudaEventElapsedTime(&a, c->sev[0], c->sev[1]) == cudaSuccess &&
             cudaEventElapsedTime(&b, c->sev[1], c->sev[2]) == cudaSuccess &&
@@ -446,6 +459,17 @@ crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_d
         }
         cudaGetLastError();
     }
+}
+
+// One segment of the checkpoint pass, waited for; on return the control
+// block is on the host.
+crac_status_t run_segment(crac_ctx *c, const Segment &sg, const CkptDesc *desc_dev,
+                          const std::vector<uint64_t> &first, uint64_t *idx_d, uint64_t *off_d,
+                          uint64_t idx_cap, uint8_t *staging, uint64_t staging_cap, int out_fp,
+                          cudaStream_t s, CkptCtrl *ctrl_out, float *ms) {
+    TRY(launch_segment(c, sg, desc_dev, first, idx_d, off_d, idx_cap, staging, staging_cap, out_fp, c->ctrl_h.p, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    pass_timings(c, ms);
     *ctrl_out = *(const CkptCtrl *)c->ctrl_h.p;
     if (ctrl_out->err & kErrLostCopy) {
         c->lost = true;
@@ -555,6 +579,296 @@ uint32_t resolve_pass_kernel(const crac_ctx *c, bool dev_res, bool all16) {
     return CRAC_PASS_LDG;
 }
 
+constexpr size_t kReservedChain = 8;   // images per chain that restart scratch is sized for ahead
+
+// The fingerprint table the next pass writes: neither the current baseline
+// nor, while passes are unsettled, the settled state's table.
+int spare_fp(const crac_ctx *c) {
+    for (int i = 0; i < 3; ++i)
+        if (i != c->fp_cur && (c->pending.empty() || i != c->settled.fp)) return i;
+    return -1;   // unreachable: at most two tables are in use
+}
+
+namespace {
+
+// Pass statistics of a settled deferred image, if no later pass has started.
+void fill_last(crac_ctx *c, const crac_image *im) {
+    if (im->seq != c->pass_seq) return;
+    c->last.k = im->k;
+    c->last.payload_bytes = im->raw_bytes;
+    c->last.stored_bytes = im->payload_bytes;
+    float ms = 0;
+    c->last.hash_ms = c->last.finalize_ms = c->last.gather_ms = 0;
+    pass_timings(c, &ms);
+    c->last.device_ms = ms;
+    if (c->prefetch_now) {
+        float pm = 0;
+        if (cudaEventElapsedTime(&pm, c->ev_p0, c->ev_p1) == cudaSuccess) c->last.prefetch_ms = pm;
+        cudaGetLastError();
+    }
+}
+
+// Settle the oldest unsettled image: wait for its pass (and drain) and
+// resolve its sizes.  On success the settled state becomes the one after it;
+// on failure the context returns to the settled state, so that its baseline
+// is as if the failed checkpoint had never been taken, and the later
+// unsettled images, which depend on it, fail too.
+void settle_front(crac_ctx *c) {
+    crac_image *im = c->pending.front();
+    c->pending.pop_front();
+    const crac_status_t st = img_wait(im, 0);
+    crac_ctx::Settled &sd = c->settled;
+    if (st == CRAC_OK) {
+        sd.fp = im->out_fp;
+        sd.valid = true;
+        sd.first.clear();
+        for (const ImgAlloc &a : im->allocs) sd.first[a.id] = a.first_chunk;
+        img_ref(im);
+        img_unref(sd.parent);
+        sd.parent = im;
+        sd.parent_epoch = im->epoch;
+        sd.epoch_max = std::max(sd.epoch_max, im->epoch);
+        if (im->had_base) {
+            c->delta_frac = (float)((double)im->k / (double)std::max<uint64_t>(im->n_chunks, 1));
+            c->delta_frac_valid = true;
+        }
+        fill_last(c, im);
+    } else {
+        if (im->lost) c->lost = true;
+        c->fp_cur = sd.fp;
+        c->base_valid = sd.valid;
+        c->base_first = sd.first;
+        img_ref(sd.parent);
+        img_unref(c->parent);
+        c->parent = sd.parent;
+        c->parent_epoch = sd.parent_epoch;
+        c->epoch_max = sd.epoch_max;
+        for (crac_image *r : c->pending) img_unref(r);   // they fail through their dep link
+        c->pending.clear();
+    }
+    img_unref(im);
+    if (c->pending.empty()) {   // the snapshot is only needed while passes are unsettled
+        img_unref(sd.parent);
+        sd.parent = nullptr;
+    }
+}
+
+}  // namespace
+
+// Settle unsettled checkpoints: all of them (block), or those whose work has
+// already completed.  A failed image reports its own error; settling it only
+// reverts the context, so this returns CRAC_OK.
+crac_status_t ctx_settle(crac_ctx *c, bool block) {
+    while (!c->pending.empty()) {
+        if (!block) {
+            const cudaError_t e = cudaEventQuery(c->pending.front()->done);
+            if (e == cudaErrorNotReady) break;
+            cudaGetLastError();
+        }
+        settle_front(c);
+    }
+    return CRAC_OK;
+}
+
+// The passes of a checkpoint that waits for each segment's dirty counts:
+// several staging segments, coded images or per-allocation launches.  Each
+// segment is enqueued, waited for, sized and drained (A2-A5) before the
+// next; on return the image's sizes are known.
+crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Segment> &segs,
+                              const std::vector<uint64_t> &first, int out_fp, bool direct, bool direct_flag,
+                              bool coded, cudaStream_t s) {
+    Arena &pa = pinned_arena();
+    Arena &da = device_arena(c->device);
+    const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
+    const uint64_t n = im->n_chunks;
+    crac_status_t st = CRAC_OK;
+    uint64_t k_base = 0, d_base = 0, raw_base = 0;
+    float ms = 0;
+    for (const Segment &sg : segs) {
+        const uint64_t nseg = sg.c1 - sg.c0;
+        Piece pc;
+        uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
+        uint8_t *stg = (uint8_t *)c->staging.p;
+        if (!host_res) {
+            // coded: pc.dev is sized by the encoder, after the pass
+            if (!coded) st = da.alloc(sg.bytes, &pc.dev);
+            if (st == CRAC_OK) st = da.alloc(nseg * 8, &pc.idx_dev);
+            if (st == CRAC_OK) st = da.alloc((nseg + 1) * 8, &pc.off_dev);
+            if (st == CRAC_OK && coded) st = da.alloc(nseg * 8, &pc.zlen_dev);
+            if (st != CRAC_OK) {
+                im->pieces.push_back(pc);
+                return st;
+            }
+            idx_d = (uint64_t *)pc.idx_dev.p;
+            if (!coded) {
+                off_d = (uint64_t *)pc.off_dev.p;
+                stg = pc.dev.p;
+            }
+        }
+        // The worst-case block comes from the pinned regions as they are
+        // (growing them, or starting their background growth, mid-loop
+        // would stall the device); without room this segment drains
+        // through staging.  The unused tail is returned after the pass.
+        const bool direct_seg = direct && pa.try_alloc(sg.bytes, &pc.host);
+        if (direct_seg) stg = pc.host.p;
+        if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) {
+            im->pieces.push_back(pc);
+            return cuda_status(cudaGetLastError());
+        }
+        CkptCtrl ctrl{};
+        st = run_segment(c, sg, (const CkptDesc *)c->desc.p, first, idx_d, off_d, nseg, stg, sg.bytes, out_fp, s,
+                         &ctrl, &ms);
+        if (st != CRAC_OK) {
+            im->pieces.push_back(pc);
+            return st;
+        }
+        pc.k0 = k_base;
+        pc.k = ctrl.k;
+        pc.off0 = d_base;
+        const bool sparse = c->sparse_ok && !host_res;
+        pc.bytes = sparse ? ctrl.payload : ctrl.D;
+        pc.span = sparse ? ctrl.D : 0;
+        bool zdirect = false;
+        if (coded && ctrl.k) {
+            uint64_t Z = 0;
+            st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zdirect);
+            if (st != CRAC_OK) {
+                im->pieces.push_back(pc);
+                return st;
+            }
+            pc.bytes = Z;
+        }
+        raw_base += sparse ? ctrl.payload : ctrl.D;
+        if (fault_hit(CRAC_FAULT_DRAIN)) {
+            im->pieces.push_back(pc);
+            t_last_cuda = (int)cudaErrorLaunchFailure;
+            return CRAC_ERR_CUDA;
+        }
+        cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
+        if (direct_seg) {
+            if (ctrl.D) pa.shrink(pc.host, ctrl.D);
+            else pa.free(pc.host);
+        } else if (host_res) {
+            if (pc.bytes && !zdirect) {
+                st = pa.alloc(pc.bytes, &pc.host);
+                if (st != CRAC_OK) {
+                    im->pieces.push_back(pc);
+                    return st;
+                }
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(pc.host.p, coded ? c->cstage.p : c->staging.p, pc.bytes,
+                                        cudaMemcpyDeviceToHost, c->side);
+            }
+        } else {
+            da.shrink(pc.dev, coded ? pc.bytes : ctrl.D);   // sparse: the span
+            da.shrink(pc.idx_dev, ctrl.k * 8);
+            da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
+            if (coded) da.shrink(pc.zlen_dev, ctrl.k * 8);
+        }
+        if (e == cudaSuccess && ctrl.k && host_res)
+            e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+        if (e == cudaSuccess && ctrl.k && host_res && coded)
+            e = cudaMemcpyAsync(im->zlen_h.p + k_base * 8, c->zlen.p, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        im->pieces.push_back(pc);
+        if (e != cudaSuccess) return cuda_status(e);
+        k_base += ctrl.k;
+        d_base += pc.bytes;
+    }
+    cudaError_t e;
+    if (host_res) {
+        e = cudaMemcpyAsync(im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+    } else {
+        // Device image: its tables stay in device memory; done once the
+        // fingerprint table has its own copy.
+        e = cudaMemcpyAsync(im->fp_dev.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(im->done, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, s);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    im->k = k_base;
+    im->payload_bytes = d_base;
+    im->raw_bytes = raw_base;
+    if (host_res) pa.shrink(im->idx_h, k_base * 8);
+    if (host_res && coded) pa.shrink(im->zlen_h, k_base * 8);
+    c->last.k = k_base;
+    c->last.payload_bytes = raw_base;
+    c->last.stored_bytes = d_base;
+    c->last.segments = (uint32_t)segs.size();
+    c->last.device_ms = ms;
+    if (c->prefetch_now) {
+        float pm = 0;
+        cudaEventElapsedTime(&pm, c->ev_p0, c->ev_p1);
+        c->last.prefetch_ms = pm;
+    }
+    return CRAC_OK;
+}
+
+// A single-segment pass into uncoded images, enqueued and not waited for
+// (A2-A5).  Its control block lands in the image's pinned ctrl_b; a device
+// image's payload, chunk list and offsets go to worst-case blocks of the
+// device arena, a host image's payload to the pinned block in pieces[0] (the
+// pass writes it there directly, or the side stream copies it from staging:
+// by the copy engine for a FULL pass, whose size is known, else by
+// drain_kernel, which reads the size from the control block).  The blocks
+// are shrunk to the counts, and the counts become the image's, when the
+// image settles.
+crac_status_t checkpoint_enqueue(crac_ctx *c, crac_image *im, const Segment &sg, const std::vector<uint64_t> &first,
+                                 int out_fp, bool direct, bool any_base, cudaStream_t s) {
+    Arena &pa = pinned_arena();
+    Arena &da = device_arena(c->device);
+    const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
+    const uint64_t n = im->n_chunks;
+    if (im->pieces.empty()) im->pieces.push_back(Piece{});
+    Piece &pc = im->pieces[0];
+    uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
+    uint8_t *stg = (uint8_t *)c->staging.p;
+    if (!host_res) {
+        TRY(da.alloc(sg.bytes, &pc.dev));
+        TRY(da.alloc(n * 8, &pc.idx_dev));
+        TRY(da.alloc((n + 1) * 8, &pc.off_dev));
+        idx_d = (uint64_t *)pc.idx_dev.p;
+        off_d = (uint64_t *)pc.off_dev.p;
+        stg = pc.dev.p;
+    } else if (direct) {
+        stg = pc.host.p;
+    }
+    TRY(pa.alloc(sizeof(CkptCtrl), &im->ctrl_b));
+    CK(cudaStreamWaitEvent(s, c->ev_last, 0));
+    TRY(launch_segment(c, sg, (const CkptDesc *)c->desc.p, first, idx_d, off_d, n, stg, sg.bytes, out_fp,
+                       im->ctrl_b.p, s));
+    if (fault_hit(CRAC_FAULT_DRAIN)) {
+        t_last_cuda = (int)cudaErrorLaunchFailure;
+        return CRAC_ERR_CUDA;
+    }
+    if (host_res) {
+        CK(cudaStreamWaitEvent(c->side, c->ev_pass, 0));
+        if (!any_base) {   // FULL: every chunk, n entries, the segment's bytes
+            if (!direct) CK(cudaMemcpyAsync(pc.host.p, c->staging.p, sg.bytes, cudaMemcpyDeviceToHost, c->side));
+            CK(cudaMemcpyAsync(im->idx_h.p, idx_d, n * 8, cudaMemcpyDeviceToHost, c->side));
+        } else {
+            CK(launch_drain((const CkptCtrl *)c->work.p, direct ? nullptr : (const uint8_t *)c->staging.p, pc.host.p,
+                            sg.bytes, idx_d, (uint64_t *)im->idx_h.p, n, c->sm_count * 2, c->side));
+        }
+        CK(cudaMemcpyAsync(im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side));
+        CK(cudaEventRecord(im->done, c->side));
+        CK(cudaEventRecord(c->ev_last, c->side));
+    } else {
+        CK(cudaMemcpyAsync(im->fp_dev.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaEventRecord(im->done, s));
+        CK(cudaEventRecord(c->ev_last, s));
+    }
+    pc.k0 = 0;
+    pc.off0 = 0;
+    im->deferred = true;
+    im->sparse_pass = c->sparse_ok && !host_res;
+    im->predicted_full = !any_base;
+    c->last.segments = 1;
+    return CRAC_OK;
+}
+
 crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
     if (!out) return CRAC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -570,6 +884,66 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         tracked += c->allocs[a].bytes;
     }
     const uint64_t n = first[na];
+    for (const AllocRec &r : c->allocs)   // host memory is read through its device mapping
+        if (r.kind == CRAC_KIND_HOST && !c->uva) return CRAC_ERR_UNSUPPORTED;
+    const bool dev_res = c->cfg.image_residency == CRAC_RESIDENCY_DEVICE;
+    const bool host_res = !dev_res;
+    // Coded images: the pass gathers into device staging as usual and the
+    // encoder writes the streams (encode_segment).
+    const bool coded = (c->cfg.flags & CRAC_FLAG_COMPRESS) != 0;
+    // Segments bounded by the staging capacity.
+    uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
+    cap = std::max(round_up(cap, 256), S);
+    // Coded images: the encoder's aligned bulk reads may pass the end of the
+    // payload by up to 15 bytes, so with a given staging capacity (a
+    // configured one, or a server lease that cannot grow) the segments leave
+    // 256 bytes of it free.
+    if (coded && c->cfg.staging_bytes && cap >= S + 256) cap -= 256;
+    const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
+    uint64_t max_seg_chunks = 0, max_seg_bytes = 0;
+    for (const Segment &sg : segs) {
+        max_seg_chunks = std::max(max_seg_chunks, sg.c1 - sg.c0);
+        max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
+    }
+    Arena &pa = pinned_arena();
+    Arena &da = device_arena(c->device);
+
+    // A single-segment batched pass into uncoded images is not waited for:
+    // the call returns once it is enqueued, and the image's sizes are settled
+    // when its work has completed (img_resolve).  Every other pass waits for
+    // the dirty counts of each segment before the next one.  At most two
+    // checkpoints stay unsettled; earlier ones whose work has completed are
+    // settled here, and all of them before a pass that waits.
+    bool defer = n > 0 && segs.size() == 1 && !coded && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
+                 (dev_res || c->uva) && !(c->cfg.flags & CRAC_FLAG_WAIT_PASS);
+    TRY(ctx_settle(c, false));
+    while (c->pending.size() >= 2) settle_front(c);
+    // Which chunks have a baseline (no settling after this point may move it).
+    auto base_of = [&](size_t a) {
+        if (!c->base_valid) return kNoBase;
+        auto it = c->base_first.find(c->allocs[a].id);
+        return it == c->base_first.end() ? kNoBase : it->second;
+    };
+    bool any_base = false;
+    for (size_t a = 0; a < na; ++a) any_base |= base_of(a) != kNoBase;
+    // A host image's payload block is taken before the pass: the whole
+    // segment for a FULL pass (its size is known), else the worst case from
+    // the pinned regions as they are (growing them mid-loop would stall the
+    // device); without room the pass waits instead.
+    Piece dpc;
+    if (defer && host_res) {
+        if (!any_base) {
+            if (pa.alloc(segs[0].bytes, &dpc.host) != CRAC_OK) defer = false;
+        } else if (!pa.try_alloc(segs[0].bytes, &dpc.host)) {
+            defer = false;
+        }
+    }
+    if (!defer) {
+        pa.free(dpc.host);
+        TRY(ctx_settle(c, true));
+        any_base = false;
+        for (size_t a = 0; a < na; ++a) any_base |= base_of(a) != kNoBase;
+    }
     c->last = crac_pass_info_t{};
     c->last.tracked_bytes = tracked;
     c->last.n_chunks = n;
@@ -585,15 +959,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
     im->allocs.resize(na);
     for (size_t a = 0; a < na; ++a)
         im->allocs[a] = ImgAlloc{c->allocs[a].id, c->allocs[a].ptr, c->allocs[a].bytes, c->allocs[a].kind, first[a]};
-    CK(cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming));
-
-    for (const AllocRec &r : c->allocs)   // host memory is read through its device mapping
-        if (r.kind == CRAC_KIND_HOST && !c->uva) {
-            cudaEventDestroy(im->done);
-            return CRAC_ERR_UNSUPPORTED;
-        }
-    Arena &pa = pinned_arena();
-    Arena &da = device_arena(c->device);
+    if (cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming) != cudaSuccess) {
+        pa.free(dpc.host);
+        return cuda_status(cudaGetLastError());
+    }
     crac_status_t st = CRAC_OK;
     auto fail = [&](crac_status_t code) {
         cudaStreamSynchronize(s);
@@ -602,10 +971,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         free_image_blocks(im.release());
         return code;
     };
+    if (dpc.host.region >= 0) im->pieces.push_back(dpc);   // freed with the image on failure
 
-    const bool dev_res = c->cfg.image_residency == CRAC_RESIDENCY_DEVICE;
     im->host_tables = !dev_res;
-    bool had_base = false;   // some chunk had a baseline: the pass measured a dirty fraction
+    int out_fp = c->fp_cur;
     if (n > 0) {
         if (dev_res) {
             st = da.alloc(n * 8, &im->fp_dev);
@@ -617,23 +986,30 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         // fingerprint tables and descriptors
         // Only the output table may grow: the baseline table keeps the previous
         // layout, which it still fully holds.
-        st = ensure_dev(c->fp[1 - c->fp_cur], n * 8);
+        out_fp = spare_fp(c);
+        // Two pinned descriptor buffers in turn: an unsettled pass's copy may
+        // not have run yet when the next pass writes its own.
+        HostBuf &dbuf = c->desc_flip ? c->desc_h2 : c->desc_h;
+        c->desc_flip ^= 1;
+        // Tables grow together, so that a steady checkpoint loop allocates
+        // nothing (allocating may synchronize the device): every fingerprint
+        // table that holds nothing still needed (not the baseline, not the
+        // settled state's) and both descriptor buffers (growing one in use
+        // waits for its copy).
+        for (int t = 0; t < 3 && st == CRAC_OK; ++t)
+            if (t == out_fp || (t != c->fp_cur && (c->pending.empty() || t != c->settled.fp)))
+                st = ensure_dev(c->fp[t], n * 8);
         if (st == CRAC_OK) st = ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8));
         if (st == CRAC_OK) st = ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8));
+        if (st == CRAC_OK) st = ensure_host(c->desc_h2, na * (sizeof(CkptDesc) + 8));
         if (st != CRAC_OK) return fail(st);
-        CkptDesc *dh = (CkptDesc *)c->desc_h.p;
+        CkptDesc *dh = (CkptDesc *)dbuf.p;
         uint64_t *prefix_h = (uint64_t *)(dh + na);   // payload bytes before each allocation
-        bool any_base = false, all16 = true;
+        bool all16 = true;
         uint64_t pre = 0;
         for (size_t a = 0; a < na; ++a) {
-            uint64_t bf = kNoBase;
-            if (c->base_valid) {
-                auto it = c->base_first.find(c->allocs[a].id);
-                if (it != c->base_first.end()) bf = it->second;
-            }
-            any_base |= bf != kNoBase;
             all16 &= (c->allocs[a].bytes & 15) == 0;
-            dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], bf};
+            dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], base_of(a)};
             prefix_h[a] = pre;
             pre += c->allocs[a].bytes;
         }
@@ -641,7 +1017,6 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         c->pass_now = resolve_pass_kernel(c, dev_res, all16);
         c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && dev_res && all16 &&
                        c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
-        had_base = any_base;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
         if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -649,6 +1024,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         // Managed regions migrate to the device before they are read.
         bool any_managed = false;
         for (const AllocRec &r : c->allocs) any_managed |= r.kind == CRAC_KIND_MANAGED;
+        c->prefetch_now = any_managed;
         if (any_managed) {
             cudaEventRecord(c->ev_p0, s);
             cudaMemLocation loc{};
@@ -661,24 +1037,6 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             }
             cudaEventRecord(c->ev_p1, s);
         }
-        // Segments bounded by the staging capacity.
-        uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
-        cap = std::max(round_up(cap, 256), S);
-        // Coded images: the encoder's aligned bulk reads may pass the end of
-        // the payload by up to 15 bytes, so with a given staging capacity (a
-        // configured one, or a server lease that cannot grow) the segments
-        // leave 256 bytes of it free.
-        if ((c->cfg.flags & CRAC_FLAG_COMPRESS) && c->cfg.staging_bytes && cap >= S + 256) cap -= 256;
-        const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
-        uint64_t max_seg_chunks = 0, max_seg_bytes = 0;
-        for (const Segment &sg : segs) {
-            max_seg_chunks = std::max(max_seg_chunks, sg.c1 - sg.c0);
-            max_seg_bytes = std::max(max_seg_bytes, sg.bytes);
-        }
-        const bool host_res = c->cfg.image_residency == CRAC_RESIDENCY_HOST;
-        // Coded images: the pass gathers into device staging as usual and the
-        // encoder writes the streams (encode_segment).
-        const bool coded = (c->cfg.flags & CRAC_FLAG_COMPRESS) != 0;
         // Direct drain: the pass (uncoded) or the encoder (coded) writes the
         // payload straight into the image's pinned block through its device
         // mapping (not the TMA pass, whose bulk stores stay within device
@@ -701,155 +1059,65 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             if (st == CRAC_OK && host_res) st = pa.alloc(n * 8, &im->zlen_h);
             if (st != CRAC_OK) return fail(st);
         }
-        uint64_t k_base = 0, d_base = 0, raw_base = 0;
-        float ms = 0;
-        for (const Segment &sg : segs) {
-            const uint64_t nseg = sg.c1 - sg.c0;
-            Piece pc;
-            uint64_t *idx_d = (uint64_t *)c->idx.p, *off_d = (uint64_t *)c->off.p;
-            uint8_t *stg = (uint8_t *)c->staging.p;
-            if (!host_res) {
-                // coded: pc.dev is sized by the encoder, after the pass
-                if (!coded) st = da.alloc(sg.bytes, &pc.dev);
-                if (st == CRAC_OK) st = da.alloc(nseg * 8, &pc.idx_dev);
-                if (st == CRAC_OK) st = da.alloc((nseg + 1) * 8, &pc.off_dev);
-                if (st == CRAC_OK && coded) st = da.alloc(nseg * 8, &pc.zlen_dev);
-                if (st != CRAC_OK) {
-                    da.free(pc.dev);
-                    da.free(pc.idx_dev);
-                    da.free(pc.off_dev);
-                    da.free(pc.zlen_dev);
-                    return fail(st);
-                }
-                idx_d = (uint64_t *)pc.idx_dev.p;
-                if (!coded) {
-                    off_d = (uint64_t *)pc.off_dev.p;
-                    stg = pc.dev.p;
-                }
-            }
-            // The worst-case block comes from the pinned regions as they are
-            // (growing them, or starting their background growth, mid-loop
-            // would stall the device); without room this segment drains
-            // through staging.  The unused tail is returned after the pass.
-            const bool direct_seg = direct && pa.try_alloc(sg.bytes, &pc.host);
-            if (direct_seg) stg = pc.host.p;
-            if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) {
-                im->pieces.push_back(pc);
-                return fail(cuda_status(cudaGetLastError()));
-            }
-            CkptCtrl ctrl{};
-            st = run_segment(c, sg, (const CkptDesc *)c->desc.p, first, idx_d, off_d, nseg, stg, sg.bytes, s,
-                             &ctrl, &ms);
-            if (st != CRAC_OK) {
-                im->pieces.push_back(pc);
-                return fail(st);
-            }
-            pc.k0 = k_base;
-            pc.k = ctrl.k;
-            pc.off0 = d_base;
-            const bool sparse = c->sparse_ok && !host_res;
-            pc.bytes = sparse ? ctrl.payload : ctrl.D;
-            pc.span = sparse ? ctrl.D : 0;
-            bool zdirect = false;
-            if (coded && ctrl.k) {
-                uint64_t Z = 0;
-                st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zdirect);
-                if (st != CRAC_OK) {
-                    im->pieces.push_back(pc);
-                    return fail(st);
-                }
-                pc.bytes = Z;
-            }
-            raw_base += sparse ? ctrl.payload : ctrl.D;
-            if (fault_hit(CRAC_FAULT_DRAIN)) {
-                im->pieces.push_back(pc);
-                t_last_cuda = (int)cudaErrorLaunchFailure;
-                return fail(CRAC_ERR_CUDA);
-            }
-            cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
-            if (direct_seg) {
-                if (ctrl.D) pa.shrink(pc.host, ctrl.D);
-                else pa.free(pc.host);
-            } else if (host_res) {
-                if (pc.bytes && !zdirect) {
-                    st = pa.alloc(pc.bytes, &pc.host);
-                    if (st != CRAC_OK) {
-                        im->pieces.push_back(pc);
-                        return fail(st);
-                    }
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(pc.host.p, coded ? c->cstage.p : c->staging.p, pc.bytes,
-                                            cudaMemcpyDeviceToHost, c->side);
-                }
-            } else {
-                da.shrink(pc.dev, coded ? pc.bytes : ctrl.D);   // sparse: the span
-                da.shrink(pc.idx_dev, ctrl.k * 8);
-                da.shrink(pc.off_dev, (ctrl.k + 1) * 8);
-                if (coded) da.shrink(pc.zlen_dev, ctrl.k * 8);
-            }
-            if (e == cudaSuccess && ctrl.k && host_res)
-                e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
-            if (e == cudaSuccess && ctrl.k && host_res && coded)
-                e = cudaMemcpyAsync(im->zlen_h.p + k_base * 8, c->zlen.p, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
-            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
-            im->pieces.push_back(pc);
-            if (e != cudaSuccess) return fail(cuda_status(e));
-            k_base += ctrl.k;
-            d_base += pc.bytes;
-        }
-        cudaError_t e;
-        if (host_res) {
-            e = cudaMemcpyAsync(im->fp_h.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToHost, c->side);
-            if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
-            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
+        // A restart of a chain of up to kReservedChain images of this layout
+        // finds its scratch ready.
+        if (c->uva && (dev_res || !(c->cfg.flags & CRAC_FLAG_STAGED_RESTORE)))
+            st = reserve_restart(c, n, na * kReservedChain, segs.size() * kReservedChain);
+        if (st != CRAC_OK) return fail(st);
+        if (defer) {
+            st = checkpoint_enqueue(c, im.get(), segs[0], first, out_fp, direct, any_base, s);
+            if (st != CRAC_OK) return fail(st);
         } else {
-            // Device image: its tables stay in device memory; done once the
-            // fingerprint table has its own copy.
-            e = cudaMemcpyAsync(im->fp_dev.p, c->fp[1 - c->fp_cur].p, n * 8, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaEventRecord(im->done, s);
-            if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, s);
-        }
-        if (e != cudaSuccess) return fail(cuda_status(e));
-        im->k = k_base;
-        im->payload_bytes = d_base;
-        im->raw_bytes = raw_base;
-        if (host_res) pa.shrink(im->idx_h, k_base * 8);
-        if (host_res && coded) pa.shrink(im->zlen_h, k_base * 8);
-        c->last.k = k_base;
-        c->last.payload_bytes = raw_base;
-        c->last.stored_bytes = d_base;
-        c->last.segments = (uint32_t)segs.size();
-        c->last.device_ms = ms;
-        if (any_managed) {
-            float pm = 0;
-            cudaEventElapsedTime(&pm, c->ev_p0, c->ev_p1);
-            c->last.prefetch_ms = pm;
+            st = checkpoint_wait(c, im.get(), segs, first, out_fp, direct, direct_flag, coded, s);
+            if (st != CRAC_OK) return fail(st);
+            if (any_base) {
+                c->delta_frac = (float)((double)im->k / (double)n);
+                c->delta_frac_valid = true;
+            }
         }
     } else {
         CK(cudaEventRecord(im->done, s));
     }
 
-    // Commit: the new fingerprints become the baseline.
-    im->flags = (im->k == n ? CRAC_IMAGE_FULL : 0u) | ((c->cfg.flags & CRAC_FLAG_COMPRESS) ? CRAC_IMAGE_CODED : 0u);
-    if (had_base) {
-        c->delta_frac = (float)((double)im->k / (double)n);
-        c->delta_frac_valid = true;
-    }
-    if (!(im->flags & CRAC_IMAGE_FULL) && c->parent) {
+    // Commit: the new fingerprints become the baseline (for an unsettled
+    // pass, provisionally: a failure found when it settles reverts this).
+    im->flags = (im->deferred ? (any_base ? 0u : CRAC_IMAGE_FULL) : (im->k == n ? CRAC_IMAGE_FULL : 0u)) |
+                (coded ? CRAC_IMAGE_CODED : 0u);
+    if (!(im->flags & CRAC_IMAGE_FULL) && c->parent) {   // an unsettled delta drops it if it turns out FULL
         img_ref(c->parent);
         im->parent = c->parent;
     }
-    c->fp_cur = 1 - c->fp_cur;
+    im->seq = ++c->pass_seq;
+    if (im->deferred) {
+        crac_ctx::Settled &sd = c->settled;
+        if (c->pending.empty()) {   // the state a failure of this pass reverts to
+            sd.fp = c->fp_cur;
+            sd.valid = c->base_valid;
+            sd.first = c->base_first;
+            img_ref(c->parent);
+            img_unref(sd.parent);
+            sd.parent = c->parent;
+            sd.parent_epoch = c->parent_epoch;
+            sd.epoch_max = c->epoch_max;
+        } else {
+            im->dep = c->pending.back();
+            img_ref(im->dep);
+        }
+        im->out_fp = out_fp;
+        im->had_base = any_base;
+    }
+    c->fp_cur = out_fp;
     c->base_first.clear();
     for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
     c->base_valid = true;
     c->epoch_max = im->epoch;
     c->parent_epoch = im->epoch;
     crac_image *img = im.release();
-    img->refs.store(2);   // the caller's reference and the context's
+    img->refs.store(img->deferred ? 3 : 2);   // the caller's, the context's (and the unsettled list's)
     img_unref(c->parent);
     c->parent = img;
     table_add(img);
+    if (img->deferred) c->pending.push_back(img);
     *out = img;
     return CRAC_OK;
 }
@@ -880,9 +1148,12 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     *d_out = 0;
     for (const AllocRec &r : c->allocs)
         if (r.kind == CRAC_KIND_HOST && !c->uva) return CRAC_ERR_UNSUPPORTED;
+    TRY(ctx_settle(c, true));
     c->last = crac_pass_info_t{};
+    ++c->pass_seq;
     if (n == 0) return CRAC_OK;
-    TRY(ensure_dev(c->fp[1 - c->fp_cur], n * 8));
+    const int out_fp = spare_fp(c);
+    TRY(ensure_dev(c->fp[out_fp], n * 8));
     TRY(ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8)));
     TRY(ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8)));
     CkptDesc *dh = (CkptDesc *)c->desc_h.p;
@@ -923,7 +1194,7 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     for (const Segment &sg : segs) {
         CkptCtrl ctrl{};
         TRY(run_segment(c, sg, (const CkptDesc *)c->desc.p, first, (uint64_t *)c->idx.p, (uint64_t *)c->off.p,
-                        sg.c1 - sg.c0, (uint8_t *)c->staging.p, sg.bytes, s, &ctrl, ms));
+                        sg.c1 - sg.c0, (uint8_t *)c->staging.p, sg.bytes, out_fp, s, &ctrl, ms));
         *k_out += ctrl.k;
         *d_out += c->sparse_ok ? ctrl.payload : ctrl.D;
     }
@@ -931,7 +1202,8 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     if (commit) {
         c->prev_base_first = c->base_first;
         c->prev_base_valid = c->base_valid;
-        c->fp_cur = 1 - c->fp_cur;
+        c->prev_fp = c->fp_cur;
+        c->fp_cur = out_fp;
         c->base_first.clear();
         for (size_t a = 0; a < na; ++a) c->base_first[c->allocs[a].id] = first[a];
         c->base_valid = true;

@@ -63,6 +63,22 @@ crac_status_t img_offsets(crac_image *im) {
     return CRAC_OK;
 }
 
+// Scratch of a device-side restore of nt target chunks from a chain with
+// `descs` allocation entries and `pieces` pieces in all (owner map, scatter
+// descriptors and their pinned copy, error word).  Checkpoints size it for
+// a chain of a few images ahead of time, so that a restart allocates
+// nothing (allocating may synchronize the device, which a request server
+// would feel as a latency spike).
+crac_status_t reserve_restart(crac_ctx *c, uint64_t nt, size_t descs, size_t pieces) {
+    const size_t bytes = round_up(descs * sizeof(ScatterDesc), 256) +
+                         round_up(std::max<size_t>(pieces, 1) * sizeof(RestorePiece), 256);
+    TRY(ensure_dev(c->owner, std::max<uint64_t>(nt, 1) * 4));
+    TRY(ensure_dev(c->sdesc, bytes));
+    TRY(ensure_host(c->sdesc_h, bytes));
+    TRY(ensure_dev(c->serr, 256));
+    return CRAC_OK;
+}
+
 // Restore a chain on the device, resolved in three launches over every
 // piece of every image of the chain: owner marks (the newest image wins), a
 // coverage check, owner-filtered scatter -- no host round trip before them.
@@ -92,12 +108,9 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
         for (const Piece &pc : im->pieces) n_pieces += pc.k ? 1 : 0;
     }
     const size_t desc_bytes = round_up(total_desc * sizeof(ScatterDesc), 256);
-    const size_t piece_bytes = round_up(std::max<size_t>(n_pieces, 1) * sizeof(RestorePiece), 256);
-    TRY(ensure_dev(c->owner, std::max<uint64_t>(nt, 1) * 4));
-    TRY(ensure_dev(c->sdesc, desc_bytes + piece_bytes));
-    TRY(ensure_host(c->sdesc_h, desc_bytes + piece_bytes));
-    TRY(ensure_dev(c->serr, 256));
-    TRY(ensure_dev(c->fp[1 - c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
+    TRY(reserve_restart(c, nt, total_desc, n_pieces));
+    const int spare = spare_fp(c);
+    TRY(ensure_dev(c->fp[spare], std::max<uint64_t>(nt, 1) * 8));
     if (c->ev_last) CK(cudaEventSynchronize(c->ev_last));   // pinned descriptor scratch reuse
     ScatterDesc *sdh = (ScatterDesc *)c->sdesc_h.p;
     RestorePiece *rph = (RestorePiece *)((uint8_t *)c->sdesc_h.p + desc_bytes);
@@ -174,7 +187,7 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     if (incremental) CK(cudaMemcpyAsync(c->ctrl_h.p, vctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
     if (nt) {
         const void *fp = img->residency == CRAC_RESIDENCY_DEVICE ? (const void *)img->fp_dev.p : (const void *)img->fp_h.p;
-        CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, fp, nt * 8, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(c->fp[spare].p, fp, nt * 8, cudaMemcpyDefault, s));
     }
     CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_last, s));
@@ -194,14 +207,18 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
         }
     }
     c->last_restart = ri;
-    c->fp_cur = 1 - c->fp_cur;
+    c->fp_cur = spare;
     restart_commit(c, img);
     return CRAC_OK;
 }
 
 crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     if (!img) return CRAC_ERR_INVALID_ARG;
-    if (img->state.load() < 0) return img->state.load();
+    {
+        DeviceGuard g(c->device);
+        TRY(ctx_settle(c, true));   // the context's unsettled checkpoints first
+    }
+    TRY(img_wait(img, 0));          // its sizes and FULL flag are known once its pass has finished
     if (img->chunk_bytes != (1u << c->log2S)) return CRAC_ERR_IMAGE_MISMATCH;
     if (img->allocs.size() != c->allocs.size()) return CRAC_ERR_IMAGE_MISMATCH;
     for (size_t a = 0; a < c->allocs.size(); ++a)
@@ -215,6 +232,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
         if (chain.size() >= 65535) return CRAC_ERR_UNSUPPORTED;
         crac_image *p = img_parent(cur);
         if (!p || p->lineage != cur->lineage || p->chunk_bytes != cur->chunk_bytes) return CRAC_ERR_IMAGE_MISMATCH;
+        TRY(img_wait(p, 0));
         cur = p;
     }
     std::reverse(chain.begin(), chain.end());
@@ -444,9 +462,10 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     }
     // The image's fingerprints go to the spare table, which becomes the
     // baseline only once the restore has succeeded.
-    TRY(ensure_dev(c->fp[1 - c->fp_cur], std::max<uint64_t>(nt, 1) * 8));
+    const int spare = spare_fp(c);
+    TRY(ensure_dev(c->fp[spare], std::max<uint64_t>(nt, 1) * 8));
     CK(cudaEventRecord(c->ev_r1, s));
-    if (nt) CK(cudaMemcpyAsync(c->fp[1 - c->fp_cur].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
+    if (nt) CK(cudaMemcpyAsync(c->fp[spare].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
@@ -454,7 +473,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     cudaEventElapsedTime(&ri.device_ms, c->ev_r0, c->ev_r1);
     ri.chunks_rewritten = nt;   // the staged path restores every chunk
     c->last_restart = ri;
-    c->fp_cur = 1 - c->fp_cur;
+    c->fp_cur = spare;
     restart_commit(c, img);
     (void)na;
     return CRAC_OK;

@@ -345,6 +345,20 @@ struct crac_image {
     cudaEvent_t done = nullptr;     // drain complete
     std::atomic<int> state{0};      // 0 pending, 1 complete, < 0 failed (status)
     std::mutex mu;
+    // A checkpoint that returned before its pass finished (single segment):
+    // the pass's counts land in ctrl_b, and k, the payload size, the FULL flag
+    // and the pieces' block sizes are settled once `done` has completed
+    // (img_resolve).  dep is the context's previous unsettled image, whose
+    // failure fails this one too.
+    bool deferred = false;
+    bool sparse_pass = false;       // the pass left an uncompacted payload
+    bool predicted_full = false;    // no baseline anywhere: k and D known before the pass
+    Block ctrl_b;                   // pinned landing of the pass's control block
+    crac_image *dep = nullptr;
+    int out_fp = -1;                // fingerprint table of the context the pass wrote
+    bool had_base = false;          // some chunk had a baseline (the pass measured a dirty fraction)
+    bool lost = false;              // its kernel reported kErrLostCopy
+    uint64_t seq = 0;               // the context's pass counter at this pass
 };
 
 namespace crac {
@@ -355,6 +369,7 @@ void img_ref(crac_image *im);
 void img_unref(crac_image *im);
 crac_status_t img_wait(const crac_image *cim, uint64_t timeout_ns);
 crac_status_t img_host_tables(crac_image *im);
+crac_status_t img_resolve(crac_image *im);
 crac_image *img_parent(crac_image *im);
 void free_image_blocks(crac_image *im);
 
@@ -383,16 +398,21 @@ struct crac_ctx {
     uint64_t epoch_max = 0;
     crac_image *parent = nullptr;
     uint64_t parent_epoch = kNoParent;
-    // fingerprint baseline
-    DevBuf fp[2];
+    // fingerprint baseline: fp[fp_cur] holds the fingerprints the next pass
+    // compares against; a pass writes spare_fp(); three tables, so that the
+    // baseline of the last settled image survives while up to two images
+    // are unsettled (their passes may still fail)
+    DevBuf fp[3];
     int fp_cur = 0;
+    int prev_fp = 1;             // autotuner shadows: the table before the last committed trial pass
     bool base_valid = false;
     std::unordered_map<uint64_t, uint64_t> base_first;   // alloc id -> first chunk in fp[fp_cur]
     std::unordered_map<uint64_t, uint64_t> prev_base_first;   // autotuner shadows: the baseline before the last
     bool prev_base_valid = false;                             // committed trial pass (still in fp[1 - fp_cur])
     // pass scratch
     DevBuf desc, work, idx, off, staging, lens, carry;
-    HostBuf desc_h, ctrl_h;
+    HostBuf desc_h, desc_h2, ctrl_h;
+    int desc_flip = 0;           // which of desc_h / desc_h2 the next pass fills
     DevBuf cstage, zwork, zoff, zlen;   // CRAC_FLAG_COMPRESS: streams, encoder scratch, tables
     // restart scratch
     DevBuf owner, sdesc, sidx, soff, serr;
@@ -420,11 +440,25 @@ struct crac_ctx {
     bool full_copy_ok = false;   // current pass: no baseline anywhere and 16-byte sizes
     bool sparse_ok = false;      // current pass: CRAC_PASS_SPARSE, device images, 16-byte sizes
     uint32_t pass_now = CRAC_PASS_SPLIT;   // kernel of the current pass (CRAC_PASS_AUTO resolved)
+    bool split_now = false;      // the current pass is the split graph (per-kernel timing events)
+    bool prefetch_now = false;   // the current pass prefetched managed memory (ev_p0 / ev_p1)
     float delta_frac = 0.f;      // dirty chunks / chunks of the last pass that had a baseline
     bool delta_frac_valid = false;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     bool cuda_ready = false;
     bool lost = false;   // a kernel reported kErrLostCopy: no further device work on this context
+    // Checkpoints whose passes were still running when the call returned, in
+    // order, and the state after the last settled one (the state a failure of
+    // an unsettled pass reverts to).
+    std::deque<crac_image *> pending;
+    struct Settled {
+        int fp = 0;
+        bool valid = false;
+        std::unordered_map<uint64_t, uint64_t> first;
+        crac_image *parent = nullptr;   // strong reference
+        uint64_t parent_epoch = kNoParent, epoch_max = 0;
+    } settled;
+    uint64_t pass_seq = 0;       // passes started; pass info describes pass `pass_seq`
     // autotuner session: one shadow context per candidate chunk size
     std::vector<crac_ctx *> tune_ctx;
     std::vector<double> tune_sum_ms, tune_sum_bytes;
@@ -442,6 +476,8 @@ crac_status_t ctx_cuda_ready(crac_ctx *c);
 void ctx_free_all(crac_ctx *c);
 void pick_split(const crac_ctx *c, int *wpc, uint32_t *cpt);
 crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out);
+crac_status_t ctx_settle(crac_ctx *c, bool block);
+int spare_fp(const crac_ctx *c);
 crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms, uint64_t *k_out,
                              uint64_t *d_out);
 crac_status_t fingerprint_against(crac_ctx *c, const uint64_t *fp_ref, cudaStream_t s, const uint64_t **fp_out,
@@ -449,6 +485,7 @@ crac_status_t fingerprint_against(crac_ctx *c, const uint64_t *fp_ref, cudaStrea
 
 // Restart (crac_restart.cpp).
 crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s);
+crac_status_t reserve_restart(crac_ctx *c, uint64_t nt, size_t descs, size_t pieces);
 
 // The autotuner (crac_tune.cpp).
 void tune_clear(crac_ctx *c);

@@ -110,10 +110,7 @@ void server_worker(crac_server *sv) {
                     crac_image *img = nullptr;
                     st = with_staging(q->ctx, lease, q->r.lease_bytes,
                                       [&] { return ctx_checkpoint(q->ctx, q->stream, &img); });
-                    if (st == CRAC_OK) {
-                        q->r.image = img;
-                        q->r.payload_bytes = img->payload_bytes;
-                    }
+                    if (st == CRAC_OK) q->r.image = img;
                 } else {
                     st = with_staging(q->ctx, lease, q->r.lease_bytes,
                                       [&] { return ctx_restart(q->ctx, q->img, q->stream); });
@@ -121,8 +118,10 @@ void server_worker(crac_server *sv) {
                 }
             }
         }
-        // The lease is free once the drain has finished reading it.
+        // The lease is free once the drain has finished reading it; the
+        // image's sizes are known then.
         if (st == CRAC_OK && q->r.image) st = img_wait(q->r.image, 0);
+        if (st == CRAC_OK && q->r.image) q->r.payload_bytes = q->r.image->payload_bytes;
         q->r.status = st;
         q->r.t_done = now_s();
         if (q->img) {

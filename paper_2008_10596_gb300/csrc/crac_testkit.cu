@@ -69,7 +69,24 @@ __global__ void rewrite_kernel(const CopyEntry *__restrict__ e, uint32_t n) {
     }
 }
 
+// Application work that keeps a stream busy for `ns` nanoseconds of the
+// device clock (one thread; the loop also stops after 2^31 iterations).
+__global__ void delay_kernel(uint64_t ns) {
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t i = 0; i < (1u << 31); ++i) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= ns) break;
+    }
+}
+
 }  // namespace
+
+extern "C" __attribute__((visibility("default"))) int crac_testkit_delay(uint64_t ns, void *stream) {
+    if (ns > 10000000000ull) return (int)cudaErrorInvalidValue;   // at most 10 s
+    delay_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ns);
+    return (int)cudaGetLastError();
+}
 
 extern "C" __attribute__((visibility("default"))) int crac_testkit_mutate_xor(const void *entries_dev,
                                                                                uint32_t n, void *stream) {

@@ -38,6 +38,7 @@ void tune_fill(const crac_ctx *c, crac_tune_result_t *out) {
 crac_status_t ctx_tune_observe(crac_ctx *c, cudaStream_t s, const uint32_t *sizes, uint32_t n,
                                crac_tune_result_t *out) {
     if (!sizes || n == 0 || n > CRAC_TUNE_MAX) return CRAC_ERR_INVALID_ARG;
+    TRY(ctx_settle(c, true));
     bool same = c->tune_ctx.size() == n;
     for (uint32_t i = 0; same && i < n; ++i) same = (1u << c->tune_ctx[i]->log2S) == sizes[i];
     if (!same) {
@@ -103,7 +104,7 @@ struct VariantTiming {
 crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
     const uint32_t S = 1u << t->log2S;
     if (t->prev_base_valid) {
-        t->fp_cur = 1 - t->fp_cur;
+        t->fp_cur = t->prev_fp;
         t->base_first = t->prev_base_first;
         t->base_valid = true;
         t->prev_base_valid = false;
@@ -164,6 +165,7 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
 
 crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_tune_result_t *out) {
     if (c->tune_ctx.empty() || c->tune_rounds == 0) return CRAC_ERR_UNSUPPORTED;
+    TRY(ctx_settle(c, true));
     const uint32_t n = (uint32_t)c->tune_ctx.size();
     std::vector<float> cost(n), drain(n);
     uint32_t best = 0;

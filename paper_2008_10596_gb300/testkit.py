@@ -18,6 +18,15 @@ _tk.crac_testkit_mutate_xor.restype = ctypes.c_int
 _tk.crac_testkit_mutate_xor.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
 _tk.crac_testkit_rewrite.restype = ctypes.c_int
 _tk.crac_testkit_rewrite.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+_tk.crac_testkit_delay.restype = ctypes.c_int
+_tk.crac_testkit_delay.argtypes = [ctypes.c_uint64, ctypes.c_void_p]
+
+
+def delay(ns: int, stream=None) -> None:
+    """Keep `stream` busy for ns nanoseconds (at most 10 s) of device time."""
+    e = _tk.crac_testkit_delay(ns, _stream(stream))
+    if e:
+        raise RuntimeError(f"delay launch failed: cudaError {e}")
 
 
 def mutate_xor(entries_dev_ptr: int, n: int, stream=None) -> None:

@@ -51,7 +51,7 @@ def test_config_validation(C):
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=512),
                 dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=128 << 10),
                 dict(pass_kernel=C.CRAC_PASS_SPARSE),         # needs device-resident images
-                dict(flags=16),
+                dict(flags=32),
                 dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE,
                      flags=C.CRAC_FLAG_COMPRESS)):       # the sparse payload is not compacted
         with pytest.raises(C.CracError) as e:
@@ -61,6 +61,7 @@ def test_config_validation(C):
                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=64 << 10),
                dict(pass_kernel=C.CRAC_PASS_SPARSE, image_residency=C.CRAC_RESIDENCY_DEVICE),
                dict(flags=C.CRAC_FLAG_COMPRESS | C.CRAC_FLAG_DIRECT_DRAIN),
+               dict(flags=C.CRAC_FLAG_WAIT_PASS),
                dict(pass_kernel=C.CRAC_PASS_TMA, chunk_bytes=4096, flags=C.CRAC_FLAG_COMPRESS)):
         C.crac_ctx_destroy(C.crac_ctx_create(C.crac_config_default(**ok)))
 

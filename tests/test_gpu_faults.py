@@ -3,8 +3,9 @@
 Failures are made on the host (fault injection at named steps) or by a
 device wait that is made to run out: the batched kernel is launched so that
 tile 0 is never processed, so tile 1's bounded look-back wait expires; the
-kernel then finishes and reports CRAC_ERR_TIMEOUT.  Nothing traps, faults or
-hangs.  After each failure the previous image and baseline must be intact:
+kernel then finishes and reports CRAC_ERR_TIMEOUT (from the checkpoint call,
+or, for a pass the call did not wait for, from its image).  Nothing traps,
+faults or hangs.  After each failure the previous image and baseline must be intact:
 the next successful checkpoint must equal the oracle's, which never saw the
 failed attempt.
 """
@@ -37,9 +38,18 @@ def test_failed_checkpoint_leaves_state(step, code, kern):
         assert lib1 == ora1
         h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, "random10"))
         C.crac_debug_inject_fault(step, 1)
-        with pytest.raises(C.CracError) as e:
-            C.crac_ctx_checkpoint(h.ctx, h.stream)
-        assert e.value.code == code
+        try:
+            img = C.crac_ctx_checkpoint(h.ctx, h.stream)
+        except C.CracError as err:
+            assert err.code == code
+        else:
+            # a pass the call did not wait for reports a device-side failure
+            # on its image
+            h.images.append(img)
+            assert step == C.CRAC_FAULT_DEVICE_WAIT
+            with pytest.raises(C.CracError) as e:
+                C.crac_image_wait(img)
+            assert e.value.code == code
         C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
         # the context is still usable and its baseline untouched
         _, lib2, ora2 = h.checkpoint()
