@@ -383,7 +383,8 @@ def run_crac(args):
         C.crac_image_release(img)
 
     def pass_rows(infos):
-        return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms) for i in infos]
+        return [(i.device_ms, i.k, i.payload_bytes, i.hash_ms, i.finalize_ms, i.gather_ms, i.in_place)
+                for i in infos]
 
     # Base images (full) for each context.
     for ctx in (ctx_dev, ctx_host, ctx_pa, ctx_b, ctx_ldg, ctx_tma, ctx_sparse, ctx_inc, ctx_inc_host):
@@ -434,6 +435,8 @@ def run_crac(args):
     hash_ms = statistics.mean(p[3] for p in pass_ms)
     fin_ms = statistics.mean(p[4] for p in pass_ms)
     gat_ms = statistics.mean(p[5] for p in pass_ms)
+    in_place = statistics.mean(p[6] for p in pass_ms)
+    spec_bytes = d_avg * in_place / k_avg if k_avg else 0.0   # chunks the hash kernel wrote as it read them
     peak, peak_src = load_peaks()
     psrc = f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"
     # The step's dominant kernel is the restore scatter (every tracked byte read
@@ -449,14 +452,17 @@ def run_crac(args):
                 "kernel": "scatter_kernel (restore, all launches of a restart)",
                 "alg_bytes_per_launch": int(alg_sc), "avg_launch_ms": sc_ms,
                 "launches_per_restart": statistics.mean(r["scatter_launches"] for r in rst), "peak_source": psrc}
-    alg_hash = B + 8 * n                          # every tracked byte read once + one accumulator per chunk
+    # every tracked byte read once + one accumulator per chunk + the predicted
+    # dirty chunks written to staging as they are read
+    alg_hash = B + 8 * n + spec_bytes
     roofline_hash = {"bound": "hbm", "achieved": alg_hash / (hash_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": alg_hash / (hash_ms / 1e3) / 1e9 / peak,
                      "traffic": profile_traffic("split_hash_c2_64KiB"), "kernel": "split_hash_kernel",
                      "alg_bytes_per_launch": int(alg_hash), "avg_launch_ms": hash_ms, "peak_source": psrc}
     alg_pass = B + d_avg + 16 * n + 16 * k_avg    # read B, write D, fp old + new, idx + off
-    pass_info = {"kernels": "split: hash -> finalize+compact -> gather (one graph)", "device_ms": dev_ms,
-                 "hash_ms": hash_ms, "finalize_ms": fin_ms, "gather_ms": gat_ms,
+    pass_info = {"kernels": "split: hash (+ predicted write-through) -> finalize+compact -> gather (one graph)",
+                 "device_ms": dev_ms, "hash_ms": hash_ms, "finalize_ms": fin_ms, "gather_ms": gat_ms,
+                 "in_place_chunks": in_place, "dirty_chunks": k_avg,
                  "alg_bytes": int(alg_pass), "achieved_gbs": alg_pass / (dev_ms / 1e3) / 1e9,
                  "frac": alg_pass / (dev_ms / 1e3) / 1e9 / peak, "tracked_gbs": B / (dev_ms / 1e3) / 1e9}
 

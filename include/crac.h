@@ -248,6 +248,9 @@ typedef struct crac_pass_info {
     uint32_t pass_kernel;    /* CRAC_PASS_* that ran */
     float codec_ms;          /* CRAC_FLAG_COMPRESS: device time of the encoder launches */
     uint64_t stored_bytes;   /* payload bytes of the image (coded: its streams) */
+    uint64_t in_place;       /* split pass: dirty chunks the hash kernel had already written to
+                                staging as it read them (the previous pass's dirty chunks, at
+                                the offsets that pass gave them), which the gather left alone */
 } crac_pass_info_t;
 
 /* ---- configuration and contexts --------------------------------------- */

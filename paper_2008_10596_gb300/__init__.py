@@ -107,6 +107,7 @@ class CracPassInfo(ctypes.Structure):
         ("chunks_per_tile", ctypes.c_uint32), ("warps_per_chunk", ctypes.c_uint32),
         ("hash_ms", ctypes.c_float), ("finalize_ms", ctypes.c_float), ("gather_ms", ctypes.c_float),
         ("pass_kernel", ctypes.c_uint32), ("codec_ms", ctypes.c_float), ("stored_bytes", ctypes.c_uint64),
+        ("in_place", ctypes.c_uint64),
     ]
 
 

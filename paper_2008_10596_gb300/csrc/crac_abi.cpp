@@ -106,6 +106,7 @@ crac_status_t crac_ctx_register_alloc(crac_ctx_t *ctx, void *ptr, size_t bytes, 
     for (const AllocRec &r : ctx->allocs)
         if (p < r.ptr + r.bytes && r.ptr < p + bytes) return CRAC_ERR_OVERLAP;
     ctx->allocs.push_back(AllocRec{ctx->next_id++, p, (uint64_t)bytes, (uint32_t)kind});
+    ctx->layout_version++;
     return CRAC_OK;
 }
 
@@ -117,6 +118,7 @@ crac_status_t crac_ctx_free(crac_ctx_t *ctx, void *ptr) {
         if (ctx->allocs[i].ptr == p) {
             ctx->base_first.erase(ctx->allocs[i].id);
             ctx->allocs.erase(ctx->allocs.begin() + i);
+            ctx->layout_version++;
             return CRAC_OK;
         }
     }

@@ -140,6 +140,8 @@ crac_status_t img_resolve(crac_image *im) {
                               (im->predicted_full && (ctrl.k != im->n_chunks || ctrl.D != total))))
             st = CRAC_ERR_CORRUPT;
         if (st == CRAC_OK) {
+            im->spec_hits = ctrl.spec_hits;
+            im->spec_writes = ctrl.spec_writes;
             pc.k = ctrl.k;
             pc.bytes = bytes;
             pc.span = im->sparse_pass ? ctrl.D : 0;

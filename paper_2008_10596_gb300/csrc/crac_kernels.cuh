@@ -23,7 +23,9 @@ struct CkptCtrl {
     unsigned long long k;      // dirty chunks in this segment
     unsigned long long D;      // dirty bytes in this segment (sparse pass: all its bytes)
     unsigned long long payload;  // sparse pass: dirty bytes in this segment
-    unsigned long long pad[4];
+    unsigned long long spec_hits;  // split pass: dirty entries found in place (predicted write-through)
+    unsigned long long spec_writes;  // ... and chunks written speculatively
+    unsigned long long pad[2];
 };
 static_assert(sizeof(CkptCtrl) == 64, "CkptCtrl layout");
 constexpr unsigned kErrTimeout = 1u;   // a look-back wait ran out
@@ -70,6 +72,16 @@ struct CkptParams {
     // TMA pass: the allocations' first_chunk column fits in the CTA's shared
     // memory (n_allocs <= ckpt_tma_cached_allocs()) and is searched there.
     uint32_t first_cached;
+    // Split pass, predicted write-through: ppos[c - c_begin] is the staging
+    // offset chunk c had in the previous pass's compacted payload (~0 if it
+    // was not dirty then).  The hash kernels write such a chunk there as they
+    // read it, and the gather leaves an entry alone when its offset is the
+    // predicted one (the bytes are already in place); any other entry is
+    // copied as usual, after the speculative writes, so the result never
+    // depends on the prediction.  The gather records this pass's offsets in
+    // ppos_next (pre-set to ~0) when at most half of the chunks are dirty.
+    const uint64_t *ppos;
+    uint64_t *ppos_next;
 };
 
 // Restore: one image allocation mapped onto the target layout.

@@ -90,7 +90,7 @@ void ctx_free_all(crac_ctx *c) {
     img_unref(c->settled.parent);
     c->settled.parent = nullptr;
     cudaDeviceSynchronize();
-    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->fp[2], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
+    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->fp[2], &c->ppos[0], &c->ppos[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
                       &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr,
                       &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff, &c->cstage, &c->zwork, &c->zoff,
                       &c->zlen})
@@ -259,18 +259,24 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         if (c->sgraph) cudaGraphDestroy(c->sgraph);
         c->sgexec = nullptr;
         c->sgraph = nullptr;
+        // memset -> event 0 -> hash => finalize => gather -> control block D2H,
+        // where => is a programmatic edge (the consumer is launched as its
+        // producer drains and waits in-kernel for its completion); events 1-3
+        // record each kernel's end on side branches, off the critical path.
         CK(cudaGraphCreate(&c->sgraph, 0));
         CK(cudaGraphAddMemsetNode(&c->s_memset, c->sgraph, nullptr, 0, &mp));
-        cudaGraphNode_t prev = c->s_memset;
         cudaGraphNode_t ev;
-        CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &prev, 1, c->sev[0]));
-        prev = ev;
-        for (int i = 0; i < 3; ++i) {
-            CK(cudaGraphAddKernelNode(&c->s_k[i], c->sgraph, &prev, 1, &kp[i]));
-            CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
-            prev = ev;
+        CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_memset, 1, c->sev[0]));
+        CK(cudaGraphAddKernelNode(&c->s_k[0], c->sgraph, &ev, 1, &kp[0]));
+        cudaGraphEdgeData pe{};
+        pe.from_port = cudaGraphKernelNodePortProgrammatic;
+        pe.type = cudaGraphDependencyTypeProgrammatic;
+        for (int i = 1; i < 3; ++i) {
+            CK(cudaGraphAddKernelNode(&c->s_k[i], c->sgraph, nullptr, 0, &kp[i]));
+            CK(cudaGraphAddDependencies(c->sgraph, &c->s_k[i - 1], &c->s_k[i], &pe, 1));
         }
-        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &prev, 1, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
+        for (int i = 0; i < 3; ++i) CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
+        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &c->s_k[2], 1, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
                                     cudaMemcpyDeviceToHost));
         CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
         c->s_hash_fn = hash_fn;
@@ -334,6 +340,10 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         P.sparse = c->sparse_ok && staging ? 1u : 0u;
         P.full_copy = (c->full_copy_ok || P.sparse) && staging ? 1u : 0u;
         P.alloc_prefix = (const uint64_t *)(desc_dev + c->allocs.size());
+        if (c->spec_now) {
+            P.ppos = c->spec_use ? (const uint64_t *)c->ppos[c->ppos_cur].p : nullptr;
+            P.ppos_next = (uint64_t *)c->ppos[1 - c->ppos_cur].p;
+        }
         {
             const size_t a0 = std::upper_bound(first.begin(), first.end(), sg.c0) - first.begin() - 1;
             uint64_t pre = 0;
@@ -349,6 +359,11 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         const int gg = c->sm_count * 8;
         const int grids[3] = {gh, gf, gg};
         TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, ctrl_dst, s));
+        if (c->spec_now) {   // this pass's offsets predict the next one's
+            c->ppos_cur ^= 1;
+            c->ppos_ok = true;
+            c->ppos_layout = c->layout_version;
+        }
         c->last.grid = (uint32_t)gh;
         c->last.chunks_per_tile = cptF;
         c->last.warps_per_chunk = 0;
@@ -591,12 +606,20 @@ int spare_fp(const crac_ctx *c) {
 
 namespace {
 
+// After a pass that wrote predicted chunks: if fewer than half of those
+// writes were found in place, the dirty set does not repeat well enough to
+// pay for them; skip the speculative writes for the next passes.
+void spec_feedback(crac_ctx *c, uint64_t hits, uint64_t writes) {
+    if (writes && 2 * hits < writes) c->spec_rest = 8;
+}
+
 // Pass statistics of a settled deferred image, if no later pass has started.
 void fill_last(crac_ctx *c, const crac_image *im) {
     if (im->seq != c->pass_seq) return;
     c->last.k = im->k;
     c->last.payload_bytes = im->raw_bytes;
     c->last.stored_bytes = im->payload_bytes;
+    c->last.in_place = im->spec_hits;
     float ms = 0;
     c->last.hash_ms = c->last.finalize_ms = c->last.gather_ms = 0;
     pass_timings(c, &ms);
@@ -632,9 +655,11 @@ void settle_front(crac_ctx *c) {
             c->delta_frac = (float)((double)im->k / (double)std::max<uint64_t>(im->n_chunks, 1));
             c->delta_frac_valid = true;
         }
+        spec_feedback(c, im->spec_hits, im->spec_writes);
         fill_last(c, im);
     } else {
         if (im->lost) c->lost = true;
+        c->ppos_ok = false;
         c->fp_cur = sd.fp;
         c->base_valid = sd.valid;
         c->base_first = sd.first;
@@ -722,6 +747,8 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
             im->pieces.push_back(pc);
             return st;
         }
+        spec_feedback(c, ctrl.spec_hits, ctrl.spec_writes);
+        c->last.in_place += ctrl.spec_hits;
         pc.k0 = k_base;
         pc.k = ctrl.k;
         pc.off0 = d_base;
@@ -969,6 +996,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         cudaStreamSynchronize(c->side);
         cudaGetLastError();
         free_image_blocks(im.release());
+        c->ppos_ok = false;   // a failed pass's offsets predict nothing
         return code;
     };
     if (dpc.host.region >= 0) im->pieces.push_back(dpc);   // freed with the image on failure
@@ -1058,6 +1086,22 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                 st = ensure_dev(c->cstage, max_seg_bytes + 16 * max_seg_chunks);
             if (st == CRAC_OK && host_res) st = pa.alloc(n * 8, &im->zlen_h);
             if (st != CRAC_OK) return fail(st);
+        }
+        // Predicted write-through: a single-segment split pass records its
+        // offsets, and uses the previous one's if the layout is unchanged and
+        // its staging is device memory (speculative writes over the host link
+        // would cost link time).
+        c->spec_now = segs.size() == 1 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
+                      c->pass_now == CRAC_PASS_SPLIT && !c->sparse_ok;
+        c->spec_use = c->spec_now && c->ppos_ok && c->ppos_layout == c->layout_version && !c->full_copy_ok &&
+                      !direct && c->spec_rest == 0;
+        if (c->spec_now && c->ppos_ok && !c->full_copy_ok && c->spec_rest) --c->spec_rest;
+        if (c->spec_now) {
+            st = ensure_dev(c->ppos[0], n * 8);
+            if (st == CRAC_OK) st = ensure_dev(c->ppos[1], n * 8);
+            if (st != CRAC_OK) return fail(st);
+        } else {
+            c->ppos_ok = false;
         }
         // A restart of a chain of up to kReservedChain images of this layout
         // finds its scratch ready.
@@ -1151,6 +1195,8 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     TRY(ctx_settle(c, true));
     c->last = crac_pass_info_t{};
     ++c->pass_seq;
+    c->spec_now = c->spec_use = false;
+    c->ppos_ok = false;
     if (n == 0) return CRAC_OK;
     const int out_fp = spare_fp(c);
     TRY(ensure_dev(c->fp[out_fp], n * 8));

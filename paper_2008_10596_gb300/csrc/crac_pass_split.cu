@@ -25,8 +25,24 @@ constexpr int kHashNT = 256;
 constexpr int kFinNT = 1024;
 constexpr int kGatherNT = 256;
 
+// In the pass graph, finalize and gather hang off their producer by a
+// programmatic edge, so they are launched while it drains: each waits here
+// until the producing grid has completed and its writes are visible before
+// touching what it wrote.  In an ordinary stream launch this returns at once.
+__device__ __forceinline__ void wait_for_producer() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// A chunk of len bytes predicted at staging offset po is written there by the
+// hash kernels (and then found in place by the gather) when the offset is
+// 16-byte aligned (vector stores) and the chunk fits the staging buffer.
+__device__ __forceinline__ bool spec_ok(const CkptParams &P, uint64_t po, uint64_t len) {
+    return po != ~0ull && (po & 15u) == 0 && po <= P.staging_cap && len <= P.staging_cap - po;
+}
+
 // Partial CRAC-FP64 sum of a segment (<= 8 KiB) whose first word is word j0
-// of its chunk, over the lanes of one warp.
+// of its chunk, over the lanes of one warp; with copy_to, the segment's bytes
+// are also stored there.
 __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, uint32_t len, uint64_t j0,
                                              int lane, uint4 *__restrict__ copy_to = nullptr) {
     const uint4 *p = reinterpret_cast<const uint4 *>(src);
@@ -65,6 +81,7 @@ __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, ui
             const uint64_t byte = t[b];
             if (b < 8) w0 |= byte << (8 * b);
             else w1 |= byte << (8 * (b - 8));
+            if (copy_to) reinterpret_cast<uint8_t *>(copy_to + nv)[b] = (uint8_t)byte;
         }
         const uint64_t kt = (j0 + 2ull * nv + 1ull) * kK1;
         acc += mixw(w0, kt);
@@ -88,6 +105,7 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
     uint64_t a_next = 0;
     uint32_t a = 0;
     bool have = false;
+    uint32_t writes = 0;   // chunks this warp wrote speculatively (lane 0)
     for (; q < q_end; ++q) {
         const uint64_t c = P.c_begin + (q >> spc);
         if (!have || c >= a_next) {
@@ -113,6 +131,12 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
             const uint64_t o = P.alloc_prefix[a] + (local << log2S) + off - P.seg_base;
             if (o + len <= P.staging_cap) copy_to = reinterpret_cast<uint4 *>(P.staging + o);
             else if (lane == 0) atomicOr(&P.ctrl->err, kErrBounds);
+        } else if (P.ppos) {   // predicted dirty: written to the offset it had last time
+            const uint64_t po = __ldg(P.ppos + (c - P.c_begin));
+            if (spec_ok(P, po, clen)) {
+                copy_to = reinterpret_cast<uint4 *>(P.staging + po + off);
+                writes += off == 0 ? 1u : 0u;
+            }
         }
         uint64_t sum = hash_seg(src, len, off >> 3, lane, copy_to);
         sum = warp_sum(sum);
@@ -128,6 +152,7 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
             }
         }
     }
+    if (lane == 0 && writes) atomicAdd(&P.ctrl->spec_writes, (unsigned long long)writes);
 }
 
 // When log2Seg == log2_chunk the hash kernel has already finalized every
@@ -140,7 +165,7 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
 template <int LPC>
 __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned long long *__restrict__ acc,
                                                 uint64_t c, const CkptDesc &d_warp, uint32_t a_warp,
-                                                uint64_t a_next, int li) {
+                                                uint64_t a_next, int li, uint32_t &writes) {
     const uint32_t log2S = P.log2_chunk;
     uint64_t sum = 0, fo = 0;
     uint32_t len = 0;
@@ -188,6 +213,22 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
             } else if (li == 0) {
                 atomicOr(&P.ctrl->err, kErrBounds);
             }
+        } else if (P.ppos) {   // predicted dirty: written to the offset it had last time
+            const uint64_t po = __ldg(P.ppos + (c - P.c_begin));
+            if (spec_ok(P, po, len)) {
+                writes += li == 0 ? 1u : 0u;
+                uint8_t *dst = P.staging + po;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t v = li + LPC * u;
+                    if (v < nv) __stcs(reinterpret_cast<uint4 *>(dst) + v, q[u]);
+                }
+                const uint32_t rem = len & 15u;
+                if (rem && (uint32_t)li == (nv % LPC)) {
+                    const uint8_t *t = reinterpret_cast<const uint8_t *>(p + nv);
+                    for (uint32_t b = 0; b < rem; ++b) dst[16 * nv + b] = t[b];
+                }
+            }
         }
         const uint32_t rem = len & 15u;
         if (rem && (uint32_t)li == (nv % LPC)) {
@@ -227,6 +268,7 @@ split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc
     uint64_t a_next = 0;
     uint32_t a = 0;
     bool have = false;
+    uint32_t writes = 0;   // chunks this lane's groups wrote speculatively (group leaders)
     for (; q < q_end; ++q) {
         const uint64_t c0 = P.c_begin + q * CPS;
         if (!have || c0 >= a_next) {
@@ -235,13 +277,25 @@ split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc
             a_next = a + 1 < P.n_allocs ? P.desc[a + 1].first_chunk : ~0ull;
             have = true;
         }
-        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a, a_next, lane % LPC);
+        hash_small_iter<LPC>(P, acc, c0 + lane / LPC, d, a, a_next, lane % LPC, writes);
     }
+    writes = __reduce_add_sync(kFull, writes);
+    if (lane == 0 && writes) atomicAdd(&P.ctrl->spec_writes, (unsigned long long)writes);
 }
+
+constexpr uint32_t kFinCachedAllocs = 4096;   // first_chunk columns the finalize keeps on chip
 
 __global__ void __launch_bounds__(kFinNT)
 split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t log2Seg) {
     const bool direct = log2Seg == P.log2_chunk;
+    // Segmented chunks need their allocation: searched in an on-chip copy of
+    // the first_chunk column when it fits (a search in global memory is a
+    // chain of dependent loads per chunk).
+    __shared__ uint64_t s_first[kFinCachedAllocs];
+    const bool cached = !direct && P.n_allocs <= kFinCachedAllocs;
+    if (cached)   // the descriptors were copied before the pass
+        for (uint32_t a = threadIdx.x; a < P.n_allocs; a += kFinNT) s_first[a] = P.desc[a].first_chunk;
+    wait_for_producer();   // the hash kernel's accumulators
     __shared__ uint32_t s_wcnt[32];
     __shared__ uint64_t s_wbytes[32];
     __shared__ uint64_t s_wdirty[32];
@@ -266,7 +320,19 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
             len = (uint32_t)v;
             dl = (v & kAccDirty) ? len : 0u;
         } else if (c < P.c_end) {
-            const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
+            uint32_t a;
+            if (cached) {
+                uint32_t lo = 0, hi = P.n_allocs;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_first[mid] <= c) lo = mid;
+                    else hi = mid;
+                }
+                a = lo;
+            } else {
+                a = find_alloc(P.desc, P.n_allocs, c);
+            }
+            const CkptDesc d = P.desc[a];
             const uint64_t local = c - d.first_chunk;
             len = (uint32_t)min(S, d.bytes - (local << log2S));
             const uint64_t fp = fp_finalize(acc[c - P.c_begin], len);
@@ -274,6 +340,7 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
             const bool dirty = d.base_first == kNoBase || P.fp_old[d.base_first + local] != fp;
             dl = dirty ? len : 0u;
         }
+        if (P.ppos_next && c < P.c_end) P.ppos_next[c - P.c_begin] = ~0ull;   // the gather sets the dirty ones
         // Bytes that advance the staging offset: the dirty ones, or in the
         // sparse pass every chunk's (each sits at its uncompacted offset).
         const uint32_t sv = P.sparse ? len : dl;
@@ -351,15 +418,34 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
 __global__ void __launch_bounds__(kGatherNT)
 split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
     if (P.full_copy) return;   // the hash kernel has already written every chunk
+    wait_for_producer();       // the finalize kernel's list and counts
     const int lane = threadIdx.x & 31;
     const uint64_t kd = (uint64_t)P.ctrl->k;
     const uint64_t k = kd < P.idx_cap ? kd : P.idx_cap;
     const uint32_t log2S = P.log2_chunk;
     const uint64_t S = 1ull << log2S;
     const uint64_t nw = ((uint64_t)gridDim.x * kGatherNT) >> 5;
+    // The next pass predicts this pass's offsets, if few enough chunks are dirty.
+    uint64_t *next = (P.ppos_next && 2 * kd <= P.c_end - P.c_begin) ? P.ppos_next : nullptr;
+    // Every entry ends by the segment's dirty bytes, which must fit staging.
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.ctrl->D > P.staging_cap) atomicOr(&P.ctrl->err, kErrBounds);
+    __shared__ unsigned int s_hits;
+    if (threadIdx.x == 0) s_hits = 0;
+    __syncthreads();
+    uint32_t hits = 0;
     for (uint64_t j = ((uint64_t)blockIdx.x * kGatherNT + threadIdx.x) >> 5; j < k; j += nw) {
         const uint64_t c = P.idx_out[j];
         const uint64_t o = P.off_out[j];
+        if (next && lane == 0) next[c - P.c_begin] = o;
+        // Written there by the hash kernel already: a predicted offset equal
+        // to the entry's is aligned, and the chunk fits (it ends by D).
+        if (P.ppos) {
+            const uint64_t po = P.ppos[c - P.c_begin];
+            if (po == o && (po & 15u) == 0) {
+                ++hits;
+                continue;
+            }
+        }
         const CkptDesc d = P.desc[find_alloc(P.desc, P.n_allocs, c)];
         const uint64_t local = c - d.first_chunk;
         const uint64_t len = min(S, d.bytes - (local << log2S));
@@ -369,6 +455,9 @@ split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
         }
         copy_group<32>(P.staging + o, reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S), len, lane);
     }
+    if (lane == 0 && hits) atomicAdd(&s_hits, hits);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_hits) atomicAdd(&P.ctrl->spec_hits, (unsigned long long)s_hits);
 }
 
 }  // namespace

@@ -359,6 +359,8 @@ struct crac_image {
     bool had_base = false;          // some chunk had a baseline (the pass measured a dirty fraction)
     bool lost = false;              // its kernel reported kErrLostCopy
     uint64_t seq = 0;               // the context's pass counter at this pass
+    uint64_t spec_hits = 0;         // ... this many of its entries were found in place
+    uint64_t spec_writes = 0;       // ... of this many chunks written speculatively
 };
 
 namespace crac {
@@ -442,6 +444,17 @@ struct crac_ctx {
     uint32_t pass_now = CRAC_PASS_SPLIT;   // kernel of the current pass (CRAC_PASS_AUTO resolved)
     bool split_now = false;      // the current pass is the split graph (per-kernel timing events)
     bool prefetch_now = false;   // the current pass prefetched managed memory (ev_p0 / ev_p1)
+    // Predicted write-through of the split pass (CkptParams::ppos): ppos[ppos_cur]
+    // holds the last such pass's staging offsets (its successor's prediction),
+    // valid while ppos_ok and the chunk layout is the one it was made for.
+    DevBuf ppos[2];
+    int ppos_cur = 0;
+    bool ppos_ok = false;
+    uint64_t ppos_layout = 0;
+    uint64_t layout_version = 0;   // bumped when the registry's chunk layout changes
+    bool spec_now = false;         // the current pass records offsets (single-segment split pass)
+    bool spec_use = false;         // ... and writes its predicted chunks as it reads them
+    uint32_t spec_rest = 0;        // passes left without speculation after a poor prediction
     float delta_frac = 0.f;      // dirty chunks / chunks of the last pass that had a baseline
     bool delta_frac_valid = false;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;

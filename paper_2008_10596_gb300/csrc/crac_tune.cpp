@@ -219,6 +219,7 @@ crac_status_t ctx_tune_apply(crac_ctx *c, cudaStream_t s, double link_gbs, crac_
     if (S != (1u << c->log2S)) {
         c->cfg.chunk_bytes = S;
         c->log2S = t->log2S;
+        c->layout_version++;
         c->base_valid = false;
         c->base_first.clear();
     }
