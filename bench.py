@@ -753,8 +753,46 @@ def run_config4(args):
             "tracked_bytes": B, "link_gbs_assumed": 190.0, "peak_gbs": peak, "points": points,
             "note": "pass = split graph (hash, finalize+compact, gather into 8 GiB staging segments), device time; "
                     "dirty bytes measured by the pass against the previous observation"}
+    if not args.no_cpu:
+        line["cpu_baseline"] = c4_oracle_subset(bufs, sizes, B)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def c4_oracle_subset(bufs, sizes, B, budget=4 * W.GIB):
+    """The oracle's checkpoint pass on a 4 GiB subset of config 4's memory
+    (its first allocations, read back to the host), 64 KiB chunks, 10% of
+    the 4 KiB pages XOR-mutated before a delta checkpoint; single-threaded
+    and with the fingerprint loop on every host core; scaled linearly to the
+    whole tracked size, stated as such."""
+    from oracle import build as ob
+    from oracle import oracle as O
+    ob.build()
+    ssz = _sample_prefix(sizes, budget)
+    host = [bufs[i].cpu().numpy().copy() for i in range(len(ssz))]
+    sub = sum(ssz)
+    rng = np.random.default_rng(W.SEED_BASE + 4)
+    pages = [(a, o) for a, n in enumerate(ssz) for o in range(0, n - 4095, 4096)]
+    pick = rng.choice(len(pages), size=len(pages) // 10, replace=False)
+    out = {"kind": "oracle", "unit": "GB/s", "sample": f"first {len(ssz)} of {len(sizes)} allocations "
+           f"({sub / 2**30:.2f} GiB), 64 KiB chunks, delta checkpoint after 10% of 4 KiB pages rewritten; "
+           f"scaled_s = seconds x {B / sub:.2f} (tracked / sample bytes)"}
+    for label, workers in (("single_thread", 1), ("all_cores", os.cpu_count() or 1)):
+        ctx = O.OracleContext(64 * W.KIB, lineage=4, workers=workers)
+        for i, n in enumerate(ssz):
+            ctx.register((i + 1) << 40, n)
+        ctx.checkpoint(host)
+        for j in pick:   # XOR-mutate the chosen pages (toggled back on the second round)
+            a, o = pages[j]
+            v = host[a][o:o + 4096].view(np.uint32)
+            v ^= np.uint32(0x9E3779B1)
+        t0 = time.perf_counter()
+        ctx.checkpoint(host)
+        dt = time.perf_counter() - t0
+        out[label] = {"cores": workers, "seconds": dt, "value": sub / dt / 1e9, "scaled_s": dt * B / sub}
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = out["all_cores"]["cores"]
+    return out
 
 
 # ---------------------------------------------------------------------------

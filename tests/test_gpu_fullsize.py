@@ -171,6 +171,11 @@ def test_config4_sweep_every_byte():
             res = C.crac_ctx_tune_apply(ctx, 190.0, stream)
             S, kern = res["chosen_chunk_bytes"], res["chosen_pass_kernel"]
             ora = mirror(S, 40 + j, ptrs, sizes, kinds)
+            if FULL_C4:
+                free, tot = torch.cuda.mem_get_info()
+                print(f"c4 point {frac}: chunk {S}, kernel {kern}; device free {free / 2**30:.1f} of "
+                      f"{tot / 2**30:.1f} GiB, torch reserved {torch.cuda.memory_reserved() / 2**30:.1f} GiB, "
+                      f"arenas {C.crac_memory_stats()}", flush=True)
             a = C.crac_ctx_checkpoint(ctx, stream)
             imgs.append(a)
             ra = verify_image(a, ora, reader)

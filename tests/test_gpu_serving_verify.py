@@ -49,15 +49,20 @@ class Replay:
         self.checked = {"checkpoint": 0, "restart": 0, "full": 0}
 
     def _keep(self, i, lib):
+        """Store an image; keep the chains of the context's last few images (a
+        restart targets the newest image the collector had seen when it was
+        submitted, which may be older than the newest one stored by now)."""
         im = O.parse_image(lib)
         self.raw[i][im.epoch] = lib
-        keep, e = set(), im.epoch       # the newest image's chain back to its FULL image
-        while True:
-            keep.add(e)
-            pe = O.parse_image(self.raw[i][e])
-            if pe.full:
-                break
-            e = pe.parent_epoch
+        keep = set()
+        for top in sorted(self.raw[i])[-6:]:
+            e = top
+            while e not in keep:
+                keep.add(e)
+                pe = O.parse_image(self.raw[i][e])
+                if pe.full:
+                    break
+                e = pe.parent_epoch
         for old in [x for x in self.raw[i] if x not in keep]:
             del self.raw[i][old]
         return im
@@ -97,7 +102,7 @@ class Replay:
 def test_serving_loop_against_oracle_replay():
     dev = torch.device("cuda", 0)
     total, n_req = (32 * W.GIB, 1200) if FULL_C5 else (1 * W.GIB, 200)
-    sr = bench.ServingRun(dev, total=total, host_reserve=3.0)
+    sr = bench.ServingRun(dev, total=total, host_reserve=2.0)
     try:
         rep = Replay(sr)
         sr.base_images(rep.on_base)
