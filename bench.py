@@ -1052,7 +1052,12 @@ class ServingRun:
     order (so in each context's own order) from the collecting thread, with
     plan = {"mut": index into procs[i]["mut_lists"], "full": bool} for a
     checkpoint and {"image": handle, "epoch": its epoch} for a restart (the
-    handle may have been released by then; the epoch names the image)."""
+    handle may have been released by then; the epoch names the image).
+    on_submit(j, i, kind, plan), when given, is called for each restart as it
+    is submitted, from the submitting thread.  max_backlog > 0 holds a request
+    back (past its arrival time) while that many earlier ones are not yet
+    collected: a slow on_result then bounds the images waiting for it instead
+    of letting them pile up in memory (latencies are then not the config's)."""
 
     def __init__(self, dev, n_ctx=64, total=32 * W.GIB, seed=W.SEED_BASE + 5, flags=0, host_reserve=2.0):
         import torch
@@ -1106,7 +1111,8 @@ class ServingRun:
                 on_base(i, img)
         self.torch.cuda.synchronize(self.dev)
 
-    def run(self, n_req, rate, on_result=None, workers=8, budget=24 * W.GIB, max_lease=4 * W.GIB):
+    def run(self, n_req, rate, on_result=None, workers=8, budget=24 * W.GIB, max_lease=4 * W.GIB,
+            on_submit=None, max_backlog=0):
         import queue as _q
         import threading
         C, torch = self.C, self.torch
@@ -1132,17 +1138,20 @@ class ServingRun:
             return C.PREPARE_FN(prep)
 
         qq = _q.Queue()
+        collected = [0]
 
         def collect():
             for j, t, i, kind, plan in iter(qq.get, None):
                 r = C.crac_server_wait(server, t)
                 p = procs[i]
-                if on_result is not None and not errors:
-                    try:
-                        on_result(j, i, int(kind), r, plan)
-                    except Exception as e:   # reported after the loop
-                        errors.append(e)
                 with lock:
+                    # under the lock: a restart is not submitted between the
+                    # callback's look at this image and its publication below
+                    if on_result is not None and not errors:
+                        try:
+                            on_result(j, i, int(kind), r, plan)
+                        except Exception as e:   # reported after the loop
+                            errors.append(e)
                     if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
                         # keep only the newest image: its chain holds what a
                         # restart needs, and each FULL image frees the history
@@ -1151,6 +1160,7 @@ class ServingRun:
                         p["images"] = [r["image"]]
                         p["latest"] = r["image"]
                     results[t] = (int(kind), r, p["bytes"])
+                    collected[0] += 1
 
         # The prepare callbacks (the application's mutator launches) run on the
         # server's worker threads and need the GIL: hand it over quickly.
@@ -1165,6 +1175,8 @@ class ServingRun:
             t_arr = t0 + float(arrivals[j])
             while C.crac_time_now() < t_arr:
                 time.sleep(min(0.002, max(0.0, t_arr - C.crac_time_now())))
+            while max_backlog and j - collected[0] >= max_backlog and th.is_alive():
+                time.sleep(0.001)
             if kinds[j] == C.CRAC_REQ_CHECKPOINT:
                 p["ckpts"] += 1
                 plan = {"mut": p["ckpts"] % 4, "full": p["ckpts"] % 4 == 0}
@@ -1175,6 +1187,8 @@ class ServingRun:
                 with lock:   # the collector releases superseded images under the lock
                     img = p["latest"]
                     plan = {"image": img, "epoch": C.crac_image_info(img)["epoch"]}
+                    if on_submit is not None:
+                        on_submit(j, i, int(kinds[j]), plan)
                     t = C.crac_server_submit(server, p["ctx"], C.CRAC_REQ_RESTART, img, p["stream"], None, None,
                                              t_arr)
             qq.put((j, t, i, int(kinds[j]), plan))
@@ -1193,17 +1207,27 @@ class ServingRun:
         lat = {"checkpoint": [], "restart": []}
         wait = {"checkpoint": [], "restart": []}
         serv = {"checkpoint": [], "restart": []}
+        # service = prepare callback (the mutator launch, Python) + the
+        # operation's call + (checkpoints) the wait for the image to settle
+        parts = {k: {"prepare": [], "call": [], "settle": []} for k in ("checkpoint", "restart")}
         full_serv, full_wait = [], []
         scanned = payload = 0
         fails = 0
+        slow = []
         for kind, r, nb in results.values():
             if r["status"] != 0:
                 fails += 1
                 continue
+            ms3 = ((r["t_op"] - r["t_admit"]) * 1e3, (r["t_op_end"] - r["t_op"]) * 1e3,
+                   (r["t_done"] - r["t_op_end"]) * 1e3)
+            slow.append(((r["t_done"] - r["t_admit"]) * 1e3, kind, nb, r["payload_bytes"],
+                         (r["t_admit"] - r["t_arrival"]) * 1e3, r["t_arrival"] - t0, ms3))
             key = "checkpoint" if kind == C.CRAC_REQ_CHECKPOINT else "restart"
             lat[key].append((r["t_done"] - r["t_arrival"]) * 1e3)
             wait[key].append((r["t_admit"] - r["t_arrival"]) * 1e3)
             serv[key].append((r["t_done"] - r["t_admit"]) * 1e3)
+            for name, v in zip(("prepare", "call", "settle"), ms3):
+                parts[key][name].append(v)
             if kind == C.CRAC_REQ_CHECKPOINT and r["payload_bytes"] >= nb:
                 full_serv.append((r["t_done"] - r["t_admit"]) * 1e3)
                 full_wait.append((r["t_admit"] - r["t_arrival"]) * 1e3)
@@ -1225,7 +1249,13 @@ class ServingRun:
                 "latency_all_ms": {"p50": pct(allv, 50), "p99": pct(allv, 99)},
                 "queue_wait_ms": {k: dist(v) for k, v in wait.items()},
                 "service_ms": {k: dist(v) for k, v in serv.items()},
+                "service_parts_ms": {k: {n: dist(v) for n, v in d.items()} for k, d in parts.items()},
                 "full_checkpoint_ms": {"service": dist(full_serv), "queue_wait": dist(full_wait)},
+                # the five longest services: what the tail is made of
+                "slowest": [{"service_ms": s, "kind": "checkpoint" if k == C.CRAC_REQ_CHECKPOINT else "restart",
+                             "context_bytes": nb, "payload_bytes": pb, "queue_wait_ms": w, "arrival_s": a,
+                             "prepare_ms": m3[0], "call_ms": m3[1], "settle_ms": m3[2]}
+                            for s, k, nb, pb, w, a, m3 in sorted(slow, key=lambda x: x[0], reverse=True)[:5]],
                 "memory": C.crac_memory_stats(),
                 "offered_gbs": sum(self.procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
                 "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
@@ -1248,12 +1278,12 @@ def run_config5(args):
     total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
     sr = ServingRun(dev, total=total, flags=restore_flags(args))
     sr.base_images()
-    out = sr.run(args.requests, args.rate)
+    out = sr.run(args.requests, args.rate, workers=args.workers)
     sr.close()
     line = {"workload": f"c5: 64 contexts, {total / 2**30:.0f} GiB total (log-uniform 0.5-8 GiB scaled by "
                         f"{total / (173 * W.GIB):.3f}), {args.requests} requests Poisson {args.rate}/s, "
                         "75% ckpt / 25% restart, 10% of chunks mutated before each checkpoint, "
-                        "24 GiB staging budget, 8 slots"}
+                        f"24 GiB staging budget, {args.workers} slots"}
     line.update(out)
     print(json.dumps(line), flush=True)
     return 0 if out["failed"] == 0 else 1
@@ -1271,6 +1301,7 @@ def main():
                     help="tracked bytes of the config-2 workload (default 4096 = the full config)")
     ap.add_argument("--requests", type=int, default=1200, help="c5: requests in the serving loop")
     ap.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
+    ap.add_argument("--workers", type=int, default=8, help="c5: request server slots (requests in flight)")
     ap.add_argument("--no-serving", action="store_true", help="c2: skip the short serving leg")
     ap.add_argument("--serving-gib", type=int, default=8, help="c2: total context memory of the serving leg")
     ap.add_argument("--serving-requests", type=int, default=200, help="c2: requests of the serving leg")

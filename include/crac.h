@@ -382,6 +382,11 @@ typedef struct crac_request_result {
     uint64_t tracked_bytes;      /* the context's registered bytes */
     uint64_t payload_bytes;      /* checkpoint: dirty bytes; restart: image payload */
     uint64_t lease_bytes;        /* staging leased while it ran */
+    /* Where the service time (t_admit .. t_done) went: t_op is when the
+     * operation was called (after the prepare callback), t_op_end when the
+     * call returned; from there to t_done a checkpoint waits for its image to
+     * settle (pass and drain finished). */
+    double t_op, t_op_end;
 } crac_request_result_t;
 
 typedef struct crac_server_stats {

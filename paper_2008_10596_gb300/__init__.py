@@ -155,7 +155,8 @@ class CracRequestResult(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("type", ctypes.c_uint32),
                 ("image", ctypes.c_void_p), ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("tracked_bytes", ctypes.c_uint64),
-                ("payload_bytes", ctypes.c_uint64), ("lease_bytes", ctypes.c_uint64)]
+                ("payload_bytes", ctypes.c_uint64), ("lease_bytes", ctypes.c_uint64),
+                ("t_op", ctypes.c_double), ("t_op_end", ctypes.c_double)]
 
 
 class CracServerStats(ctypes.Structure):

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
     __shared__ uint64_t s_zpre[kCodecTileMax + 1];   // tile-local prefix of padded stream lengths
     __shared__ uint64_t s_base;                      // the tile's output offset
     __shared__ uint32_t s_boff[kWinBlocks];          // prefix of unit counts over a window's blocks
+    __shared__ uint8_t s_bent[kWinBlocks];           // one-window tile: the entry of each block
     __shared__ __align__(16) uint8_t s_units[kCodecWarps][512];   // per warp: a block's units
     __shared__ uint64_t s_off[kCodecTileMax + 1];    // the tile's entry offsets in staging
     __shared__ uint64_t s_hdr[kWinBlocks];           // header words of the window's blocks
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
             // fault injection: tile 0 is never processed, so the wait of the
             // tiles after it runs out (bounded) and the launch reports kErrTimeout
             if (P.skip_first_ticket && t == 0) t = atomicAdd(P.ticket, 1u);
-            s_tile = t;
+            s_tile = P.tile_begin + t;
         }
         __syncthreads();
         const uint32_t tile = s_tile;
@@ -204,10 +205,39 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
         if ((uint32_t)tid < ne) s_nbp[tid] = nb_ex;
         if (tid == 0) s_nbp[ne] = nb_all;
         __syncthreads();
+        // Entry of each block, searched once (a several-window tile is one
+        // entry): the passes below look it up instead of searching per block.
+        if (n_win == 1 && (uint32_t)tid < nb_all) {
+            uint32_t lo = 0, hi = ne;   // last entry whose first block is <= tid
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_nbp[mid] <= (uint32_t)tid) lo = mid;
+                else hi = mid;
+            }
+            s_bent[tid] = (uint8_t)lo;
+        }
+        __syncthreads();
 
-        // Phase 1: every block's header word, from shared memory.
+        // Phase 1: every block's header word -- made by the pass (then only a
+        // one-window tile's window is brought in here, for phase 2), else
+        // computed from the window in shared memory.
         bool dead = false;
-        for (uint32_t w = 0; w < n_win; ++w) {
+        if (P.chdr) {
+            if (n_win == 1) {
+                const uint8_t *sb = nullptr;
+                dead = !load_window(P, sdata, bar, &phase, r0, r1, &sb);   // uniform across the CTA
+            }
+            for (uint32_t fb = tid; fb < nb_all && !dead; fb += kCodecNT) {
+                const uint32_t lo = n_win == 1 ? s_bent[fb] : 0u;
+                const uint32_t b = fb - s_nbp[lo];
+                const uint64_t h = P.chdr[(P.idx[e0 + lo] << P.log2_bpc) + b];
+                if (n_win == 1) s_hdr[fb] = h;
+                else P.hdr[(s_off[lo] >> 9) + b] = h;   // read back window by window in phase 2
+                atomicAdd(&s_wsum[lo], crz_width_sum(h));
+            }
+            __syncthreads();
+        }
+        for (uint32_t w = 0; w < (P.chdr ? 0u : n_win); ++w) {
             const uint64_t wa = r0 + (uint64_t)w * kWin, wb = umin64(r1, wa + kWin);
             const uint8_t *sb = nullptr;
             if (!load_window(P, sdata, bar, &phase, wa, wb, &sb)) {
@@ -218,12 +248,7 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
             const uint32_t f0 = n_win == 1 ? 0u : w * kWinBlocks;
             const uint32_t f1 = n_win == 1 ? nb_all : (uint32_t)umin64(nb_all, (uint64_t)(w + 1) * kWinBlocks);
             for (uint32_t fb = f0 + warp; fb < f1; fb += kCodecWarps) {
-                uint32_t lo = 0, hi = ne;   // last entry whose first block is <= fb
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s_nbp[mid] <= fb) lo = mid;
-                    else hi = mid;
-                }
+                const uint32_t lo = n_win == 1 ? s_bent[fb] : 0u;
                 const uint32_t b = fb - s_nbp[lo];
                 const uint64_t o = s_off[lo];
                 const uint4 v = load16_any(sb + (o - wa) + 512ull * b + 16u * lane);
@@ -272,19 +297,16 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
         __syncthreads();
         const uint64_t base = s_base;
         if ((uint32_t)tid < ne) P.zoff[e0 + tid] = base + s_zpre[tid];
-        if (tid == 0 && e0 + ne == P.k) P.zoff[P.k] = base + tile_bytes;
+        // The end offset of the last tile (of the launch): zoff[k], or the
+        // first offset of the next launch's first tile, which writes the same.
+        if (tid == 0 && (e0 + ne == P.k || tile + 1 == P.n_tiles)) P.zoff[e0 + ne] = base + tile_bytes;
         if (dead) return;   // a copy that never completed: this CTA stops (error reported)
         if (s_skip) continue;
 
         // Phase 2: headers and padding of every coded entry, then the units
         // and raw bytes window by window.
         for (uint32_t fb = tid; fb < nb_all; fb += kCodecNT) {
-            uint32_t lo = 0, hi = ne;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_nbp[mid] <= fb) lo = mid;
-                else hi = mid;
-            }
+            const uint32_t lo = n_win == 1 ? s_bent[fb] : 0u;
             const uint64_t o = s_off[lo], L = s_off[lo + 1] - o;
             if (s_z[lo] == L) continue;   // raw entry
             const uint32_t b = fb - s_nbp[lo];
@@ -314,27 +336,13 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
             uint32_t wcount = 0;
             {
                 uint32_t v = 0;
-                if (f0 + tid < f1) {
-                    const uint32_t fb = f0 + tid;
-                    uint32_t lo = 0, hi = ne;
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (s_nbp[mid] <= fb) lo = mid;
-                        else hi = mid;
-                    }
-                    v = crz_width_sum(s_hdr[fb - f0]);
-                }
+                if (f0 + tid < f1) v = crz_width_sum(s_hdr[tid]);
                 const uint32_t ex = cta_excl_scan<uint32_t>(v, s_w32, &wcount);
                 if ((uint32_t)tid < kWinBlocks) s_boff[tid] = ex;
             }
             __syncthreads();
             for (uint32_t fb = f0 + warp; fb < f1; fb += kCodecWarps) {
-                uint32_t lo = 0, hi = ne;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s_nbp[mid] <= fb) lo = mid;
-                    else hi = mid;
-                }
+                const uint32_t lo = n_win == 1 ? s_bent[fb] : 0u;
                 const uint64_t o = s_off[lo], L = s_off[lo + 1] - o;
                 if (s_z[lo] == L) continue;   // raw entry: copied below
                 const uint32_t b = fb - s_nbp[lo];

@@ -82,6 +82,13 @@ struct CkptParams {
     // ppos_next (pre-set to ~0) when at most half of the chunks are dirty.
     const uint64_t *ppos;
     uint64_t *ppos_next;
+    // Coded contexts, split pass on chunks of 8 KiB and more: the CRZ1 header
+    // word of every 512-byte block of every chunk written to staging, at
+    // (c << (log2_chunk - 9)) + block, written by whichever kernel writes the
+    // chunk (hash: FULL or predicted; gather: the rest) from the vectors it
+    // holds (laid out across the warp as the encoder lays out a block), so
+    // that the encoder does not compute them again.
+    uint64_t *crz_hdr;
 };
 
 // Restore: one image allocation mapped onto the target layout.
@@ -142,12 +149,12 @@ cudaError_t ckpt_tma_prepare();   // raise the dynamic shared memory limit (once
 // run in order H -> F -> G.  acc holds one u64 per chunk of the segment and
 // must be zero before H; F uses cpt = split_finalize_threads() chunks per
 // tile and the look-back status words; G reads k from ctrl.
-const void *split_hash_fn();
+const void *split_hash_fn(bool crz_headers = false);
 // Hash kernel for 512 B <= chunk < 8 KiB: lanes_per_chunk = 32 * chunk / 8192;
 // it finalizes every chunk itself, so finalize runs with log2Seg = log2_chunk.
 const void *split_hash_small_fn(int lanes_per_chunk);
 const void *split_finalize_fn();
-const void *split_gather_fn();
+const void *split_gather_fn(bool crz_headers);
 int split_hash_threads();
 int split_finalize_threads();
 int split_gather_threads();
@@ -223,12 +230,21 @@ struct CodecParams {
     uint64_t *zlen;           // out: k stream lengths
     uint64_t *hdr;            // scratch: block header words, entry e's from off[e] / 512
     uint64_t *status;         // scratch: one look-back word per tile, zeroed
-    uint32_t *ticket;         // scratch: tile counter, zeroed
+    uint32_t *ticket;         // scratch: tile counter of this launch, zeroed
     unsigned int *err;        // kErr* bits, zeroed
     uint32_t tile_entries;    // entries per tile, 1..crz_tile_max()
+    // This launch encodes tiles [tile_begin, n_tiles); an earlier launch on the
+    // same stream has encoded the tiles before (their look-back words are
+    // final).  The last tile writes zoff[its last entry + 1].
+    uint32_t tile_begin;
     uint32_t n_tiles;
     uint64_t timeout_ns;
     uint32_t skip_first_ticket;   // fault injection: tile 0 is never processed
+    // Block header words made by the pass (CkptParams::crz_hdr), or null:
+    // entry e's block b has chdr[(idx[e] << log2_bpc) + b].
+    const uint64_t *chdr;
+    const uint64_t *idx;          // the entries' global chunk ids
+    uint32_t log2_bpc;            // log2 of 512-byte blocks per chunk
 };
 cudaError_t launch_crz_encode(const CodecParams &p, int grid, cudaStream_t s);
 uint32_t crz_tile_max();

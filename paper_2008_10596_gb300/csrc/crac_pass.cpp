@@ -64,7 +64,8 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     CK(cudaEventCreate(&c->ev_r0));
     CK(cudaEventCreate(&c->ev_r1));
     CK(prepare_drain());
-    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl) + 64));   // + the encoder's total and error bits
+    TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl) + 16 * (1 + kEncPieces)));   // + the encoder's offsets, errors
+    for (cudaEvent_t &e : c->ev_piece) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     TRY(ensure_host(c->serr_h, 256));
     if (c->cfg.reserve_host_bytes) {
         TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
@@ -90,7 +91,7 @@ void ctx_free_all(crac_ctx *c) {
     img_unref(c->settled.parent);
     c->settled.parent = nullptr;
     cudaDeviceSynchronize();
-    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->fp[2], &c->ppos[0], &c->ppos[1], &c->desc, &c->work, &c->idx, &c->off, &c->staging,
+    for (DevBuf *b : {&c->fp[0], &c->fp[1], &c->fp[2], &c->ppos[0], &c->ppos[1], &c->chdr, &c->desc, &c->work, &c->idx, &c->off, &c->staging,
                       &c->lens, &c->carry, &c->owner, &c->sdesc, &c->sidx, &c->soff, &c->serr,
                       &c->vdesc, &c->vwork, &c->vfp, &c->vidx, &c->voff, &c->cstage, &c->zwork, &c->zoff,
                       &c->zlen})
@@ -103,6 +104,8 @@ void ctx_free_all(crac_ctx *c) {
     if (c->sgraph) cudaGraphDestroy(c->sgraph);
     for (cudaEvent_t e : {c->ev_last, c->ev_pass, c->ev_t0, c->ev_t1, c->ev_p0, c->ev_p1, c->sev[0], c->sev[1],
                           c->sev[2], c->sev[3], c->ev_r0, c->ev_r1})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_piece)
         if (e) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
     cudaGetLastError();
@@ -223,7 +226,9 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
 crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
                                  uint32_t log2Seg, const void *hash_fn, const int grids[3], void *ctrl_dst,
                                  cudaStream_t s) {
-    const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn()};
+    // The gather instance follows P.crz_hdr, which only the hash instance
+    // split_hash_kernel<true> runs with: hash_fn alone keys the cached graph.
+    const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn(P.crz_hdr != nullptr)};
     const int thr[3] = {split_hash_threads(), split_finalize_threads(), split_gather_threads()};
     CkptParams Pc = P;
     unsigned long long *accv = acc;
@@ -314,8 +319,13 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         // 512 B..4 KiB chunks: several whole chunks per warp iteration.
         const bool small = c->log2S >= 9 && c->log2S < 13;
         const uint32_t log2Seg = std::min<uint32_t>(c->log2S, 13);
-        const void *hash_fn = small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn();
+        // Coded contexts with chunks of 8 KiB and more: the kernel that writes a
+        // chunk to staging (hash or gather) also writes its CRZ1 block headers
+        // for the encoder.
+        uint64_t *crz_hdr = c->crz_hdr_now ? (uint64_t *)c->chdr.p : nullptr;
+        const void *hash_fn = small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn(crz_hdr != nullptr);
         CkptParams P{};
+        P.crz_hdr = crz_hdr;
         P.desc = desc_dev;
         P.n_allocs = (uint32_t)c->allocs.size();
         P.log2_chunk = c->log2S;
@@ -501,37 +511,53 @@ uint32_t crz_tile_entries(uint32_t log2S) {
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(crz_tile_max(), 65536ull >> std::min<uint32_t>(log2S, 16)));
 }
 
-// Encoder scratch of a segment with k entries and D raw bytes: control
-// words, one look-back word per tile, block header words.
+// Encoder scratch of a segment with k entries and D raw bytes: the error
+// word, one tile counter per launch, then one look-back word per tile and the
+// block header words of multi-window chunks.
+constexpr size_t kZworkHead = 48;     // 4 + 4 * kEncPieces bytes, rounded up to 16
+static_assert(4 + 4 * kEncPieces <= kZworkHead, "encoder scratch head");
+
 size_t crz_work_bytes(uint64_t k, uint64_t D, uint32_t log2S) {
     const uint64_t tiles = (k + crz_tile_entries(log2S) - 1) / crz_tile_entries(log2S);
-    return 16 + 8 * tiles + 8 * (D / 512 + 1);
+    return kZworkHead + 8 * tiles + 8 * (D / 512 + 1);
 }
 
 // CRAC_FLAG_COMPRESS: the segment's raw payload (device staging, offsets in
 // c->off) -> its streams.  Host images: into the piece's pinned block when
-// direct drain finds room (*zdirect), else into c->cstage for the side
-// stream's copy; tables in c->zoff / c->zlen.  Device images: into pc.dev,
-// with the stream offsets in pc.off_dev and lengths in pc.zlen_dev.  On
-// return the total stream bytes are known (*Z).
+// direct drain finds room, else into c->cstage, from where the side stream
+// copies them to the piece's pinned block; tables in c->zoff / c->zlen.
+// Staged encodes of many tiles run as several launches over consecutive tile
+// ranges, and each range's streams are copied as soon as the host sees that
+// launch end (its end offset comes back with it), so the copy of the first
+// ranges overlaps the encoding of the rest; the pinned block is carved at the
+// worst case from the regions as they are (else the copy follows the whole
+// encode, as for a single launch).  Device images: into pc.dev, with the
+// stream offsets in pc.off_dev and lengths in pc.zlen_dev.  On return the
+// total stream bytes are known (*Z), and *zplaced says that the streams are
+// in pc.host, or on their way there on the side stream.
 crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
-                             cudaStream_t s, uint64_t *Z, bool *zdirect) {
+                             cudaStream_t s, uint64_t *Z, bool *zplaced) {
     const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
     const uint32_t T = crz_tile_entries(c->log2S);
     const uint64_t n_tiles = (k + T - 1) / T;
     if (n_tiles > 0x7fffffffull) return CRAC_ERR_UNSUPPORTED;
-    *zdirect = false;
+    *zplaced = false;
     TRY(ensure_dev(c->zwork, crz_work_bytes(k, D, c->log2S)));
+    const int grid_max = (int)std::max<uint64_t>(1, (uint64_t)c->sm_count * crz_encode_max_ctas_per_sm());
+    uint32_t pieces = 1;
     CodecParams P{};
     if (host_res) {
         P.zoff = (uint64_t *)c->zoff.p;
         P.zlen = (uint64_t *)c->zlen.p;
         if (direct_flag && pinned_arena().try_alloc(zmax, &pc.host)) {
             P.dst = pc.host.p;
-            *zdirect = true;
+            *zplaced = true;
         } else {
             TRY(ensure_dev(c->cstage, zmax));
             P.dst = (uint8_t *)c->cstage.p;
+            // a launch of at least four waves of tiles per piece
+            pieces = (uint32_t)std::min<uint64_t>(kEncPieces, n_tiles / (4ull * grid_max));
+            if (pieces > 1 && !pinned_arena().try_alloc(zmax, &pc.host)) pieces = 1;
         }
     } else {
         TRY(device_arena(c->device).alloc(zmax, &pc.dev));
@@ -539,43 +565,91 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
         P.zoff = (uint64_t *)pc.off_dev.p;
         P.zlen = (uint64_t *)pc.zlen_dev.p;
     }
+    if (pieces < 1) pieces = 1;
     uint8_t *w = (uint8_t *)c->zwork.p;
     P.src = (const uint8_t *)c->staging.p;
     P.off = (const uint64_t *)c->off.p;
+    if (c->crz_hdr_now) {   // the pass made the block headers
+        P.chdr = (const uint64_t *)c->chdr.p;
+        P.idx = host_res ? (const uint64_t *)c->idx.p : (const uint64_t *)pc.idx_dev.p;
+        P.log2_bpc = c->log2S - 9;
+    }
     P.k = k;
     P.dst_cap = zmax;
     P.err = (unsigned int *)w;
-    P.ticket = (uint32_t *)(w + 4);
-    P.status = (uint64_t *)(w + 16);
+    P.status = (uint64_t *)(w + kZworkHead);
     P.hdr = P.status + n_tiles;
     P.tile_entries = T;
-    P.n_tiles = (uint32_t)n_tiles;
     P.timeout_ns = c->cfg.timeout_ns;
-    P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_ENCODE_WAIT)) ? 1u : 0u;
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * crz_encode_max_ctas_per_sm()));
-    uint8_t *out_h = (uint8_t *)c->ctrl_h.p + sizeof(CkptCtrl);
-    CK(cudaMemsetAsync(w, 0, 16 + 8 * n_tiles, s));
+    const bool inject = n_tiles >= 2 && fault_hit(CRAC_FAULT_ENCODE_WAIT);
+    // out_h: the total and the error bits; then per piece its end offset and
+    // its error bits (16 bytes each)
+    uint64_t *out_h = (uint64_t *)((uint8_t *)c->ctrl_h.p + sizeof(CkptCtrl));
+    std::memset(out_h, 0, 16 * (1 + kEncPieces));
+    CK(cudaMemsetAsync(w, 0, kZworkHead + 8 * n_tiles, s));
     CK(cudaEventRecord(c->ev_t0, s));
-    CK(launch_crz_encode(P, grid, s));
+    for (uint32_t i = 0; i < pieces; ++i) {
+        const uint64_t t0 = n_tiles * i / pieces, t1 = n_tiles * (i + 1) / pieces;
+        CodecParams Q = P;
+        Q.ticket = (uint32_t *)(w + 4) + i;
+        Q.tile_begin = (uint32_t)t0;
+        Q.n_tiles = (uint32_t)t1;
+        Q.skip_first_ticket = (i == 0 && inject) ? 1u : 0u;
+        CK(launch_crz_encode(Q, (int)std::min<uint64_t>(t1 - t0, (uint64_t)grid_max), s));
+        if (pieces > 1) {
+            CK(cudaMemcpyAsync(out_h + 2 + 2 * i, P.zoff + std::min<uint64_t>(k, t1 * T), 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(out_h + 3 + 2 * i, w, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(c->ev_piece[i], s));
+        }
+    }
     CK(cudaEventRecord(c->ev_t1, s));
     CK(cudaMemcpyAsync(out_h, P.zoff + k, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(out_h + 8, w, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out_h + 1, w, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(c->ev_pass, s));
+    c->last.kernel_launches += pieces;
+    if (pieces > 1) {
+        // Copy each piece's streams once it has ended; a piece with an error,
+        // or an end offset out of order, stops the copies (the total's check
+        // below reports it).
+        uint64_t z0 = 0;
+        bool stop = false;
+        for (uint32_t i = 0; i < pieces; ++i) {
+            CK(cudaEventSynchronize(c->ev_piece[i]));
+            const uint64_t z1 = out_h[2 + 2 * i];
+            if (stop || (uint32_t)out_h[3 + 2 * i] != 0 || z1 < z0 || z1 > zmax) {
+                stop = true;
+                continue;
+            }
+            if (z1 > z0) {
+                CK(cudaStreamWaitEvent(c->side, c->ev_piece[i], 0));
+                CK(cudaMemcpyAsync(pc.host.p + z0, c->cstage.p + z0, z1 - z0, cudaMemcpyDeviceToHost, c->side));
+            }
+            z0 = z1;
+        }
+        *zplaced = true;
+    }
     CK(cudaEventSynchronize(c->ev_pass));
-    c->last.kernel_launches += 1;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1) == cudaSuccess) c->last.codec_ms += ms;
     cudaGetLastError();
-    const unsigned err = *(const unsigned *)(out_h + 8);
+    const unsigned err = (uint32_t)out_h[1];
+    crac_status_t st = CRAC_OK;
     if (err & kErrLostCopy) {
         c->lost = true;
-        return CRAC_ERR_CUDA;
+        st = CRAC_ERR_CUDA;
+    } else if (err & kErrTimeout) {
+        st = CRAC_ERR_TIMEOUT;
+    } else if (err || out_h[0] > zmax) {
+        st = CRAC_ERR_CORRUPT;
     }
-    if (err & kErrTimeout) return CRAC_ERR_TIMEOUT;
-    if (err) return CRAC_ERR_CORRUPT;
-    *Z = *(const uint64_t *)out_h;
-    if (*Z > zmax) return CRAC_ERR_CORRUPT;
-    if (*zdirect) pinned_arena().shrink(pc.host, *Z);
+    if (st != CRAC_OK) {
+        // the pinned block goes back with the failed image: no copy may
+        // still be writing it
+        if (pieces > 1) cudaStreamSynchronize(c->side);
+        return st;
+    }
+    *Z = out_h[0];
+    if (*zplaced) pinned_arena().shrink(pc.host, *Z);
     return CRAC_OK;
 }
 
@@ -755,10 +829,10 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
         const bool sparse = c->sparse_ok && !host_res;
         pc.bytes = sparse ? ctrl.payload : ctrl.D;
         pc.span = sparse ? ctrl.D : 0;
-        bool zdirect = false;
+        bool zplaced = false;
         if (coded && ctrl.k) {
             uint64_t Z = 0;
-            st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zdirect);
+            st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zplaced);
             if (st != CRAC_OK) {
                 im->pieces.push_back(pc);
                 return st;
@@ -776,7 +850,7 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
             if (ctrl.D) pa.shrink(pc.host, ctrl.D);
             else pa.free(pc.host);
         } else if (host_res) {
-            if (pc.bytes && !zdirect) {
+            if (pc.bytes && !zplaced) {
                 st = pa.alloc(pc.bytes, &pc.host);
                 if (st != CRAC_OK) {
                     im->pieces.push_back(pc);
@@ -1078,6 +1152,14 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
             if (st == CRAC_OK) st = ensure_dev(c->off, (max_seg_chunks + 1) * 8);
             if (st != CRAC_OK) return fail(st);
         }
+        // The split pass writes the CRZ1 block headers of chunks of 8 KiB and
+        // more (one word per 512 bytes) for the encoder.
+        c->crz_hdr_now = coded && log2S >= 13 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED &&
+                         c->pass_now == CRAC_PASS_SPLIT;
+        if (c->crz_hdr_now) {
+            st = ensure_dev(c->chdr, (n << (log2S - 9)) * 8);
+            if (st != CRAC_OK) return fail(st);
+        }
         if (coded) {
             st = ensure_dev(c->zwork, crz_work_bytes(max_seg_chunks, max_seg_bytes, log2S));
             if (st == CRAC_OK && host_res) st = ensure_dev(c->zoff, (max_seg_chunks + 1) * 8);
@@ -1197,6 +1279,7 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     ++c->pass_seq;
     c->spec_now = c->spec_use = false;
     c->ppos_ok = false;
+    c->crz_hdr_now = false;
     if (n == 0) return CRAC_OK;
     const int out_fp = spare_fp(c);
     TRY(ensure_dev(c->fp[out_fp], n * 8));

@@ -1,6 +1,6 @@
 // The split pass (hash -> finalize + compaction -> gather, one graph) and its
 // sparse variant.
-#include "crac_device.cuh"
+#include "crac_codec.cuh"
 
 namespace crac {
 
@@ -42,9 +42,14 @@ __device__ __forceinline__ bool spec_ok(const CkptParams &P, uint64_t po, uint64
 
 // Partial CRAC-FP64 sum of a segment (<= 8 KiB) whose first word is word j0
 // of its chunk, over the lanes of one warp; with copy_to, the segment's bytes
-// are also stored there.
+// are also stored there, and then (kHdr) the CRZ1 header word of each whole
+// 512-byte block of the segment goes to hdr[block] (lane l holds bytes
+// 16l .. 16l+15 of block u in q[u], the encoder's layout of a block).  Only
+// chunks written to staging get headers, so their cost follows the dirty bytes.
+template <bool kHdr = false>
 __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, uint32_t len, uint64_t j0,
-                                             int lane, uint4 *__restrict__ copy_to = nullptr) {
+                                             int lane, uint4 *__restrict__ copy_to = nullptr,
+                                             uint64_t *__restrict__ hdr = nullptr) {
     const uint4 *p = reinterpret_cast<const uint4 *>(src);
     const uint32_t nv = len >> 4;
     constexpr int U = 16;
@@ -73,6 +78,17 @@ __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, ui
         }
         key += kStep;
     }
+    if (kHdr && copy_to) {
+        const uint32_t nb = len >> 9;   // whole blocks (warp-uniform)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if ((uint32_t)u < nb) {
+                const uint32_t r[4] = {crz_rot(q[u].x), crz_rot(q[u].y), crz_rot(q[u].z), crz_rot(q[u].w)};
+                const uint64_t h = crz_block_header(r);
+                if (lane == 0) hdr[u] = h;
+            }
+        }
+    }
     const uint32_t rem = len & 15u;
     if (rem && lane == (int)(nv & 31u)) {
         const uint8_t *t = src + 16ull * nv;
@@ -90,6 +106,41 @@ __device__ __forceinline__ uint64_t hash_seg(const uint8_t *__restrict__ src, ui
     return acc;
 }
 
+// One warp copies a chunk of len bytes from src (16-byte aligned) to dst and
+// stores the CRZ1 header word of each whole 512-byte block b at hdr[b], in the
+// encoder's layout (lane l holds bytes 16l .. 16l+15 of the block).  A dst off
+// the 16-byte grid is copied by copy_group, which re-reads the (cached) source.
+__device__ __forceinline__ void copy_with_headers(uint8_t *__restrict__ dst, const uint8_t *__restrict__ src,
+                                                  uint64_t len, int lane, uint64_t *__restrict__ hdr) {
+    const uint64_t nb = len >> 9;
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const bool vec = ((uintptr_t)dst & 15u) == 0;
+    constexpr int U = 8;
+    for (uint64_t b = 0; b < nb; b += U) {   // warp-uniform
+        uint4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b + u < nb) q[u] = __ldg(s + 32 * (b + u) + lane);
+        if (vec) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (b + u < nb) __stcs(d + 32 * (b + u) + lane, q[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b + u < nb) {
+                const uint32_t r[4] = {crz_rot(q[u].x), crz_rot(q[u].y), crz_rot(q[u].z), crz_rot(q[u].w)};
+                const uint64_t h = crz_block_header(r);
+                if (lane == 0) hdr[b + u] = h;
+            }
+        }
+    }
+    if (vec) copy_group<32>(dst + (nb << 9), src + (nb << 9), len - (nb << 9), lane);
+    else copy_group<32>(dst, src, len, lane);
+}
+
+template <bool kHdr>
 __global__ void __launch_bounds__(kHashNT, 2)
 split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t log2Seg) {
     const int lane = threadIdx.x & 31;
@@ -138,7 +189,9 @@ split_hash_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint
                 writes += off == 0 ? 1u : 0u;
             }
         }
-        uint64_t sum = hash_seg(src, len, off >> 3, lane, copy_to);
+        uint64_t sum = kHdr ? hash_seg<true>(src, len, off >> 3, lane, copy_to,
+                                             P.crz_hdr + (c << (log2S - 9)) + (off >> 9))
+                            : hash_seg(src, len, off >> 3, lane, copy_to);
         sum = warp_sum(sum);
         if (lane == 0) {
             if (spc == 0) {
@@ -415,6 +468,9 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
     }
 }
 
+// kHdr: P.crz_hdr is set, and each copied chunk's block headers are written
+// too (a separate instance, so that the plain gather keeps its registers low).
+template <bool kHdr>
 __global__ void __launch_bounds__(kGatherNT)
 split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
     if (P.full_copy) return;   // the hash kernel has already written every chunk
@@ -453,7 +509,9 @@ split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
             if (lane == 0) atomicOr(&P.ctrl->err, kErrBounds);
             continue;
         }
-        copy_group<32>(P.staging + o, reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S), len, lane);
+        const uint8_t *src = reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S);
+        if (kHdr) copy_with_headers(P.staging + o, src, len, lane, P.crz_hdr + (c << (log2S - 9)));
+        else copy_group<32>(P.staging + o, src, len, lane);
     }
     if (lane == 0 && hits) atomicAdd(&s_hits, hits);
     __syncthreads();
@@ -462,7 +520,10 @@ split_gather_kernel(const CkptParams P, unsigned long long *, uint32_t) {
 
 }  // namespace
 
-const void *split_hash_fn() { return reinterpret_cast<const void *>(&split_hash_kernel); }
+const void *split_hash_fn(bool crz_headers) {
+    return crz_headers ? reinterpret_cast<const void *>(&split_hash_kernel<true>)
+                       : reinterpret_cast<const void *>(&split_hash_kernel<false>);
+}
 const void *split_hash_small_fn(int lanes_per_chunk) {
     switch (lanes_per_chunk) {
     case 2: return reinterpret_cast<const void *>(&split_hash_small_kernel<2>);
@@ -473,7 +534,10 @@ const void *split_hash_small_fn(int lanes_per_chunk) {
     }
 }
 const void *split_finalize_fn() { return reinterpret_cast<const void *>(&split_finalize_kernel); }
-const void *split_gather_fn() { return reinterpret_cast<const void *>(&split_gather_kernel); }
+const void *split_gather_fn(bool crz_headers) {
+    return crz_headers ? reinterpret_cast<const void *>(&split_gather_kernel<true>)
+                       : reinterpret_cast<const void *>(&split_gather_kernel<false>);
+}
 int split_hash_threads() { return kHashNT; }
 int split_finalize_threads() { return kFinNT; }
 int split_gather_threads() { return kGatherNT; }

@@ -48,6 +48,7 @@ constexpr uint64_t kHeaderBytes = 80;
 constexpr uint64_t kAllocEntryBytes = 40;
 constexpr uint64_t kDefaultStagingMax = 8ull << 30;
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+constexpr uint32_t kEncPieces = 8;   // launches of a pipelined encode of host images (at most)
 
 extern thread_local int t_last_cuda;
 extern std::atomic<int> g_fault_step;
@@ -161,7 +162,9 @@ class Arena {
             }
         }
         grows_++;
-        uint64_t sz = std::max(len, quantum_);
+        // Whole quanta: a region made for one block is reusable for any block
+        // up to its size (blocks sized by staging segments vary by a few KiB).
+        uint64_t sz = round_up(std::max(len, quantum_), quantum_);
         void *p = nullptr;
         cudaError_t e;
         {
@@ -424,6 +427,7 @@ struct crac_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_last = nullptr, ev_pass = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     cudaEvent_t ev_p0 = nullptr, ev_p1 = nullptr;
+    cudaEvent_t ev_piece[crac::kEncPieces] = {};   // ends of the launches of a pipelined encode
     // graph for the fused pass: memset(ctrl+status) -> kernel -> D2H(ctrl)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -452,6 +456,8 @@ struct crac_ctx {
     bool ppos_ok = false;
     uint64_t ppos_layout = 0;
     uint64_t layout_version = 0;   // bumped when the registry's chunk layout changes
+    DevBuf chdr;                   // coded contexts: CRZ1 block headers made by the split pass
+    bool crz_hdr_now = false;      // the current pass makes them (split pass, chunks >= 8 KiB)
     bool spec_now = false;         // the current pass records offsets (single-segment split pass)
     bool spec_use = false;         // ... and writes its predicted chunks as it reads them
     uint32_t spec_rest = 0;        // passes left without speculation after a poor prediction

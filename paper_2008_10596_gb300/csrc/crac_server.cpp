@@ -101,6 +101,7 @@ void server_worker(crac_server *sv) {
         q->r.t_admit = now_s();
         void *lease = q->r.lease_bytes ? (uint8_t *)sv->staging + q->lease_off : nullptr;
         if (q->prep) q->prep((crac_stream_t)q->stream, q->prep_arg);
+        q->r.t_op = now_s();
         crac_status_t st;
         {
             std::lock_guard<std::mutex> lk(q->ctx->mu);
@@ -118,6 +119,7 @@ void server_worker(crac_server *sv) {
                 }
             }
         }
+        q->r.t_op_end = now_s();
         // The lease is free once the drain has finished reading it; the
         // image's sizes are known then.
         if (st == CRAC_OK && q->r.image) st = img_wait(q->r.image, 0);

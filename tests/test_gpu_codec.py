@@ -386,3 +386,52 @@ def test_mixed_coded_and_plain_chain(base_coded):
                 C.crac_image_release(i)
     finally:
         h.close()
+
+
+def test_pipelined_staged_encode_matches_oracle():
+    """A FULL coded checkpoint into host images with enough 64 KiB tiles that
+    the encoder runs as several launches, each launch's streams copied to the
+    image while the next ones encode (given pinned regions with room for its
+    worst case): the image must equal the oracle's byte
+    for byte (fp32, zero and incompressible allocations, a ragged tail), have
+    taken more encoder launches than the same pass into device images, and
+    restart exactly; then the same with the first launch's first tile never
+    processed: CRAC_ERR_TIMEOUT, and the baseline untouched."""
+    S = 64 * KIB
+    sizes = [150 * 1024 * KIB + 48, 56 * 1024 * KIB, 56 * 1024 * KIB, 5 * 1024 * KIB + 16]
+    kinds = ["f32_normal", "zeros", "u8", "bf16"]
+    infos = {}
+    for residency in (C.CRAC_RESIDENCY_DEVICE, C.CRAC_RESIDENCY_HOST):
+        # the pipelined encode carves its worst-case pinned block from existing regions only
+        h = Harness(S, lineage=1900 + residency, image_residency=residency, flags=CODED, timeout_ns=50_000_000,
+                    reserve_host_bytes=1 << 30)
+        try:
+            for i, (n, kd) in enumerate(zip(sizes, kinds)):
+                h.add(n, data=_contents(kd, n, 90 + i))
+            img, lib, ora = h.checkpoint(compare=residency == C.CRAC_RESIDENCY_HOST)
+            infos[residency] = C.crac_ctx_last_pass(h.ctx)
+            if residency == C.CRAC_RESIDENCY_DEVICE:
+                continue
+            assert lib == ora
+            want = h.host()
+            for b in h.bufs:
+                b.zero()
+            h.restart(img)
+            for b, w in zip(h.bufs, want):
+                assert np.array_equal(b.read(), w)
+            # a failed pipelined encode: reported, and the baseline stays the first image's
+            h.oracle.invalidate()
+            C.crac_ctx_invalidate(h.ctx)
+            C.crac_debug_inject_fault(C.CRAC_FAULT_ENCODE_WAIT, 1)
+            with pytest.raises(C.CracError) as e:
+                C.crac_ctx_checkpoint(h.ctx, h.stream)
+            assert e.value.code == C.CRAC_ERR_TIMEOUT
+            C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
+            h.mutate(pattern_mutations(h.first(), sizes, S, "random10", seed=5))
+            _, lib2, ora2 = h.checkpoint()
+            assert lib2 == ora2
+        finally:
+            C.crac_debug_inject_fault(C.CRAC_FAULT_NONE, 0)
+            h.close()
+    dev, host = infos[C.CRAC_RESIDENCY_DEVICE], infos[C.CRAC_RESIDENCY_HOST]
+    assert host["kernel_launches"] >= dev["kernel_launches"] + 1, (host, dev)
