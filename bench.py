@@ -917,7 +917,7 @@ def run_codec(args):
     launches0 = C.crac_kernel_launches()
     mem0 = None
     rows = []
-    enc = []   # encoder launches into device memory: (raw bytes, stored bytes, entries, ms)
+    enc = []   # encoder launches into device images: (raw bytes, stored bytes, entries, ms)
     for kind in ("f32_normal", "bf16_normal", "zeros", "u8_uniform"):
         for name, cfg in variants.items():
             fill("u8_uniform", wl.seed + 7)   # the untimed first image: other bytes everywhere
@@ -952,7 +952,7 @@ def run_codec(args):
                     full = rec
                 else:
                     deltas.append(rec)
-                if pi["codec_ms"] > 0 and name != "host_coded_direct":
+                if pi["codec_ms"] > 0 and name == "device_coded":
                     enc.append((kind, r == 0, pi["payload_bytes"], pi["stored_bytes"], pi["k"], pi["codec_ms"]))
             want = [bufs[i][:4096].clone() for i in (0, len(bufs) // 2, len(bufs) - 1)]
             for b in bufs[::17]:
@@ -1006,21 +1006,24 @@ def run_codec(args):
                "decode_gbs": raw_d / t_dec / 1e9, "ratio": sum(len(z) for z in streams) / raw,
                "sample": f"{len(sample)} allocations, {raw / 2**20:.0f} MiB of the fp32 content in 64 KiB chunks "
                          f"(decode: the first {raw_d / 2**20:.0f} MiB); numpy, single thread"}
-    # The encoder's roofline: it reads the raw payload from staging once (bulk
-    # copies into shared memory, where both of its passes read it) and writes
-    # the streams, plus 16 B of stream offset and length per entry:
-    # alg = D + Z + 16 k per launch.
+    # The encoder's roofline (64 KiB chunks: the pass made the block headers):
+    # crz_size_kernel reads every block's header word (8 B per 512 B) and
+    # writes each stream's length and offset; crz_encode_sized_kernel reads
+    # the raw payload from staging once, the header words again, and writes
+    # the streams: alg = D + Z + 16 k + 2 D / 64 for the two launches, timed
+    # together (the device time of both).
     full_f32 = [e for e in enc if e[0] == "f32_normal" and e[1]]
     kind, _, D, Z, k, ms = full_f32[0]
-    alg = D + Z + 16 * k
-    roofline = {"bound": "hbm", "kernel": "crz_encode_kernel (full checkpoint, fp32 N(0,1), device images)",
+    alg = D + Z + 16 * k + 2 * (D // 64)
+    roofline = {"bound": "hbm", "kernel": "crz_size_kernel + crz_encode_sized_kernel (full checkpoint, fp32 "
+                                          "N(0,1), device images)",
                 "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                 "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": profile_traffic("crz_encode_c2_f32"),
                 "alg_bytes_per_launch": int(alg), "avg_launch_ms": ms, "raw_gbs": D / (ms / 1e3) / 1e9,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
     encoder = [{"content": e[0], "checkpoint": "full" if e[1] else "delta", "raw_bytes": e[2],
                 "stored_bytes": e[3], "k": e[4], "ms": e[5], "raw_gbs": e[2] / (e[5] / 1e3) / 1e9,
-                "hbm_frac": (e[2] + e[3] + 16 * e[4]) / (e[5] / 1e3) / 1e9 / peak} for e in enc]
+                "hbm_frac": (e[2] + e[3] + 16 * e[4] + 2 * (e[2] // 64)) / (e[5] / 1e3) / 1e9 / peak} for e in enc]
     line = {"workload": "codec: c2 layout (256 allocs = 4 GiB, 64 KiB chunks, 10% hot set), contents "
                         "fp32 N(0,1) / bf16 N(0,1) / zeros / uniform bytes; plain vs CRZ1-coded images",
             "tracked_bytes": B, "n_chunks": n, "steps": steps, "roofline": roofline, "rows": rows,

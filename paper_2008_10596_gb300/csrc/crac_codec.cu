@@ -377,9 +377,217 @@ __global__ void __launch_bounds__(kCodecNT, 3) crz_encode_kernel(const CodecPara
     }
 }
 
+// ---- the encoder when the pass made the block headers --------------------
+// With every block's header word already in P.chdr, a stream's length needs
+// only its headers' widths: crz_size_kernel sizes and places every stream
+// first, and crz_encode_sized_kernel then codes without any wait between
+// CTAs, one warp per 64 KiB segment of an entry, straight from staging.
+constexpr uint32_t kSizeTile = kCodecNT;   // entries per tile of the sizing kernel
+constexpr uint32_t kSegBlocks = 128;       // blocks per work item of the sized encoder
+
+// zlen and zoff of every entry (and zoff[k]) from the header widths: one warp
+// per entry sums them; a tile's padded lengths are scanned and placed by a
+// decoupled look-back over the earlier tiles (tiles are taken in ticket
+// order, so every predecessor has started).  piece_off[i] receives zoff of
+// entry k * i / pieces, for i = 0 .. pieces.
+__global__ void __launch_bounds__(kCodecNT) crz_size_kernel(const CodecParams P) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_z[kSizeTile];
+    __shared__ uint64_t s_w64[kCodecWarps];
+    __shared__ uint64_t s_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (;;) {
+        __syncthreads();   // the previous tile's shared state is consumed
+        if (tid == 0) {
+            uint32_t t = atomicAdd(P.ticket, 1u);
+            // fault injection: tile 0 is never sized, so the later tiles'
+            // bounded look-back waits run out and the launch reports kErrTimeout
+            if (P.skip_first_ticket && t == 0) t = atomicAdd(P.ticket, 1u);
+            s_tile = t;
+        }
+        __syncthreads();
+        const uint64_t e0 = (uint64_t)s_tile * kSizeTile;
+        if (e0 >= P.k) return;
+        const uint32_t ne = (uint32_t)umin64(kSizeTile, P.k - e0);
+        for (uint32_t t = warp; t < ne; t += kCodecWarps) {
+            const uint64_t e = e0 + t;
+            const uint64_t L = P.off[e + 1] - P.off[e], nb = L >> 9;
+            const uint64_t *h = P.chdr + (P.idx[e] << P.log2_bpc);
+            uint32_t w = 0;
+            for (uint64_t b = lane; b < nb; b += 32) w += crz_width_sum(h[b]);
+            w = __reduce_add_sync(kFull, w);   // <= 32 per block, nb <= 2^15
+            if (lane == 0) {
+                const uint64_t zc = crz_head_bytes(nb) + 16ull * w + (L & 511u);
+                const uint64_t z = (nb && zc < L) ? zc : L;
+                P.zlen[e] = z;
+                s_z[t] = (z + 15) & ~15ull;
+            }
+        }
+        __syncthreads();
+        uint64_t tile_bytes;
+        const uint64_t ex = cta_excl_scan<uint64_t>((uint32_t)tid < ne ? s_z[tid] : 0ull, s_w64, &tile_bytes);
+        const uint32_t tile = (uint32_t)(e0 / kSizeTile);
+        if (warp == 0) {
+            uint64_t base = 0;
+            if (tile == 0) {
+                if (lane == 0) st_status(P.status, kFlagInc | tile_bytes);
+            } else {
+                if (lane == 0) st_status(P.status + tile, kFlagAgg | tile_bytes);
+                base = lookback1(P.status, tile, lane, P.timeout_ns, P.err);
+                if (lane == 0) st_status(P.status + tile, kFlagInc | ((base + tile_bytes) & kValMask));
+            }
+            if (lane == 0) s_base = base;
+        }
+        __syncthreads();
+        const uint64_t base = s_base;
+        if ((uint32_t)tid < ne) {
+            const uint64_t e = e0 + tid, zo = base + ex;
+            P.zoff[e] = zo;
+            // entries that start a piece: k * i / pieces == e for some i
+            const uint64_t i = (e * P.pieces + P.k - 1) / P.k;   // smallest i with k * i / pieces >= e
+            if (i < P.pieces && P.k * i / P.pieces == e) P.piece_off[i] = zo;
+        }
+        if (tid == 0 && e0 + ne == P.k) {
+            P.zoff[P.k] = base + tile_bytes;
+            P.piece_off[P.pieces] = base + tile_bytes;
+        }
+    }
+}
+
+// Bytes [x0, x1) of a raw entry (src, any alignment) to d (16-byte aligned),
+// one warp.
+__device__ __forceinline__ void copy_raw_warp(uint8_t *d, const uint8_t *src, uint64_t x0, uint64_t x1, int lane) {
+    const uint64_t nv = (x1 - x0) >> 4;
+    for (uint64_t v = lane; v < nv; v += 32)
+        *reinterpret_cast<uint4 *>(d + x0 + 16 * v) = load16_any(src + x0 + 16 * v);
+    for (uint64_t i = x0 + 16 * nv + lane; i < x1; i += 32) d[i] = src[i];
+}
+
+// Entries [e_begin, e_end) -> their streams at zoff (made by crz_size_kernel):
+// work item = (entry, 64 KiB segment), one warp each, in entry order.  A
+// coded segment writes its blocks' header words and units (unit offsets: the
+// widths of the entry's earlier blocks, then a warp scan over the segment's),
+// and the segment holding the entry's last block also the header pad, the
+// raw tail and the stream pad; a raw entry is copied segment by segment.
+__global__ void __launch_bounds__(kCodecNT, 4) crz_encode_sized_kernel(const CodecParams P) {
+    __shared__ __align__(16) uint8_t s_units[kCodecWarps][512];
+    __shared__ uint32_t s_boff[kCodecWarps][kSegBlocks];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const CrzLane LT = crz_lane(lane);
+    const uint32_t spe = P.segs_per_entry;
+    const uint64_t items = (P.e_end - P.e_begin) * spe;
+    const uint64_t nw = ((uint64_t)gridDim.x * kCodecNT) >> 5;
+    for (uint64_t it = ((uint64_t)blockIdx.x * kCodecNT + tid) >> 5; it < items; it += nw) {
+        const uint64_t e = P.e_begin + it / spe;
+        const uint32_t sg = (uint32_t)(it % spe);
+        const uint64_t o = P.off[e], L = P.off[e + 1] - o;
+        const uint64_t z = P.zlen[e];
+        uint8_t *d = P.dst + P.zoff[e];
+        const uint8_t *src = P.src + o;
+        if (z == L) {   // stored raw
+            const uint64_t x0 = (uint64_t)sg * (512ull * kSegBlocks);
+            if (x0 >= L) continue;
+            const uint64_t x1 = umin64(L, x0 + 512ull * kSegBlocks);
+            copy_raw_warp(d, src, x0, x1, lane);
+            if (x1 == L)
+                for (uint64_t i = L + lane; i < ((L + 15) & ~15ull); i += 32) d[i] = 0;
+            continue;
+        }
+        const uint64_t nb = L >> 9;   // >= 1: a coded stream is shorter than its entry
+        const uint32_t last = (uint32_t)((nb - 1) / kSegBlocks);
+        if (sg > last) continue;
+        const uint64_t b0 = (uint64_t)sg * kSegBlocks;
+        const uint32_t nseg = (uint32_t)umin64(kSegBlocks, nb - b0);
+        const uint64_t *h = P.chdr + (P.idx[e] << P.log2_bpc);
+        uint64_t *dh = reinterpret_cast<uint64_t *>(d);
+        // units of the entry's blocks before this segment
+        uint32_t before = 0;
+        for (uint64_t b = lane; b < b0; b += 32) before += crz_width_sum(h[b]);
+        before = __reduce_add_sync(kFull, before);
+        // lane l: blocks b0 + 4l .. 4l + 3 of the segment -> header words, unit offsets
+        uint32_t wq[4], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t j = 4u * lane + q;
+            wq[q] = 0;
+            if (j < nseg) {
+                const uint64_t hw = h[b0 + j];
+                dh[b0 + j] = hw;
+                wq[q] = crz_width_sum(hw);
+            }
+            sum += wq[q];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, s);
+            if (lane >= s) inc += t;
+        }
+        uint32_t run = before + inc - sum;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t j = 4u * lane + q;
+            if (j < nseg) s_boff[warp][j] = run;
+            run += wq[q];
+        }
+        const uint64_t head = crz_head_bytes(nb);
+        if (sg == last && lane == 0 && (nb & 1)) dh[nb] = 0;   // header pad
+        __syncwarp();
+        // blocks, the next one's 16 bytes loaded while this one is coded
+        uint4 v = load16_any(src + 512ull * b0 + 16u * lane);
+        for (uint32_t j = 0; j < nseg; ++j) {
+            const uint64_t b = b0 + j;
+            uint4 nx = v;
+            if (j + 1 < nseg) nx = load16_any(src + 512ull * (b + 1) + 16u * lane);
+            const uint32_t r[4] = {crz_rot(v.x), crz_rot(v.y), crz_rot(v.z), crz_rot(v.w)};
+            uint32_t pw[4];
+            crz_bytes_transpose(r, pw);
+            crz_block_units(__ldg(h + b), pw, d + head + 16ull * s_boff[warp][j], lane, LT, s_units[warp]);
+            v = nx;
+        }
+        if (sg == last) {   // the raw tail, then the stream pad
+            const uint64_t tl = L & 511u;
+            copy_raw_warp(d + z - tl - 512ull * nb, src, 512ull * nb, L, lane);
+            for (uint64_t i = z + lane; i < ((z + 15) & ~15ull); i += 32) d[i] = 0;
+        }
+        __syncwarp();   // s_boff is rewritten by the warp's next item
+    }
+}
+
 }  // namespace
 
 uint32_t crz_tile_max() { return kCodecTileMax; }
+
+uint32_t crz_sized_segs(uint32_t log2S) { return log2S > 16 ? 1u << (log2S - 16) : 1u; }
+
+cudaError_t launch_crz_size(const CodecParams &p, int grid, cudaStream_t s) {
+    if (p.k == 0) return cudaSuccess;
+    crz_size_kernel<<<grid, kCodecNT, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_crz_encode_sized(const CodecParams &p, int grid, cudaStream_t s) {
+    if (p.e_end <= p.e_begin) return cudaSuccess;
+    crz_encode_sized_kernel<<<grid, kCodecNT, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+int crz_sized_max_ctas_per_sm() {
+    static int v = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, crz_encode_sized_kernel, kCodecNT, 0) != cudaSuccess)
+            n = 1;
+        cudaGetLastError();
+        v = n > 0 ? n : 1;
+    });
+    return v;
+}
 
 int crz_encode_max_ctas_per_sm() {
     static int v = 0;

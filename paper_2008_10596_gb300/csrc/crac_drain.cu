@@ -33,13 +33,35 @@ __global__ void __launch_bounds__(kDrainNT) drain_kernel(const CkptCtrl *ctrl, c
     for (uint64_t j = tid; j < k; j += nt) idx_dst[j] = idx_src[j];
 }
 
+// A small report (a pass's control block, an encoder launch's end offset and
+// error bits, a restart's error word) for the host: n 8-byte words from
+// device memory, then one 4-byte word zero-extended, stored by one warp into
+// pinned host memory through its device mapping.  A copy-engine copy of these
+// few bytes would queue behind the bulk drains on the copy engines (other
+// images', other contexts') and hold up whoever waits for the report.
+__global__ void report_kernel(const uint64_t *words, uint32_t n, const uint32_t *word32, uint64_t *dst) {
+    for (uint32_t i = threadIdx.x; i < n; i += 32) dst[i] = words[i];
+    if (word32 && threadIdx.x == 0) dst[n] = *word32;
+}
+
 }  // namespace
+
+const void *report_fn() { return reinterpret_cast<const void *>(&report_kernel); }
+
+cudaError_t launch_report(const void *words, uint32_t n, const uint32_t *word32, void *dst, cudaStream_t s) {
+    report_kernel<<<1, 32, 0, s>>>(reinterpret_cast<const uint64_t *>(words), n, word32,
+                                   reinterpret_cast<uint64_t *>(dst));
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
 
 // Load the kernel now (modules load lazily on first launch, which can block
 // the host): a checkpoint that returns once enqueued must not be the first.
 cudaError_t prepare_drain() {
     cudaFuncAttributes a;
-    return cudaFuncGetAttributes(&a, drain_kernel);
+    const cudaError_t e = cudaFuncGetAttributes(&a, drain_kernel);
+    return e != cudaSuccess ? e : cudaFuncGetAttributes(&a, report_kernel);
 }
 
 cudaError_t launch_drain(const CkptCtrl *ctrl, const uint8_t *src, uint8_t *dst, uint64_t cap,

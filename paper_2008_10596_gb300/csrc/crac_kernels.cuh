@@ -177,6 +177,11 @@ cudaError_t launch_scatter(const ScatterParams &p, int grid, cudaStream_t s);
 // Side-stream drain of a delta pass into host images, sized on the device
 // from the pass's control block (crac_drain.cu); prepare_drain loads it.
 cudaError_t prepare_drain();
+// n 8-byte words at `words` (device), then the 4-byte word32 (device, or
+// null) zero-extended, to dst (pinned host memory, through its device
+// mapping), by a one-warp kernel on s rather than by a copy engine.
+cudaError_t launch_report(const void *words, uint32_t n, const uint32_t *word32, void *dst, cudaStream_t s);
+const void *report_fn();   // the kernel, for graph nodes: args (words, n, word32, dst)
 cudaError_t launch_drain(const CkptCtrl *ctrl, const uint8_t *src, uint8_t *dst, uint64_t cap,
                          const uint64_t *idx_src, uint64_t *idx_dst, uint64_t idx_cap, int grid, cudaStream_t s);
 // One piece of a device-resident image in a multi-image restore: its chunk
@@ -245,8 +250,20 @@ struct CodecParams {
     const uint64_t *chdr;
     const uint64_t *idx;          // the entries' global chunk ids
     uint32_t log2_bpc;            // log2 of 512-byte blocks per chunk
+    // With chdr, the streams are sized and placed first (crz_size_kernel:
+    // zlen, zoff; piece_off[i] = zoff[k * i / pieces], i = 0 .. pieces), then
+    // coded by crz_encode_sized_kernel over entries [e_begin, e_end), each
+    // entry as segs_per_entry work items of 64 KiB.
+    uint64_t *piece_off;
+    uint32_t pieces;
+    uint32_t segs_per_entry;
+    uint64_t e_begin, e_end;
 };
 cudaError_t launch_crz_encode(const CodecParams &p, int grid, cudaStream_t s);
+cudaError_t launch_crz_size(const CodecParams &p, int grid, cudaStream_t s);
+cudaError_t launch_crz_encode_sized(const CodecParams &p, int grid, cudaStream_t s);
+int crz_sized_max_ctas_per_sm();
+uint32_t crz_sized_segs(uint32_t log2S);   // work items per entry of the sized encoder
 uint32_t crz_tile_max();
 int crz_encode_max_ctas_per_sm();
 

@@ -66,6 +66,8 @@ crac_status_t ctx_cuda_ready(crac_ctx *c) {
     CK(prepare_drain());
     TRY(ensure_host(c->ctrl_h, sizeof(CkptCtrl) + 16 * (1 + kEncPieces)));   // + the encoder's offsets, errors
     for (cudaEvent_t &e : c->ev_piece) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreate(&c->ev_z0));
+    CK(cudaEventCreate(&c->ev_z1));
     TRY(ensure_host(c->serr_h, 256));
     if (c->cfg.reserve_host_bytes) {
         TRY(pinned_arena().reserve(c->cfg.reserve_host_bytes));
@@ -106,6 +108,8 @@ void ctx_free_all(crac_ctx *c) {
                           c->sev[2], c->sev[3], c->ev_r0, c->ev_r1})
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_piece)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {c->ev_z0, c->ev_z1})
         if (e) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
     cudaGetLastError();
@@ -170,7 +174,28 @@ std::vector<Segment> make_segments(const std::vector<AllocRec> &allocs, const st
     return out;
 }
 
-// Build (or update) the graph memset -> fused kernel -> ctrl D2H and launch it.
+// Kernel-node parameters of the control block's report to the host (args
+// must outlive the node's add or update call).
+struct ReportNode {
+    const void *words;
+    uint32_t n = sizeof(CkptCtrl) / 8;
+    const uint32_t *word32 = nullptr;
+    void *dst;
+    void *args[4];
+    cudaKernelNodeParams kp{};
+    ReportNode(const void *src, void *to) : words(src), dst(to) {
+        args[0] = &words;
+        args[1] = &n;
+        args[2] = &word32;
+        args[3] = &dst;
+        kp.func = const_cast<void *>(report_fn());
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+    }
+};
+
+// Build (or update) the graph memset -> fused kernel -> ctrl report and launch it.
 crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, const void *fn,
                                  int threads, size_t smem, int grid, void *ctrl_dst, cudaStream_t s) {
     if (!fn) return CRAC_ERR_INVALID_ARG;
@@ -190,12 +215,12 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     mp.height = 1;
     mp.pitch = 0;
     bool rebuilt = false;
+    ReportNode rep(P.ctrl, ctrl_dst);
     if (c->gexec && c->g_fn == fn) {
         // Width changes of a memset node may be rejected; rebuild then.
         if (cudaGraphExecMemsetNodeSetParams(c->gexec, c->g_memset, &mp) != cudaSuccess ||
             cudaGraphExecKernelNodeSetParams(c->gexec, c->g_kernel, &kp) != cudaSuccess ||
-            cudaGraphExecMemcpyNodeSetParams1D(c->gexec, c->g_copy, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
-                                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGraphExecKernelNodeSetParams(c->gexec, c->g_copy, &rep.kp) != cudaSuccess) {
             cudaGetLastError();
             c->g_fn = nullptr;
         }
@@ -208,8 +233,7 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         CK(cudaGraphCreate(&c->graph, 0));
         CK(cudaGraphAddMemsetNode(&c->g_memset, c->graph, nullptr, 0, &mp));
         CK(cudaGraphAddKernelNode(&c->g_kernel, c->graph, &c->g_memset, 1, &kp));
-        CK(cudaGraphAddMemcpyNode1D(&c->g_copy, c->graph, &c->g_kernel, 1, ctrl_dst, P.ctrl,
-                                    sizeof(CkptCtrl), cudaMemcpyDeviceToHost));
+        CK(cudaGraphAddKernelNode(&c->g_copy, c->graph, &c->g_kernel, 1, &rep.kp));
         CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
         c->g_fn = fn;
         c->g_threads = threads;
@@ -218,7 +242,7 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     (void)rebuilt;
     CK(cudaEventRecord(c->ev_t0, s));   // after the host-side updates: times the device work only
     CK(cudaGraphLaunch(c->gexec, s));
-    count_launches(1);
+    count_launches(2);
     return CRAC_OK;
 }
 
@@ -249,14 +273,13 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
     mp.elementSize = 4;
     mp.width = work_bytes / 4;
     mp.height = 1;
+    ReportNode rep(P.ctrl, ctrl_dst);
     bool ok = c->sgexec != nullptr && c->s_hash_fn == hash_fn;
     if (ok) {
         ok = cudaGraphExecMemsetNodeSetParams(c->sgexec, c->s_memset, &mp) == cudaSuccess;
         for (int i = 0; ok && i < 3; ++i)
             ok = cudaGraphExecKernelNodeSetParams(c->sgexec, c->s_k[i], &kp[i]) == cudaSuccess;
-        if (ok)
-            ok = cudaGraphExecMemcpyNodeSetParams1D(c->sgexec, c->s_copy, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
-                                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (ok) ok = cudaGraphExecKernelNodeSetParams(c->sgexec, c->s_copy, &rep.kp) == cudaSuccess;
         if (!ok) cudaGetLastError();
     }
     if (!ok) {
@@ -264,7 +287,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         if (c->sgraph) cudaGraphDestroy(c->sgraph);
         c->sgexec = nullptr;
         c->sgraph = nullptr;
-        // memset -> event 0 -> hash => finalize => gather -> control block D2H,
+        // memset -> event 0 -> hash => finalize => gather -> control block report,
         // where => is a programmatic edge (the consumer is launched as its
         // producer drains and waits in-kernel for its completion); events 1-3
         // record each kernel's end on side branches, off the critical path.
@@ -281,14 +304,13 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
             CK(cudaGraphAddDependencies(c->sgraph, &c->s_k[i - 1], &c->s_k[i], &pe, 1));
         }
         for (int i = 0; i < 3; ++i) CK(cudaGraphAddEventRecordNode(&ev, c->sgraph, &c->s_k[i], 1, c->sev[i + 1]));
-        CK(cudaGraphAddMemcpyNode1D(&c->s_copy, c->sgraph, &c->s_k[2], 1, ctrl_dst, P.ctrl, sizeof(CkptCtrl),
-                                    cudaMemcpyDeviceToHost));
+        CK(cudaGraphAddKernelNode(&c->s_copy, c->sgraph, &c->s_k[2], 1, &rep.kp));
         CK(cudaGraphInstantiate(&c->sgexec, c->sgraph, 0));
         c->s_hash_fn = hash_fn;
     }
     CK(cudaEventRecord(c->ev_t0, s));
     CK(cudaGraphLaunch(c->sgexec, s));
-    count_launches(3);
+    count_launches(4);
     return CRAC_OK;
 }
 
@@ -377,7 +399,7 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         c->last.grid = (uint32_t)gh;
         c->last.chunks_per_tile = cptF;
         c->last.warps_per_chunk = 0;
-        c->last.kernel_launches += 3;
+        c->last.kernel_launches += 4;   // hash, finalize, gather, control-block report
         c->last.pass_kernel = P.sparse ? CRAC_PASS_SPARSE : CRAC_PASS_SPLIT;
     } else if (c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) {
         const uint64_t S = 1ull << c->log2S;
@@ -437,7 +459,7 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         c->last.grid = (uint32_t)grid;
         c->last.chunks_per_tile = cpt;
         c->last.warps_per_chunk = (uint32_t)wpc;
-        c->last.kernel_launches += 1;
+        c->last.kernel_launches += 2;   // the pass, control-block report
     } else {
         TRY(ensure_dev(c->work, sizeof(CkptCtrl)));
         TRY(ensure_dev(c->lens, nseg * sizeof(uint32_t)));
@@ -459,7 +481,8 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
                                    u1 - u0, idx_cap, staging, staging_cap, ctrl, g, s));
             c->last.kernel_launches += 3;
         }
-        CK(cudaMemcpyAsync(ctrl_dst, ctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
+        CK(launch_report(ctrl, sizeof(CkptCtrl) / 8, nullptr, ctrl_dst, s));
+        c->last.kernel_launches += 1;
     }
     c->split_now = split;
     CK(cudaEventRecord(c->ev_t1, s));
@@ -514,8 +537,10 @@ uint32_t crz_tile_entries(uint32_t log2S) {
 // Encoder scratch of a segment with k entries and D raw bytes: the error
 // word, one tile counter per launch, then one look-back word per tile and the
 // block header words of multi-window chunks.
-constexpr size_t kZworkHead = 48;     // 4 + 4 * kEncPieces bytes, rounded up to 16
-static_assert(4 + 4 * kEncPieces <= kZworkHead, "encoder scratch head");
+constexpr size_t kZworkTickets = 4;                             // after the error word
+constexpr size_t kZworkPieceOff = 48;                           // the sized encoder's piece offsets
+constexpr size_t kZworkHead = kZworkPieceOff + 8 * (kEncPieces + 1) + 8;   // rounded up to 16
+static_assert(kZworkTickets + 4 * kEncPieces <= kZworkPieceOff && kZworkHead % 16 == 0, "encoder scratch head");
 
 size_t crz_work_bytes(uint64_t k, uint64_t D, uint32_t log2S) {
     const uint64_t tiles = (k + crz_tile_entries(log2S) - 1) / crz_tile_entries(log2S);
@@ -535,8 +560,110 @@ size_t crz_work_bytes(uint64_t k, uint64_t D, uint32_t log2S) {
 // stream offsets in pc.off_dev and lengths in pc.zlen_dev.  On return the
 // total stream bytes are known (*Z), and *zplaced says that the streams are
 // in pc.host, or on their way there on the side stream.
+// encode_segment when the pass made the block headers (c->crz_hdr_now):
+// crz_size_kernel sizes and places every stream from the headers, the host
+// reads the total (and the piece boundaries), takes an exact destination,
+// and crz_encode_sized_kernel codes in up to kEncPieces launches; for staged
+// host images each launch's streams are copied to the pinned block as soon
+// as it ends (its bytes are known already), overlapping the later launches.
+crac_status_t encode_segment_sized(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
+                                   cudaStream_t s, uint64_t *Z, bool *zplaced) {
+    const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
+    *zplaced = false;
+    TRY(ensure_dev(c->zwork, crz_work_bytes(k, D, c->log2S)));
+    uint8_t *w = (uint8_t *)c->zwork.p;
+    const uint64_t size_tiles = (k + 255) / 256;
+    const uint32_t spe = crz_sized_segs(c->log2S);
+    const uint64_t warps = (uint64_t)c->sm_count * crz_sized_max_ctas_per_sm() * 8;
+    // staged host images: launches of at least 32 MiB of raw payload each (the
+    // copy of a piece's streams takes far longer than its encoding)
+    uint32_t pieces = 1;
+    if (host_res && !direct_flag)
+        pieces = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({(uint64_t)kEncPieces, k, D >> 25}));
+    CodecParams P{};
+    P.src = (const uint8_t *)c->staging.p;
+    P.off = (const uint64_t *)c->off.p;
+    P.k = k;
+    P.chdr = (const uint64_t *)c->chdr.p;
+    P.idx = host_res ? (const uint64_t *)c->idx.p : (const uint64_t *)pc.idx_dev.p;
+    P.log2_bpc = c->log2S - 9;
+    P.zoff = host_res ? (uint64_t *)c->zoff.p : (uint64_t *)pc.off_dev.p;
+    P.zlen = host_res ? (uint64_t *)c->zlen.p : (uint64_t *)pc.zlen_dev.p;
+    P.err = (unsigned int *)w;
+    P.ticket = (uint32_t *)(w + kZworkTickets);
+    P.status = (uint64_t *)(w + kZworkHead);
+    P.piece_off = (uint64_t *)(w + kZworkPieceOff);
+    P.pieces = pieces;
+    P.segs_per_entry = spe;
+    P.timeout_ns = c->cfg.timeout_ns;
+    P.skip_first_ticket = (size_tiles >= 2 && fault_hit(CRAC_FAULT_ENCODE_WAIT)) ? 1u : 0u;
+    uint64_t *out_h = (uint64_t *)((uint8_t *)c->ctrl_h.p + sizeof(CkptCtrl));
+    std::memset(out_h, 0, 16 * (1 + kEncPieces));
+    CK(cudaMemsetAsync(w, 0, kZworkHead + 8 * size_tiles, s));
+    CK(cudaEventRecord(c->ev_t0, s));
+    CK(launch_crz_size(P, (int)std::max<uint64_t>(1, std::min<uint64_t>(size_tiles, (uint64_t)c->sm_count * 4)), s));
+    CK(cudaEventRecord(c->ev_z0, s));
+    CK(launch_report(P.piece_off, pieces + 1, P.err, out_h, s));   // piece offsets, then the error bits
+    CK(cudaEventRecord(c->ev_pass, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    const unsigned err = (uint32_t)out_h[pieces + 1];
+    if (err & kErrTimeout) return CRAC_ERR_TIMEOUT;
+    if (err) return CRAC_ERR_CORRUPT;
+    for (uint32_t i = 0; i < pieces; ++i)
+        if (out_h[i] > out_h[i + 1]) return CRAC_ERR_CORRUPT;
+    const uint64_t z_all = out_h[pieces];
+    if (out_h[0] != 0 || z_all > zmax) return CRAC_ERR_CORRUPT;
+    uint64_t poff[kEncPieces + 1];
+    for (uint32_t i = 0; i <= pieces; ++i) poff[i] = out_h[i];
+    bool piped = false;
+    if (host_res) {
+        P.zoff = (uint64_t *)c->zoff.p;
+        if (direct_flag && pinned_arena().try_alloc(z_all, &pc.host)) {
+            P.dst = pc.host.p;
+            *zplaced = true;
+        } else {
+            TRY(ensure_dev(c->cstage, std::max<uint64_t>(z_all, 16)));
+            P.dst = (uint8_t *)c->cstage.p;
+            if (pieces > 1 && pinned_arena().alloc(z_all, &pc.host) == CRAC_OK) piped = *zplaced = true;
+        }
+    } else {
+        TRY(device_arena(c->device).alloc(std::max<uint64_t>(z_all, 16), &pc.dev));
+        P.dst = pc.dev.p;
+    }
+    const int grid = (int)std::max<uint64_t>(1, warps / 8);
+    CK(cudaEventRecord(c->ev_z1, s));
+    for (uint32_t i = 0; i < pieces; ++i) {
+        CodecParams Q = P;
+        Q.e_begin = k * i / pieces;
+        Q.e_end = k * (i + 1) / pieces;
+        CK(launch_crz_encode_sized(Q, grid, s));
+        if (piped) {
+            CK(cudaEventRecord(c->ev_piece[i], s));
+            if (poff[i + 1] > poff[i]) {
+                CK(cudaStreamWaitEvent(c->side, c->ev_piece[i], 0));
+                CK(cudaMemcpyAsync(pc.host.p + poff[i], c->cstage.p + poff[i], poff[i + 1] - poff[i],
+                                   cudaMemcpyDeviceToHost, c->side));
+            }
+        }
+    }
+    CK(cudaEventRecord(c->ev_t1, s));
+    CK(cudaEventRecord(c->ev_pass, s));
+    CK(cudaEventSynchronize(c->ev_pass));
+    c->last.kernel_launches += 2 + pieces;
+    // device time of the sizing and of the coding (not the host's read of the
+    // sizes in between)
+    float ms = 0, ms2 = 0;
+    if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_z0) == cudaSuccess &&
+        cudaEventElapsedTime(&ms2, c->ev_z1, c->ev_t1) == cudaSuccess)
+        c->last.codec_ms += ms + ms2;
+    cudaGetLastError();
+    *Z = z_all;
+    return CRAC_OK;
+}
+
 crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
                              cudaStream_t s, uint64_t *Z, bool *zplaced) {
+    if (c->crz_hdr_now) return encode_segment_sized(c, pc, ctrl, host_res, direct_flag, s, Z, zplaced);
     const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
     const uint32_t T = crz_tile_entries(c->log2S);
     const uint64_t n_tiles = (k + T - 1) / T;
@@ -579,6 +706,7 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
     P.err = (unsigned int *)w;
     P.status = (uint64_t *)(w + kZworkHead);
     P.hdr = P.status + n_tiles;
+    P.piece_off = (uint64_t *)(w + kZworkPieceOff);
     P.tile_entries = T;
     P.timeout_ns = c->cfg.timeout_ns;
     const bool inject = n_tiles >= 2 && fault_hit(CRAC_FAULT_ENCODE_WAIT);
@@ -591,22 +719,20 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
     for (uint32_t i = 0; i < pieces; ++i) {
         const uint64_t t0 = n_tiles * i / pieces, t1 = n_tiles * (i + 1) / pieces;
         CodecParams Q = P;
-        Q.ticket = (uint32_t *)(w + 4) + i;
+        Q.ticket = (uint32_t *)(w + kZworkTickets) + i;
         Q.tile_begin = (uint32_t)t0;
         Q.n_tiles = (uint32_t)t1;
         Q.skip_first_ticket = (i == 0 && inject) ? 1u : 0u;
         CK(launch_crz_encode(Q, (int)std::min<uint64_t>(t1 - t0, (uint64_t)grid_max), s));
-        if (pieces > 1) {
-            CK(cudaMemcpyAsync(out_h + 2 + 2 * i, P.zoff + std::min<uint64_t>(k, t1 * T), 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(out_h + 3 + 2 * i, w, 4, cudaMemcpyDeviceToHost, s));
+        if (pieces > 1) {   // the piece's end offset and error bits so far
+            CK(launch_report(P.zoff + std::min<uint64_t>(k, t1 * T), 1, P.err, out_h + 2 + 2 * i, s));
             CK(cudaEventRecord(c->ev_piece[i], s));
         }
     }
     CK(cudaEventRecord(c->ev_t1, s));
-    CK(cudaMemcpyAsync(out_h, P.zoff + k, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(out_h + 1, w, 4, cudaMemcpyDeviceToHost, s));
+    CK(launch_report(P.zoff + k, 1, P.err, out_h, s));   // the total and the error bits
     CK(cudaEventRecord(c->ev_pass, s));
-    c->last.kernel_launches += pieces;
+    c->last.kernel_launches += pieces + (pieces > 1 ? pieces : 0) + 1;
     if (pieces > 1) {
         // Copy each piece's streams once it has ended; a piece with an error,
         // or an end offset out of order, stops the copies (the total's check

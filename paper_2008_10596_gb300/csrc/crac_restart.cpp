@@ -184,12 +184,12 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
         CK(launch_restore_unmark(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((nt + 255) / 256, grid)), s));
     CK(launch_restore_scatter(P, (int)std::max<uint64_t>(1, std::min<uint64_t>((entries + 7) / 8, grid)), s));
     CK(cudaEventRecord(c->ev_r1, s));
-    if (incremental) CK(cudaMemcpyAsync(c->ctrl_h.p, vctrl, sizeof(CkptCtrl), cudaMemcpyDeviceToHost, s));
+    if (incremental) CK(launch_report(vctrl, sizeof(CkptCtrl) / 8, nullptr, c->ctrl_h.p, s));
     if (nt) {
         const void *fp = img->residency == CRAC_RESIDENCY_DEVICE ? (const void *)img->fp_dev.p : (const void *)img->fp_h.p;
         CK(cudaMemcpyAsync(c->fp[spare].p, fp, nt * 8, cudaMemcpyDefault, s));
     }
-    CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(launch_report(nullptr, 0, (const uint32_t *)c->serr.p, c->serr_h.p, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
     const unsigned err = *(const unsigned *)c->serr_h.p;
@@ -466,7 +466,7 @@ crac_status_t ctx_restart(crac_ctx *c, crac_image *img, cudaStream_t s) {
     TRY(ensure_dev(c->fp[spare], std::max<uint64_t>(nt, 1) * 8));
     CK(cudaEventRecord(c->ev_r1, s));
     if (nt) CK(cudaMemcpyAsync(c->fp[spare].p, img->fp_h.p, nt * 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->serr_h.p, c->serr.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(launch_report(nullptr, 0, (const uint32_t *)c->serr.p, c->serr_h.p, s));
     CK(cudaEventRecord(c->ev_last, s));
     CK(cudaEventSynchronize(c->ev_last));
     if (*(const unsigned *)c->serr_h.p) return CRAC_ERR_CORRUPT;

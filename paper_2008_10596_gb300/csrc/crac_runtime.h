@@ -428,6 +428,7 @@ struct crac_ctx {
     cudaEvent_t ev_last = nullptr, ev_pass = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     cudaEvent_t ev_p0 = nullptr, ev_p1 = nullptr;
     cudaEvent_t ev_piece[crac::kEncPieces] = {};   // ends of the launches of a pipelined encode
+    cudaEvent_t ev_z0 = nullptr, ev_z1 = nullptr;   // the sized encoder: end of sizing, start of coding
     // graph for the fused pass: memset(ctrl+status) -> kernel -> D2H(ctrl)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;

@@ -427,7 +427,7 @@ def test_launch_modes_and_residency(mode):
         assert info["chain_length"] == 3 and info["restored_bytes"] == sum(sizes)
         if mode in ("per_alloc", "direct_per_alloc"):
             info = C.crac_ctx_last_pass(h.ctx)
-            assert info["kernel_launches"] == 3 * len(sizes)
+            assert info["kernel_launches"] == 3 * len(sizes) + 1   # + the control-block report
     finally:
         h.close()
 
