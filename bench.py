@@ -852,6 +852,9 @@ def run_passes(args):
     return 0
 
 
+N_FULL = 3   # codec: timed full checkpoints per variant
+
+
 def run_codec(args):
     """Coded images (CRAC_FLAG_COMPRESS) against plain ones on the config-2
     layout (256 allocations, 4 GiB, 64 KiB chunks, the same 10% hot set),
@@ -931,12 +934,16 @@ def run_codec(args):
             # scratch; the timed full one follows the fill with this content
             # (every chunk dirty, steady state), then the deltas of the 10%
             # hot set.
-            imgs, full, deltas = [C.crac_ctx_checkpoint(ctx, stream)], None, []
+            imgs, fulls, deltas = [C.crac_ctx_checkpoint(ctx, stream)], [], []
             C.crac_image_wait(imgs[0])
             fill(kind, wl.seed)
-            for r in range(steps + 1):
-                if r:
+            # three full checkpoints (the first finds every chunk rewritten, the
+            # next two follow an invalidation: the same work), then the deltas
+            for r in range(N_FULL + steps):
+                if r >= N_FULL:
                     testkit.mutate_xor(ent_dev.data_ptr(), len(muts), stream)
+                elif r:
+                    C.crac_ctx_invalidate(ctx)
                 torch.cuda.synchronize()
                 nvtx.range_push(f"codec_{name}")
                 t0 = time.perf_counter()
@@ -948,12 +955,17 @@ def run_codec(args):
                 pi = C.crac_ctx_last_pass(ctx)
                 rec = {"wall_ms": wall, "device_ms": pi["device_ms"], "codec_ms": pi["codec_ms"],
                        "raw_bytes": pi["payload_bytes"], "stored_bytes": pi["stored_bytes"], "k": pi["k"]}
-                if r == 0:
-                    full = rec
+                if r < N_FULL:
+                    fulls.append(rec)
+                    # a full image needs no earlier one: release them, so that
+                    # the pinned arena stays under its 80% mark
+                    for old in imgs[:-1]:
+                        C.crac_image_release(old)
+                    imgs = imgs[-1:]
                 else:
                     deltas.append(rec)
                 if pi["codec_ms"] > 0 and name == "device_coded":
-                    enc.append((kind, r == 0, pi["payload_bytes"], pi["stored_bytes"], pi["k"], pi["codec_ms"]))
+                    enc.append((kind, r < N_FULL, pi["payload_bytes"], pi["stored_bytes"], pi["k"], pi["codec_ms"]))
             want = [bufs[i][:4096].clone() for i in (0, len(bufs) // 2, len(bufs) - 1)]
             for b in bufs[::17]:
                 b.zero_()
@@ -968,9 +980,13 @@ def run_codec(args):
                 C.crac_image_release(img)
             C.crac_ctx_destroy(ctx)
             med = lambda key: statistics.median(d[key] for d in deltas)   # noqa: E731
+            fmed = lambda key: statistics.median(d[key] for d in fulls)   # noqa: E731
             rows.append({
                 "content": kind, "images": name,
-                "full": dict(full, ratio=full["stored_bytes"] / full["raw_bytes"]),
+                "full": {"wall_ms": fmed("wall_ms"), "wall_ms_each": [d["wall_ms"] for d in fulls],
+                         "device_ms": fmed("device_ms"), "codec_ms": fmed("codec_ms"),
+                         "raw_bytes": fulls[0]["raw_bytes"], "stored_bytes": fulls[0]["stored_bytes"],
+                         "k": fulls[0]["k"], "ratio": fulls[0]["stored_bytes"] / fulls[0]["raw_bytes"]},
                 "delta": {"wall_ms": med("wall_ms"), "device_ms": med("device_ms"), "codec_ms": med("codec_ms"),
                           "raw_bytes": med("raw_bytes"), "stored_bytes": med("stored_bytes"),
                           "ratio": med("stored_bytes") / med("raw_bytes")},
@@ -1013,7 +1029,8 @@ def run_codec(args):
     # the streams: alg = D + Z + 16 k + 2 D / 64 for the two launches, timed
     # together (the device time of both).
     full_f32 = [e for e in enc if e[0] == "f32_normal" and e[1]]
-    kind, _, D, Z, k, ms = full_f32[0]
+    kind, _, D, Z, k, _ = full_f32[0]
+    ms = statistics.median(e[5] for e in full_f32)
     alg = D + Z + 16 * k + 2 * (D // 64)
     roofline = {"bound": "hbm", "kernel": "crz_size_kernel + crz_encode_sized_kernel (full checkpoint, fp32 "
                                           "N(0,1), device images)",
@@ -1029,9 +1046,10 @@ def run_codec(args):
             "tracked_bytes": B, "n_chunks": n, "steps": steps, "roofline": roofline, "rows": rows,
             "encoder_launches": encoder, "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu,
             "arena_growth": {k: mem1[k] - mem0[k] for k in ("host_grow_events", "device_grow_events")},
-            "note": "wall_ms includes the drain wait; full = a steady-state full checkpoint (every chunk "
-                    "rewritten after a first, untimed one of uniform bytes); delta rows are medians over the steps; the restart "
-                    "restores the chain of 2 full + steps deltas after zeroing every 17th allocation"}
+            "note": "wall_ms includes the drain wait; full = the median of three full checkpoints (the first "
+                    "finds every chunk rewritten after an untimed one of uniform bytes, the next two follow an "
+                    "invalidation); delta rows are medians over the steps; the restart restores the chain of the "
+                    "last full image + steps deltas after zeroing every 17th allocation"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1156,6 +1174,8 @@ class ServingRun:
                         except Exception as e:   # reported after the loop
                             errors.append(e)
                     if kind == C.CRAC_REQ_CHECKPOINT and r["status"] == 0:
+                        # the drain's own device time (settled: the request waited for it)
+                        r["drain_ms"] = C.crac_image_info(r["image"])["drain_ms"]
                         # keep only the newest image: its chain holds what a
                         # restart needs, and each FULL image frees the history
                         for old in p["images"]:
@@ -1165,6 +1185,7 @@ class ServingRun:
                     results[t] = (int(kind), r, p["bytes"])
                     collected[0] += 1
 
+        m0 = C.crac_memory_stats()
         # The prepare callbacks (the application's mutator launches) run on the
         # server's worker threads and need the GIL: hand it over quickly.
         switch = sys.getswitchinterval()
@@ -1203,7 +1224,12 @@ class ServingRun:
         C.crac_server_destroy(server)
         if errors:
             raise errors[0]
-        return self._summary(results, stats, t0, t_end, arrivals, targets, n_req, rate, workers, budget)
+        m1 = C.crac_memory_stats()
+        out = self._summary(results, stats, t0, t_end, arrivals, targets, n_req, rate, workers, budget)
+        # CUDA allocations made inside the loop (each can stall the requests in flight)
+        out["growth_in_loop"] = {k: m1[k] - m0[k] for k in ("host_grow_events", "device_grow_events",
+                                                             "scratch_grow_events")}
+        return out
 
     def _summary(self, results, stats, t0, t_end, arrivals, targets, n_req, rate, workers, budget):
         C = self.C
@@ -1214,6 +1240,7 @@ class ServingRun:
         # operation's call + (checkpoints) the wait for the image to settle
         parts = {k: {"prepare": [], "call": [], "settle": []} for k in ("checkpoint", "restart")}
         full_serv, full_wait = [], []
+        drain_gbs, full_drain_gbs = [], []   # payload bytes / drain device time, per checkpoint
         scanned = payload = 0
         fails = 0
         slow = []
@@ -1224,13 +1251,18 @@ class ServingRun:
             ms3 = ((r["t_op"] - r["t_admit"]) * 1e3, (r["t_op_end"] - r["t_op"]) * 1e3,
                    (r["t_done"] - r["t_op_end"]) * 1e3)
             slow.append(((r["t_done"] - r["t_admit"]) * 1e3, kind, nb, r["payload_bytes"],
-                         (r["t_admit"] - r["t_arrival"]) * 1e3, r["t_arrival"] - t0, ms3))
+                         (r["t_admit"] - r["t_arrival"]) * 1e3, r["t_arrival"] - t0, ms3, r.get("drain_ms", 0.0)))
             key = "checkpoint" if kind == C.CRAC_REQ_CHECKPOINT else "restart"
             lat[key].append((r["t_done"] - r["t_arrival"]) * 1e3)
             wait[key].append((r["t_admit"] - r["t_arrival"]) * 1e3)
             serv[key].append((r["t_done"] - r["t_admit"]) * 1e3)
             for name, v in zip(("prepare", "call", "settle"), ms3):
                 parts[key][name].append(v)
+            if kind == C.CRAC_REQ_CHECKPOINT and r.get("drain_ms", 0) > 0 and r["payload_bytes"] >= (1 << 20):
+                g = r["payload_bytes"] / (r["drain_ms"] / 1e3) / 1e9
+                drain_gbs.append(g)
+                if r["payload_bytes"] >= nb:
+                    full_drain_gbs.append(g)
             if kind == C.CRAC_REQ_CHECKPOINT and r["payload_bytes"] >= nb:
                 full_serv.append((r["t_done"] - r["t_admit"]) * 1e3)
                 full_wait.append((r["t_admit"] - r["t_arrival"]) * 1e3)
@@ -1254,11 +1286,19 @@ class ServingRun:
                 "service_ms": {k: dist(v) for k, v in serv.items()},
                 "service_parts_ms": {k: {n: dist(v) for n, v in d.items()} for k, d in parts.items()},
                 "full_checkpoint_ms": {"service": dist(full_serv), "queue_wait": dist(full_wait)},
+                # the drains' own rate (payload / device time of the drain on the
+                # context's side stream, checkpoints of at least 1 MiB): a slow
+                # tail here is the host link, not queueing or host code
+                "drain_gbs": {"all": {"p50": pct(drain_gbs, 50), "p1": pct(drain_gbs, 1),
+                                      "min": min(drain_gbs) if drain_gbs else None, "n": len(drain_gbs)},
+                              "full": {"p50": pct(full_drain_gbs, 50), "p1": pct(full_drain_gbs, 1),
+                                       "min": min(full_drain_gbs) if full_drain_gbs else None,
+                                       "n": len(full_drain_gbs)}},
                 # the five longest services: what the tail is made of
                 "slowest": [{"service_ms": s, "kind": "checkpoint" if k == C.CRAC_REQ_CHECKPOINT else "restart",
                              "context_bytes": nb, "payload_bytes": pb, "queue_wait_ms": w, "arrival_s": a,
-                             "prepare_ms": m3[0], "call_ms": m3[1], "settle_ms": m3[2]}
-                            for s, k, nb, pb, w, a, m3 in sorted(slow, key=lambda x: x[0], reverse=True)[:5]],
+                             "prepare_ms": m3[0], "call_ms": m3[1], "settle_ms": m3[2], "drain_ms": dm}
+                            for s, k, nb, pb, w, a, m3, dm in sorted(slow, key=lambda x: x[0], reverse=True)[:5]],
                 "memory": C.crac_memory_stats(),
                 "offered_gbs": sum(self.procs[int(t)]["bytes"] for t in targets) / (float(arrivals[-1]) or 1) / 1e9,
                 "achieved_tracked_gbs": scanned / wall / 1e9, "achieved_payload_gbs": payload / wall / 1e9,
@@ -1307,7 +1347,7 @@ def main():
     ap.add_argument("--workers", type=int, default=8, help="c5: request server slots (requests in flight)")
     ap.add_argument("--no-serving", action="store_true", help="c2: skip the short serving leg")
     ap.add_argument("--serving-gib", type=int, default=8, help="c2: total context memory of the serving leg")
-    ap.add_argument("--serving-requests", type=int, default=200, help="c2: requests of the serving leg")
+    ap.add_argument("--serving-requests", type=int, default=600, help="c2: requests of the serving leg")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "passes", "codec"],
                     help="c2 (default): the headline line; c3/c4/c5/passes: their own JSON lines")
     ap.add_argument("--staged-restore", action="store_true",

@@ -225,6 +225,11 @@ typedef struct crac_image_info {
     uint32_t complete;       /* 1 once the drain has finished */
     uint64_t raw_bytes;      /* bytes of the chunks present before coding (payload_bytes,
                                 the stored bytes, for an uncoded image) */
+    float drain_ms;          /* host image, once complete: device time on the context's side
+                                stream from the start of its drain (the pass's end, or the
+                                first copy of a coded image's streams) to its completion;
+                                else 0 */
+    uint32_t reserved;
 } crac_image_info_t;
 #define CRAC_IMAGE_FULL 1u
 #define CRAC_IMAGE_CODED 2u  /* chunks are stored as CRZ1 streams (CRAC_FLAG_COMPRESS) */
@@ -348,7 +353,7 @@ CRAC_API crac_status_t crac_ctx_restart(crac_ctx_t *ctx, const crac_image_t *ima
  * (checkpoint or restart of a context) are queued in arrival order; a
  * request is admitted when a worker slot is free, no earlier request of the
  * same context is still running, and its staging lease fits in the staging
- * budget (first-fit in one device region; an earlier request that does not
+ * budget (best-fit in one device region; an earlier request that does not
  * fit blocks later ones, so none starves).  Admitted requests run at once on
  * their own streams, so the passes of different contexts overlap on the
  * device, and requests arriving meanwhile join as slots and staging free up.
@@ -590,6 +595,10 @@ typedef struct crac_memory_stats {
                                        starts once the pinned arena is 80% used, is not
                                        counted) */
     uint32_t device_grow_events;
+    uint32_t scratch_grow_events;   /* context scratch buffers (re)allocated from CUDA: fingerprint
+                                       tables, staging, chunk lists, restart tables; a growth
+                                       that replaces a buffer synchronizes the device first */
+    uint32_t reserved;
 } crac_memory_stats_t;
 
 CRAC_API crac_status_t crac_memory_stats(crac_memory_stats_t *out);

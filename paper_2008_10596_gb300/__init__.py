@@ -95,6 +95,7 @@ class CracImageInfo(ctypes.Structure):
         ("n_chunks", ctypes.c_uint64), ("k", ctypes.c_uint64), ("payload_bytes", ctypes.c_uint64),
         ("serialized_bytes", ctypes.c_uint64), ("residency", ctypes.c_uint32),
         ("complete", ctypes.c_uint32), ("raw_bytes", ctypes.c_uint64),
+        ("drain_ms", ctypes.c_float), ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -170,7 +171,8 @@ class CracMemoryStats(ctypes.Structure):
     _fields_ = [("host_region_bytes", ctypes.c_uint64), ("host_used_bytes", ctypes.c_uint64),
                 ("device_region_bytes", ctypes.c_uint64), ("device_used_bytes", ctypes.c_uint64),
                 ("host_regions", ctypes.c_uint32), ("device_regions", ctypes.c_uint32),
-                ("host_grow_events", ctypes.c_uint32), ("device_grow_events", ctypes.c_uint32)]
+                ("host_grow_events", ctypes.c_uint32), ("device_grow_events", ctypes.c_uint32),
+                ("scratch_grow_events", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 CRAC_REQ_CHECKPOINT = 0

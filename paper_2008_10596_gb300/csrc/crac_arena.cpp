@@ -1,6 +1,8 @@
 // Device and pinned-host arenas for image payloads, and grow-only buffers.
 #include "crac_runtime.h"
 
+#include <atomic>
+
 using namespace crac;
 
 namespace {
@@ -26,11 +28,14 @@ Arena &pinned_arena() {
     return *g_pinned_arena;
 }
 
+std::atomic<uint32_t> g_scratch_grows{0};
+
 crac_status_t ensure_dev(DevBuf &b, size_t bytes) {
     bytes = std::max<size_t>(bytes, 256);
     if (b.cap >= bytes) return CRAC_OK;
     if (b.borrowed) return CRAC_ERR_OOM;   // a lease cannot grow (and is not ours to free)
     if (fault_hit(CRAC_FAULT_ALLOC)) return CRAC_ERR_OOM;
+    g_scratch_grows++;
     if (b.p) {
         CK(cudaDeviceSynchronize());
         CK(cudaFree(b.p));
@@ -57,6 +62,7 @@ crac_status_t ensure_dev(DevBuf &b, size_t bytes) {
 crac_status_t ensure_host(HostBuf &b, size_t bytes) {
     bytes = std::max<size_t>(bytes, 256);
     if (b.cap >= bytes) return CRAC_OK;
+    g_scratch_grows++;
     if (b.p) {
         CK(cudaFreeHost(b.p));
         b = HostBuf{};
@@ -85,6 +91,7 @@ crac_status_t crac_memory_stats(crac_memory_stats_t *out) {
         out->device_regions += r;
         out->device_grow_events += gcount;
     }
+    out->scratch_grow_events = g_scratch_grows.load();
     return CRAC_OK;
 }
 

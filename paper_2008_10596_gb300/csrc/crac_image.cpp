@@ -68,6 +68,7 @@ void img_unref(crac_image *im) {
             DeviceGuard g(im->device);
             cudaEventSynchronize(im->done);
             cudaEventDestroy(im->done);
+            if (im->drain0) cudaEventDestroy(im->drain0);
             cudaGetLastError();
         }
         table_remove(im);
@@ -260,6 +261,12 @@ crac_status_t crac_image_info(const crac_image_t *image, crac_image_info_t *out)
     out->residency = im->residency;
     out->complete = im->state.load() == 1 ? 1u : 0u;
     out->raw_bytes = im->raw_bytes;
+    if (out->complete && im->drain0 && im->done) {
+        DeviceGuard g(im->device);
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, im->drain0, im->done) == cudaSuccess) out->drain_ms = ms;
+        cudaGetLastError();
+    }
     return CRAC_OK;
 }
 

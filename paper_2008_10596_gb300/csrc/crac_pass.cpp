@@ -567,7 +567,7 @@ size_t crz_work_bytes(uint64_t k, uint64_t D, uint32_t log2S) {
 // host images each launch's streams are copied to the pinned block as soon
 // as it ends (its bytes are known already), overlapping the later launches.
 crac_status_t encode_segment_sized(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
-                                   cudaStream_t s, uint64_t *Z, bool *zplaced) {
+                                   cudaStream_t s, uint64_t *Z, bool *zplaced, cudaEvent_t *drain0) {
     const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
     *zplaced = false;
     TRY(ensure_dev(c->zwork, crz_work_bytes(k, D, c->log2S)));
@@ -641,6 +641,8 @@ crac_status_t encode_segment_sized(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl,
             CK(cudaEventRecord(c->ev_piece[i], s));
             if (poff[i + 1] > poff[i]) {
                 CK(cudaStreamWaitEvent(c->side, c->ev_piece[i], 0));
+                if (drain0 && *drain0) CK(cudaEventRecord(*drain0, c->side));   // the image's drain starts here
+                if (drain0) *drain0 = nullptr;
                 CK(cudaMemcpyAsync(pc.host.p + poff[i], c->cstage.p + poff[i], poff[i + 1] - poff[i],
                                    cudaMemcpyDeviceToHost, c->side));
             }
@@ -662,8 +664,8 @@ crac_status_t encode_segment_sized(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl,
 }
 
 crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool host_res, bool direct_flag,
-                             cudaStream_t s, uint64_t *Z, bool *zplaced) {
-    if (c->crz_hdr_now) return encode_segment_sized(c, pc, ctrl, host_res, direct_flag, s, Z, zplaced);
+                             cudaStream_t s, uint64_t *Z, bool *zplaced, cudaEvent_t *drain0) {
+    if (c->crz_hdr_now) return encode_segment_sized(c, pc, ctrl, host_res, direct_flag, s, Z, zplaced, drain0);
     const uint64_t k = ctrl.k, D = ctrl.D, zmax = D + 16 * k;
     const uint32_t T = crz_tile_entries(c->log2S);
     const uint64_t n_tiles = (k + T - 1) / T;
@@ -782,13 +784,18 @@ crac_status_t encode_segment(crac_ctx *c, Piece &pc, const CkptCtrl &ctrl, bool 
 // CRAC_PASS_AUTO: the split pass, unless the last pass with a baseline found
 // more than half of the chunks dirty; then a pass that reads every byte once
 // (at 100% dirty 4 KiB pages and 64 KiB chunks: sparse 0.94, TMA 0.72, LDG
-// 0.69, split 0.66 of the HBM peak), the best one the images and sizes allow.
+// 0.69, split 0.66 of the HBM peak), the best one the images and sizes allow,
+// except for coded images on chunks of 8 KiB and more.
 uint32_t resolve_pass_kernel(const crac_ctx *c, bool dev_res, bool all16) {
     const bool coded = (c->cfg.flags & CRAC_FLAG_COMPRESS) != 0;
     // the encoder reads a compact payload, which the sparse pass does not leave
     if (c->cfg.pass_kernel == CRAC_PASS_SPARSE && coded) return CRAC_PASS_SPLIT;
     if (c->cfg.pass_kernel != CRAC_PASS_AUTO) return c->cfg.pass_kernel;
     if (!c->delta_frac_valid || c->delta_frac <= 0.5f) return CRAC_PASS_SPLIT;
+    // coded images on chunks of 8 KiB and more: the split pass makes the block
+    // headers of the two-launch encoder (4 GiB fp32, every chunk dirty: split
+    // 2.0 + 2.1 ms, TMA 1.7 + 3.8 ms for the one-launch encoder)
+    if (coded && c->log2S >= 13 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED) return CRAC_PASS_SPLIT;
     if (dev_res && all16 && !coded) return CRAC_PASS_SPARSE;
     if (c->log2S >= 10 && c->log2S <= 16) return CRAC_PASS_TMA;
     return CRAC_PASS_LDG;
@@ -909,6 +916,7 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
     crac_status_t st = CRAC_OK;
     uint64_t k_base = 0, d_base = 0, raw_base = 0;
     float ms = 0;
+    bool drain_started = false;   // drain0 recorded (host images)
     for (const Segment &sg : segs) {
         const uint64_t nseg = sg.c1 - sg.c0;
         Piece pc;
@@ -958,7 +966,9 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
         bool zplaced = false;
         if (coded && ctrl.k) {
             uint64_t Z = 0;
-            st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zplaced);
+            cudaEvent_t d0 = drain_started || !host_res ? nullptr : im->drain0;
+            st = encode_segment(c, pc, ctrl, host_res, direct_flag, s, &Z, &zplaced, &d0);
+            if (host_res && !d0) drain_started = true;   // recorded as the first copy was issued
             if (st != CRAC_OK) {
                 im->pieces.push_back(pc);
                 return st;
@@ -972,6 +982,8 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
             return CRAC_ERR_CUDA;
         }
         cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_pass, 0);
+        if (e == cudaSuccess && host_res && !drain_started) e = cudaEventRecord(im->drain0, c->side);
+        drain_started = true;
         if (direct_seg) {
             if (ctrl.D) pa.shrink(pc.host, ctrl.D);
             else pa.free(pc.host);
@@ -1072,6 +1084,7 @@ crac_status_t checkpoint_enqueue(crac_ctx *c, crac_image *im, const Segment &sg,
     }
     if (host_res) {
         CK(cudaStreamWaitEvent(c->side, c->ev_pass, 0));
+        CK(cudaEventRecord(im->drain0, c->side));
         if (!any_base) {   // FULL: every chunk, n entries, the segment's bytes
             if (!direct) CK(cudaMemcpyAsync(pc.host.p, c->staging.p, sg.bytes, cudaMemcpyDeviceToHost, c->side));
             CK(cudaMemcpyAsync(im->idx_h.p, idx_d, n * 8, cudaMemcpyDeviceToHost, c->side));
@@ -1186,7 +1199,9 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
     im->allocs.resize(na);
     for (size_t a = 0; a < na; ++a)
         im->allocs[a] = ImgAlloc{c->allocs[a].id, c->allocs[a].ptr, c->allocs[a].bytes, c->allocs[a].kind, first[a]};
-    if (cudaEventCreateWithFlags(&im->done, cudaEventDisableTiming) != cudaSuccess) {
+    // done and drain0 time the drain of a host image (crac_image_info_t.drain_ms)
+    if (cudaEventCreate(&im->done) != cudaSuccess ||
+        (host_res && cudaEventCreate(&im->drain0) != cudaSuccess)) {
         pa.free(dpc.host);
         return cuda_status(cudaGetLastError());
     }

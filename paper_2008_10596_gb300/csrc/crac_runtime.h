@@ -91,17 +91,20 @@ struct DeviceGuard {
 class RangeAlloc {
   public:
     explicit RangeAlloc(uint64_t size) { free_[0] = size; }
+    // Best fit (the smallest free range that holds len, the lowest such on a
+    // tie): small tables fill small holes and leave the large ones for
+    // payloads, which matters in a loop that mixes 64-byte control blocks,
+    // per-image tables and multi-GiB images.
     bool alloc(uint64_t len, uint64_t *off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= len) {
-                const uint64_t o = it->first, rest = it->second - len;
-                free_.erase(it);
-                if (rest) free_[o + len] = rest;
-                *off = o;
-                return true;
-            }
-        }
-        return false;
+        auto best = free_.end();
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= len && (best == free_.end() || it->second < best->second)) best = it;
+        if (best == free_.end()) return false;
+        const uint64_t o = best->first, rest = best->second - len;
+        free_.erase(best);
+        if (rest) free_[o + len] = rest;
+        *off = o;
+        return true;
     }
     void release(uint64_t off, uint64_t len) {
         if (!len) return;
@@ -132,7 +135,7 @@ struct Block {
 };
 
 // Device or pinned-host memory arena: regions from cudaMalloc/cudaHostAlloc,
-// carved first-fit.  Image payloads and tables live here so that a steady
+// carved best-fit.  Image payloads and tables live here so that a steady
 // checkpoint loop allocates nothing from CUDA after warm-up.
 class Arena {
   public:
@@ -346,6 +349,7 @@ struct crac_image {
     std::vector<Piece> pieces;
     crac_image *parent = nullptr;   // strong reference, set for delta images
     cudaEvent_t done = nullptr;     // drain complete
+    cudaEvent_t drain0 = nullptr;   // host images: recorded on the side stream as the drain starts
     std::atomic<int> state{0};      // 0 pending, 1 complete, < 0 failed (status)
     std::mutex mu;
     // A checkpoint that returned before its pass finished (single segment):

@@ -134,6 +134,10 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
         if (v == CRAC_PASS_SPARSE && t->cfg.image_residency != CRAC_RESIDENCY_DEVICE) continue;
         if (v == CRAC_PASS_SPARSE && (t->cfg.flags & CRAC_FLAG_COMPRESS)) continue;   // needs a compact payload
+        // Coded images on chunks of 8 KiB and more: only the split pass makes
+        // the block headers that the two-launch encoder needs; a read-once
+        // pass saves less in the pass than the one-launch encoder costs.
+        if (v != CRAC_PASS_SPLIT && (t->cfg.flags & CRAC_FLAG_COMPRESS) && S >= 8192) continue;
         t->cfg.pass_kernel = v;
         float bestm = 0;
         const bool ldg_tiles = v == CRAC_PASS_LDG && saved_cpt == 0;
