@@ -26,7 +26,7 @@ namespace crac {
 namespace {
 
 constexpr uint32_t kCrzBlock = 512;
-constexpr int kCrzDecodeGroup = 3;                           // blocks decoded per step
+constexpr int kCrzDecodeGroup = 2;                           // blocks decoded per step
 constexpr int kCrzDecodeScratch = 512 * kCrzDecodeGroup;     // shared bytes per decoding warp
 
 __device__ __forceinline__ uint32_t crz_rot(uint32_t w) {

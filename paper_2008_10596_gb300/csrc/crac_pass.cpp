@@ -1240,8 +1240,8 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         // settled state's) and both descriptor buffers (growing one in use
         // waits for its copy).
         for (int t = 0; t < 3 && st == CRAC_OK; ++t)
-            if (t == out_fp || (t != c->fp_cur && (c->pending.empty() || t != c->settled.fp)))
-                st = ensure_dev(c->fp[t], n * 8);
+            if (t == out_fp || !c->fp[t].p || (t != c->fp_cur && (c->pending.empty() || t != c->settled.fp)))
+                st = ensure_dev(c->fp[t], n * 8);   // (a table never allocated holds nothing either)
         if (st == CRAC_OK) st = ensure_dev(c->desc, na * (sizeof(CkptDesc) + 8));
         if (st == CRAC_OK) st = ensure_host(c->desc_h, na * (sizeof(CkptDesc) + 8));
         if (st == CRAC_OK) st = ensure_host(c->desc_h2, na * (sizeof(CkptDesc) + 8));

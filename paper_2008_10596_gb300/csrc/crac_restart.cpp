@@ -164,11 +164,11 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     // Reads of host images are paced by the host link, which one CTA per SM
     // already saturates (4 KiB in flight per warp); a bigger grid would only
     // keep SMs from other streams' work for the length of the transfer.
-    // Decoding coded images is compute-heavy: three CTAs per SM (the coded
+    // Decoding coded images is compute-heavy: four CTAs per SM (the coded
     // scatter's occupancy) keep the link busy while they decode.
     bool any_host = false;
     for (const crac_image *im : chain) any_host = any_host || im->residency != CRAC_RESIDENCY_DEVICE;
-    const uint64_t grid = (uint64_t)c->sm_count * (any_host ? (P.coded ? 3 : 1) : 8);
+    const uint64_t grid = (uint64_t)c->sm_count * (any_host ? (P.coded ? 4 : 1) : 8);
     // Incremental: fingerprint the current contents against the target's
     // table first; chunks that match are then left alone.
     const bool incremental = (c->cfg.flags & CRAC_FLAG_INCREMENTAL_RESTORE) && nt > 0;

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kScatterNT) restore_scatter_kernel(const Resto
     restore_scatter_body<false>(P, nullptr);
 }
 
-__global__ void __launch_bounds__(kScatterNT, 3) restore_scatter_coded_kernel(const RestoreParams P) {
+__global__ void __launch_bounds__(kScatterNT, 4) restore_scatter_coded_kernel(const RestoreParams P) {
     __shared__ __align__(16) uint8_t scratch[kCrzDecodeScratch * (kScatterNT / 32)];
     restore_scatter_body<true>(P, scratch);
 }

@@ -201,3 +201,36 @@ def test_wait_pass_flag_makes_the_call_wait():
         _same(C.crac_image_serialize(img), h.oracle.checkpoint(want), "image")
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("residency", RESIDENCY)
+def test_restart_then_mutator_then_checkpoint_on_one_stream(residency):
+    """A restart returns once its restore has run (it checks the restore's
+    error word before adopting the image); the application's next work and
+    the next checkpoint are then enqueued behind a busy stream with no host
+    synchronization, and that checkpoint equals the oracle's delta against
+    the restored image."""
+    h = _setup(image_residency=residency)
+    try:
+        _, lib0, ora0 = h.checkpoint()
+        assert lib0 == ora0
+        m1 = pattern_mutations(h.first(), SIZES, S, "random10", seed=13)
+        m2 = pattern_mutations(h.first(), SIZES, S, "alternating", seed=14)
+        e1, e2 = _rows(h, m1), _rows(h, m2)
+        testkit.mutate_xor(e1.data_ptr(), len(m1), h.stream)
+        torch.cuda.synchronize()
+        img1, lib1, ora1 = h.checkpoint()
+        assert lib1 == ora1
+        s1 = h.host()
+        testkit.mutate_xor(e2.data_ptr(), len(m2), h.stream)   # lost by the restart below
+        C.crac_ctx_restart(h.ctx, img1, h.stream)
+        testkit.delay(100_000_000, h.stream)
+        testkit.mutate_xor(e2.data_ptr(), len(m2), h.stream)
+        img = C.crac_ctx_checkpoint(h.ctx, h.stream)
+        h.images.append(img)
+        want = _host_after(s1, h, m2)
+        _same(C.crac_image_serialize(img), h.oracle.checkpoint(want), "image after the restart")
+        im = O.parse_image(C.crac_image_serialize(img))
+        assert not im.full and im.parent_epoch == O.parse_image(lib1).epoch
+    finally:
+        h.close()
