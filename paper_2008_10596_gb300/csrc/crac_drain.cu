@@ -33,6 +33,28 @@ __global__ void __launch_bounds__(kDrainNT) drain_kernel(const CkptCtrl *ctrl, c
     for (uint64_t j = tid; j < k; j += nt) idx_dst[j] = idx_src[j];
 }
 
+// A copy of `bytes` between device memory and pinned host memory (either
+// direction) by SM loads and stores through the pinned memory's device
+// mapping.  On GB300 the copy engines' device-to-host rate into pinned memory
+// was seen to fall to 12-30 GB/s for seconds at a time while SM stores over
+// the same link held 185-193 GB/s, and every other copy-engine transfer
+// (descriptor uploads, fingerprint tables) then queued behind the slow one;
+// the library's per-operation transfers therefore go through this kernel.
+// Both pointers 16-byte aligned take the vector path; otherwise bytes.
+__global__ void __launch_bounds__(kDrainNT) link_copy_kernel(uint8_t *dst, const uint8_t *src, uint64_t bytes) {
+    const uint64_t tid = (uint64_t)blockIdx.x * kDrainNT + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * kDrainNT;
+    uint64_t done = 0;
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
+        const uint64_t nv = bytes >> 4;
+        const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d16 = reinterpret_cast<uint4 *>(dst);
+        for (uint64_t v = tid; v < nv; v += nt) __stcs(d16 + v, __ldcs(s16 + v));
+        done = nv << 4;
+    }
+    for (uint64_t i = done + tid; i < bytes; i += nt) dst[i] = src[i];
+}
+
 // A small report (a pass's control block, an encoder launch's end offset and
 // error bits, a restart's error word) for the host: n 8-byte words from
 // device memory, then one 4-byte word zero-extended, stored by one warp into
@@ -60,8 +82,22 @@ cudaError_t launch_report(const void *words, uint32_t n, const uint32_t *word32,
 // the host): a checkpoint that returns once enqueued must not be the first.
 cudaError_t prepare_drain() {
     cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, drain_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&a, drain_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, link_copy_kernel);
     return e != cudaSuccess ? e : cudaFuncGetAttributes(&a, report_kernel);
+}
+
+cudaError_t launch_link_copy(void *dst, const void *src, uint64_t bytes, int max_grid, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    // one CTA per 64 KiB, up to max_grid: a descriptor table takes one CTA,
+    // a bulk drain two per SM (one per SM already paces the link)
+    const uint64_t want = (bytes + (64u << 10) - 1) >> 16;
+    const int grid = (int)(want < (uint64_t)max_grid ? want : (uint64_t)max_grid);
+    link_copy_kernel<<<grid > 0 ? grid : 1, kDrainNT, 0, s>>>(reinterpret_cast<uint8_t *>(dst),
+                                                             reinterpret_cast<const uint8_t *>(src), bytes);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
 }
 
 cudaError_t launch_drain(const CkptCtrl *ctrl, const uint8_t *src, uint8_t *dst, uint64_t cap,

@@ -1005,9 +1005,9 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
             if (coded) da.shrink(pc.zlen_dev, ctrl.k * 8);
         }
         if (e == cudaSuccess && ctrl.k && host_res)
-            e = cudaMemcpyAsync(im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+            e = link_copy(c, im->idx_h.p + k_base * 8, idx_d, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
         if (e == cudaSuccess && ctrl.k && host_res && coded)
-            e = cudaMemcpyAsync(im->zlen_h.p + k_base * 8, c->zlen.p, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
+            e = link_copy(c, im->zlen_h.p + k_base * 8, c->zlen.p, ctrl.k * 8, cudaMemcpyDeviceToHost, c->side);
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
         im->pieces.push_back(pc);
         if (e != cudaSuccess) return cuda_status(e);
@@ -1016,7 +1016,7 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
     }
     cudaError_t e;
     if (host_res) {
-        e = cudaMemcpyAsync(im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side);
+        e = link_copy(c, im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side);
         if (e == cudaSuccess) e = cudaEventRecord(im->done, c->side);
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_last, c->side);
     } else {
@@ -1049,9 +1049,9 @@ crac_status_t checkpoint_wait(crac_ctx *c, crac_image *im, const std::vector<Seg
 // (A2-A5).  Its control block lands in the image's pinned ctrl_b; a device
 // image's payload, chunk list and offsets go to worst-case blocks of the
 // device arena, a host image's payload to the pinned block in pieces[0] (the
-// pass writes it there directly, or the side stream copies it from staging:
-// by the copy engine for a FULL pass, whose size is known, else by
-// drain_kernel, which reads the size from the control block).  The blocks
+// pass writes it there directly, or drain_kernel on the side stream copies
+// it from staging, reading the sizes from the control block; SM stores, not
+// a copy engine, whose device-to-host rate was seen to collapse).  The blocks
 // are shrunk to the counts, and the counts become the image's, when the
 // image settles.
 crac_status_t checkpoint_enqueue(crac_ctx *c, crac_image *im, const Segment &sg, const std::vector<uint64_t> &first,
@@ -1085,14 +1085,12 @@ crac_status_t checkpoint_enqueue(crac_ctx *c, crac_image *im, const Segment &sg,
     if (host_res) {
         CK(cudaStreamWaitEvent(c->side, c->ev_pass, 0));
         CK(cudaEventRecord(im->drain0, c->side));
-        if (!any_base) {   // FULL: every chunk, n entries, the segment's bytes
-            if (!direct) CK(cudaMemcpyAsync(pc.host.p, c->staging.p, sg.bytes, cudaMemcpyDeviceToHost, c->side));
-            CK(cudaMemcpyAsync(im->idx_h.p, idx_d, n * 8, cudaMemcpyDeviceToHost, c->side));
-        } else {
-            CK(launch_drain((const CkptCtrl *)c->work.p, direct ? nullptr : (const uint8_t *)c->staging.p, pc.host.p,
-                            sg.bytes, idx_d, (uint64_t *)im->idx_h.p, n, c->sm_count * 2, c->side));
-        }
-        CK(cudaMemcpyAsync(im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side));
+        // FULL or delta alike: the sizes come from the control block, the
+        // bytes cross by SM stores into the pinned blocks (this path requires
+        // the device mapping of pinned memory)
+        CK(launch_drain((const CkptCtrl *)c->work.p, direct ? nullptr : (const uint8_t *)c->staging.p, pc.host.p,
+                        sg.bytes, idx_d, (uint64_t *)im->idx_h.p, n, c->sm_count * 2, c->side));
+        CK(link_copy(c, im->fp_h.p, c->fp[out_fp].p, n * 8, cudaMemcpyDeviceToHost, c->side));
         CK(cudaEventRecord(im->done, c->side));
         CK(cudaEventRecord(c->ev_last, c->side));
     } else {
@@ -1262,7 +1260,7 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
                        c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
-        if (cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (link_copy(c, c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(cuda_status(cudaGetLastError()));
         // Managed regions migrate to the device before they are read.
         bool any_managed = false;
@@ -1449,7 +1447,7 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && c->cfg.image_residency == CRAC_RESIDENCY_DEVICE &&
                    all16 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
-    CK(cudaMemcpyAsync(c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
+    CK(link_copy(c, c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
     uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);
     cap = std::max(round_up(cap, 256), S);
     const std::vector<Segment> segs = make_segments(c->allocs, first, log2S, cap);
@@ -1509,7 +1507,7 @@ crac_status_t fingerprint_against(crac_ctx *c, const uint64_t *fp_ref, cudaStrea
     CkptDesc *dh = (CkptDesc *)c->vdesc_h.p;
     for (size_t a = 0; a < na; ++a)   // the reference table has the same chunk layout
         dh[a] = CkptDesc{c->allocs[a].ptr, c->allocs[a].bytes, first[a], first[a]};
-    CK(cudaMemcpyAsync(c->vdesc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s));
+    CK(link_copy(c, c->vdesc.p, dh, na * sizeof(CkptDesc), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->vwork.p, 0, work_bytes, s));
     const bool small = log2S >= 9 && log2S < 13;
     uint32_t log2Seg = std::min<uint32_t>(log2S, 13);

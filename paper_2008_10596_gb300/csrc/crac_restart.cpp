@@ -145,7 +145,7 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(cudaMemsetAsync(c->serr.p, 0, 256, s));
     if (nt) CK(cudaMemsetAsync(c->owner.p, 0, nt * 4, s));
-    CK(cudaMemcpyAsync(c->sdesc.p, c->sdesc_h.p, desc_bytes + ppos * sizeof(RestorePiece), cudaMemcpyHostToDevice, s));
+    CK(link_copy(c, c->sdesc.p, c->sdesc_h.p, desc_bytes + ppos * sizeof(RestorePiece), cudaMemcpyHostToDevice, s));
     crac_restart_info_t ri{};
     ri.chain_length = ri.images_used = (uint32_t)chain.size();
     for (const ImgAlloc &a : img->allocs) ri.restored_bytes += a.bytes;
@@ -187,7 +187,7 @@ crac_status_t restart_device(crac_ctx *c, crac_image *img, const std::vector<cra
     if (incremental) CK(launch_report(vctrl, sizeof(CkptCtrl) / 8, nullptr, c->ctrl_h.p, s));
     if (nt) {
         const void *fp = img->residency == CRAC_RESIDENCY_DEVICE ? (const void *)img->fp_dev.p : (const void *)img->fp_h.p;
-        CK(cudaMemcpyAsync(c->fp[spare].p, fp, nt * 8, cudaMemcpyDefault, s));
+        CK(link_copy(c, c->fp[spare].p, fp, nt * 8, cudaMemcpyDefault, s));
     }
     CK(launch_report(nullptr, 0, (const uint32_t *)c->serr.p, c->serr_h.p, s));
     CK(cudaEventRecord(c->ev_last, s));

@@ -520,4 +520,19 @@ crac_status_t default_ctx(crac_ctx **out);
 // Steady clock in seconds (crac_time_now).
 double now_s();
 
+// bytes from src to dst, one of them pinned host memory addressed through its
+// device mapping (or both device memory), by SM loads and stores on s with at
+// most max_grid CTAs, instead of a copy engine (crac_drain.cu).
+cudaError_t launch_link_copy(void *dst, const void *src, uint64_t bytes, int max_grid, cudaStream_t s);
+
+// A per-operation transfer between device memory and pinned host memory on
+// s: by an SM copy kernel where the device addresses pinned memory directly
+// (the copy engines' device-to-host rate was seen to collapse for seconds on
+// GB300, and transfers queued behind it), else by the copy engine.
+inline cudaError_t link_copy(const crac_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                             cudaStream_t s) {
+    if (c->uva) return launch_link_copy(dst, src, bytes, c->sm_count * 2, s);
+    return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
+
 }  // namespace crac
