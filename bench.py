@@ -174,6 +174,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "sm_mhz_min": min(sm) if sm else None,
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
@@ -602,7 +603,10 @@ def run_crac(args):
         total5 = args.serving_gib * W.GIB
         sr = ServingRun(dev, total=total5)
         sr.base_images()
+        sampler5 = ClockSampler(None)   # the loop is mostly idle: the clocks it runs at
+        sampler5.start()
         serving = sr.run(args.serving_requests, args.rate)
+        serving["clocks"] = sampler5.stop()
         sr.close()
         serving["workload"] = (f"c5 shape: 64 contexts, {args.serving_gib} GiB total (log-uniform 0.5-8 GiB scaled "
                                f"by {total5 / (173 * W.GIB):.3f}), {args.serving_requests} requests Poisson "
@@ -1321,7 +1325,10 @@ def run_config5(args):
     total = (args.total_mib << 20) if args.total_mib != 4096 else 32 * W.GIB
     sr = ServingRun(dev, total=total, flags=restore_flags(args))
     sr.base_images()
+    sampler5 = ClockSampler(None)
+    sampler5.start()
     out = sr.run(args.requests, args.rate, workers=args.workers)
+    out["clocks"] = sampler5.stop()
     sr.close()
     line = {"workload": f"c5: 64 contexts, {total / 2**30:.0f} GiB total (log-uniform 0.5-8 GiB scaled by "
                         f"{total / (173 * W.GIB):.3f}), {args.requests} requests Poisson {args.rate}/s, "

@@ -64,10 +64,12 @@ struct CkptParams {
     uint32_t full_copy;
     const uint64_t *alloc_prefix;   // payload bytes of all allocations before each one
     uint64_t seg_base;              // payload offset of the segment's first chunk
-    // Sparse split pass (with full_copy, on delta checkpoints too): every
-    // chunk is written at its uncompacted offset, each dirty entry's offset
-    // points there, ctrl->D counts the segment's bytes and ctrl->payload the
-    // dirty ones; nothing is gathered.
+    // Sparse split pass (with full_copy, on delta checkpoints too): chunks
+    // are written at their uncompacted offsets (on a delta with chunks of
+    // 512 B - 4 KiB only the dirty ones, which the hash kernel holds in
+    // registers until their fingerprint is known; larger chunks all), each
+    // dirty entry's offset points there, ctrl->D counts the segment's bytes
+    // and ctrl->payload the dirty ones; nothing is gathered.
     uint32_t sparse;
     // TMA pass: the allocations' first_chunk column fits in the CTA's shared
     // memory (n_allocs <= ckpt_tma_cached_allocs()) and is searched there.

@@ -221,23 +221,29 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
                                                 uint64_t a_next, int li, uint32_t &writes) {
     const uint32_t log2S = P.log2_chunk;
     uint64_t sum = 0, fo = 0;
-    uint32_t len = 0;
+    uint32_t len = 0, nv = 0;
     bool has = false;
     CkptDesc d = d_warp;
     uint32_t a = a_warp;
+    uint64_t local = 0;
+    uint4 q[16];
+    // Sparse delta pass: the group holds its whole chunk in q until the
+    // fingerprint is known and stores it only if it is dirty (B + D of HBM
+    // traffic instead of B + B); clean chunks' bytes are never referenced.
+    bool hold = false;
     if (c < P.c_end) {
         if (c >= a_next) {   // the segment crosses an allocation end
             a = find_alloc(P.desc, P.n_allocs, c);
             d = P.desc[a];
         }
-        const uint64_t local = c - d.first_chunk;
+        local = c - d.first_chunk;
         const uint64_t rest = d.bytes - (local << log2S);
         len = (uint32_t)umin64(rest, 1ull << log2S);
         has = d.base_first != kNoBase;
+        hold = P.sparse && has;
         if (li == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
         const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S));
-        const uint32_t nv = len >> 4;
-        uint4 q[16];
+        nv = len >> 4;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const uint32_t v = li + LPC * u;
@@ -254,7 +260,7 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
             }
             key += kStep;
         }
-        if (P.full_copy) {   // FULL checkpoint: the chunk goes straight to its staging offset
+        if (P.full_copy && !hold) {   // FULL checkpoint: the chunk goes straight to its staging offset
             const uint64_t o = P.alloc_prefix[a] + (local << log2S) - P.seg_base;
             if (o + len <= P.staging_cap) {
                 uint4 *dst = reinterpret_cast<uint4 *>(P.staging + o);
@@ -297,12 +303,29 @@ __device__ __forceinline__ void hash_small_iter(const CkptParams &P, unsigned lo
             if (rem > 8) sum += mixw(w1, kt + kK1);
         }
     }
+    // butterfly: every lane of the group ends with the group's sum
 #pragma unroll
     for (int o = LPC / 2; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    const uint64_t fp = fp_finalize(sum, len);
+    // the group leader's baseline fingerprint, for every lane of the group
+    fo = __shfl_sync(kFull, fo, (int)(threadIdx.x & 31u) - li);
+    const bool dirty = !has || fo != fp;
     if (li == 0 && c < P.c_end) {
-        const uint64_t fp = fp_finalize(sum, len);
         P.fp_new[c] = fp;
-        acc[c - P.c_begin] = len | ((!has || fo != fp) ? kAccDirty : 0ull);
+        acc[c - P.c_begin] = len | (dirty ? kAccDirty : 0ull);
+    }
+    if (hold && dirty) {   // sparse delta pass: sizes are multiples of 16 (no tail bytes)
+        const uint64_t o = P.alloc_prefix[a] + (local << log2S) - P.seg_base;
+        if (o + len <= P.staging_cap) {
+            uint4 *dst = reinterpret_cast<uint4 *>(P.staging + o);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint32_t v = li + LPC * u;
+                if (v < nv) __stcs(dst + v, q[u]);
+            }
+        } else if (li == 0) {
+            atomicOr(&P.ctrl->err, kErrBounds);
+        }
     }
 }
 

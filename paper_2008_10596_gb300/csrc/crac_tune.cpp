@@ -120,20 +120,29 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
         vt->tiles[1] = lo != t0 ? lo : 0;
         vt->tiles[2] = hi != t0 ? hi : 0;
     }
+    uint64_t k_seen = 0;   // dirty chunks of the timed passes (all see the same dirty set)
     auto time_pass = [&](float *best_ms) {
         for (int r = 0; r < 2; ++r) {
             float ms = 0;
             uint64_t k = 0, d = 0;
             TRY(ctx_trial_pass(t, s, false, &ms, &k, &d));
+            k_seen = k;
             if (r == 0 || ms < *best_ms) *best_ms = ms;
         }
         return CRAC_OK;
     };
+    uint64_t n_chunks = 0;
+    for (const AllocRec &r : t->allocs) n_chunks += (r.bytes + S - 1) / S;
     for (uint32_t v : {(uint32_t)CRAC_PASS_SPLIT, (uint32_t)CRAC_PASS_LDG, (uint32_t)CRAC_PASS_TMA,
                        (uint32_t)CRAC_PASS_SPARSE}) {
         if (v == CRAC_PASS_TMA && (S < 1024 || S > 65536)) continue;
         if (v == CRAC_PASS_SPARSE && t->cfg.image_residency != CRAC_RESIDENCY_DEVICE) continue;
         if (v == CRAC_PASS_SPARSE && (t->cfg.flags & CRAC_FLAG_COMPRESS)) continue;   // needs a compact payload
+        // A sparse image holds every tracked byte's room whatever the dirty
+        // bytes, so it is timed only where at least half of the chunks are
+        // dirty (at most twice the room of a compact image; the split pass,
+        // timed first, gives the count).
+        if (v == CRAC_PASS_SPARSE && 2 * k_seen < n_chunks) continue;
         // Coded images on chunks of 8 KiB and more: only the split pass makes
         // the block headers that the two-launch encoder needs; a read-once
         // pass saves less in the pass than the one-launch encoder costs.
