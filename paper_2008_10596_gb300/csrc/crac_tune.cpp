@@ -139,10 +139,10 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
         if (v == CRAC_PASS_SPARSE && t->cfg.image_residency != CRAC_RESIDENCY_DEVICE) continue;
         if (v == CRAC_PASS_SPARSE && (t->cfg.flags & CRAC_FLAG_COMPRESS)) continue;   // needs a compact payload
         // A sparse image holds every tracked byte's room whatever the dirty
-        // bytes, so it is timed only where at least half of the chunks are
-        // dirty (at most twice the room of a compact image; the split pass,
-        // timed first, gives the count).
-        if (v == CRAC_PASS_SPARSE && 2 * k_seen < n_chunks) continue;
+        // bytes, so it is timed only where at least 40% of the chunks are
+        // dirty (at most 2.5 times the room of a compact image; the split
+        // pass, timed first, gives the count).
+        if (v == CRAC_PASS_SPARSE && 5 * k_seen < 2 * n_chunks) continue;
         // Coded images on chunks of 8 KiB and more: only the split pass makes
         // the block headers that the two-launch encoder needs; a read-once
         // pass saves less in the pass than the one-launch encoder costs.
