@@ -746,7 +746,16 @@ def run_config4(args):
             alg = B + d + 16 * nch + 16 * kk
             per.append({"chunk_bytes": S, "pass_ms": ms, "dirty_bytes": d, "tracked_gbs": B / (ms / 1e3) / 1e9,
                         "hbm_frac": alg / (ms / 1e3) / 1e9 / peak})
-        points.append({"dirty_fraction_4k_pages": frac, "per_chunk_size": per,
+        # the chosen size and kernel: its timed pass against B + D + 16n + 16k at that size
+        Sc = res["chosen_chunk_bytes"]
+        pc = next((q for q in per if q["chunk_bytes"] == Sc), None)
+        ms_c = res["variant_ms"][res["chosen_pass_kernel"]] if res["chosen_pass_kernel"] < len(res["variant_ms"]) else 0
+        chosen = None
+        if pc is not None and ms_c > 0:
+            nch = sum(-(-n // Sc) for n in sizes)
+            alg = B + pc["dirty_bytes"] + 16 * nch + 16 * (pc["dirty_bytes"] // Sc)
+            chosen = {"pass_ms": ms_c, "tracked_gbs": B / (ms_c / 1e3) / 1e9, "hbm_frac": alg / (ms_c / 1e3) / 1e9 / peak}
+        points.append({"dirty_fraction_4k_pages": frac, "per_chunk_size": per, "chosen": chosen,
                        "chosen_chunk_bytes": res["chosen_chunk_bytes"],
                        "chosen_pass_kernel": res["chosen_pass_kernel"], "cost_ms": res["cost_ms"],
                        "variant_ms_at_chosen": res["variant_ms"],
@@ -755,8 +764,9 @@ def run_config4(args):
         C.crac_ctx_destroy(ctx)
     line = {"workload": f"c4: {len(sizes)} allocations, Zipf(1.1) sizes = {B / 2**30:.1f} GiB, uint8/fp32/int64",
             "tracked_bytes": B, "link_gbs_assumed": 190.0, "peak_gbs": peak, "points": points,
-            "note": "pass = split graph (hash, finalize+compact, gather into 8 GiB staging segments), device time; "
-                    "dirty bytes measured by the pass against the previous observation"}
+            "note": "per_chunk_size: the split graph (hash, finalize+compact, gather into 8 GiB staging segments) "
+                    "at each candidate size, device time, dirty bytes measured by the pass against the previous "
+                    "observation; chosen: the tuner's size and kernel, its timed pass at that size"}
     if not args.no_cpu:
         line["cpu_baseline"] = c4_oracle_subset(bufs, sizes, B)
     print(json.dumps(line), flush=True)

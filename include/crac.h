@@ -199,9 +199,10 @@ typedef struct crac_config {
 #define CRAC_PASS_SPLIT 3  /* three kernels in one graph: streaming hash, finalize +
                               compaction, gather */
 #define CRAC_PASS_SPARSE 4 /* the split pass without compaction: the hash kernel writes
-                              every chunk to its uncompacted offset in the image's
-                              payload buffer and the dirty list points into it, so no
-                              byte is read twice (B read + B written, against B + 2D).
+                              every chunk (on 512 B - 4 KiB chunks only the dirty
+                              ones) to its uncompacted offset in the image's payload
+                              buffer and the dirty list points into it, so no byte is
+                              read twice (B read + B, or D, written, against B + 2D).
                               Pays off when most chunks are dirty.  Device-resident
                               images only; an image then holds the tracked bytes of
                               its segments instead of the dirty ones (serialization

@@ -66,6 +66,29 @@ __global__ void report_kernel(const uint64_t *words, uint32_t n, const uint32_t 
     if (word32 && threadIdx.x == 0) dst[n] = *word32;
 }
 
+
+// Entries [0, n) of a sparse device piece packed back to back: entry j's
+// cum[j+1] - cum[j] bytes from span + off[j] to dst + cum[j] - cum[0], one
+// warp per entry (serialization and ranged reads of sparse images, whose
+// dirty chunks are scattered over the span one or two at a time).
+__global__ void __launch_bounds__(kDrainNT) sparse_pack_kernel(uint8_t *dst, const uint8_t *span,
+                                                               const uint64_t *off, const uint64_t *cum, uint64_t n) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * kDrainNT) >> 5;
+    const uint64_t base = cum[0];
+    for (uint64_t j = ((uint64_t)blockIdx.x * kDrainNT + threadIdx.x) >> 5; j < n; j += nw) {
+        const uint64_t o = off[j], d = cum[j] - base, len = cum[j + 1] - cum[j];
+        const uint8_t *s = span + o;
+        uint8_t *t = dst + d;
+        if (((o | d | len) & 15u) == 0) {
+            for (uint64_t v = lane; v < (len >> 4); v += 32)
+                reinterpret_cast<uint4 *>(t)[v] = reinterpret_cast<const uint4 *>(s)[v];
+        } else {
+            for (uint64_t i = lane; i < len; i += 32) t[i] = s[i];
+        }
+    }
+}
+
 }  // namespace
 
 const void *report_fn() { return reinterpret_cast<const void *>(&report_kernel); }
@@ -103,6 +126,16 @@ cudaError_t launch_link_copy(void *dst, const void *src, uint64_t bytes, int max
 cudaError_t launch_drain(const CkptCtrl *ctrl, const uint8_t *src, uint8_t *dst, uint64_t cap,
                          const uint64_t *idx_src, uint64_t *idx_dst, uint64_t idx_cap, int grid, cudaStream_t s) {
     drain_kernel<<<grid, kDrainNT, 0, s>>>(ctrl, src, dst, cap, idx_src, idx_dst, idx_cap);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_sparse_pack(void *dst, const void *span, const uint64_t *off, const uint64_t *cum, uint64_t n,
+                               int grid, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    sparse_pack_kernel<<<grid, kDrainNT, 0, s>>>(reinterpret_cast<uint8_t *>(dst),
+                                                 reinterpret_cast<const uint8_t *>(span), off, cum, n);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(1);
     return e;

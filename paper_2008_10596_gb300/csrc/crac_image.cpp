@@ -342,12 +342,43 @@ crac_status_t sparse_tables(crac_image *im, Piece &pc) {
 }
 
 // Bytes [a, b) of a sparse piece's compact payload (its entries' chunks in
-// list order, taken from their uncompacted offsets): one copy per run of
-// entries that lie back to back in the span.
+// list order, taken from their offsets in the span): one copy per run of
+// entries that lie back to back in the span when there are few runs, else
+// the entries are packed on the device (sparse_pack_kernel) in windows of
+// up to 256 MiB and each window is copied out once.
 crac_status_t sparse_range(crac_image *im, Piece &pc, uint64_t a, uint64_t b, uint8_t *out) {
     TRY(sparse_tables(im, pc));
     const std::vector<uint64_t> &off = pc.sp_off, &cum = pc.sp_cum;
-    uint64_t j = (uint64_t)(std::upper_bound(cum.begin(), cum.end(), a) - cum.begin()) - 1;
+    const uint64_t j0 = (uint64_t)(std::upper_bound(cum.begin(), cum.end(), a) - cum.begin()) - 1;
+    const uint64_t j1 = std::min<uint64_t>(pc.k, (uint64_t)(std::lower_bound(cum.begin(), cum.end(), b) - cum.begin()));
+    uint64_t runs = 1;
+    for (uint64_t j = j0 + 1; j < j1 && runs <= 64; ++j) runs += off[j] != off[j - 1] + (cum[j] - cum[j - 1]);
+    if (runs > 64) {
+        constexpr uint64_t kWindow = 256ull << 20;
+        Arena &da = device_arena(im->device);
+        Block win, dcum;
+        TRY(da.alloc(std::min<uint64_t>(kWindow, cum[j1] - cum[j0]), &win));
+        crac_status_t st = da.alloc((j1 - j0 + 1) * 8, &dcum);
+        if (st == CRAC_OK) {
+            const cudaError_t e = cudaMemcpy(dcum.p, cum.data() + j0, (j1 - j0 + 1) * 8, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_status(e);
+        }
+        for (uint64_t w0 = j0; st == CRAC_OK && w0 < j1;) {
+            uint64_t w1 = w0 + 1;   // one entry always fits: entries are at most a chunk
+            while (w1 < j1 && cum[w1 + 1] - cum[w0] <= kWindow) ++w1;
+            cudaError_t e = launch_sparse_pack(win.p, pc.dev.p, (const uint64_t *)pc.off_dev.p + w0,
+                                               (const uint64_t *)dcum.p + (w0 - j0), w1 - w0, 1024, 0);
+            const uint64_t lo = std::max(a, cum[w0]), hi = std::min(b, cum[w1]);
+            if (e == cudaSuccess && lo < hi)
+                e = cudaMemcpy(out + (lo - a), win.p + (lo - cum[w0]), hi - lo, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) st = cuda_status(e);
+            w0 = w1;
+        }
+        da.free(dcum);
+        da.free(win);
+        return st;
+    }
+    uint64_t j = j0;
     uint64_t pos = a;
     while (pos < b && j < pc.k) {
         const uint64_t src = off[j] + (pos - cum[j]);

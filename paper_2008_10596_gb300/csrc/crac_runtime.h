@@ -525,6 +525,12 @@ double now_s();
 // most max_grid CTAs, instead of a copy engine (crac_drain.cu).
 cudaError_t launch_link_copy(void *dst, const void *src, uint64_t bytes, int max_grid, cudaStream_t s);
 
+// Entries [0, n) of a sparse device piece packed back to back into device
+// memory dst: entry j's cum[j+1] - cum[j] bytes from span + off[j] to
+// dst + cum[j] - cum[0]; off and cum are device arrays (crac_drain.cu).
+cudaError_t launch_sparse_pack(void *dst, const void *span, const uint64_t *off, const uint64_t *cum, uint64_t n,
+                               int grid, cudaStream_t s);
+
 // A per-operation transfer between device memory and pinned host memory on
 // s: by an SM copy kernel where the device addresses pinned memory directly
 // (the copy engines' device-to-host rate was seen to collapse for seconds on
