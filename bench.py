@@ -34,6 +34,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The serving leg runs 64 contexts, each with its own stream and the
+# library's side stream: with the default 8 hardware work queues, work of
+# unrelated streams shares a queue and waits behind it.  32 queues (the
+# maximum) is the setting a many-context server runs with; it must be set
+# before CUDA starts in this process, and a value the caller set is kept.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
@@ -607,6 +614,7 @@ def run_crac(args):
         sampler5.start()
         serving = sr.run(args.serving_requests, args.rate)
         serving["clocks"] = sampler5.stop()
+        serving["cuda_device_max_connections"] = os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")
         sr.close()
         serving["workload"] = (f"c5 shape: 64 contexts, {args.serving_gib} GiB total (log-uniform 0.5-8 GiB scaled "
                                f"by {total5 / (173 * W.GIB):.3f}), {args.serving_requests} requests Poisson "
