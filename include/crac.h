@@ -206,7 +206,10 @@ typedef struct crac_config {
                               Pays off when most chunks are dirty.  Device-resident
                               images only; an image then holds the tracked bytes of
                               its segments instead of the dirty ones (serialization
-                              still writes the compact payload).  Falls back to the
+                              still writes the compact payload), except on 512 B -
+                              4 KiB chunks after a delta that found under a quarter
+                              of the chunks dirty: the dirty chunks are then placed
+                              back to back and the image holds only them.  Falls back to the
                               split pass when an allocation size is not a multiple of
                               16 bytes. */
 

@@ -248,8 +248,8 @@ crac_status_t launch_fused_graph(crac_ctx *c, const CkptParams &P, size_t work_b
 
 // Build (or update) the split-pass graph and launch it.
 crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_bytes, unsigned long long *acc,
-                                 uint32_t log2Seg, const void *hash_fn, const int grids[3], void *ctrl_dst,
-                                 cudaStream_t s) {
+                                 uint32_t log2Seg, const void *hash_fn, size_t hash_smem, const int grids[3],
+                                 void *ctrl_dst, cudaStream_t s) {
     // The gather instance follows P.crz_hdr, which only the hash instance
     // split_hash_kernel<true> runs with: hash_fn alone keys the cached graph.
     const void *fns[3] = {hash_fn, split_finalize_fn(), split_gather_fn(P.crz_hdr != nullptr)};
@@ -264,7 +264,7 @@ crac_status_t launch_split_graph(crac_ctx *c, const CkptParams &P, size_t work_b
         kp[i].func = const_cast<void *>(fns[i]);
         kp[i].gridDim = dim3(grids[i]);
         kp[i].blockDim = dim3(thr[i]);
-        kp[i].sharedMemBytes = 0;
+        kp[i].sharedMemBytes = i == 0 ? (unsigned)hash_smem : 0u;
         kp[i].kernelParams = args;
     }
     cudaMemsetParams mp{};
@@ -345,7 +345,13 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         // chunk to staging (hash or gather) also writes its CRZ1 block headers
         // for the encoder.
         uint64_t *crz_hdr = c->crz_hdr_now ? (uint64_t *)c->chdr.p : nullptr;
-        const void *hash_fn = small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn(crz_hdr != nullptr);
+        // The sparse pass on 512 B - 4 KiB chunks may place the dirty chunks
+        // densely (a bulk store per warp iteration from shared memory).
+        const bool dense = small && c->sparse_ok && staging && c->dense_now;
+        const void *hash_fn = dense ? split_hash_small_dense_fn(1 << (c->log2S - 8))
+                              : small ? split_hash_small_fn(1 << (c->log2S - 8)) : split_hash_fn(crz_hdr != nullptr);
+        const size_t hash_smem = dense ? split_dense_smem() : 0;
+        if (dense) CK(split_dense_prepare(hash_fn));
         CkptParams P{};
         P.crz_hdr = crz_hdr;
         P.desc = desc_dev;
@@ -369,7 +375,7 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         P.skip_first_ticket = (n_tiles >= 2 && fault_hit(CRAC_FAULT_DEVICE_WAIT)) ? 1u : 0u;
         // FULL pass, or the sparse pass: chunks are written to staging by the
         // hash kernel, at their uncompacted offsets.
-        P.sparse = c->sparse_ok && staging ? 1u : 0u;
+        P.sparse = c->sparse_ok && staging ? (dense ? 2u : 1u) : 0u;
         P.full_copy = (c->full_copy_ok || P.sparse) && staging ? 1u : 0u;
         P.alloc_prefix = (const uint64_t *)(desc_dev + c->allocs.size());
         if (c->spec_now) {
@@ -386,11 +392,12 @@ crac_status_t launch_segment(crac_ctx *c, const Segment &sg, const CkptDesc *des
         const uint64_t n_slots = small ? (nseg + (8192u >> c->log2S) - 1) / (8192u >> c->log2S)
                                        : nseg << (c->log2S - log2Seg);
         const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>(
-                           (n_slots + 7) / 8, (uint64_t)c->sm_count * split_max_ctas_per_sm(hash_fn, split_hash_threads())));
+                           (n_slots + 7) / 8,
+                           (uint64_t)c->sm_count * split_max_ctas_per_sm_smem(hash_fn, split_hash_threads(), hash_smem)));
         const int gf = (int)std::min<uint64_t>(n_tiles, (uint64_t)c->sm_count * 2);
         const int gg = c->sm_count * 8;
         const int grids[3] = {gh, gf, gg};
-        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, grids, ctrl_dst, s));
+        TRY(launch_split_graph(c, P, work_bytes, acc, log2Seg, hash_fn, hash_smem, grids, ctrl_dst, s));
         if (c->spec_now) {   // this pass's offsets predict the next one's
             c->ppos_cur ^= 1;
             c->ppos_ok = true;
@@ -1258,6 +1265,10 @@ crac_status_t ctx_checkpoint(crac_ctx *c, cudaStream_t s, crac_image_t **out) {
         c->pass_now = resolve_pass_kernel(c, dev_res, all16);
         c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && dev_res && all16 &&
                        c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
+        // Dense placement takes one atomic on a single counter per warp
+        // iteration with dirty chunks, whose rate bounds it once many chunks
+        // are dirty: only after a delta that found under a quarter dirty.
+        c->dense_now = c->sparse_ok && any_base && c->delta_frac_valid && c->delta_frac < 0.25f;
         // Order after the previous operation of this context (drain / restore).
         if (cudaStreamWaitEvent(s, c->ev_last, 0) != cudaSuccess) return fail(cuda_status(cudaGetLastError()));
         if (link_copy(c, c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1446,6 +1457,7 @@ crac_status_t ctx_trial_pass(crac_ctx *c, cudaStream_t s, bool commit, float *ms
     c->pass_now = c->cfg.pass_kernel == CRAC_PASS_AUTO ? (uint32_t)CRAC_PASS_SPLIT : c->cfg.pass_kernel;
     c->sparse_ok = c->pass_now == CRAC_PASS_SPARSE && c->cfg.image_residency == CRAC_RESIDENCY_DEVICE &&
                    all16 && c->cfg.launch_mode == CRAC_LAUNCH_BATCHED;
+    c->dense_now = c->sparse_ok && any_base && c->dense_hint;
     CK(cudaStreamWaitEvent(s, c->ev_last, 0));
     CK(link_copy(c, c->desc.p, dh, na * (sizeof(CkptDesc) + 8), cudaMemcpyHostToDevice, s));
     uint64_t cap = c->cfg.staging_bytes ? c->cfg.staging_bytes : std::min(tracked, kDefaultStagingMax);

@@ -359,6 +359,154 @@ split_hash_small_kernel(const CkptParams P, unsigned long long *__restrict__ acc
     if (lane == 0 && writes) atomicAdd(&P.ctrl->spec_writes, (unsigned long long)writes);
 }
 
+// ---------------------------------------------------------------------------
+// Sparse pass on 512 B - 4 KiB chunks with dense placement (P.sparse == 2).
+// Each warp iteration hashes 8 KiB of whole chunks as split_hash_small_kernel
+// does, then stages its dirty chunks back to back in the warp's 8 KiB of
+// shared memory and takes their room in the image from a running byte
+// counter (P.ctrl->pad[0], one atomicAdd per iteration with dirty bytes).
+// The counter's answer is used one iteration later: after the next
+// iteration's loads are issued, one lane stores the staged bytes with a bulk
+// copy (shared -> global) and the group leaders record each chunk's offset
+// in its accumulator word, so neither the atomic's round trip nor the store
+// holds the loads up.  The image's span is then exactly its dirty bytes.
+// Sizes are multiples of 16 (a sparse pass requires it), so every staged
+// chunk and every offset is 16-byte aligned.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kDenseWarpBytes = 8192;   // shared memory per warp
+constexpr uint64_t kAccLenMask = (1ull << 24) - 1;   // accumulator word: length in bits 0-23,
+constexpr int kAccPosShift = 24;                     // the chunk's offset in bits 24-62 (dense
+constexpr uint64_t kAccPosMask = (1ull << 39) - 1;   // sparse placement), kAccDirty in bit 63
+
+__device__ __forceinline__ void dense_bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"((uint32_t)__cvta_generic_to_shared(src_smem)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void dense_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void dense_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void dense_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int LPC>
+__global__ void __launch_bounds__(kHashNT, 2)
+split_hash_small_dense_kernel(const CkptParams P, unsigned long long *__restrict__ acc, uint32_t) {
+    extern __shared__ __align__(128) uint8_t dense_smem[];
+    constexpr int CPS = 32 / LPC;   // chunks per 8 KiB iteration
+    const int lane = threadIdx.x & 31;
+    const int li = lane % LPC;
+    uint8_t *buf = dense_smem + (threadIdx.x >> 5) * kDenseWarpBytes;
+    const uint64_t warp_g = ((uint64_t)blockIdx.x * kHashNT + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * kHashNT) >> 5;
+    const uint64_t n_slots = (P.c_end - P.c_begin + CPS - 1) / CPS;
+    const uint64_t per = (n_slots + n_warps - 1) / n_warps;
+    uint64_t q = warp_g * per;
+    const uint64_t q_end = umin64(q + per, n_slots);
+    const uint32_t log2S = P.log2_chunk;
+    CkptDesc dw{};
+    uint64_t a_next = 0;
+    uint32_t aw = 0;
+    bool have = false;
+    // the previous iteration's staged chunks: warp-uniform byte count, the
+    // counter's answer (lane 0), and each group's chunk, length and offset
+    uint32_t pend_total = 0;
+    unsigned long long pend_base = 0;
+    uint64_t pend_c = 0;
+    uint32_t pend_len = 0, pend_loc = 0;
+    bool pend_dirty = false;
+    auto flush = [&]() {
+        if (!pend_total) return;   // warp-uniform
+        const uint64_t base = __shfl_sync(kFull, (uint64_t)pend_base, 0);
+        const bool fits = base + pend_total <= P.staging_cap;
+        if (lane == 0) {
+            if (fits) dense_bulk_store(P.staging + base, buf, pend_total);
+            else atomicOr(&P.ctrl->err, kErrBounds);
+        }
+        if (li == 0 && pend_dirty)
+            acc[pend_c - P.c_begin] = pend_len | kAccDirty | ((fits ? base + pend_loc : 0ull) << kAccPosShift);
+        pend_total = 0;
+    };
+    for (; q < q_end; ++q) {
+        const uint64_t c0 = P.c_begin + q * CPS;
+        if (!have || c0 >= a_next) {
+            aw = find_alloc(P.desc, P.n_allocs, c0);
+            dw = P.desc[aw];
+            a_next = aw + 1 < P.n_allocs ? P.desc[aw + 1].first_chunk : ~0ull;
+            have = true;
+        }
+        const uint64_t c = c0 + lane / LPC;
+        uint64_t sum = 0, fo = 0;
+        uint32_t len = 0, nv = 0;
+        bool has = false;
+        uint4 v16[16];
+        if (c < P.c_end) {
+            CkptDesc d = dw;
+            if (c >= a_next) d = P.desc[find_alloc(P.desc, P.n_allocs, c)];   // the iteration crosses an allocation end
+            const uint64_t local = c - d.first_chunk;
+            len = (uint32_t)umin64(d.bytes - (local << log2S), 1ull << log2S);
+            has = d.base_first != kNoBase;
+            if (li == 0 && has) fo = __ldg(P.fp_old + d.base_first + local);
+            const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(d.ptr) + (local << log2S));
+            nv = len >> 4;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint32_t v = li + LPC * u;
+                if (v < nv) v16[u] = __ldg(p + v);
+            }
+        }
+        flush();   // the previous iteration's chunks leave shared memory while these loads are in flight
+        if (c < P.c_end) {
+            uint64_t key = (2ull * (uint64_t)li + 1ull) * kK1;
+            constexpr uint64_t kStep = 2ull * LPC * kK1;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const uint32_t v = li + LPC * u;
+                if (v < nv) {
+                    sum += mixw(((uint64_t)v16[u].y << 32) | v16[u].x, key);
+                    sum += mixw(((uint64_t)v16[u].w << 32) | v16[u].z, key + kK1);
+                }
+                key += kStep;
+            }
+        }
+#pragma unroll
+        for (int o = LPC / 2; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        const uint64_t fp = fp_finalize(sum, len);
+        fo = __shfl_sync(kFull, fo, lane - li);
+        const bool dirty = c < P.c_end && (!has || fo != fp);
+        if (li == 0 && c < P.c_end) {
+            P.fp_new[c] = fp;
+            if (!dirty) acc[c - P.c_begin] = len;
+        }
+        // stage the dirty chunks back to back in the warp's buffer
+        const uint64_t mine = (li == 0 && dirty) ? len : 0u;
+        const uint64_t incl = warp_incl_scan(mine, lane);
+        const uint32_t total = (uint32_t)__shfl_sync(kFull, incl, 31);
+        const uint32_t loc = (uint32_t)__shfl_sync(kFull, incl - mine, lane - li);
+        if (total) {   // warp-uniform
+            if (lane == 0) dense_wait_read();   // the previous bulk store has read the buffer
+            __syncwarp();
+            if (dirty) {
+                uint4 *dst = reinterpret_cast<uint4 *>(buf + loc);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t v = li + LPC * u;
+                    if (v < nv) dst[v] = v16[u];
+                }
+            }
+            dense_fence();   // the staged bytes are visible to the bulk copy
+            __syncwarp();
+            if (lane == 0) pend_base = atomicAdd(&P.ctrl->pad[0], (unsigned long long)total);
+        }
+        pend_total = total;
+        pend_c = c;
+        pend_len = len;
+        pend_loc = loc;
+        pend_dirty = dirty;
+    }
+    flush();
+    if (lane == 0) dense_wait_all();   // shared memory stays until the bulk stores have finished
+}
+
 constexpr uint32_t kFinCachedAllocs = 4096;   // first_chunk columns the finalize keeps on chip
 
 __global__ void __launch_bounds__(kFinNT)
@@ -391,10 +539,12 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
         if (tile >= P.n_tiles) break;
         const uint64_t c = P.c_begin + (uint64_t)tile * kFinNT + threadIdx.x;
         uint32_t dl = 0, len = 0;
+        uint64_t dpos = 0;   // dense sparse placement: the chunk's offset in the span
         if (c < P.c_end && direct) {
             const uint64_t v = acc[c - P.c_begin];
-            len = (uint32_t)v;
+            len = (uint32_t)(v & kAccLenMask);
             dl = (v & kAccDirty) ? len : 0u;
+            dpos = (v >> kAccPosShift) & kAccPosMask;
         } else if (c < P.c_end) {
             uint32_t a;
             if (cached) {
@@ -418,8 +568,10 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
         }
         if (P.ppos_next && c < P.c_end) P.ppos_next[c - P.c_begin] = ~0ull;   // the gather sets the dirty ones
         // Bytes that advance the staging offset: the dirty ones, or in the
-        // sparse pass every chunk's (each sits at its uncompacted offset).
-        const uint32_t sv = P.sparse ? len : dl;
+        // sparse pass every chunk's (each sits at its uncompacted offset);
+        // under dense placement the dirty ones, whose offsets the hash kernel
+        // recorded.
+        const uint32_t sv = P.sparse == 1u ? len : dl;
         const unsigned m = __ballot_sync(kFull, dl != 0);
         const uint64_t incl = warp_incl_scan(sv, lane);
         if (P.sparse) {
@@ -482,7 +634,7 @@ split_finalize_kernel(const CkptParams P, unsigned long long *__restrict__ acc, 
             const uint64_t j = s_k0 + s_wcnt[warp] + __popc(m & ((1u << lane) - 1u));
             if (j < P.idx_cap) {
                 P.idx_out[j] = c;
-                P.off_out[j] = s_d0 + s_wbytes[warp] + incl - sv;
+                P.off_out[j] = P.sparse == 2u ? dpos : s_d0 + s_wbytes[warp] + incl - sv;
             } else {
                 atomicOr(&P.ctrl->err, kErrBounds);
             }
@@ -564,6 +716,24 @@ const void *split_gather_fn(bool crz_headers) {
 int split_hash_threads() { return kHashNT; }
 int split_finalize_threads() { return kFinNT; }
 int split_gather_threads() { return kGatherNT; }
+const void *split_hash_small_dense_fn(int lanes_per_chunk) {
+    switch (lanes_per_chunk) {
+    case 2: return reinterpret_cast<const void *>(&split_hash_small_dense_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&split_hash_small_dense_kernel<4>);
+    case 8: return reinterpret_cast<const void *>(&split_hash_small_dense_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&split_hash_small_dense_kernel<16>);
+    default: return nullptr;
+    }
+}
+size_t split_dense_smem() { return (size_t)(kHashNT / 32) * kDenseWarpBytes; }
+cudaError_t split_dense_prepare(const void *fn) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_dense_smem());
+}
+int split_max_ctas_per_sm_smem(const void *fn, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
 int split_max_ctas_per_sm(const void *fn, int threads) {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 1;

@@ -450,6 +450,8 @@ struct crac_ctx {
     crac_restart_info_t last_restart{};
     bool full_copy_ok = false;   // current pass: no baseline anywhere and 16-byte sizes
     bool sparse_ok = false;      // current pass: CRAC_PASS_SPARSE, device images, 16-byte sizes
+    bool dense_now = false;      // ... and, on 512 B - 4 KiB chunks, dense placement of the dirty chunks
+    bool dense_hint = false;     // trial passes: dense placement (set by the tuner for a sparse timing)
     uint32_t pass_now = CRAC_PASS_SPLIT;   // kernel of the current pass (CRAC_PASS_AUTO resolved)
     bool split_now = false;      // the current pass is the split graph (per-kernel timing events)
     bool prefetch_now = false;   // the current pass prefetched managed memory (ev_p0 / ev_p1)
@@ -524,6 +526,15 @@ double now_s();
 // device mapping (or both device memory), by SM loads and stores on s with at
 // most max_grid CTAs, instead of a copy engine (crac_drain.cu).
 cudaError_t launch_link_copy(void *dst, const void *src, uint64_t bytes, int max_grid, cudaStream_t s);
+
+// The sparse pass's dense-placement hash kernel for 512 B - 4 KiB chunks
+// (lanes_per_chunk = chunk bytes / 256), the dynamic shared memory it runs
+// with, the attribute that allows it (before its first launch or graph
+// node), and occupancy with dynamic shared memory (crac_pass_split.cu).
+const void *split_hash_small_dense_fn(int lanes_per_chunk);
+size_t split_dense_smem();
+cudaError_t split_dense_prepare(const void *fn);
+int split_max_ctas_per_sm_smem(const void *fn, int threads, size_t smem);
 
 // Entries [0, n) of a sparse device piece packed back to back into device
 // memory dst: entry j's cum[j+1] - cum[j] bytes from span + off[j] to

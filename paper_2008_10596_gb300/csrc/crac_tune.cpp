@@ -141,8 +141,12 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
         // A sparse image holds every tracked byte's room whatever the dirty
         // bytes, so it is timed only where at least 40% of the chunks are
         // dirty (at most 2.5 times the room of a compact image; the split
-        // pass, timed first, gives the count).
-        if (v == CRAC_PASS_SPARSE && 5 * k_seen < 2 * n_chunks) continue;
+        // pass, timed first, gives the count), or, on chunks of 512 B -
+        // 4 KiB, where under a quarter are: its passes then place the dirty
+        // chunks densely, as the context's passes will after such a delta.
+        const bool dense = S < 8192 && 4 * k_seen < n_chunks;
+        if (v == CRAC_PASS_SPARSE && !dense && 5 * k_seen < 2 * n_chunks) continue;
+        t->dense_hint = v == CRAC_PASS_SPARSE && dense;
         // Coded images on chunks of 8 KiB and more: only the split pass makes
         // the block headers that the two-launch encoder needs; a read-once
         // pass saves less in the pass than the one-launch encoder costs.
@@ -160,6 +164,7 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
             t->cfg.chunks_per_tile = saved_cpt;
             if (st != CRAC_OK) {
                 t->cfg.pass_kernel = saved;
+                t->dense_hint = false;
                 return st;
             }
             if (v == CRAC_PASS_LDG) vt->tile_ms[j] = ms;
@@ -168,6 +173,7 @@ crac_status_t time_variants(crac_ctx *t, cudaStream_t s, VariantTiming *vt) {
                 if (ldg_tiles) vt->best_tile = vt->tiles[j];
             }
         }
+        t->dense_hint = false;
         vt->vms[v] = bestm;
         if (vt->vms[vt->best_v] == 0 || bestm < vt->vms[vt->best_v]) vt->best_v = v;
     }

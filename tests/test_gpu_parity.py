@@ -178,35 +178,42 @@ def test_sparse_pass(S, staging, pattern):
 
 @pytest.mark.parametrize("S", [512, 1 * KIB, 4 * KIB])
 def test_sparse_dirty_only_with_new_allocation(S):
-    """On 512 B - 4 KiB chunks the sparse pass stores only the dirty chunks
-    (each at its uncompacted offset): a delta that mixes chunks with a
-    baseline and a newly registered allocation's chunks (no baseline, all
-    dirty) gives the oracle's image, its payload size is the dirty bytes, the
-    scattered dirty chunks serialize back into chunk order, and the chain
-    restores on the device and from deserialized copies."""
+    """On 512 B - 4 KiB chunks the sparse pass stores only the dirty chunks:
+    at their uncompacted offsets, or, after a delta that found under a
+    quarter of the chunks dirty, back to back in the order the warps reach
+    them.  Deltas that mix baselined chunks with a newly registered
+    allocation's (no baseline, all dirty) -- the first with uncompacted
+    placement, the second with dense placement -- give the oracle's images
+    with the dirty bytes as payload, the scattered chunks serialize back
+    into chunk order, and the chain restores on the device and from
+    deserialized copies."""
     sizes = [S * 37 + 16 * 3, 4096 * 5, 48000 // 16 * 16]
     h = Harness(S, lineage=740 + S // 256, pass_kernel=C.CRAC_PASS_SPARSE,
                 image_residency=C.CRAC_RESIDENCY_DEVICE)
     try:
         for i, n in enumerate(sizes):
             h.add(n, seed=170 + i)
+        libs, oras, imgs = [], [], []
         _, lib1, ora1 = h.checkpoint()
         assert lib1 == ora1
-        h.add(S * 9 + 32, seed=180)    # registered after the FULL image: no baseline
-        all_sizes = [b.nbytes for b in h.bufs]
-        h.mutate(pattern_mutations(h.first(), all_sizes, S, "random10", seed=4))
-        img2, lib2, ora2 = h.checkpoint()
-        assert lib2 == ora2
-        info = C.crac_ctx_last_pass(h.ctx)
-        assert info["pass_kernel"] == C.CRAC_PASS_SPARSE
-        assert C.crac_image_info(img2)["payload_bytes"] == len(O.parse_image(ora2).payload)
-        h.mutate(pattern_mutations(h.first(), all_sizes, S, "alternating", seed=5))
-        img3, lib3, ora3 = h.checkpoint()
-        assert lib3 == ora3
+        libs.append(lib1)
+        oras.append(ora1)
+        for step, (extra, pattern) in enumerate(((S * 2 + 32, "random10"), (S * 3 + 16, "random10"),
+                                                 (None, "alternating"))):
+            if extra:
+                h.add(extra, seed=180 + step)   # registered after the last image: no baseline
+            h.mutate(pattern_mutations(h.first(), [b.nbytes for b in h.bufs], S, pattern, seed=4 + step))
+            img, lib, ora = h.checkpoint()
+            assert lib == ora, step
+            assert C.crac_ctx_last_pass(h.ctx)["pass_kernel"] == C.CRAC_PASS_SPARSE
+            assert C.crac_image_info(img)["payload_bytes"] == len(O.parse_image(ora).payload)
+            libs.append(lib)
+            oras.append(ora)
+            imgs.append(img)
         want = h.host()
         for b in h.bufs:
             b.zero()
-        h.restart(img3)
+        h.restart(imgs[-1])
         for b, w in zip(h.bufs, want):
             assert np.array_equal(b.read(), w)
         # the same chain from deserialized copies, in a fresh context
@@ -214,13 +221,13 @@ def test_sparse_dirty_only_with_new_allocation(S):
         try:
             for b in h.bufs:
                 h2.add(b.nbytes, data=np.zeros(b.nbytes, dtype=np.uint8))
-            ds = [C.crac_image_deserialize(x) for x in (lib1, lib2, lib3)]
+            ds = [C.crac_image_deserialize(x) for x in libs]
             h2.images += ds
-            h2.restart(ds[2], [ora1, ora2, ora3])
+            h2.restart(ds[-1], oras)
             for b, w in zip(h2.bufs, want):
                 assert np.array_equal(b.read(), w)
-            _, lib4, ora4 = h2.checkpoint()   # the restored image is the baseline
-            assert lib4 == ora4 and O.parse_image(lib4).k == 0
+            _, lib5, ora5 = h2.checkpoint()   # the restored image is the baseline
+            assert lib5 == ora5 and O.parse_image(lib5).k == 0
         finally:
             h2.close()
     finally:
