@@ -190,8 +190,10 @@ typedef struct crac_config {
 #define CRAC_PASS_AUTO  0  /* the split pass, or, when the last pass with a baseline
                               found more than half of the chunks dirty, the first of
                               SPARSE (device images, 16-byte sizes), TMA (1-64 KiB
-                              chunks), LDG that applies; trial passes of the tuner
-                              use the split pass */
+                              chunks), LDG that applies, or SPARSE (dense placement)
+                              when it found under a quarter dirty on 512 B - 4 KiB
+                              chunks of device images with 16-byte sizes; trial
+                              passes of the tuner use the split pass */
 #define CRAC_PASS_LDG   1  /* one fused persistent kernel, 128-bit loads to registers;
                               the gather re-reads dirty chunks from L2 */
 #define CRAC_PASS_TMA   2  /* one fused kernel, bulk copies into a shared-memory ring,
