@@ -34,12 +34,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# The serving leg runs 64 contexts, each with its own stream and the
-# library's side stream: with the default 8 hardware work queues, work of
-# unrelated streams shares a queue and waits behind it.  32 queues (the
-# maximum) is the setting a many-context server runs with; it must be set
-# before CUDA starts in this process, and a value the caller set is kept.
-os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
@@ -1405,4 +1399,11 @@ def main():
 
 
 if __name__ == "__main__":
+    # The serving leg runs 64 contexts, each with its own stream and the
+    # library's side stream: with the default 8 hardware work queues, work of
+    # unrelated streams shares a queue and waits behind it.  32 queues (the
+    # maximum) is the setting a many-context server runs with; it must be set
+    # before CUDA starts in this process (a value the caller set is kept), and
+    # only when the benchmark itself runs, not when a test imports it.
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     sys.exit(main())
